@@ -1,0 +1,392 @@
+"""History-aware adaptive ROM: plain FP64 restatement of Algorithms 1 and 2 (oracle).
+
+Test infrastructure only; see the package docstring. Each function follows one
+passage of the paper:
+
+* ``preprocess``     Sec. 3.1, Eqs. scaling_matrix_local_block and
+                     variable_normalization: q_ref = initial solution,
+                     D_v = 1/phi_v with phi_v the time-space mean of the squared
+                     centred training field (read literally as a mean square).
+* ``pod``            Sec. 3.1 / Algorithm 1 (POD step): leading r left singular
+                     vectors and values of D (Q_train - q_ref 1^T).
+* ``galerkin_step``  Eq. galerkin_continuous_rom discretised by backward Euler
+                     (Eq. be_residual_rom_section), solved by Newton with the
+                     exact reduced Jacobian I - dt Phi^T D J_f D^-1 Phi.
+* ``hyper_step``     Eq. deim_galerkin_rom (DEIM with U = Phi) discretised the
+                     same way: a - a^n - dt (P^T Phi)^+ P^T D f(q~(a)) = 0.
+* ``qdeim``          Eq. qdeim_qr: first pivots of a column-pivoted QR of Phi^T.
+* ``fgs_extend``     Eq. fgs_selection with the feature map Theta(y) = y: the
+                     cells with the largest squared forward difference of the
+                     correction snapshot, skipping cells already chosen.
+* ``isvd_update``    Algorithm 2 / Eqs. isvd_residual ... isvd_truncation.
+* ``AdaptiveROM``    Algorithm 1.
+
+Readings where the paper is silent: see the module-level constants and the
+docstrings (Newton stopping rule, rank-deficient iSVD residual, sign
+convention of singular vectors, oversampling rule for n_s > r).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+from . import fv
+
+RANK_TOL = 1e-10      # numerical-rank tolerance relative to the largest singular value
+PHI_FLOOR = 1e-300    # preprocessing: guard for a variable with no variation
+
+
+class NewtonNoConvergence(RuntimeError):
+    pass
+
+
+# ----------------------------------------------------------------------------
+# offline pieces
+# ----------------------------------------------------------------------------
+
+def fom_trajectory(q0, n_steps, cfg):
+    """Fine backward-Euler FOM states q^1..q^n_steps as columns (Eq. fom_lmm
+    with the BE coefficients, Eq. fom_discrete_solve)."""
+    out = np.empty((q0.shape[0], n_steps))
+    q = q0
+    for k in range(n_steps):
+        q = fv.be_step(q, cfg.dt, cfg.problem, cfg.nu, cfg.gamma,
+                       cfg.newton_tol, cfg.newton_max)
+        out[:, k] = q
+    return out
+
+
+def preprocess(Q_train, q0, n_var):
+    """(q_ref, diag(D), D (Q_train - q_ref 1^T)).
+
+    q_ref is the initial solution. For each variable v the characteristic
+    magnitude phi_v is the mean over snapshots and cells of the squared centred
+    field, and every cell block of D carries 1/phi_v.
+    """
+    q_ref = q0.copy()
+    Xc = Q_train - q_ref[:, None]
+    n_cells = q0.shape[0] // n_var
+    dvals = np.empty(n_var)
+    for v in range(n_var):
+        blk = Xc[v * n_cells:(v + 1) * n_cells, :]
+        phi = float(np.mean(blk * blk))
+        if phi < PHI_FLOOR:
+            phi = 1.0
+        dvals[v] = 1.0 / phi
+    d = np.repeat(dvals, n_cells)
+    return q_ref, d, d[:, None] * Xc
+
+
+def sign_normalise(U):
+    """Flip each column so that its largest-magnitude entry is positive
+    (tie -> lowest index). Singular vectors are unique only up to sign."""
+    U = U.copy()
+    for j in range(U.shape[1]):
+        i = int(np.argmax(np.abs(U[:, j])))
+        if U[i, j] < 0:
+            U[:, j] = -U[:, j]
+    return U
+
+
+def pod(Xhat, r):
+    """Leading r left singular vectors and singular values (LAPACK thin SVD)."""
+    U, s, _ = np.linalg.svd(Xhat, full_matrices=False)
+    U = sign_normalise(U[:, :r])
+    s = s[:r].copy()
+    return drop_null_directions(U, s)
+
+
+def drop_null_directions(U, s):
+    """Zero the columns (and singular values) with s_j <= RANK_TOL * s_1: such
+    directions carry no information above rounding. A zero column is inert in
+    every reduced operator (its coordinate keeps its value, zero)."""
+    U = U.copy()
+    s = s.copy()
+    if s.shape[0] and s[0] > 0:
+        null = s <= RANK_TOL * s[0]
+        U[:, null] = 0.0
+        s[null] = 0.0
+    return U, s
+
+
+# ----------------------------------------------------------------------------
+# reduced steps
+# ----------------------------------------------------------------------------
+
+def lift(a, Phi, q_ref, d):
+    """q~ = q_ref + D^-1 Phi a (Eq. trial_approximation)."""
+    return q_ref + (Phi @ a) / d
+
+
+def galerkin_residual(a, a_prev, Phi, q_ref, d, cfg):
+    qt = lift(a, Phi, q_ref, d)
+    f = fv.fom_f(qt, cfg.problem, cfg.nu, cfg.gamma)
+    return a - a_prev - cfg.dt * (Phi.T @ (d * f))
+
+
+def galerkin_jacobian(a, Phi, q_ref, d, cfg):
+    qt = lift(a, Phi, q_ref, d)
+    Jf = fv.fom_jac(qt, cfg.problem, cfg.nu, cfg.gamma)
+    JfPhi = Jf @ (Phi / d[:, None])
+    return np.eye(Phi.shape[1]) - cfg.dt * (Phi.T @ (d[:, None] * JfPhi))
+
+
+def hyper_residual(a, a_prev, Phi, q_ref, d, P, M, cfg):
+    """a - a^n - dt (P^T Phi)^+ P^T D f(q~(a)). f is evaluated on the full
+    lifted state and then sampled, which is slow but obviously equal to
+    evaluating it on the sample mesh."""
+    qt = lift(a, Phi, q_ref, d)
+    f = fv.fom_f(qt, cfg.problem, cfg.nu, cfg.gamma)
+    return a - a_prev - cfg.dt * (M @ (d * f)[P])
+
+
+def hyper_jacobian(a, Phi, q_ref, d, P, M, cfg):
+    qt = lift(a, Phi, q_ref, d)
+    Jf = fv.fom_jac(qt, cfg.problem, cfg.nu, cfg.gamma)
+    JfPhi = Jf @ (Phi / d[:, None])
+    return np.eye(Phi.shape[1]) - cfg.dt * (M @ (d[:, None] * JfPhi)[P, :])
+
+
+def _newton(a_prev, resid, jac, tol, max_iter):
+    """Newton from a_prev; stop once max|delta| <= tol (1 + max|a|)."""
+    a = a_prev.copy()
+    for it in range(1, max_iter + 1):
+        g = resid(a)
+        J = jac(a)
+        delta = np.linalg.solve(J, -g)
+        a = a + delta
+        if np.max(np.abs(delta)) <= tol * (1.0 + np.max(np.abs(a))):
+            return a, it
+    raise NewtonNoConvergence(f"reduced Newton did not converge in {max_iter} iterations")
+
+
+def galerkin_step(a_prev, Phi, q_ref, d, cfg):
+    """One backward-Euler Galerkin ROM step (plain projection)."""
+    return _newton(a_prev,
+                   lambda a: galerkin_residual(a, a_prev, Phi, q_ref, d, cfg),
+                   lambda a: galerkin_jacobian(a, Phi, q_ref, d, cfg),
+                   cfg.newton_tol, cfg.newton_max)
+
+
+def hyper_step(a_prev, Phi, q_ref, d, P, M, cfg):
+    """One backward-Euler DEIM-Galerkin ROM step (U = Phi, sample set P)."""
+    return _newton(a_prev,
+                   lambda a: hyper_residual(a, a_prev, Phi, q_ref, d, P, M, cfg),
+                   lambda a: hyper_jacobian(a, Phi, q_ref, d, P, M, cfg),
+                   cfg.newton_tol, cfg.newton_max)
+
+
+# ----------------------------------------------------------------------------
+# sampling
+# ----------------------------------------------------------------------------
+
+def numerical_rank(Phi):
+    """Number of non-zero (non-null) basis columns."""
+    return int(np.count_nonzero(np.any(Phi != 0.0, axis=0)))
+
+
+def qdeim(Phi, m):
+    """First min(m, rank) pivots of the column-pivoted QR of Phi^T (Eq. qdeim_qr).
+    Beyond the rank of Phi the pivoted QR has nothing left to pivot on."""
+    _, piv = sla.qr(Phi.T, mode="r", pivoting=True)
+    return [int(i) for i in piv[:min(m, numerical_rank(Phi))]]
+
+
+def fgs_scores(y):
+    """Squared forward difference (y_{i+1} - y_i)^2 (periodic), i.e. the squared
+    gradient of the feature Theta(y) = y up to the constant 1/dx^2."""
+    return (np.roll(y, -1) - y) ** 2
+
+
+def fgs_extend(y, chosen, count):
+    """Greedy feature-guided points: largest scores first (tie -> lowest index),
+    skipping cells already in ``chosen``."""
+    g = fgs_scores(y)
+    order = np.lexsort((np.arange(g.shape[0]), -g))
+    taken = set(chosen)
+    out = []
+    for i in order:
+        if len(out) == count:
+            break
+        if int(i) not in taken:
+            out.append(int(i))
+            taken.add(int(i))
+    return out
+
+
+def sample_points(Phi, y_corr, n_s):
+    """QDEIM points (up to r) extended to n_s by feature-guided points."""
+    P = qdeim(Phi, n_s)
+    if n_s > len(P):
+        P = P + fgs_extend(y_corr, P, n_s - len(P))
+    return P
+
+
+def sampled_pinv(Phi, P):
+    """(P^T Phi)^+ by SVD-based pseudo-inverse (NumPy pinv)."""
+    return np.linalg.pinv(Phi[P, :])
+
+
+# ----------------------------------------------------------------------------
+# iSVD (Algorithm 2)
+# ----------------------------------------------------------------------------
+
+def project_cgs2(Phi, y):
+    """Least-squares coordinates p = Phi^+ y and residual q = y - Phi p for an
+    orthonormal Phi, by classical Gram-Schmidt applied twice: the second pass
+    removes the component that rounding leaves in span(Phi) when ||q|| is much
+    smaller than ||y|| (Eq. isvd_residual)."""
+    p1 = Phi.T @ y
+    q1 = y - Phi @ p1
+    p2 = Phi.T @ q1
+    q = q1 - Phi @ p2
+    return p1 + p2, q
+
+
+def isvd_update(Phi, sigma, yhat, lam, r, return_core=False):
+    """Rank-one incremental SVD with forgetting factor, truncated to rank r.
+
+    p solves min ||yhat - Phi p|| (least squares, by ``project_cgs2``);
+    q = yhat - Phi p; the core
+    K = [[lam Sigma, p], [0, ||q||]] is decomposed by a dense SVD, the augmented
+    basis [Phi, q/||q||] is rotated by its left singular vectors and the
+    leading r directions are kept. If ||q|| <= RANK_TOL * max(||yhat||, sigma_1)
+    the new direction is empty: q/||q|| is replaced by 0 and K's corner by 0.
+    """
+    k = Phi.shape[1]
+    p, q = project_cgs2(Phi, yhat)
+    rho = float(np.linalg.norm(q))
+    scale = max(float(np.linalg.norm(yhat)), float(sigma[0]) if k else 0.0)
+    if rho <= RANK_TOL * scale:
+        qhat = np.zeros_like(q)
+        rho = 0.0
+    else:
+        qhat = q / rho
+    K = np.zeros((k + 1, k + 1))
+    K[:k, :k] = lam * np.diag(sigma)
+    K[:k, k] = p
+    K[k, k] = rho
+    Ub, sb, _ = np.linalg.svd(K)
+    Phit = np.hstack([Phi, qhat[:, None]]) @ Ub
+    keep = min(r, k + 1)
+    Phi_new, s_new = drop_null_directions(sign_normalise(Phit[:, :keep]), sb[:keep])
+    if return_core:
+        return Phi_new, s_new, K, Ub, sb
+    return Phi_new, s_new
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 1
+# ----------------------------------------------------------------------------
+
+class AdaptiveROM:
+    """History-aware adaptive ROM (Algorithm 1) with the iSVD update.
+
+    Offline (lines 2-8): w_init fine FOM steps, preprocessing, POD, initial
+    reduced state, first coarse correction state, initial sampling points.
+    Online (lines 9-20): one reduced BE step per call of ``step``; every z
+    steps an adaptation event advances the coarse FOM by z*dt, updates the
+    basis by iSVD, refreshes the sampling points and transfers the state.
+    """
+
+    def __init__(self, cfg, q0, Q_train=None):
+        self.cfg = cfg
+        self.q0 = np.asarray(q0, dtype=np.float64).copy()
+        if Q_train is None:
+            Q_train = fom_trajectory(self.q0, cfg.w_init, cfg)
+        self.Q_train = Q_train
+        self.q_ref, self.d, Xhat = preprocess(Q_train, self.q0, cfg.n_var)
+        self.Phi, self.sigma = pod(Xhat, cfg.r)
+        q_last = Q_train[:, -1]
+        self.a = self.Phi.T @ (self.d * (q_last - self.q_ref))
+        self.y_corr = self.coarse_step(q_last)
+        self.P = None
+        self.M = None
+        if cfg.n_s > 0:
+            self._refresh_sampling()
+        self.n = cfg.w_init
+        self.events = 0
+        self.newton_iters = []
+        self.min_gap = np.inf
+
+    # -- pieces --------------------------------------------------------------
+    def coarse_step(self, y):
+        c = self.cfg
+        return fv.be_step(y, c.z * c.dt, c.problem, c.nu, c.gamma, c.newton_tol, c.newton_max)
+
+    def _refresh_sampling(self):
+        self.P = sample_points(self.Phi, self.y_corr, self.cfg.n_s)
+        self.M = sampled_pinv(self.Phi, self.P)
+
+    def rom_step(self, a_prev):
+        c = self.cfg
+        if c.n_s > 0:
+            return hyper_step(a_prev, self.Phi, self.q_ref, self.d, self.P, self.M, c)
+        return galerkin_step(a_prev, self.Phi, self.q_ref, self.d, c)
+
+    def lifted(self):
+        return lift(self.a, self.Phi, self.q_ref, self.d)
+
+    def is_event(self, n):
+        return (n + 1 - self.cfg.w_init) % self.cfg.z == 0
+
+    def adapt(self, q_tilde):
+        """Lines 13-18 of Algorithm 1 for the reconstructed state q_tilde."""
+        c = self.cfg
+        self.y_corr = self.coarse_step(self.y_corr)
+        yhat = self.d * (self.y_corr - self.q_ref)
+        Phi_new, sigma_new, _, _, s_all = isvd_update(self.Phi, self.sigma, yhat, c.lam, c.r,
+                                                      return_core=True)
+        if s_all.shape[0] > c.r and s_all[0] > 0:
+            self.min_gap = min(self.min_gap, (s_all[c.r - 1] - s_all[c.r]) / s_all[0])
+        self.Phi, self.sigma = Phi_new, sigma_new
+        if c.n_s > 0:
+            self._refresh_sampling()
+        self.a = self.Phi.T @ (self.d * (q_tilde - self.q_ref))
+        self.events += 1
+
+    # -- driver --------------------------------------------------------------
+    def step(self):
+        """One iteration of the online loop; returns q~^{n+1} (before transfer)."""
+        a_new, iters = self.rom_step(self.a)
+        self.newton_iters.append(iters)
+        self.a = a_new
+        q_tilde = self.lifted()
+        if self.is_event(self.n):
+            self.adapt(q_tilde)
+        self.n += 1
+        return q_tilde
+
+    def run(self, n_steps, record_every=1):
+        """Run n_steps online steps; returns (steps, trajectory columns)."""
+        steps, traj = [], []
+        for k in range(n_steps):
+            qt = self.step()
+            if (k + 1) % record_every == 0 or k + 1 == n_steps:
+                steps.append(self.n)
+                traj.append(qt)
+        return np.array(steps), np.stack(traj, axis=1)
+
+    # -- state import / export ---------------------------------------------------
+    def get_state(self):
+        return dict(Phi=self.Phi.copy(), sigma=self.sigma.copy(), a=self.a.copy(),
+                    y_corr=self.y_corr.copy(), n=self.n,
+                    P=None if self.P is None else list(self.P))
+
+    def set_state(self, Phi, sigma, a, y_corr, n, P=None):
+        self.Phi = np.array(Phi, dtype=np.float64)
+        self.sigma = np.array(sigma, dtype=np.float64)
+        self.a = np.array(a, dtype=np.float64)
+        self.y_corr = np.array(y_corr, dtype=np.float64)
+        self.n = int(n)
+        if self.cfg.n_s > 0:
+            if P is None:
+                self._refresh_sampling()
+            else:
+                self.P = list(P)
+                self.M = sampled_pinv(self.Phi, self.P)
+
+
+def relative_error(q_tilde, q_fom):
+    """epsilon^n = ||q~ - q|| / ||q|| (Eq. relative_error)."""
+    return float(np.linalg.norm(q_tilde - q_fom) / np.linalg.norm(q_fom))

@@ -1,0 +1,313 @@
+"""Pins of the oracle's reduced-order pieces: iSVD against batch SVD and the
+covariance recursion, Galerkin/DEIM steps against the FOM in the full-basis
+limit, QDEIM against brute-force greedy pivoting, and Algorithm 1's schedule
+and qualitative behaviour (no GPU)."""
+import copy
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import fv, rom
+
+
+def principal_angle_sin(A, B):
+    """Largest sine of the principal angles between span(A) and span(B)."""
+    Qa, _ = np.linalg.qr(A)
+    Qb, _ = np.linalg.qr(B)
+    return float(np.linalg.norm(Qb - Qa @ (Qa.T @ Qb), 2))
+
+
+def low_rank_stream(n, rank, count, seed, decay=0.5):
+    rng = np.random.default_rng(seed)
+    B = np.linalg.qr(rng.standard_normal((n, rank)))[0]
+    C = rng.standard_normal((rank, count)) * (decay ** np.arange(rank))[:, None]
+    return B @ C
+
+
+# ------------------------------------------------------------------ iSVD ---
+
+@pytest.mark.parametrize("lam", [1.0, 0.5, 0.1])
+def test_isvd_equals_batch_svd_of_weighted_history(lam):
+    """Columns from a rank-5 matrix, r = 5: after every update the iSVD
+    singular values equal those of the exponentially weighted snapshot matrix
+    [lam^(k-1) y_1, ..., y_k] and the subspaces coincide (Eqs.
+    weighted_snapshot_matrix, isvd_augmented_history)."""
+    n, r, count = 60, 5, 25
+    Y = low_rank_stream(n, r, count, seed=11)
+    Phi, s = rom.pod(Y[:, :r], r)
+    for k in range(r, count):
+        Phi, s = rom.isvd_update(Phi, s, Y[:, k], lam, r)
+        # the POD batch (first r columns) enters with one common weight
+        w = lam ** np.minimum(np.arange(k, -1, -1), k - r + 1).astype(float)
+        W = Y[:, :k + 1] * w[None, :]
+        U, sb, _ = np.linalg.svd(W, full_matrices=False)
+        nz = sb[:r] > rom.RANK_TOL * sb[0]
+        assert np.allclose(s[nz], sb[:r][nz], rtol=1e-10, atol=1e-12 * sb[0])
+        assert principal_angle_sin(Phi[:, nz], U[:, :r][:, nz]) < 1e-8
+
+
+def test_isvd_rank_growing_equals_batch_svd():
+    """lam = 1 and no truncation (target rank above the data count): the
+    stream reproduces the thin SVD of the concatenated matrix exactly."""
+    n, count = 40, 12
+    rng = np.random.default_rng(3)
+    Y = rng.standard_normal((n, count))
+    Phi, s = rom.pod(Y[:, :1], 1)
+    for k in range(1, count):
+        Phi, s = rom.isvd_update(Phi, s, Y[:, k], 1.0, count)
+    U, sb, _ = np.linalg.svd(Y, full_matrices=False)
+    assert np.allclose(s, sb, rtol=1e-12)
+    # columns equal up to sign
+    sg = np.sign(np.sum(Phi * U, axis=0))
+    assert np.max(np.abs(Phi * sg - U)) < 1e-9
+
+
+def test_isvd_covariance_recursion():
+    """Rank <= r: Phi Sigma^2 Phi^T tracks C_{k+1} = lam^2 C_k + y y^T."""
+    n, r, lam = 30, 4, 0.7
+    Y = low_rank_stream(n, r, 15, seed=5)
+    Phi, s = rom.pod(Y[:, :r], r)
+    C = Y[:, :r] @ Y[:, :r].T
+    for k in range(r, 15):
+        C = lam**2 * C + np.outer(Y[:, k], Y[:, k])
+        Phi, s = rom.isvd_update(Phi, s, Y[:, k], lam, r)
+        assert np.max(np.abs(Phi @ np.diag(s**2) @ Phi.T - C)) < 1e-10 * np.max(np.abs(C))
+
+
+def test_isvd_keeps_orthonormality_over_many_updates():
+    n, r = 48, 6
+    rng = np.random.default_rng(9)
+    Phi, s = rom.pod(rng.standard_normal((n, r)), r)
+    for k in range(10000):
+        Phi, s = rom.isvd_update(Phi, s, rng.standard_normal(n), 0.9, r)
+    assert np.max(np.abs(Phi.T @ Phi - np.eye(r))) <= 1e-13
+
+
+def test_isvd_transfer_identity():
+    """Phi_new^T Phi_old a == U(1:r,1:r)^T a when q/||q|| is orthogonal to Phi."""
+    n, r = 50, 5
+    rng = np.random.default_rng(2)
+    Phi, s = rom.pod(rng.standard_normal((n, r)), r)
+    a = rng.standard_normal(r)
+    y = rng.standard_normal(n)
+    # iSVD without the sign normalisation, to compare with the raw U
+    p, q = rom.project_cgs2(Phi, y)
+    rho = np.linalg.norm(q)
+    K = np.zeros((r + 1, r + 1))
+    K[:r, :r] = 0.5 * np.diag(s)
+    K[:r, r] = p
+    K[r, r] = rho
+    U, _, _ = np.linalg.svd(K)
+    Phi_new = np.hstack([Phi, (q / rho)[:, None]]) @ U[:, :r]
+    assert np.allclose(Phi_new.T @ (Phi @ a), U[:r, :r].T @ a, atol=1e-13)
+
+
+def test_isvd_brute_force_tiny():
+    """N = 4, r = 2: the update is the rank-2 truncation of the explicit
+    4 x 3 matrix [lam Phi Sigma, y] (the factorisation of Eq. isvd_factorization)."""
+    rng = np.random.default_rng(1)
+    Phi, s = rom.pod(rng.standard_normal((4, 2)), 2)
+    y = rng.standard_normal(4)
+    lam = 0.3
+    Phi2, s2 = rom.isvd_update(Phi, s, y, lam, 2)
+    M = np.hstack([lam * Phi * s[None, :], y[:, None]])
+    U, sb, _ = np.linalg.svd(M, full_matrices=False)
+    assert np.allclose(s2, sb[:2], rtol=1e-13)
+    assert principal_angle_sin(Phi2, U[:, :2]) < 1e-12
+
+
+def test_isvd_empty_residual_keeps_span():
+    n, r = 20, 3
+    rng = np.random.default_rng(4)
+    Phi, s = rom.pod(rng.standard_normal((n, r)), r)
+    y = Phi @ rng.standard_normal(r)          # y in span(Phi): q = 0
+    Phi2, s2 = rom.isvd_update(Phi, s, y, 0.5, r)
+    assert principal_angle_sin(Phi2, Phi) < 1e-12
+    assert np.max(np.abs(Phi2.T @ Phi2 - np.eye(r))) < 1e-13
+
+
+def test_rank_truncation_zeroes_null_directions():
+    n = 30
+    rng = np.random.default_rng(6)
+    X = rng.standard_normal((n, 2)) @ rng.standard_normal((2, 8))   # rank 2
+    Phi, s = rom.pod(X, 5)
+    assert np.count_nonzero(s) == 2
+    assert np.all(Phi[:, 2:] == 0.0)
+    assert rom.numerical_rank(Phi) == 2
+
+
+# ------------------------------------------------------------ preprocess ---
+
+def test_preprocess_mean_square_scaling():
+    n_cells = 8
+    rng = np.random.default_rng(0)
+    q0 = rng.standard_normal(3 * n_cells)
+    Q = q0[:, None] + rng.standard_normal((3 * n_cells, 5)) * np.repeat([1.0, 2.0, 3.0], n_cells)[:, None]
+    q_ref, d, Xhat = rom.preprocess(Q, q0, 3)
+    for v in range(3):
+        blk = (Q - q0[:, None])[v * n_cells:(v + 1) * n_cells]
+        assert np.allclose(d[v * n_cells:(v + 1) * n_cells], 1.0 / np.mean(blk**2))
+    assert np.allclose(Xhat, d[:, None] * (Q - q0[:, None]))
+
+
+def test_burgers_trajectory_invariant_under_scalar_scaling():
+    """For a single variable D is a scalar; q~ does not depend on it."""
+    cfg = synth.config_burgers_small()
+    cfg.n_cells, cfg.n_online, cfg.w_init, cfg.r = 64, 40, 20, 4
+    q0 = synth.initial_state(cfg)
+    A = rom.AdaptiveROM(cfg, q0)
+    B = rom.AdaptiveROM(cfg, q0, A.Q_train)
+    B.d = B.d * 7.0
+    B.sigma = B.sigma * 7.0
+    B.a = B.a * 7.0
+    for _ in range(cfg.n_online):
+        qa, qb = A.step(), B.step()
+        assert np.max(np.abs(qa - qb)) <= 1e-12 * np.max(np.abs(qa))
+
+
+# ------------------------------------------------------------- ROM steps ---
+
+def _full_basis_setup(n=24, seed=0):
+    cfg = synth.config_burgers_small()
+    cfg.n_cells = n
+    rng = np.random.default_rng(seed)
+    Phi = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    q_ref = synth.burgers_ic(n, seed)
+    d = np.full(n, 3.0)
+    return cfg, Phi, q_ref, d
+
+
+def test_galerkin_full_basis_equals_fom_step():
+    """r = N: the BE Galerkin ROM step is the FOM BE step."""
+    cfg, Phi, q_ref, d = _full_basis_setup()
+    q_prev = synth.burgers_ic(cfg.n_cells, 9)
+    a_prev = Phi.T @ (d * (q_prev - q_ref))
+    a, _ = rom.galerkin_step(a_prev, Phi, q_ref, d, cfg)
+    q_fom = fv.be_step(q_prev, cfg.dt, 0, cfg.nu)
+    assert np.max(np.abs(rom.lift(a, Phi, q_ref, d) - q_fom)) < 1e-12
+
+
+def test_hyper_full_sampling_equals_fom_step():
+    """r = n_s = N: DEIM with every cell sampled is the FOM BE step."""
+    cfg, Phi, q_ref, d = _full_basis_setup(seed=1)
+    P = list(np.random.default_rng(2).permutation(cfg.n_cells))
+    M = rom.sampled_pinv(Phi, P)
+    q_prev = synth.burgers_ic(cfg.n_cells, 4)
+    a_prev = Phi.T @ (d * (q_prev - q_ref))
+    a, _ = rom.hyper_step(a_prev, Phi, q_ref, d, P, M, cfg)
+    q_fom = fv.be_step(q_prev, cfg.dt, 0, cfg.nu)
+    assert np.max(np.abs(rom.lift(a, Phi, q_ref, d) - q_fom)) < 1e-11
+
+
+def test_galerkin_jacobian_matches_finite_differences():
+    cfg, _, q_ref, d = _full_basis_setup(n=32)
+    Phi = synth.random_orthonormal(32, 5, 3)
+    a0 = np.random.default_rng(5).standard_normal(5) * 0.1
+    J = rom.galerkin_jacobian(a0, Phi, q_ref, d, cfg)
+    g = lambda a: rom.galerkin_residual(a, a0, Phi, q_ref, d, cfg)
+    Jfd = np.stack([(g(a0 + e) - g(a0 - e)) / 2e-7 for e in np.eye(5) * 1e-7], axis=1)
+    assert np.max(np.abs(J - Jfd)) < 1e-7
+
+
+# -------------------------------------------------------------- sampling ---
+
+def brute_greedy_pivots(Phi, m):
+    """Column-pivoted Gram-Schmidt on the rows of Phi (= columns of Phi^T):
+    repeatedly take the row with the largest remaining norm and remove its
+    direction from every row."""
+    R = Phi.copy()
+    out = []
+    for _ in range(m):
+        norms = np.sum(R * R, axis=1)
+        norms[out] = -1.0
+        i = int(np.argmax(norms))
+        out.append(i)
+        v = R[i] / np.linalg.norm(R[i])
+        R = R - np.outer(R @ v, v)
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_qdeim_matches_brute_force_greedy(seed):
+    Phi = synth.random_orthonormal(200, 8, seed)
+    assert rom.qdeim(Phi, 8) == brute_greedy_pivots(Phi, 8)
+    P = rom.qdeim(Phi, 8)
+    M = rom.sampled_pinv(Phi, P)
+    assert np.allclose(M @ Phi[P, :], np.eye(8), atol=1e-12)
+
+
+def test_fgs_greedy_order_and_ties():
+    y = np.array([0.0, 1.0, 1.0, 3.0, 3.0, 2.0, 0.0, 0.0])
+    # forward differences: 1, 0, 2, 0, -1, -2, 0, 0 -> squares 1,0,4,0,1,4,0,0
+    assert rom.fgs_extend(y, [], 4) == [2, 5, 0, 4]
+    assert rom.fgs_extend(y, [5], 2) == [2, 0]
+
+
+def test_sample_points_oversample_to_ns():
+    Phi = synth.random_orthonormal(100, 4, 1)
+    y = np.sin(np.linspace(0, 6, 100))
+    P = rom.sample_points(Phi, y, 12)
+    assert len(P) == 12 and len(set(P)) == 12
+    assert P[:4] == rom.qdeim(Phi, 12)
+
+
+# ------------------------------------------------------------ Algorithm 1 ---
+
+def small_cfg(n_online=200):
+    cfg = synth.config_burgers_small()
+    cfg.n_cells, cfg.n_online = 128, n_online
+    return cfg
+
+
+def test_event_schedule():
+    cfg = small_cfg(95)
+    m = rom.AdaptiveROM(cfg, synth.initial_state(cfg))
+    m.run(cfg.n_online, record_every=1000)
+    assert m.events == cfg.n_online // cfg.z
+    assert m.n == cfg.w_init + cfg.n_online
+
+
+def test_adaptive_rom_beats_correction_signal_and_static_rom():
+    """Qualitative claims of Sec. 5.1: the adaptive ROM stays close to the
+    fine FOM, closer than the coarse correction signal that informs it, and
+    far closer than the static ROM."""
+    cfg = small_cfg(600)
+    q0 = synth.initial_state(cfg)
+    # the correction snapshot runs z steps ahead of the ROM
+    Q = rom.fom_trajectory(q0, cfg.w_init + cfg.n_online + cfg.z, cfg)
+    A = rom.AdaptiveROM(cfg, q0, Q[:, :cfg.w_init])
+    S = rom.AdaptiveROM(cfg, q0, Q[:, :cfg.w_init])
+    S.is_event = lambda n: False
+    for _ in range(cfg.n_online):
+        qa, qs = A.step(), S.step()
+    q_true = Q[:, A.n - 1]
+    e_rom = rom.relative_error(qa, q_true)
+    e_sig = rom.relative_error(A.y_corr, Q[:, A.n - 1 + cfg.z])
+    e_static = rom.relative_error(qs, q_true)
+    assert e_rom < 1e-3
+    assert e_rom < e_sig
+    assert e_static > 10 * e_rom
+
+
+def test_trajectory_insensitive_to_rounding_with_rank_tolerance():
+    """With the numerical-rank tolerance, perturbing every correction snapshot
+    at the rounding level (1e-16 relative) moves the trajectory by far less
+    than the 1e-10 parity tolerance."""
+    cfg = small_cfg(300)
+    q0 = synth.initial_state(cfg)
+    A = rom.AdaptiveROM(cfg, q0)
+    B = rom.AdaptiveROM(cfg, q0, A.Q_train)
+    rng = np.random.default_rng(7)
+    orig = rom.project_cgs2
+    worst = 0.0
+    try:
+        for _ in range(cfg.n_online):
+            qa = A.step()
+            rom.project_cgs2 = lambda P, y: orig(P, y * (1 + 1e-16 * rng.standard_normal(y.shape)))
+            qb = B.step()
+            rom.project_cgs2 = orig
+            worst = max(worst, np.linalg.norm(qa - qb) / np.linalg.norm(qa))
+    finally:
+        rom.project_cgs2 = orig
+    assert worst < 1e-11
