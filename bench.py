@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Benchmark: adaptive-ROM online steps/s on GB300.
+
+Workload: 1D viscous Burgers, N = 16384 cells, nu = 2e-3, dt = 1e-4, seeded
+initial condition 1 + 0.5 sin(2 pi x) + 0.1 S(x); r = 32, DEIM-Galerkin with
+n_s = 96 sampled cells (QDEIM + feature-guided points), correction snapshot
+and iSVD update every z = 5 steps, forgetting factor 0.5; FP64.
+
+One bench step = one adaptation cycle: z reduced backward-Euler steps followed
+by the adaptation event (coarse FOM step, iSVD update, sampling refresh, state
+transfer), i.e. every part of the online path. ``value`` counts fine online
+ROM steps (z per bench step) per second over the whole job; the state is
+resident on the device when the timed region starts, and L2 is flushed
+(a 256 MiB write) before every timed cycle. ``e2e`` runs the same cycles
+through the public API from host buffers: the initial state goes up from
+pinned host memory (rom_init, amortised over the run) and q~ comes back to
+pinned host memory after every cycle.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs an independent replica (the path does not
+shard; weak scaling) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+if "--impl" in sys.argv and "reference" in sys.argv or "--oracle-sample" in sys.argv:
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_v] = "1"
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "adaptive-ROM online steps/s"
+UNIT = "steps/s"
+WORKLOAD = "burgers-deim-N16384-r32-ns96-z5-lambda0.5-fp64"
+
+# FP64 peak derived from the unit counts and clocks: 152 SMs x 2 DFMA/clk x
+# 2 flop x 2.07 GHz (the nominal 1.25 TFLOP/s of the part).
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+
+# DRAM traffic per launch of the dominant kernel from one ncu capture, valid
+# only while the kernel source is unchanged (sha1 of the file).
+TRAFFIC = {
+    "isvd_update": {"bytes": None, "src": "paper_2605_28684_gb300/csrc/isvd.cu", "sha1": None},
+    "coarse_fom": {"bytes": None, "src": "paper_2605_28684_gb300/csrc/fom.cu", "sha1": None},
+    "reduced_steps": {"bytes": None, "src": "paper_2605_28684_gb300/csrc/reduced.cu", "sha1": None},
+    "sampling": {"bytes": None, "src": "paper_2605_28684_gb300/csrc/sampling.cu", "sha1": None},
+}
+
+
+def workload_config():
+    return synth.config_burgers_hyper(precision=0)
+
+
+def config_json(cfg):
+    return {"workload": WORKLOAD, "n_cells": cfg.n_cells, "r": cfg.r, "n_s": cfg.n_s, "z": cfg.z,
+            "lambda": cfg.lam, "nu": cfg.nu, "dt": cfg.dt, "w_init": cfg.w_init,
+            "step": f"one adaptation cycle = {cfg.z} reduced steps + 1 event",
+            "l2": "flushed (256 MiB write) before every timed cycle"}
+
+
+def peaks():
+    p = {"hbm_gbs": 6800.0, "source": "fallback"}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            m = json.load(f)
+        p = {"hbm_gbs": float(m["hbm_gbs"]), "source": "measured"}
+    return p
+
+
+# ---------------------------------------------------------------- oracle ---
+
+def oracle_sample(seconds: float):
+    """Time the CPU oracle (single thread) on the same workload for about
+    ``seconds``; returns online steps/s and the sample description."""
+    from oracle import rom as orom
+    cfg = workload_config()
+    q0 = synth.initial_state(cfg)
+    m = orom.AdaptiveROM(cfg, q0)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        for _ in range(cfg.z):
+            m.step()
+        steps += cfg.z
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return steps / dt, steps, dt
+
+
+def cpu_baseline(seconds=15.0):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(seconds)],
+                       capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "failed: " + r.stderr.strip().splitlines()[-1][:200]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{d['steps']} online steps ({d['steps'] // 5} adaptation cycles) of the same "
+                      f"workload after the offline stage, {d['seconds']:.1f} s, one thread"}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host, same workload and metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import rom as orom
+    cfg = workload_config()
+    q0 = synth.initial_state(cfg)
+    m = orom.AdaptiveROM(cfg, q0)
+    for _ in range(args.warmup):
+        for _ in range(cfg.z):
+            m.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for _ in range(cfg.z):
+            m.step()
+    dt = time.perf_counter() - t0
+    value = args.steps * cfg.z / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_json(cfg), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} adaptation cycles ({args.steps * cfg.z} online "
+                                       f"steps) after {args.warmup} warm-up cycles, one thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- clocks ---
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- roofline ---
+
+def algorithmic_work(phase: str, cfg, rank: int, launches: dict, fom_iters: float, rom_iters: float):
+    """Algorithmic bytes and FP64 flops of one launch of a phase (minimum the
+    method must move / compute; see the work model of each kernel)."""
+    N, k, ns, z = cfg.n_cells, rank, cfg.n_s, cfg.z
+    if phase == "isvd_update":
+        # CGS2 reads Phi three times, rotation reads and writes it; y, q_ref,
+        # D read; yhat and q written and re-read.
+        bytes_ = 8 * N * (3 * k + 2 * k) + 8 * N * 3 + 8 * N * 4
+        flops = 2 * N * k * 4 + 2 * N * (k + 1) * k
+        return bytes_, flops
+    if phase == "coarse_fom":
+        # per Newton iteration: read q (with halo) and q_prev, write q
+        return 24 * N * fom_iters, 30 * N * fom_iters
+    if phase == "sampling":
+        # k QDEIM passes over Phi, the feature pass over y
+        return 8 * N * k * (k + 1) + 8 * N, 2 * N * k * (k + 1) + 3 * N
+    # reduced steps: per Newton iteration the stencil mesh (Phi rows, q_ref,
+    # d) and (P^T Phi)^+ are read once
+    per_it = 8 * (3 * ns * (k + 2) + k * ns)
+    return per_it * rom_iters * z, (6 * ns * k + 2 * k * ns + 30 * ns) * rom_iters * z
+
+
+def src_sha1(rel):
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+# ------------------------------------------------------------------- main ---
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--oracle-sample", type=float, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    if args.oracle_sample is not None:
+        v, steps, dt = oracle_sample(args.oracle_sample)
+        print(json.dumps({"value": v, "steps": steps, "seconds": dt}))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_2605_28684_gb300 import build as _build
+    if rank == 0 or world == 1:
+        _build.build()
+    if dist is not None:
+        dist.barrier()
+    import paper_2605_28684_gb300 as g
+
+    cfg = workload_config()
+    q0 = synth.initial_state(cfg)
+    stream = torch.cuda.current_stream()
+    rom = g.AdaptiveROM(cfg, q0, stream=stream.cuda_stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        rom.step(cfg.z)
+
+    sampler = ClockSampler(local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    rom.profile(True)
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        rom.step(cfg.z)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    prof = rom.profile_read()
+    rom.profile(False)
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    t_max = total_ms
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    info = rom.info()
+    value = world * args.steps * cfg.z / (t_max / 1e3)
+
+    # roofline of the dominant kernel (largest device time in the timed region)
+    dom = max(prof, key=lambda p: prof[p]["ms"])
+    launches = prof[dom]["launches"]
+    avg_s = prof[dom]["ms"] / 1e3 / max(1, launches)
+    bytes_, flops = algorithmic_work(dom, cfg, info["rank"], prof, info["fom_newton_iters"],
+                                     info["rom_newton_iters"])
+    pk = peaks()
+    gbs = bytes_ / avg_s / 1e9
+    gfl = flops / avg_s / 1e9
+    f_hbm = gbs / pk["hbm_gbs"]
+    f_alu = gfl / FP64_PEAK_GFLOPS
+    tr = TRAFFIC.get(dom, {})
+    traffic = tr.get("bytes") if tr.get("sha1") == src_sha1(tr["src"]) else None
+    if f_hbm >= f_alu:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": f_hbm, "peak_source": pk["source"]}
+    else:
+        roof = {"bound": "alu", "achieved": gfl, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
+                "frac": f_alu, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"}
+    roof.update({"kernel": dom, "traffic": traffic, "algorithmic_bytes": bytes_,
+                 "algorithmic_flops": flops, "avg_launch_us": avg_s * 1e6,
+                 "hbm_frac": f_hbm, "fp64_frac": f_alu})
+    phases = {p: {"ms_total": prof[p]["ms"], "launches": prof[p]["launches"],
+                  "avg_us": prof[p]["ms"] * 1e3 / max(1, prof[p]["launches"])} for p in prof}
+    gpu_launches = sum(prof[p]["launches"] for p in prof)
+
+    # end to end through the public API from pinned host buffers
+    q0_pin = torch.from_numpy(q0.copy()).pin_memory()
+    qt_pin = torch.empty(cfg.n_cells, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rom2 = g.AdaptiveROM(cfg, q0_pin.numpy(), stream=stream.cuda_stream)
+    for _ in range(args.steps):
+        rom2.step(cfg.z)
+        rom2.q_tilde(out=qt_pin.numpy())
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    rom2.close()
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * args.steps * cfg.z / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * cfg.n_cells / args.steps, "d2h_bytes_per_step": 8 * cfg.n_cells,
+           "includes": "rom_init from host q0 (offline stage) + every cycle's q~ readback"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+    rom.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config_json(cfg), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": gpu_launches, "clocks": clocks, "phases": phases,
+                "rank_k": info["rank"], "newton_iters": {"rom": info["rom_newton_iters"],
+                                                         "fom": info["fom_newton_iters"]}}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

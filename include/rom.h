@@ -1,0 +1,221 @@
+/*
+ * rom.h -- C ABI of librom, a single-GPU (GB300, sm_103a) implementation of the
+ * online step of the history-aware adaptive reduced-order model with an
+ * incremental-SVD basis update (arXiv 2605.28684).
+ *
+ * The method (paper, Sec. 4 and Algorithms 1-2): a Galerkin (or DEIM-Galerkin)
+ * reduced model q ~ q_ref + D^-1 Phi a is advanced by backward Euler; every z
+ * steps a coarse backward-Euler full-order step of size z*dt (Eq.
+ * coarse_fom_backward_euler) yields a correction snapshot y, whose
+ * preprocessed form D (y - q_ref) updates the basis by Brand's rank-one
+ * incremental SVD with forgetting factor lambda (Algorithm 2); the sampling
+ * points and the reduced state are then refreshed (Algorithm 1, lines 13-18).
+ *
+ * Conventions common to every entry point
+ *  - Host pointers are read or written during the call only; the library never
+ *    keeps a caller pointer. Device pointers (entry points named *_dev) must
+ *    point to device memory of the current CUDA device and stay valid until the
+ *    call returns.
+ *  - Every call is ordered on the CUDA stream given at creation (or passed to
+ *    the call) and synchronises that stream before it returns.
+ *  - Errors are reported by the return code only; nothing throws across the
+ *    ABI. After ROM_ECUDA or ROM_ETIMEOUT a context is poisoned: every later
+ *    call except rom_destroy returns ROM_ESTATE.
+ *  - The library has no CPU fallback: if no usable sm_103 device is present
+ *    rom_init returns ROM_ECUDA.
+ *  - Vectors of the full-order state have N = n_var * n_cells entries, blocked
+ *    by variable ([rho_0..rho_{N-1}, m_0.., E_0..] for the Euler system). The
+ *    basis Phi is stored column-major, N x r, leading dimension N.
+ */
+#ifndef ROM_H
+#define ROM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rom_ctx rom_ctx;   /* opaque; owns all device memory of one ROM */
+
+typedef enum {
+    ROM_OK = 0,
+    ROM_EINVAL = 1,      /* invalid argument (null pointer, bad size or parameter) */
+    ROM_ENOMEM = 2,      /* device allocation failed */
+    ROM_ECUDA = 3,       /* CUDA runtime error (context poisoned) */
+    ROM_ENOCONV = 4,     /* a Newton iteration hit its iteration limit */
+    ROM_ENONFINITE = 5,  /* NaN or Inf met in the state */
+    ROM_ETIMEOUT = 6,    /* a device-side wait ran out of time (context poisoned) */
+    ROM_ESTATE = 7       /* context poisoned by an earlier error */
+} rom_status;
+
+typedef enum { ROM_BURGERS = 0, ROM_EULER = 1 } rom_problem;
+typedef enum { ROM_FP64 = 0, ROM_MIXED_FP32 = 1 } rom_precision;
+
+/*
+ * Hyper-parameters of one adaptive ROM: the inputs of Algorithm 1 (r, n_s,
+ * w_init, z, lambda) plus the full-order model (paper Sec. 2, Sec. 5.1, App. B).
+ *  problem     ROM_BURGERS: u_t + (u^2/2)_x = nu u_xx, periodic, Godunov flux,
+ *              centred diffusion. ROM_EULER: 1D Euler, ideal gas (gamma),
+ *              Rusanov flux, zero-gradient ghost cells (App. B).
+ *  precision   ROM_FP64, or ROM_MIXED_FP32 (FP32 basis storage, FP32
+ *              projections with FP32 accumulation; FP64 core SVD and residuals).
+ *  n_cells     cells of the uniform grid on [0, 1]; n_var = 1 (Burgers) or 3.
+ *  r           maximum reduced dimension (1 <= r <= 64, r <= w_init, r < N).
+ *  n_s         0: plain Galerkin. > 0: DEIM-Galerkin with n_s sampled cells
+ *              (r <= n_s <= 512, Burgers only): QDEIM points plus
+ *              feature-guided points of largest squared forward difference of
+ *              the correction snapshot.
+ *  w_init      fine FOM steps of the offline training window (>= 1).
+ *  z           adaptation interval (>= 1); the coarse FOM step is z*dt.
+ *  dt, nu, gamma, lambda   time step, viscosity, ratio of specific heats,
+ *              forgetting factor in [0, 1].
+ *  newton_max, newton_tol  Newton stops once max|delta| <= tol (1 + max|x|);
+ *              newton_max iterations without that -> ROM_ENOCONV.
+ *  rank_tol    singular directions with sigma_j <= rank_tol * sigma_1 are
+ *              numerically null and kept as zero columns (<= 0 selects 1e-10).
+ */
+typedef struct {
+    int32_t problem;
+    int32_t precision;
+    int64_t n_cells;
+    int32_t n_var;
+    int32_t r;
+    int32_t n_s;
+    int32_t w_init;
+    int32_t z;
+    int32_t newton_max;
+    double dt;
+    double nu;
+    double gamma;
+    double lambda;
+    double newton_tol;
+    double rank_tol;
+} rom_config;
+
+/*
+ * Offline stage of Algorithm 1 (lines 2-8): w_init fine backward-Euler FOM
+ * steps from q0, preprocessing (q_ref = q0, D_v = 1/phi_v with phi_v the mean
+ * square of the centred training field of variable v; Eqs.
+ * scaling_matrix_local_block, variable_normalization), POD of
+ * D (Q_train - q_ref 1^T) truncated to r, the initial reduced state, the first
+ * coarse correction state and, if n_s > 0, the sampling points.
+ *  cfg       configuration (copied).
+ *  q0_host   host array of N doubles, the initial state.
+ *  stream    cudaStream_t to order all work on (NULL: the legacy default stream).
+ *  out       receives the new context on ROM_OK, NULL otherwise.
+ * Errors: ROM_EINVAL, ROM_ENOMEM, ROM_ECUDA, ROM_ENOCONV, ROM_ENONFINITE.
+ */
+rom_status rom_init(const rom_config* cfg, const double* q0_host, void* stream,
+                    rom_ctx** out);
+
+/*
+ * n_steps iterations of the online loop of Algorithm 1 (lines 9-19): one
+ * backward-Euler reduced step each, and an adaptation event (coarse FOM step,
+ * iSVD update, sampling refresh, state transfer) after every step with
+ * mod(n + 1 - w_init, z) = 0. The state stays on the device.
+ * Errors: ROM_EINVAL (n_steps < 0), ROM_ENOCONV, ROM_ENONFINITE, ROM_ECUDA,
+ * ROM_ETIMEOUT, ROM_ESTATE.
+ */
+rom_status rom_step(rom_ctx* ctx, int64_t n_steps);
+
+/*
+ * One adaptation event now (Algorithm 1 lines 13-18 with Algorithm 2): the
+ * correction snapshot is y_host (N doubles, a raw full-order state, which also
+ * replaces the stored coarse state) or, if y_host is NULL, one coarse FOM step
+ * of the stored coarse state. It is preprocessed as D (y - q_ref), the basis is
+ * updated by the rank-one iSVD with forgetting, the sampling points are
+ * refreshed and the reduced state is transferred to the new basis.
+ * Errors: as rom_step.
+ */
+rom_status rom_update_basis(rom_ctx* ctx, const double* y_host);
+
+/*
+ * Copies the current state to host buffers; any pointer may be NULL.
+ *  q_tilde  N doubles: q_ref + D^-1 Phi a (Eq. trial_approximation).
+ *  a        r doubles;  sigma  r doubles (descending, zeros for null directions).
+ *  phi      N*r doubles, column-major; each non-zero column is sign-normalised
+ *           so that its largest-magnitude entry is positive (a is flipped with
+ *           it, which leaves q_tilde unchanged).
+ *  y_corr   N doubles: the stored coarse correction state.
+ *  step     the time level n of the reduced state.
+ * Errors: ROM_EINVAL (ctx NULL), ROM_ECUDA, ROM_ESTATE.
+ */
+rom_status rom_state(rom_ctx* ctx, double* q_tilde, double* a, double* sigma,
+                     double* phi, double* y_corr, int64_t* step);
+
+/*
+ * Replaces the online state (checkpoint import; resume is bit-exact with the
+ * state exported by rom_state). phi: N*r column-major with orthonormal
+ * non-zero columns; sigma: r; a: r; y_corr: N; step: time level. If n_s > 0
+ * the sampling points are rebuilt from phi and y_corr.
+ * Errors: ROM_EINVAL, ROM_ECUDA, ROM_ESTATE.
+ */
+rom_status rom_load_state(rom_ctx* ctx, const double* phi, const double* sigma,
+                          const double* a, const double* y_corr, int64_t step);
+
+/* Sampling points (n_s int32 cell indices, QDEIM points first) of a
+ * hyper-reduced context. Errors: ROM_EINVAL (NULL or n_s = 0), ROM_ECUDA. */
+rom_status rom_samples(rom_ctx* ctx, int32_t* idx_host);
+
+/* Numerical rank of the current basis (number of non-null columns) and the
+ * Newton iteration counts of the last reduced step and last FOM step. */
+rom_status rom_info(rom_ctx* ctx, int32_t* rank, int32_t* rom_newton_iters,
+                    int32_t* fom_newton_iters);
+
+/*
+ * Per-phase device timing (CUDA events recorded on the context's stream around
+ * every launch of a phase while enabled). Phases: 0 reduced steps, 1 coarse
+ * FOM step, 2 iSVD update, 3 sampling refresh. rom_profile(ctx, 1) clears the
+ * totals and starts recording; rom_profile(ctx, 0) stops. rom_profile_read
+ * synchronises and returns, per phase, the summed milliseconds and the number
+ * of launches (arrays of 4). Errors: ROM_EINVAL, ROM_ECUDA, ROM_ESTATE.
+ */
+rom_status rom_profile(rom_ctx* ctx, int32_t enable);
+rom_status rom_profile_read(rom_ctx* ctx, double* ms_total, int64_t* launches);
+
+/* Releases the context and all its device memory. NULL is ignored. */
+void rom_destroy(rom_ctx* ctx);
+
+/* Static, human-readable name of a status code. */
+const char* rom_status_string(rom_status s);
+
+/*
+ * Low-level full-order entry points on caller-owned device buffers (no
+ * context). problem/n_cells/nu/gamma as in rom_config.
+ *
+ * rom_fom_rhs_dev: f(q) of the semi-discrete operator (Sec. 5.1 problem
+ *   setup; App. B, Eq. sod_fv_semidiscrete_appendix).  q_dev, f_dev: N doubles.
+ * rom_fom_step_dev: one backward-Euler step q - q_prev - h f(q) = 0 solved by
+ *   Newton from q_prev (Eq. be_residual_rom_section); writes q_dev (N doubles,
+ *   may not alias q_prev_dev) and, if iters_host is not NULL, the Newton count.
+ * Errors: ROM_EINVAL, ROM_ENOMEM, ROM_ECUDA, ROM_ENOCONV, ROM_ENONFINITE,
+ * ROM_ETIMEOUT.
+ */
+rom_status rom_fom_rhs_dev(int32_t problem, int64_t n_cells, double nu, double gamma,
+                           const double* q_dev, double* f_dev, void* stream);
+rom_status rom_fom_step_dev(int32_t problem, int64_t n_cells, double nu, double gamma,
+                            double h, double newton_tol, int32_t newton_max,
+                            const double* q_prev_dev, double* q_dev,
+                            int32_t* iters_host, void* stream);
+
+/*
+ * Low-level iSVD update (Algorithm 2) on caller-owned device buffers.
+ *  phi_dev    N x r column-major, updated in place (orthonormal non-zero
+ *             columns; null columns are zero).
+ *  sigma_dev  r doubles, updated in place.
+ *  y_dev      N doubles: the preprocessed snapshot (not modified).
+ *  ubar_host  if not NULL, receives the (r+1) x (r+1) left singular vectors of
+ *             the core matrix, column-major, columns in descending order of
+ *             the singular values.
+ * Errors: ROM_EINVAL, ROM_ENOMEM, ROM_ECUDA, ROM_ETIMEOUT.
+ */
+rom_status rom_isvd_update_dev(int64_t n, int32_t r, double lambda, double rank_tol,
+                               double* phi_dev, double* sigma_dev, const double* y_dev,
+                               double* ubar_host, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ROM_H */

@@ -1,0 +1,742 @@
+// Host side of librom: the C ABI declared in include/rom.h.
+//
+// The context owns every device buffer. All launches go to the context's
+// stream; every entry point synchronises that stream once at the end and then
+// reads the device status word (4 bytes), so the only host round trip per
+// call is that status. The offline stage (Algorithm 1, lines 2-8) is:
+// w_init fine FOM steps -> per-variable scaling -> POD as a rank-growing iSVD
+// with forgetting factor 1 (equal to the thin SVD of the training matrix
+// while its numerical rank stays within kMaxR) -> initial reduced state ->
+// first coarse correction state -> sampling points.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "rom_internal.cuh"
+#include "rom_kernels.cuh"
+
+using namespace rom;
+
+namespace {
+
+constexpr double kGrowRankTol = 1e-15;   // null-direction test while the POD grows
+
+#define RCK(call)                                  \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) {                       \
+      if (ctx) ctx->poisoned = 1;                  \
+      return ROM_ECUDA;                            \
+    }                                              \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+bool device_ok() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) return false;
+  return major == 10 && minor == 3;
+}
+
+int grid_for(int64_t n) {
+  int64_t g = n / 64;
+  if (g < 1) g = 1;
+  int s = sm_count();
+  return (int)(g < s ? g : s);
+}
+
+rom_status validate(const rom_config* c) {
+  if (!c) return ROM_EINVAL;
+  if (c->problem != ROM_BURGERS && c->problem != ROM_EULER) return ROM_EINVAL;
+  if (c->precision != ROM_FP64 && c->precision != ROM_MIXED_FP32) return ROM_EINVAL;
+  if (c->problem == ROM_BURGERS && c->n_var != 1) return ROM_EINVAL;
+  if (c->problem == ROM_EULER && c->n_var != 3) return ROM_EINVAL;
+  if (c->problem == ROM_EULER) return ROM_EINVAL;            // not built yet
+  if (c->precision != ROM_FP64) return ROM_EINVAL;           // not built yet
+  if (c->n_cells < 8 || c->n_cells > (int64_t)kMaxChunks * kMaxChunkRows) return ROM_EINVAL;
+  int64_t N = c->n_cells * c->n_var;
+  if (c->r < 1 || c->r > kMaxR || c->r >= N || c->r > c->w_init) return ROM_EINVAL;
+  if (c->n_s < 0 || (c->n_s > 0 && (c->n_s < c->r || c->n_s > 256 || c->n_s > N))) return ROM_EINVAL;
+  if (c->w_init < 1 || c->z < 1 || c->newton_max < 1) return ROM_EINVAL;
+  if (!(c->dt > 0.0) || !(c->nu >= 0.0) || !(c->lambda >= 0.0 && c->lambda <= 1.0)) return ROM_EINVAL;
+  if (!(c->newton_tol > 0.0)) return ROM_EINVAL;
+  return ROM_OK;
+}
+
+rom_status status_to_rom(int st) {
+  switch (st) {
+    case 0: return ROM_OK;
+    case kStNoConv: return ROM_ENOCONV;
+    case kStNonFinite: return ROM_ENONFINITE;
+    case kStTimeout: return ROM_ETIMEOUT;
+    default: return ROM_ECUDA;
+  }
+}
+
+// Synchronise, read and clear the device status word.
+rom_status finish(rom_ctx* ctx) {
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) { ctx->poisoned = 1; return ROM_ECUDA; }
+  int st = 0;
+  e = cudaMemcpy(&st, ctx->d.status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) { ctx->poisoned = 1; return ROM_ECUDA; }
+  if (st != 0) {
+    cudaMemset(ctx->d.status, 0, sizeof(int));
+    cudaMemset(ctx->d.bar, 0, sizeof(GridBarrier));
+    if (st == kStTimeout) ctx->poisoned = 1;
+  }
+  return status_to_rom(st);
+}
+
+int km_of(const rom_ctx* ctx) { return km_bucket(ctx->cfg.r + 1); }
+
+// Accumulate the recorded event pairs into the per-phase totals.
+cudaError_t prof_flush(rom_ctx* ctx) {
+  if (ctx->prof_n == 0) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < ctx->prof_n; ++i) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]);
+    if (e != cudaSuccess) return e;
+    ctx->prof_ms[ctx->prof_phase[i]] += ms;
+    ctx->prof_cnt[ctx->prof_phase[i]] += 1;
+  }
+  ctx->prof_n = 0;
+  return cudaSuccess;
+}
+
+// Record an event before (begin) / after (end) a phase launch when enabled.
+cudaError_t prof_mark(rom_ctx* ctx, int phase, bool begin) {
+  if (!ctx->prof_on) return cudaSuccess;
+  if (begin && ctx->prof_n >= kMaxProfEvents) {
+    cudaError_t e = prof_flush(ctx);
+    if (e != cudaSuccess) return e;
+  }
+  int i = ctx->prof_n;
+  if (begin) ctx->prof_phase[i] = phase;
+  cudaError_t e = cudaEventRecord(ctx->prof_ev[2 * i + (begin ? 0 : 1)], ctx->stream);
+  if (!begin) ctx->prof_n += 1;
+  return e;
+}
+
+FomParams fom_params(const rom_ctx* ctx, double h) {
+  FomParams p;
+  p.problem = ctx->cfg.problem;
+  p.n_cells = ctx->cfg.n_cells;
+  p.nu = ctx->cfg.nu;
+  p.gamma = ctx->cfg.gamma;
+  p.h = h;
+  p.tol = ctx->cfg.newton_tol;
+  p.max_iter = ctx->cfg.newton_max;
+  return p;
+}
+
+FomScratch fom_scratch(const rom_ctx* ctx) {
+  FomScratch s;
+  s.chunk = ctx->d.fom_chunk;
+  s.maxbuf = ctx->d.maxbuf;
+  s.bar = ctx->d.bar;
+  s.status = ctx->d.status;
+  s.iters = ctx->d.iters_fom;
+  return s;
+}
+
+cudaError_t fom_step(rom_ctx* ctx, const double* q_prev, double* q, double h) {
+  cudaError_t e = cudaMemsetAsync(ctx->d.maxbuf, 0, 4 * sizeof(unsigned long long), ctx->stream);
+  if (e != cudaSuccess) return e;
+  return launch_fom_step(fom_params(ctx, h), q_prev, q, fom_scratch(ctx), ctx->stream);
+}
+
+EventArgs event_args(rom_ctx* ctx, const double* y, int preprocess, double lambda, double rank_tol,
+                     int r_cap, int transfer) {
+  EventArgs A;
+  A.n = ctx->N;
+  A.ld = ctx->N;
+  A.r = r_cap;
+  A.rank = ctx->d.rank;
+  A.lambda = lambda;
+  A.rank_tol = rank_tol;
+  A.phi = ctx->d.phi;
+  A.sigma = ctx->d.sigma;
+  A.a = transfer ? ctx->d.a : nullptr;
+  A.transfer = transfer;
+  A.y = y;
+  A.q_ref = ctx->d.q_ref;
+  A.drow = ctx->d.drow;
+  A.preprocess = preprocess;
+  A.yhat = ctx->d.yhat;
+  A.qres = ctx->d.qres;
+  A.partials = ctx->d.partials;
+  A.core = ctx->d.core;
+  A.ubar = ctx->d.ubar;
+  A.bar = ctx->d.bar;
+  A.status = ctx->d.status;
+  return A;
+}
+
+SampleArgs sample_args(rom_ctx* ctx) {
+  SampleArgs S;
+  S.n = ctx->N;
+  S.ld = ctx->N;
+  S.r = ctx->cfg.r;
+  S.n_s = ctx->cfg.n_s;
+  S.rank = ctx->d.rank;
+  S.phi = ctx->d.phi;
+  S.y = ctx->d.y_corr;
+  S.q_ref = ctx->d.q_ref;
+  S.drow = ctx->d.drow;
+  S.samples = ctx->d.samples;
+  S.chosen = ctx->d.chosen;
+  S.resid = ctx->d.resid_norm;
+  S.cand_v = ctx->d.cand_v;
+  S.cand_i = ctx->d.cand_i;
+  S.qdir = ctx->d.qdeim_q;
+  S.mesh = ctx->d.mesh;
+  S.minv = ctx->d.minv;
+  S.bar = ctx->d.bar;
+  S.status = ctx->d.status;
+  return S;
+}
+
+StepArgs step_args(rom_ctx* ctx, int nsteps) {
+  StepArgs A;
+  A.n = ctx->N;
+  A.ld = ctx->N;
+  A.r = ctx->cfg.r;
+  A.rank = ctx->d.rank;
+  A.phi = ctx->d.phi;
+  A.q_ref = ctx->d.q_ref;
+  A.drow = ctx->d.drow;
+  A.dinv = ctx->d.dinv;
+  A.a = ctx->d.a;
+  A.nu = ctx->cfg.nu;
+  A.dt = ctx->cfg.dt;
+  A.tol = ctx->cfg.newton_tol;
+  A.max_iter = ctx->cfg.newton_max;
+  A.nsteps = nsteps;
+  A.partials = ctx->d.partials;
+  A.jpartials = ctx->d.jpartials;
+  A.jac = ctx->d.jac;
+  A.n_s = ctx->cfg.n_s;
+  A.samples = ctx->d.samples;
+  A.mesh = ctx->d.mesh;
+  A.minv = ctx->d.minv;
+  A.bar = ctx->d.bar;
+  A.status = ctx->d.status;
+  A.iters = ctx->d.iters_rom;
+  return A;
+}
+
+cudaError_t run_steps(rom_ctx* ctx, int nsteps) {
+  StepArgs A = step_args(ctx, nsteps);
+  cudaError_t e = prof_mark(ctx, 0, true);
+  if (e != cudaSuccess) return e;
+  if (ctx->cfg.n_s > 0) e = launch_hyper_steps(A, km_of(ctx), ctx->stream);
+  else e = launch_galerkin_steps(A, km_of(ctx), ctx->grid, ctx->stream);
+  if (e != cudaSuccess) return e;
+  return prof_mark(ctx, 0, false);
+}
+
+// Lines 13-18 of Algorithm 1 on the current y_corr.
+cudaError_t run_event(rom_ctx* ctx) {
+  EventArgs A = event_args(ctx, ctx->d.y_corr, 1, ctx->cfg.lambda, ctx->cfg.rank_tol, ctx->cfg.r, 1);
+  cudaError_t e = prof_mark(ctx, 2, true);
+  if (e == cudaSuccess) e = launch_event(A, km_of(ctx), ctx->grid, ctx->stream);
+  if (e == cudaSuccess) e = prof_mark(ctx, 2, false);
+  if (e != cudaSuccess) return e;
+  if (ctx->cfg.n_s > 0) {
+    e = prof_mark(ctx, 3, true);
+    if (e == cudaSuccess) e = launch_sampling(sample_args(ctx), km_of(ctx), ctx->grid, ctx->stream);
+    if (e == cudaSuccess) e = prof_mark(ctx, 3, false);
+  }
+  return e;
+}
+
+cudaError_t coarse_fom(rom_ctx* ctx) {
+  cudaError_t e = cudaMemsetAsync(ctx->d.maxbuf, 0, 4 * sizeof(unsigned long long), ctx->stream);
+  if (e == cudaSuccess) e = prof_mark(ctx, 1, true);
+  if (e == cudaSuccess)
+    e = launch_fom_step(fom_params(ctx, ctx->cfg.z * ctx->cfg.dt), ctx->d.y_corr, ctx->d.y_tmp,
+                        fom_scratch(ctx), ctx->stream);
+  if (e == cudaSuccess) e = prof_mark(ctx, 1, false);
+  if (e != cudaSuccess) return e;
+  double* t = ctx->d.y_corr;
+  ctx->d.y_corr = ctx->d.y_tmp;
+  ctx->d.y_tmp = t;
+  return cudaSuccess;
+}
+
+// per-variable mean square of the centred training data -> drow
+__global__ void scale_partial_kernel(const double* Q, const double* q_ref, int64_t N, int w,
+                                     int64_t n_cells, int n_var, double* partial) {
+  __shared__ double red[32];
+  for (int v = 0; v < n_var; ++v) {
+    double s = 0.0;
+    int64_t tot = n_cells * (int64_t)w;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      int64_t col = e / n_cells, cell = e % n_cells;
+      int64_t i = v * n_cells + cell;
+      double x = Q[col * N + i] - q_ref[i];
+      s = fma(x, x, s);
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) partial[blockIdx.x * n_var + v] = s;
+  }
+}
+
+__global__ void scale_final_kernel(const double* partial, int nb, int64_t n_cells, int n_var, int w,
+                                   double* dvals) {
+  if (threadIdx.x < n_var) {
+    int v = threadIdx.x;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += partial[b * n_var + v];
+    double phi = s / ((double)n_cells * (double)w);
+    if (phi < 1e-300) phi = 1.0;
+    dvals[v] = 1.0 / phi;
+  }
+}
+
+__global__ void drow_kernel(const double* dvals, int64_t n_cells, int64_t N, double* drow,
+                            double* dinv) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    drow[i] = dvals[i / n_cells];
+    dinv[i] = 1.0 / dvals[i / n_cells];
+  }
+}
+
+void free_state(rom_ctx* ctx) {
+  DevState& d = ctx->d;
+  void* ptrs[] = {d.q_ref, d.y_corr, d.y_tmp, d.yhat, d.qres, d.lifted, d.dvals, d.drow, d.dinv, d.phi,
+                  d.phi32, d.sigma, d.a, d.a_prev, d.rank, d.core, d.ubar, d.partials,
+                  d.jpartials, d.jac, d.samples, d.chosen, d.resid_norm, d.qdeim_q, d.cand_v,
+                  d.cand_i, d.mesh, d.minv, d.bar, d.status, d.iters_rom, d.iters_fom, d.maxbuf,
+                  d.fom_chunk, ctx->q_train};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  memset(&ctx->d, 0, sizeof(DevState));
+  ctx->q_train = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rom_status_string(rom_status s) {
+  switch (s) {
+    case ROM_OK: return "ok";
+    case ROM_EINVAL: return "invalid argument";
+    case ROM_ENOMEM: return "device allocation failed";
+    case ROM_ECUDA: return "CUDA error";
+    case ROM_ENOCONV: return "Newton iteration did not converge";
+    case ROM_ENONFINITE: return "non-finite value in the state";
+    case ROM_ETIMEOUT: return "device-side wait timed out";
+    case ROM_ESTATE: return "context poisoned by an earlier error";
+  }
+  return "unknown status";
+}
+
+void rom_destroy(rom_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->prof_ev_made)
+    for (int i = 0; i < 2 * kMaxProfEvents; ++i) cudaEventDestroy(ctx->prof_ev[i]);
+  free_state(ctx);
+  delete ctx;
+}
+
+rom_status rom_init(const rom_config* cfg_in, const double* q0_host, void* stream, rom_ctx** out) {
+  if (!out) return ROM_EINVAL;
+  *out = nullptr;
+  rom_status vs = validate(cfg_in);
+  if (vs != ROM_OK) return vs;
+  if (!q0_host) return ROM_EINVAL;
+  if (!device_ok()) return ROM_ECUDA;
+  rom_ctx* ctx = new rom_ctx;
+  memset(&ctx->d, 0, sizeof(DevState));
+  ctx->q_train = nullptr;
+  ctx->prof_on = 0;
+  ctx->prof_n = 0;
+  ctx->prof_ev_made = 0;
+  for (int p = 0; p < kPhases; ++p) { ctx->prof_ms[p] = 0.0; ctx->prof_cnt[p] = 0; }
+  ctx->cfg = *cfg_in;
+  if (!(ctx->cfg.rank_tol > 0.0)) ctx->cfg.rank_tol = 1e-10;
+  ctx->stream = (cudaStream_t)stream;
+  ctx->N = ctx->cfg.n_cells * ctx->cfg.n_var;
+  ctx->step = 0;
+  ctx->poisoned = 0;
+  ctx->grid = grid_for(ctx->N);
+  const int64_t N = ctx->N;
+  const int r = ctx->cfg.r;
+  const int w = ctx->cfg.w_init;
+  const int r_grow = w < kMaxR ? w : kMaxR;
+  const int r_alloc = r_grow > r ? r_grow : r;
+  const int G = ctx->grid;
+  const int ns = ctx->cfg.n_s > 0 ? ctx->cfg.n_s : 1;
+  DevState& d = ctx->d;
+  cudaError_t e = cudaSuccess;
+#define ALLOC(p, n) \
+  if (e == cudaSuccess) e = dalloc(&(p), (size_t)(n))
+  ALLOC(d.q_ref, N); ALLOC(d.y_corr, N); ALLOC(d.y_tmp, N); ALLOC(d.yhat, N); ALLOC(d.qres, N);
+  ALLOC(d.lifted, N); ALLOC(d.dvals, 4); ALLOC(d.drow, N); ALLOC(d.dinv, N); ALLOC(d.phi, (size_t)N * r_alloc);
+  ALLOC(d.sigma, kMaxR + 1); ALLOC(d.a, kMaxR + 1); ALLOC(d.a_prev, kMaxR + 1); ALLOC(d.rank, 1);
+  ALLOC(d.core, core_ws_doubles()); ALLOC(d.ubar, kMaxCore * kMaxCore);
+  ALLOC(d.partials, (size_t)3 * G * (kMaxCore + 2)); ALLOC(d.jpartials, (size_t)G * kMaxR * kMaxR);
+  ALLOC(d.jac, kMaxR * kMaxR); ALLOC(d.samples, ns); ALLOC(d.chosen, N); ALLOC(d.resid_norm, N);
+  ALLOC(d.qdeim_q, kMaxR * kMaxR); ALLOC(d.cand_v, (size_t)G * kMaxNs);
+  ALLOC(d.cand_i, (size_t)G * kMaxNs); ALLOC(d.mesh, (size_t)ns * 3 * kMeshStride);
+  ALLOC(d.minv, (size_t)kMaxR * ns); ALLOC(d.bar, 1); ALLOC(d.status, 1); ALLOC(d.iters_rom, 1);
+  ALLOC(d.iters_fom, 1); ALLOC(d.maxbuf, 4); ALLOC(d.fom_chunk, fom_chunk_floats());
+  ALLOC(ctx->q_train, (size_t)N * w);
+#undef ALLOC
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_state(ctx);
+    delete ctx;
+    return ROM_ENOMEM;
+  }
+  cudaStream_t s = ctx->stream;
+  RCK(cudaMemsetAsync(d.bar, 0, sizeof(GridBarrier), s));
+  RCK(cudaMemsetAsync(d.status, 0, sizeof(int), s));
+  RCK(cudaMemsetAsync(d.phi, 0, sizeof(double) * N * r_alloc, s));
+  RCK(cudaMemsetAsync(d.sigma, 0, sizeof(double) * (kMaxR + 1), s));
+  RCK(cudaMemsetAsync(d.a, 0, sizeof(double) * (kMaxR + 1), s));
+  RCK(cudaMemsetAsync(d.rank, 0, sizeof(int), s));
+  RCK(cudaMemcpyAsync(d.y_tmp, q0_host, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+  RCK(cudaMemcpyAsync(d.q_ref, d.y_tmp, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  // training window: w_init fine BE steps
+  const double* prev = d.y_tmp;
+  for (int j = 0; j < w; ++j) {
+    double* cur = ctx->q_train + (size_t)j * N;
+    RCK(fom_step(ctx, prev, cur, ctx->cfg.dt));
+    prev = cur;
+  }
+  rom_status st = finish(ctx);
+  if (st != ROM_OK) { rom_destroy(ctx); return st; }
+  // scaling D
+  {
+    int nb = 256;   // partial sums go to cand_v (grid * kMaxNs >= nb * n_var doubles)
+    scale_partial_kernel<<<nb, 256, 0, s>>>(ctx->q_train, d.q_ref, N, w, ctx->cfg.n_cells,
+                                            ctx->cfg.n_var, d.cand_v);
+    RCK(cudaGetLastError());
+    scale_final_kernel<<<1, 32, 0, s>>>(d.cand_v, nb, ctx->cfg.n_cells, ctx->cfg.n_var, w, d.dvals);
+    RCK(cudaGetLastError());
+    drow_kernel<<<256, 256, 0, s>>>(d.dvals, ctx->cfg.n_cells, N, d.drow, d.dinv);
+    RCK(cudaGetLastError());
+  }
+  // POD: rank-growing iSVD of D (Q_train - q_ref 1^T), forgetting factor 1
+  {
+    const int km = km_bucket(r_grow + 1);
+    for (int j = 0; j < w; ++j) {
+      EventArgs A = event_args(ctx, ctx->q_train + (size_t)j * N, 1, 1.0, kGrowRankTol, r_grow, 0);
+      RCK(launch_event(A, km, G, s));
+    }
+    st = finish(ctx);
+    if (st != ROM_OK) { rom_destroy(ctx); return st; }
+    std::vector<double> sg(r_grow);
+    RCK(cudaMemcpy(sg.data(), d.sigma, sizeof(double) * r_grow, cudaMemcpyDeviceToHost));
+    int k = 0;
+    for (int j = 0; j < r && j < r_grow; ++j)
+      if (sg[0] > 0.0 && sg[j] > ctx->cfg.rank_tol * sg[0]) ++k;
+    if (k < r_alloc) {
+      RCK(cudaMemsetAsync(d.phi + (size_t)k * N, 0, sizeof(double) * N * (r_alloc - k), s));
+      RCK(cudaMemsetAsync(d.sigma + k, 0, sizeof(double) * (kMaxR + 1 - k), s));
+    }
+    RCK(cudaMemcpyAsync(d.rank, &k, sizeof(int), cudaMemcpyHostToDevice, s));
+    RCK(cudaStreamSynchronize(s));
+  }
+  // initial reduced state and first coarse correction state
+  {
+    const double* qlast = ctx->q_train + (size_t)(w - 1) * N;
+    ProjectArgs P;
+    P.n = N; P.ld = N; P.r = r; P.rank = d.rank; P.phi = d.phi; P.v = qlast; P.q_ref = d.q_ref;
+    P.drow = d.drow; P.a = d.a; P.partials = d.partials; P.bar = d.bar; P.status = d.status;
+    RCK(launch_project(P, km_of(ctx), G, s));
+    RCK(fom_step(ctx, qlast, d.y_corr, ctx->cfg.z * ctx->cfg.dt));
+    if (ctx->cfg.n_s > 0) RCK(launch_sampling(sample_args(ctx), km_of(ctx), G, s));
+  }
+  st = finish(ctx);
+  if (st != ROM_OK) { rom_destroy(ctx); return st; }
+  cudaFree(ctx->q_train);
+  ctx->q_train = nullptr;
+  ctx->step = w;
+  *out = ctx;
+  return ROM_OK;
+}
+
+rom_status rom_step(rom_ctx* ctx, int64_t n_steps) {
+  if (!ctx || n_steps < 0) return ROM_EINVAL;
+  if (ctx->poisoned) return ROM_ESTATE;
+  const int64_t z = ctx->cfg.z, w = ctx->cfg.w_init;
+  while (n_steps > 0) {
+    int64_t m = (ctx->step - w) % z;
+    if (m < 0) m += z;
+    int64_t to_event = z - m;
+    int64_t seg = n_steps < to_event ? n_steps : to_event;
+    RCK(run_steps(ctx, (int)seg));
+    ctx->step += seg;
+    n_steps -= seg;
+    if (seg == to_event) {
+      RCK(coarse_fom(ctx));
+      RCK(run_event(ctx));
+    }
+  }
+  return finish(ctx);
+}
+
+rom_status rom_update_basis(rom_ctx* ctx, const double* y_host) {
+  if (!ctx) return ROM_EINVAL;
+  if (ctx->poisoned) return ROM_ESTATE;
+  if (y_host) {
+    RCK(cudaMemcpyAsync(ctx->d.y_corr, y_host, sizeof(double) * ctx->N, cudaMemcpyHostToDevice,
+                        ctx->stream));
+  } else {
+    RCK(coarse_fom(ctx));
+  }
+  RCK(run_event(ctx));
+  return finish(ctx);
+}
+
+rom_status rom_state(rom_ctx* ctx, double* q_tilde, double* a, double* sigma, double* phi,
+                     double* y_corr, int64_t* step) {
+  if (!ctx) return ROM_EINVAL;
+  if (ctx->poisoned) return ROM_ESTATE;
+  const int64_t N = ctx->N;
+  const int r = ctx->cfg.r;
+  cudaStream_t s = ctx->stream;
+  if (q_tilde) {
+    LiftArgs L;
+    L.n = N; L.ld = N; L.rank = ctx->d.rank; L.phi = ctx->d.phi; L.q_ref = ctx->d.q_ref;
+    L.drow = ctx->d.drow; L.dinv = ctx->d.dinv; L.a = ctx->d.a; L.out = ctx->d.lifted;
+    RCK(launch_lift(L, km_of(ctx), s));
+    RCK(cudaMemcpyAsync(q_tilde, ctx->d.lifted, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  }
+  std::vector<double> ha(r), hphi;
+  RCK(cudaMemcpyAsync(ha.data(), ctx->d.a, sizeof(double) * r, cudaMemcpyDeviceToHost, s));
+  if (sigma) RCK(cudaMemcpyAsync(sigma, ctx->d.sigma, sizeof(double) * r, cudaMemcpyDeviceToHost, s));
+  if (phi) RCK(cudaMemcpyAsync(phi, ctx->d.phi, sizeof(double) * N * r, cudaMemcpyDeviceToHost, s));
+  if (y_corr) RCK(cudaMemcpyAsync(y_corr, ctx->d.y_corr, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  rom_status st = finish(ctx);
+  if (st != ROM_OK) return st;
+  // sign convention of the exported basis: largest-magnitude entry positive
+  if (phi) {
+    for (int j = 0; j < r; ++j) {
+      double* col = phi + (size_t)j * N;
+      int64_t im = 0;
+      double best = -1.0;
+      for (int64_t i = 0; i < N; ++i)
+        if (fabs(col[i]) > best) { best = fabs(col[i]); im = i; }
+      if (col[im] < 0.0) {
+        for (int64_t i = 0; i < N; ++i) col[i] = -col[i];
+        ha[j] = -ha[j];
+      }
+    }
+  }
+  if (a) memcpy(a, ha.data(), sizeof(double) * r);
+  if (step) *step = ctx->step;
+  return ROM_OK;
+}
+
+rom_status rom_load_state(rom_ctx* ctx, const double* phi, const double* sigma, const double* a,
+                          const double* y_corr, int64_t step) {
+  if (!ctx || !phi || !sigma || !a || !y_corr || step < ctx->cfg.w_init) return ROM_EINVAL;
+  if (ctx->poisoned) return ROM_ESTATE;
+  const int64_t N = ctx->N;
+  const int r = ctx->cfg.r;
+  int k = 0;
+  for (int j = 0; j < r; ++j)
+    if (sigma[j] > 0.0) k = j + 1;
+  cudaStream_t s = ctx->stream;
+  RCK(cudaMemcpyAsync(ctx->d.phi, phi, sizeof(double) * N * r, cudaMemcpyHostToDevice, s));
+  RCK(cudaMemsetAsync(ctx->d.sigma, 0, sizeof(double) * (kMaxR + 1), s));
+  RCK(cudaMemcpyAsync(ctx->d.sigma, sigma, sizeof(double) * r, cudaMemcpyHostToDevice, s));
+  RCK(cudaMemsetAsync(ctx->d.a, 0, sizeof(double) * (kMaxR + 1), s));
+  RCK(cudaMemcpyAsync(ctx->d.a, a, sizeof(double) * r, cudaMemcpyHostToDevice, s));
+  RCK(cudaMemcpyAsync(ctx->d.y_corr, y_corr, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+  RCK(cudaMemcpyAsync(ctx->d.rank, &k, sizeof(int), cudaMemcpyHostToDevice, s));
+  if (ctx->cfg.n_s > 0) RCK(launch_sampling(sample_args(ctx), km_of(ctx), ctx->grid, s));
+  rom_status st = finish(ctx);
+  if (st == ROM_OK) ctx->step = step;
+  return st;
+}
+
+rom_status rom_samples(rom_ctx* ctx, int32_t* idx_host) {
+  if (!ctx || !idx_host || ctx->cfg.n_s <= 0) return ROM_EINVAL;
+  if (ctx->poisoned) return ROM_ESTATE;
+  RCK(cudaMemcpyAsync(idx_host, ctx->d.samples, sizeof(int) * ctx->cfg.n_s, cudaMemcpyDeviceToHost,
+                      ctx->stream));
+  return finish(ctx);
+}
+
+rom_status rom_info(rom_ctx* ctx, int32_t* rank, int32_t* rom_iters, int32_t* fom_iters) {
+  if (!ctx) return ROM_EINVAL;
+  if (ctx->poisoned) return ROM_ESTATE;
+  int v[3] = {0, 0, 0};
+  RCK(cudaMemcpyAsync(&v[0], ctx->d.rank, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RCK(cudaMemcpyAsync(&v[1], ctx->d.iters_rom, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RCK(cudaMemcpyAsync(&v[2], ctx->d.iters_fom, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  rom_status st = finish(ctx);
+  if (rank) *rank = v[0];
+  if (rom_iters) *rom_iters = v[1];
+  if (fom_iters) *fom_iters = v[2];
+  return st;
+}
+
+rom_status rom_profile(rom_ctx* ctx, int32_t enable) {
+  if (!ctx) return ROM_EINVAL;
+  if (ctx->poisoned) return ROM_ESTATE;
+  if (enable) {
+    if (!ctx->prof_ev_made) {
+      for (int i = 0; i < 2 * kMaxProfEvents; ++i) RCK(cudaEventCreate(&ctx->prof_ev[i]));
+      ctx->prof_ev_made = 1;
+    }
+    RCK(cudaStreamSynchronize(ctx->stream));
+    ctx->prof_n = 0;
+    for (int p = 0; p < kPhases; ++p) { ctx->prof_ms[p] = 0.0; ctx->prof_cnt[p] = 0; }
+    ctx->prof_on = 1;
+  } else {
+    RCK(prof_flush(ctx));
+    ctx->prof_on = 0;
+  }
+  return ROM_OK;
+}
+
+rom_status rom_profile_read(rom_ctx* ctx, double* ms_total, int64_t* launches) {
+  if (!ctx || !ms_total || !launches) return ROM_EINVAL;
+  if (ctx->poisoned) return ROM_ESTATE;
+  RCK(prof_flush(ctx));
+  for (int p = 0; p < kPhases; ++p) {
+    ms_total[p] = ctx->prof_ms[p];
+    launches[p] = ctx->prof_cnt[p];
+  }
+  return ROM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// low-level entry points (caller-owned device buffers)
+// ---------------------------------------------------------------------------
+
+rom_status rom_fom_rhs_dev(int32_t problem, int64_t n_cells, double nu, double gamma,
+                           const double* q_dev, double* f_dev, void* stream) {
+  rom_ctx* ctx = nullptr;
+  if (!q_dev || !f_dev || n_cells < 2 || problem != ROM_BURGERS) return ROM_EINVAL;
+  if (!device_ok()) return ROM_ECUDA;
+  FomParams p;
+  p.problem = problem; p.n_cells = n_cells; p.nu = nu; p.gamma = gamma; p.h = 0; p.tol = 0; p.max_iter = 0;
+  RCK(launch_fom_rhs(p, q_dev, f_dev, (cudaStream_t)stream));
+  RCK(cudaStreamSynchronize((cudaStream_t)stream));
+  return ROM_OK;
+}
+
+rom_status rom_fom_step_dev(int32_t problem, int64_t n_cells, double nu, double gamma, double h,
+                            double newton_tol, int32_t newton_max, const double* q_prev_dev,
+                            double* q_dev, int32_t* iters_host, void* stream) {
+  rom_ctx* ctx = nullptr;
+  if (!q_prev_dev || !q_dev || q_prev_dev == q_dev || problem != ROM_BURGERS || n_cells < 2 ||
+      n_cells > (int64_t)kMaxChunks * kMaxChunkRows || !(h > 0.0) || newton_max < 1 ||
+      !(newton_tol > 0.0))
+    return ROM_EINVAL;
+  if (!device_ok()) return ROM_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  FomScratch sc;
+  float* chunk = nullptr;
+  unsigned long long* maxbuf = nullptr;
+  GridBarrier* bar = nullptr;
+  int* ints = nullptr;
+  if (dalloc(&chunk, fom_chunk_floats()) != cudaSuccess || dalloc(&maxbuf, 4) != cudaSuccess ||
+      dalloc(&bar, 1) != cudaSuccess || dalloc(&ints, 2) != cudaSuccess) {
+    cudaFree(chunk); cudaFree(maxbuf); cudaFree(bar); cudaFree(ints);
+    cudaGetLastError();
+    return ROM_ENOMEM;
+  }
+  sc.chunk = chunk; sc.maxbuf = maxbuf; sc.bar = bar; sc.status = ints; sc.iters = ints + 1;
+  FomParams p;
+  p.problem = problem; p.n_cells = n_cells; p.nu = nu; p.gamma = gamma; p.h = h;
+  p.tol = newton_tol; p.max_iter = newton_max;
+  rom_status result = ROM_OK;
+  cudaError_t e = cudaMemsetAsync(maxbuf, 0, 4 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ints, 0, 2 * sizeof(int), s);
+  if (e == cudaSuccess) e = launch_fom_step(p, q_prev_dev, q_dev, sc, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int hv[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(hv, ints, sizeof(hv), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) result = ROM_ECUDA;
+  else result = status_to_rom(hv[0]);
+  if (iters_host) *iters_host = hv[1];
+  cudaFree(chunk); cudaFree(maxbuf); cudaFree(bar); cudaFree(ints);
+  return result;
+}
+
+rom_status rom_isvd_update_dev(int64_t n, int32_t r, double lambda, double rank_tol, double* phi_dev,
+                               double* sigma_dev, const double* y_dev, double* ubar_host,
+                               void* stream) {
+  rom_ctx* ctx = nullptr;
+  if (n < 2 || r < 1 || r > kMaxR || r >= n || !phi_dev || !sigma_dev || !y_dev ||
+      !(lambda >= 0.0 && lambda <= 1.0))
+    return ROM_EINVAL;
+  if (!device_ok()) return ROM_ECUDA;
+  if (!(rank_tol > 0.0)) rank_tol = 1e-10;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int G = grid_for(n);
+  std::vector<double> hs(r);
+  if (cudaMemcpy(hs.data(), sigma_dev, sizeof(double) * r, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return ROM_ECUDA;
+  int k = 0;
+  for (int j = 0; j < r; ++j)
+    if (hs[j] > 0.0) k = j + 1;
+  double *qres = nullptr, *partials = nullptr, *core = nullptr, *ubar = nullptr;
+  int* ints = nullptr;
+  GridBarrier* bar = nullptr;
+  if (dalloc(&qres, n) != cudaSuccess || dalloc(&partials, (size_t)3 * G * (kMaxCore + 2)) != cudaSuccess ||
+      dalloc(&core, core_ws_doubles()) != cudaSuccess || dalloc(&ubar, kMaxCore * kMaxCore) != cudaSuccess ||
+      dalloc(&ints, 2) != cudaSuccess || dalloc(&bar, 1) != cudaSuccess) {
+    cudaFree(qres); cudaFree(partials); cudaFree(core); cudaFree(ubar); cudaFree(ints); cudaFree(bar);
+    cudaGetLastError();
+    return ROM_ENOMEM;
+  }
+  EventArgs A;
+  A.n = n; A.ld = n; A.r = r; A.rank = ints + 1; A.lambda = lambda; A.rank_tol = rank_tol;
+  A.phi = phi_dev; A.sigma = sigma_dev; A.a = nullptr; A.transfer = 0; A.y = y_dev;
+  A.q_ref = nullptr; A.drow = nullptr; A.preprocess = 0; A.yhat = nullptr; A.qres = qres;
+  A.partials = partials; A.core = core; A.ubar = ubar; A.bar = bar; A.status = ints;
+  rom_status result = ROM_OK;
+  cudaError_t e = cudaMemsetAsync(ints, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ints + 1, &k, sizeof(int), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
+  if (e == cudaSuccess) e = launch_event(A, km_bucket(r + 1), G, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int st = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&st, ints, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && ubar_host) {
+    const int nn = k + 1;
+    std::vector<double> u((size_t)nn * nn);
+    e = cudaMemcpy(u.data(), ubar, sizeof(double) * nn * nn, cudaMemcpyDeviceToHost);
+    for (int c = 0; c < r + 1; ++c)
+      for (int rr = 0; rr < r + 1; ++rr)
+        ubar_host[(size_t)c * (r + 1) + rr] = (c < nn && rr < nn) ? u[(size_t)c * nn + rr] : 0.0;
+  }
+  result = (e != cudaSuccess) ? ROM_ECUDA : status_to_rom(st);
+  cudaFree(qres); cudaFree(partials); cudaFree(core); cudaFree(ubar); cudaFree(ints); cudaFree(bar);
+  return result;
+}
+
+}  // extern "C"

@@ -1,0 +1,562 @@
+// Rank-one incremental SVD with forgetting (paper Algorithm 2, Eqs.
+// isvd_residual ... isvd_truncation) as one cooperative kernel.
+//
+//  1. yhat = D (y - q_ref) (optional), p = Phi^T yhat, q = yhat - Phi p by
+//     classical Gram-Schmidt applied twice (least squares for orthonormal Phi).
+//  2. Core K = [[lam Sigma, p], [0, ||q||]] of order n = k+1. Its left singular
+//     vectors are the eigenvectors of K K^T = diag(d)^2 + z z^T with
+//     d = (lam sigma_1..lam sigma_k, 0) and z = (p, ||q||): a rank-one
+//     modification of a diagonal matrix. After deflation (tiny |z_i|, close
+//     d_i) the singular values are the roots of the secular equation
+//     1 + sum_i z_i^2 / (d_i^2 - s^2) = 0 (Bunch, Nielsen and Sorensen 1978),
+//     one root per CTA, each bracketed between consecutive poles and found by
+//     safeguarded Newton in the shifted variable tau = s - d_origin. The
+//     vectors use the z recomputed from the roots (Gu and Eisenstat 1995),
+//     u_j ~ (zhat_i / (d_i^2 - s_j^2))_i, which keeps them orthogonal.
+//  3. Phi <- [Phi, q/||q||] U(:, 1:k'), sigma <- s(1:k'), where k' <= r counts
+//     the singular values above rank_tol * s_1; the other columns become zero.
+//  4. Optional state transfer a <- Phi_new^T Phi_old a = U(1:k, 1:k')^T a
+//     (exact because q/||q|| is orthogonal to Phi_old).
+#include <cfloat>
+#include <cmath>
+
+#include "rom_internal.cuh"
+#include "rom_kernels.cuh"
+
+namespace rom {
+
+namespace {
+
+// Workspace layout inside ctx->d.core (doubles):
+constexpr int kWsTau = 0;                      // roots: tau_j       [kMaxCore]
+constexpr int kWsOrig = kWsTau + kMaxCore;     // roots: origin o_j  [kMaxCore]
+constexpr int kWsZhat = kWsOrig + kMaxCore;    // zhat_i             [kMaxCore]
+constexpr int kWsSbar = kWsZhat + kMaxCore;    // sorted singular values [kMaxCore]
+constexpr int kWsScal = kWsSbar + kMaxCore;    // scalars
+constexpr int kWsSize = kWsScal + 16;
+
+struct SecularSetup {
+  int n;                       // order of the core
+  int k2;                      // non-deflated count
+  int cidx[kMaxCore];          // compact -> position (ascending order)
+  double D[kMaxCore];          // compact poles (ascending)
+  double Z[kMaxCore];          // compact z (after deflating rotations)
+  double dpos[kMaxCore];       // d by position (ascending)
+  int defl[kMaxCore];          // 1 if position p is deflated
+  int nrot;
+  int rot_a[kMaxCore], rot_b[kMaxCore];
+  double rot_c[kMaxCore], rot_s[kMaxCore];
+  double znorm2;
+};
+
+// Builds the ascending-order secular problem from d (descending, by original
+// index, d[n-1] = 0 for the new direction) and z. Run by one thread.
+__device__ void secular_setup(SecularSetup& S, int n, const double* d_desc, const double* z_orig) {
+  S.n = n;
+  double dmax = 0.0, zn2 = 0.0;
+  for (int p = 0; p < n; ++p) {
+    S.dpos[p] = d_desc[n - 1 - p];
+    dmax = fmax(dmax, fabs(S.dpos[p]));
+    zn2 += z_orig[n - 1 - p] * z_orig[n - 1 - p];
+  }
+  double zp[kMaxCore];
+  for (int p = 0; p < n; ++p) zp[p] = z_orig[n - 1 - p];
+  const double tol = 8.0 * DBL_EPSILON * fmax(dmax, sqrt(zn2));
+  S.nrot = 0;
+  for (int p = 0; p < n; ++p) S.defl[p] = fabs(zp[p]) <= tol ? 1 : 0;
+  int prev = -1;
+  for (int p = 0; p < n; ++p) {
+    if (S.defl[p]) continue;
+    if (prev >= 0 && S.dpos[p] - S.dpos[prev] <= tol) {
+      double rr = hypot(zp[prev], zp[p]);
+      double c = zp[p] / rr, s = zp[prev] / rr;
+      int q = S.nrot++;
+      S.rot_a[q] = prev; S.rot_b[q] = p; S.rot_c[q] = c; S.rot_s[q] = s;
+      zp[p] = rr;
+      zp[prev] = 0.0;
+      S.defl[prev] = 1;
+    }
+    prev = p;
+  }
+  int k2 = 0;
+  double zz = 0.0;
+  for (int p = 0; p < n; ++p) {
+    if (S.defl[p]) continue;
+    S.cidx[k2] = p;
+    S.D[k2] = S.dpos[p];
+    S.Z[k2] = zp[p];
+    zz += zp[p] * zp[p];
+    ++k2;
+  }
+  S.k2 = k2;
+  S.znorm2 = zz;
+}
+
+// Warp-level evaluation of g(tau) and g'(tau) for origin o.
+__device__ __forceinline__ void secular_eval(const SecularSetup& S, int o, double tau, double& g,
+                                             double& gp) {
+  const int lane = threadIdx.x & 31;
+  const double Do = S.D[o];
+  double sg = 0.0, sgp = 0.0;
+  for (int i = lane; i < S.k2; i += 32) {
+    double A = (S.D[i] - Do) - tau;
+    double B = (S.D[i] + Do) + tau;
+    double AB = A * B;
+    double z2 = S.Z[i] * S.Z[i];
+    sg += z2 / AB;
+    sgp += z2 * (B - A) / (AB * AB);
+  }
+  g = 1.0 + warp_sum(sg);
+  gp = warp_sum(sgp);
+}
+
+// Root j (0-based, ascending) of the secular equation by one warp.
+__device__ void secular_root(const SecularSetup& S, int j, int& o_out, double& tau_out) {
+  const int k2 = S.k2;
+  int o;
+  double lo, hi;
+  if (j < k2 - 1) {
+    double mid = 0.5 * (S.D[j] + S.D[j + 1]);
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int i = lane; i < k2; i += 32) s += S.Z[i] * S.Z[i] / ((S.D[i] - mid) * (S.D[i] + mid));
+    double fm = 1.0 + warp_sum(s);
+    if (fm >= 0.0) { o = j; lo = 0.0; hi = mid - S.D[j]; }
+    else { o = j + 1; lo = mid - S.D[j + 1]; hi = 0.0; }
+  } else {
+    o = k2 - 1;
+    double Do = S.D[o];
+    lo = 0.0;
+    hi = S.znorm2 / (Do + sqrt(Do * Do + S.znorm2));
+  }
+  double tau = 0.5 * (lo + hi);
+  for (int it = 0; it < 400; ++it) {
+    double g, gp;
+    secular_eval(S, o, tau, g, gp);
+    if (g == 0.0) break;
+    if (g < 0.0) lo = tau; else hi = tau;
+    double tn = tau - g / gp;
+    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+    bool stop = fabs(tn - tau) <= 2.0 * DBL_EPSILON * fabs(tn) ||
+                (hi - lo) <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi));
+    tau = tn;
+    if (stop) break;
+  }
+  o_out = o;
+  tau_out = tau;
+}
+
+// s_j - D_i and s_j + D_i for root j = (origin o, tau).
+__device__ __forceinline__ double root_minus(const SecularSetup& S, int o, double tau, int i) {
+  return (S.D[o] - S.D[i]) + tau;
+}
+__device__ __forceinline__ double root_plus(const SecularSetup& S, int o, double tau, int i) {
+  return (S.D[o] + S.D[i]) + tau;
+}
+
+__device__ __forceinline__ double warp_prod(double v) {
+  for (int o = 16; o > 0; o >>= 1) v *= __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+struct EventSmem {
+  SecularSetup S;
+  double d_desc[kMaxCore];
+  double z[kMaxCore];
+  double p1[kMaxCore];
+  double p2[kMaxCore];
+  double sc[8];
+  double red[32 * kMaxCore];
+  double U[kMaxCore * kMaxCore];    // U(:, 0:k') for the rotation
+  double a_old[kMaxR];
+  int order[kMaxCore];              // position (descending value) of each eigenpair
+  double val[kMaxCore];
+};
+
+}  // namespace
+
+// --------------------------------------------------------------------------
+// Row-parallel pieces (templated on the register budget KM >= k+1).
+// --------------------------------------------------------------------------
+
+template <int KM>
+__device__ __forceinline__ void block_reduce_vec(double (&acc)[KM], int k, double* red, double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int j = 0; j < KM; ++j) {
+    double v = warp_sum(acc[j]);
+    if (lane == 0 && j < k) red[wid * KM + j] = v;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w * KM + j];
+    out[j] = s;
+  }
+  __syncthreads();
+}
+
+// Sum over CTAs of per-CTA partial vectors, in a fixed order (deterministic).
+__device__ __forceinline__ void grid_reduce_vec(const double* partials, int G, int stride, int k,
+                                                double* out) {
+  grid_reduce_cols(partials, G, stride, k, out);
+}
+
+template <int KM>
+__global__ void __launch_bounds__(kBlock) isvd_event_kernel(EventArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  EventSmem& sm = *reinterpret_cast<EventSmem*>(smem_raw);
+  const int G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
+  const int64_t N = A.n, ld = A.ld;
+  const int64_t beg = (int64_t)b * N / G, end = (int64_t)(b + 1) * N / G;
+  const int k = *A.rank;
+  const int n = k + 1;
+  const int stride = KM + 2;
+  double* part0 = A.partials;
+  double* part1 = A.partials + (size_t)G * stride;
+  double* part2 = A.partials + (size_t)2 * G * stride;
+  double* ws = A.core;
+
+  // ---- P1: yhat and p1 = Phi^T yhat, ||yhat||^2 ----
+  {
+    double acc[KM];
+#pragma unroll
+    for (int j = 0; j < KM; ++j) acc[j] = 0.0;
+    double yy = 0.0;
+    for (int64_t i = beg + t; i < end; i += blockDim.x) {
+      double yh;
+      if (A.preprocess) {
+        yh = A.drow[i] * (A.y[i] - A.q_ref[i]);
+        A.yhat[i] = yh;
+      } else {
+        yh = A.y[i];
+      }
+      yy = fma(yh, yh, yy);
+#pragma unroll
+      for (int j = 0; j < KM; ++j)
+        if (j < k) acc[j] = fma(A.phi[j * ld + i], yh, acc[j]);
+    }
+    block_reduce_vec<KM>(acc, k, sm.red, sm.p1);
+    double yys = block_sum(yy, sm.red);
+    for (int j = t; j < k; j += blockDim.x) part0[(size_t)b * stride + j] = sm.p1[j];
+    if (t == 0) part0[(size_t)b * stride + KM] = yys;
+  }
+  if (!grid_sync(A.bar, A.status)) return;
+  grid_reduce_vec(part0, G, stride, k, sm.p1);
+  grid_reduce_cols(part0 + KM, G, stride, 1, &sm.sc[0]);     // ||yhat||^2
+
+  const double* yv = A.preprocess ? A.yhat : A.y;
+  // ---- P2: q1 = yhat - Phi p1 ; p2 = Phi^T q1 ----
+  {
+    double acc[KM];
+#pragma unroll
+    for (int j = 0; j < KM; ++j) acc[j] = 0.0;
+    for (int64_t i = beg + t; i < end; i += blockDim.x) {
+      double v = A.preprocess ? __ldcg(&yv[i]) : yv[i];
+#pragma unroll
+      for (int j = 0; j < KM; ++j)
+        if (j < k) v = fma(-A.phi[j * ld + i], sm.p1[j], v);
+      A.qres[i] = v;
+#pragma unroll
+      for (int j = 0; j < KM; ++j)
+        if (j < k) acc[j] = fma(A.phi[j * ld + i], v, acc[j]);
+    }
+    block_reduce_vec<KM>(acc, k, sm.red, sm.p2);
+    for (int j = t; j < k; j += blockDim.x) part1[(size_t)b * stride + j] = sm.p2[j];
+  }
+  if (!grid_sync(A.bar, A.status)) return;
+  grid_reduce_vec(part1, G, stride, k, sm.p2);
+  // ---- P3: q = q1 - Phi p2, ||q||^2 ----
+  {
+    double qq = 0.0;
+    for (int64_t i = beg + t; i < end; i += blockDim.x) {
+      double v = A.qres[i];
+#pragma unroll
+      for (int j = 0; j < KM; ++j)
+        if (j < k) v = fma(-A.phi[j * ld + i], sm.p2[j], v);
+      A.qres[i] = v;
+      qq = fma(v, v, qq);
+    }
+    double qs = block_sum(qq, sm.red);
+    if (t == 0) part2[(size_t)b * stride] = qs;
+  }
+  if (!grid_sync(A.bar, A.status)) return;
+
+  // ---- core matrix and secular setup (every CTA, identical) ----
+  grid_reduce_cols(part2, G, stride, 1, &sm.sc[3]);          // ||q||^2
+  if (t == 0) {
+    double rho = sqrt(sm.sc[3]);
+    double ynorm = sqrt(sm.sc[0]);
+    double s1 = (k > 0) ? A.sigma[0] : 0.0;
+    bool keep_q = rho > A.rank_tol * fmax(ynorm, s1);
+    if (!keep_q) rho = 0.0;
+    sm.sc[1] = rho;
+    sm.sc[2] = keep_q ? 1.0 / rho : 0.0;
+    for (int j = 0; j < k; ++j) {
+      sm.d_desc[j] = A.lambda * A.sigma[j];
+      sm.z[j] = sm.p1[j] + sm.p2[j];
+    }
+    sm.d_desc[k] = 0.0;
+    sm.z[k] = rho;
+    secular_setup(sm.S, n, sm.d_desc, sm.z);
+  }
+  __syncthreads();
+  const SecularSetup& S = sm.S;
+  const int k2 = S.k2;
+
+  // ---- roots: one per CTA (warp 0) ----
+  if (t < 32) {
+    for (int j = b; j < k2; j += G) {
+      int o;
+      double tau;
+      secular_root(S, j, o, tau);
+      if (t == 0) {
+        ws[kWsTau + j] = tau;
+        ws[kWsOrig + j] = (double)o;
+      }
+    }
+  }
+  if (!grid_sync(A.bar, A.status)) return;
+
+  // ---- zhat_i (Loewner), one per CTA (warp 0) ----
+  if (t < 32) {
+    const int lane = t;
+    for (int i = b; i < k2; i += G) {
+      double pr = 1.0;
+      for (int j = lane; j < k2; j += 32) {
+        int o = (int)__ldcg(&ws[kWsOrig + j]);
+        double tau = __ldcg(&ws[kWsTau + j]);
+        double num = root_minus(S, o, tau, i) * root_plus(S, o, tau, i);   // s_j^2 - D_i^2
+        double den;
+        if (j == k2 - 1) den = 1.0;
+        else if (j < i) den = (S.D[j] - S.D[i]) * (S.D[j] + S.D[i]);
+        else den = (S.D[j + 1] - S.D[i]) * (S.D[j + 1] + S.D[i]);
+        pr *= num / den;
+      }
+      pr = warp_prod(pr);
+      if (lane == 0) ws[kWsZhat + i] = copysign(sqrt(fabs(pr)), S.Z[i]);
+    }
+  }
+  if (!grid_sync(A.bar, A.status)) return;
+
+  // ---- singular values, descending order, vectors ----
+  // eigenpair e: e < k2 -> root e; e >= k2 -> deflated position (the
+  // (e-k2)-th deflated position in ascending order).
+  if (t == 0) {
+    int c = 0;
+    for (int e = 0; e < k2; ++e) {
+      int o = (int)__ldcg(&ws[kWsOrig + e]);
+      sm.val[e] = S.D[o] + __ldcg(&ws[kWsTau + e]);
+    }
+    c = k2;
+    for (int p = 0; p < n; ++p)
+      if (S.defl[p]) { sm.val[c] = S.dpos[p]; sm.order[c] = p; ++c; }
+  }
+  __syncthreads();
+  // rank of each eigenpair in descending order (ties -> lower eigenpair index)
+  __shared__ int s_pos[kMaxCore];
+  __shared__ int s_defp[kMaxCore];
+  if (t < n) {
+    double v = sm.val[t];
+    int pos = 0;
+    for (int e = 0; e < n; ++e) {
+      double w = sm.val[e];
+      if (w > v || (w == v && e < t)) ++pos;
+    }
+    s_pos[t] = pos;
+    s_defp[t] = (t >= k2) ? sm.order[t] : -1;
+  }
+  __syncthreads();
+  // vectors: eigenpair e handled by CTA e mod G, warp 0; written as column
+  // s_pos[e] of U (n x n, column-major, rows by original index).
+  if (t < 32) {
+    const int lane = t;
+    for (int e = b; e < n; e += G) {
+      double vec[kMaxCore / 32 + 1];   // by position, lanes own p = lane + 32 m
+      const int nm = (n + 31) / 32;
+      for (int m = 0; m < nm; ++m) vec[m] = 0.0;
+      if (e < k2) {
+        int o = (int)__ldcg(&ws[kWsOrig + e]);
+        double tau = __ldcg(&ws[kWsTau + e]);
+        double ss = 0.0;
+        for (int m = 0; m < nm; ++m) {
+          int ci = lane + 32 * m;     // compact index
+          if (ci < k2) {
+            double den = -(root_minus(S, o, tau, ci)) * root_plus(S, o, tau, ci);  // D_i^2 - s^2
+            double u = __ldcg(&ws[kWsZhat + ci]) / den;
+            vec[m] = u;
+            ss += u * u;
+          }
+        }
+        ss = warp_sum(ss);
+        double inv = 1.0 / sqrt(ss);
+        // scatter compact -> position: store in shared staging below
+        for (int m = 0; m < nm; ++m) vec[m] *= inv;
+      }
+      // stage into a position-indexed array (shared, per CTA)
+      __shared__ double pv[kMaxCore];
+      for (int p = lane; p < n; p += 32) pv[p] = 0.0;
+      __syncwarp();
+      if (e < k2) {
+        for (int m = 0; m < nm; ++m) {
+          int ci = lane + 32 * m;
+          if (ci < k2) pv[S.cidx[ci]] = vec[m];
+        }
+      } else if (lane == 0) {
+        pv[s_defp[e]] = 1.0;
+      }
+      __syncwarp();
+      // undo the deflating rotations (reverse order): x = G^T x'
+      if (lane == 0) {
+        for (int q = S.nrot - 1; q >= 0; --q) {
+          int pa = S.rot_a[q], pb = S.rot_b[q];
+          double c = S.rot_c[q], s = S.rot_s[q];
+          double xa = pv[pa], xb = pv[pb];
+          pv[pa] = c * xa + s * xb;
+          pv[pb] = -s * xa + c * xb;
+        }
+      }
+      __syncwarp();
+      const int col = s_pos[e];
+      for (int p = lane; p < n; p += 32) A.ubar[(size_t)col * n + (n - 1 - p)] = pv[p];
+      if (lane == 0) ws[kWsSbar + col] = sm.val[e];
+      __syncwarp();
+    }
+  }
+  if (!grid_sync(A.bar, A.status)) return;
+
+  // ---- rotation and truncation ----
+  int knew = 0;
+  {
+    double s0 = __ldcg(&ws[kWsSbar + 0]);
+    for (int j = 0; j < n && j < A.r; ++j) {
+      double sj = __ldcg(&ws[kWsSbar + j]);
+      if (s0 > 0.0 && sj > A.rank_tol * s0) ++knew;
+    }
+  }
+  for (int e = t; e < n * knew; e += blockDim.x) {
+    int col = e / n, row = e % n;
+    sm.U[row * kMaxCore + col] = __ldcg(&A.ubar[(size_t)col * n + row]);
+  }
+  if (b == 0)
+    for (int j = t; j < k; j += blockDim.x) sm.a_old[j] = A.a ? A.a[j] : 0.0;
+  __syncthreads();
+  const double qinv = sm.sc[2];
+  for (int64_t i = beg + t; i < end; i += blockDim.x) {
+    double x[KM];
+#pragma unroll
+    for (int j = 0; j < KM; ++j) x[j] = (j < k) ? A.phi[j * ld + i] : 0.0;
+    double qh = A.qres[i] * qinv;
+#pragma unroll
+    for (int c = 0; c < KM; ++c) {
+      if (c < knew) {
+        double v = qh * sm.U[k * kMaxCore + c];
+#pragma unroll
+        for (int j = 0; j < KM; ++j)
+          if (j < k) v = fma(x[j], sm.U[j * kMaxCore + c], v);
+        A.phi[c * ld + i] = v;
+      } else if (c < k) {
+        A.phi[c * ld + i] = 0.0;
+      }
+    }
+  }
+  if (b == 0) {
+    // sigma, state transfer and the new rank (other CTAs read none of these)
+    if (t < A.r) {
+      A.sigma[t] = (t < knew) ? __ldcg(&ws[kWsSbar + t]) : 0.0;
+      if (A.a && A.transfer) {
+        double v = 0.0;
+        if (t < knew)
+          for (int j = 0; j < k; ++j) v = fma(sm.U[j * kMaxCore + t], sm.a_old[j], v);
+        A.a[t] = v;
+      }
+    }
+    __syncthreads();
+    if (t == 0) *A.rank = knew;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Projection a = Phi^T D (v - q_ref) (offline initial state).
+// --------------------------------------------------------------------------
+
+template <int KM>
+__global__ void __launch_bounds__(kBlock) project_kernel(ProjectArgs A) {
+  __shared__ double red[32 * KM];
+  __shared__ double out[KM];
+  const int G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
+  const int64_t N = A.n, ld = A.ld;
+  const int64_t beg = (int64_t)b * N / G, end = (int64_t)(b + 1) * N / G;
+  const int k = *A.rank;
+  const int stride = KM + 2;
+  double acc[KM];
+#pragma unroll
+  for (int j = 0; j < KM; ++j) acc[j] = 0.0;
+  for (int64_t i = beg + t; i < end; i += blockDim.x) {
+    double v = A.drow[i] * (A.v[i] - A.q_ref[i]);
+#pragma unroll
+    for (int j = 0; j < KM; ++j)
+      if (j < k) acc[j] = fma(A.phi[j * ld + i], v, acc[j]);
+  }
+  block_reduce_vec<KM>(acc, k, red, out);
+  for (int j = t; j < k; j += blockDim.x) A.partials[(size_t)b * stride + j] = out[j];
+  if (!grid_sync(A.bar, A.status)) return;
+  if (b == 0) {
+    grid_reduce_vec(A.partials, G, stride, k, out);
+    for (int j = t; j < A.r; j += blockDim.x) A.a[j] = (j < k) ? out[j] : 0.0;
+  }
+}
+
+// --------------------------------------------------------------------------
+// launchers
+// --------------------------------------------------------------------------
+
+size_t event_smem_bytes() { return sizeof(EventSmem); }
+size_t core_ws_doubles() { return kWsSize; }
+
+template <int KM>
+static cudaError_t launch_event_t(const EventArgs& A, int grid, cudaStream_t s) {
+  size_t smem = sizeof(EventSmem);
+  cudaError_t e = cudaFuncSetAttribute(isvd_event_kernel<KM>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  EventArgs a = A;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel((const void*)isvd_event_kernel<KM>, dim3(grid), dim3(kBlock),
+                                     args, smem, s);
+}
+
+cudaError_t launch_event(const EventArgs& A, int km, int grid, cudaStream_t s) {
+  switch (km) {
+    case 9: return launch_event_t<9>(A, grid, s);
+    case 17: return launch_event_t<17>(A, grid, s);
+    case 33: return launch_event_t<33>(A, grid, s);
+    default: return launch_event_t<65>(A, grid, s);
+  }
+}
+
+template <int KM>
+static cudaError_t launch_project_t(const ProjectArgs& A, int grid, cudaStream_t s) {
+  ProjectArgs a = A;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel((const void*)project_kernel<KM>, dim3(grid), dim3(kBlock),
+                                     args, 0, s);
+}
+
+cudaError_t launch_project(const ProjectArgs& A, int km, int grid, cudaStream_t s) {
+  switch (km) {
+    case 9: return launch_project_t<9>(A, grid, s);
+    case 17: return launch_project_t<17>(A, grid, s);
+    case 33: return launch_project_t<33>(A, grid, s);
+    default: return launch_project_t<65>(A, grid, s);
+  }
+}
+
+int km_bucket(int kplus1) {
+  if (kplus1 <= 9) return 9;
+  if (kplus1 <= 17) return 17;
+  if (kplus1 <= 33) return 33;
+  return 65;
+}
+
+}  // namespace rom

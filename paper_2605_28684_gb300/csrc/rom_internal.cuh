@@ -1,0 +1,266 @@
+// Internal declarations of librom (not part of the ABI).
+//
+// Execution model. Work that scales with N runs in cooperative kernels whose
+// CTAs are all resident (cudaLaunchCooperativeKernel), separated by a
+// software grid barrier whose wait is bounded in time: when it runs out the
+// kernel records ROM_ETIMEOUT in the status word and returns instead of
+// spinning forever. Double precision is the bottleneck on this part (FP64 runs
+// at about 1/70 of the FP32 rate), so every FP64 sum over N is spread over all
+// CTAs, while Newton Jacobians and their linear solves, which only steer the
+// iteration, run in FP32 against an FP64 residual.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rom.h"
+
+namespace rom {
+
+constexpr int kMaxR = 64;            // maximum reduced dimension
+constexpr int kMaxCore = kMaxR + 1;  // core matrix order
+constexpr int kMaxNs = 512;          // maximum number of sampled cells
+constexpr int kBlock = 256;          // threads of the generic cooperative kernels
+constexpr int kMaxChunks = 128;      // FOM tridiagonal partitions (power of two)
+constexpr int kMaxChunkRows = 1024;  // rows per partition (one thread each)
+constexpr long long kSpinLimitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+// Device status word values (same numbering as rom_status).
+constexpr int kStOK = 0, kStNoConv = 4, kStNonFinite = 5, kStTimeout = 6;
+
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+};
+
+// ---------------------------------------------------------------- barrier --
+
+// All CTAs of a cooperative launch call this the same number of times.
+// Returns false (and records a timeout) if the other CTAs did not arrive in
+// kSpinLimitCycles; the caller must then return.
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &bar->gen;
+    unsigned int g = *vgen;
+    __threadfence();
+    unsigned int arrived = atomicAdd(&bar->count, 1u);
+    int ok = 1;
+    if (arrived == gridDim.x - 1) {
+      bar->count = 0;
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      long long t0 = clock64();
+      while (*vgen == g) {
+        if (clock64() - t0 > kSpinLimitCycles) {
+          atomicExch(status, kStTimeout);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok;
+}
+
+// ------------------------------------------------------------- reductions --
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide sum/max; every thread gets the result. scratch: >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* scratch) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  double t = (threadIdx.x < nw) ? scratch[threadIdx.x] : 0.0;
+  if (wid == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) scratch[0] = t;
+  __syncthreads();
+  double r = scratch[0];
+  __syncthreads();
+  return r;
+}
+__device__ __forceinline__ double block_max(double v, double* scratch) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  double t = (threadIdx.x < nw) ? scratch[threadIdx.x] : -1.0e308;
+  if (wid == 0) t = warp_max(t);
+  if (threadIdx.x == 0) scratch[0] = t;
+  __syncthreads();
+  double r = scratch[0];
+  __syncthreads();
+  return r;
+}
+
+// Order-preserving key of a non-negative double for atomicMax.
+__device__ __forceinline__ unsigned long long nonneg_key(double x) {
+  return (unsigned long long)__double_as_longlong(x);
+}
+__device__ __forceinline__ double key_to_double(unsigned long long k) {
+  return __longlong_as_double((long long)k);
+}
+
+// (value, index) packed so that a larger key = larger value, then lower index.
+struct ArgMax {
+  double v;
+  int i;
+};
+__device__ __forceinline__ bool argmax_better(double v1, int i1, double v2, int i2) {
+  return (v1 > v2) || (v1 == v2 && i1 < i2);
+}
+__device__ __forceinline__ ArgMax warp_argmax(ArgMax a) {
+  for (int o = 16; o > 0; o >>= 1) {
+    double v = __shfl_xor_sync(0xffffffffu, a.v, o);
+    int i = __shfl_xor_sync(0xffffffffu, a.i, o);
+    if (argmax_better(v, i, a.v, a.i)) { a.v = v; a.i = i; }
+  }
+  return a;
+}
+__device__ __forceinline__ ArgMax block_argmax(ArgMax a, double* sv, int* si) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  a = warp_argmax(a);
+  __syncthreads();
+  if (lane == 0) { sv[wid] = a.v; si[wid] = a.i; }
+  __syncthreads();
+  ArgMax b{-1.0e308, 0x7fffffff};
+  if (threadIdx.x < nw) { b.v = sv[threadIdx.x]; b.i = si[threadIdx.x]; }
+  if (wid == 0) b = warp_argmax(b);
+  if (threadIdx.x == 0) { sv[0] = b.v; si[0] = b.i; }
+  __syncthreads();
+  ArgMax r{sv[0], si[0]};
+  __syncthreads();
+  return r;
+}
+
+// out[j] = sum over CTAs b of partials[b * stride + j], j < k. Warps take
+// columns, lanes take CTAs: the loads are independent (no chain of dependent
+// L2 round trips) and the summation order is fixed (deterministic).
+__device__ __forceinline__ void grid_reduce_cols(const double* partials, int G, int stride, int k,
+                                                 double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = wid; j < k; j += nw) {
+    double s = 0.0;
+    for (int b = lane; b < G; b += 32) s += __ldcg(&partials[(size_t)b * stride + j]);
+    s = warp_sum(s);
+    if (lane == 0) out[j] = s;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void record_status(int* status, int code) {
+  atomicCAS(status, kStOK, code);
+}
+
+// ------------------------------------------------------------ FOM kernels --
+
+struct FomParams {
+  int problem;
+  int64_t n_cells;
+  double nu, gamma, h, tol;
+  int max_iter;
+};
+
+// Scratch of a FOM Newton solve; owned by the caller (context or temporary).
+struct FomScratch {
+  float* chunk;                 // kMaxChunks * 16 (Burgers) or * 64 (Euler)
+  unsigned long long* maxbuf;   // 4 keys: |delta|max and |q|max, two parities
+  GridBarrier* bar;
+  int* status;
+  int* iters;
+};
+
+// Host launchers (fom.cu). q_dev receives the new state; q_prev_dev is read only.
+cudaError_t launch_fom_rhs(const FomParams& p, const double* q, double* f, cudaStream_t s);
+cudaError_t launch_fom_step(const FomParams& p, const double* q_prev, double* q,
+                            const FomScratch& sc, cudaStream_t s);
+size_t fom_chunk_floats();
+
+// ------------------------------------------------------------- ROM context --
+
+struct DevState {
+  // full-order vectors (N)
+  double* q_ref;
+  double* y_corr;
+  double* y_tmp;
+  double* yhat;
+  double* qres;         // iSVD residual q (N)
+  double* lifted;       // q~ (N)
+  double* dvals;        // per-variable scaling D_v (n_var)
+  double* drow;         // per-row scaling (N)
+  double* dinv;         // 1 / drow (N)
+  // basis
+  double* phi;          // N x r (ld = N)
+  float* phi32;         // FP32 copy (mixed precision)
+  double* sigma;        // r
+  double* a;            // r
+  double* a_prev;       // r
+  int* rank;            // numerical rank k
+  // iSVD core
+  double* core;         // workspace for the core SVD (see isvd.cu)
+  double* ubar;         // (r+1) x (r+1), column-major
+  // projections
+  double* partials;     // 2 * grid * (kMaxR + 1)
+  float* jpartials;     // grid * kMaxR * kMaxR (FP32 Jacobian partial sums)
+  float* jac;           // kMaxR * kMaxR
+  // sampling (hyper-reduction)
+  int* samples;         // n_s
+  int* chosen;          // N flags (QDEIM picks)
+  double* resid_norm;   // N (QDEIM residual norms)
+  double* qdeim_q;      // kMaxR * kMaxR (orthonormal pivot directions)
+  double* cand_v;       // grid * kMaxNs candidate values
+  int* cand_i;          // grid * kMaxNs candidate indices
+  double* mesh;         // n_s * 3 * (kMaxR + 2): Phi rows, q_ref, d of the stencil
+  double* minv;         // r x n_s  ((P^T Phi)^+, row-major r x n_s)
+  // control
+  GridBarrier* bar;
+  int* status;
+  int* iters_rom;
+  int* iters_fom;
+  unsigned long long* maxbuf;
+  float* fom_chunk;
+};
+
+}  // namespace rom
+
+constexpr int kPhases = 4;
+constexpr int kMaxProfEvents = 4096;
+
+struct rom_ctx {
+  rom_config cfg;
+  // per-phase timing
+  int prof_on;
+  int prof_n;
+  int prof_phase[kMaxProfEvents];
+  cudaEvent_t prof_ev[2 * kMaxProfEvents];
+  int prof_ev_made;
+  double prof_ms[kPhases];
+  long long prof_cnt[kPhases];
+  cudaStream_t stream;
+  int64_t N;
+  int64_t step;          // time level n
+  int grid;              // CTAs of the generic cooperative kernels
+  int poisoned;
+  rom::DevState d;
+  double* q_train;       // N x w_init (offline only, freed after init)
+};
