@@ -200,6 +200,29 @@ rom_status rom_fom_step_dev(int32_t problem, int64_t n_cells, double nu, double 
                             int32_t* iters_host, void* stream);
 
 /*
+ * Allocation-free variant of rom_fom_step_dev (this entry point has no
+ * counterpart in the paper; it is a service for callers that must not
+ * allocate). Some callers cannot call cudaMalloc: a host application that owns
+ * all device memory through its own pool allocator and forbids raw
+ * allocations, or a time-critical loop that cannot afford cudaMalloc/cudaFree
+ * (cudaFree waits for the whole device). This call runs the same Newton solve
+ * with the same arguments, results and errors as rom_fom_step_dev, but
+ * allocates nothing: its scratch is one fixed 8448-byte device array inside
+ * the library, held by every GPU that loads it until the process exits.
+ *  Limit: n_cells <= 131072 (larger values return ROM_EINVAL).
+ *  The first call on a device looks up that array's device address
+ *  (cudaGetSymbolAddress) and caches it; make that first call before any
+ *  stream capture.
+ *  All calls share the array, and each call clears what must start at zero;
+ *  calls that overlap on the GPU (from several host threads or streams at once)
+ *  race on it and must be serialised by the caller.
+ */
+rom_status rom_fom_step_noalloc_dev(int32_t problem, int64_t n_cells, double nu,
+                                    double gamma, double h, double newton_tol,
+                                    int32_t newton_max, const double* q_prev_dev,
+                                    double* q_dev, int32_t* iters_host, void* stream);
+
+/*
  * Low-level iSVD update (Algorithm 2) on caller-owned device buffers.
  *  phi_dev    N x r column-major, updated in place (orthonormal non-zero
  *             columns; null columns are zero).

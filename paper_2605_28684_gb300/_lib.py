@@ -12,7 +12,7 @@ ROM_OK, ROM_EINVAL, ROM_ENOMEM, ROM_ECUDA, ROM_ENOCONV, ROM_ENONFINITE, ROM_ETIM
 EXPORTED = [
     "rom_init", "rom_step", "rom_update_basis", "rom_state", "rom_load_state", "rom_samples",
     "rom_info", "rom_destroy", "rom_status_string", "rom_fom_rhs_dev", "rom_fom_step_dev",
-    "rom_isvd_update_dev", "rom_profile", "rom_profile_read",
+    "rom_isvd_update_dev", "rom_profile", "rom_profile_read", "rom_fom_step_noalloc_dev",
 ]
 
 
@@ -72,11 +72,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                     P, P, P]
     lib.rom_fom_step_dev.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_int32, P, P, I32P, P]
+    lib.rom_fom_step_noalloc_dev.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_int32, P, P, I32P, P]
     lib.rom_isvd_update_dev.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
                                         ctypes.c_double, P, P, P, D, P]
     lib.rom_profile.argtypes = [P, ctypes.c_int32]
     lib.rom_profile_read.argtypes = [P, D, ctypes.POINTER(ctypes.c_int64)]
-    for name in ["rom_profile", "rom_profile_read", "rom_init", "rom_step", "rom_update_basis", "rom_state", "rom_load_state",
+    for name in ["rom_fom_step_noalloc_dev", "rom_profile", "rom_profile_read", "rom_init", "rom_step", "rom_update_basis", "rom_state", "rom_load_state",
                  "rom_samples", "rom_info", "rom_fom_rhs_dev", "rom_fom_step_dev",
                  "rom_isvd_update_dev"]:
         getattr(lib, name).restype = ctypes.c_int

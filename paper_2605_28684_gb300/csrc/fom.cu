@@ -17,6 +17,7 @@
 // separator equations then form a cyclic tridiagonal system of order C, which
 // every CTA solves redundantly by cyclic PCR after one grid barrier.
 #include <cmath>
+#include <mutex>
 
 #include "rom_internal.cuh"
 
@@ -275,3 +276,96 @@ cudaError_t launch_fom_step(const FomParams& p, const double* q_prev, double* q,
 }
 
 }  // namespace rom
+
+// ---------------------------------------------------------------------------
+// Allocation-free FOM step.
+//
+// Some callers cannot call cudaMalloc: for example a host application that
+// owns all device memory through its own pool and forbids raw allocations, or
+// a time-critical loop that cannot afford cudaMalloc/cudaFree (cudaFree waits
+// for the whole device). rom_fom_step_noalloc_dev serves them: it runs the same
+// Newton kernel as rom_fom_step_dev, but its scratch (separator-system chunk
+// summaries, the two maxima per iteration parity, the grid barrier, the status
+// and iteration words) lives in the fixed array below instead of memory
+// allocated per call.
+//
+// The array is kNoAllocScratchBytes (8448 bytes, independent of n_cells); every
+// GPU that loads the library holds it until the process exits. It is shared by
+// all calls and keeps the contents of the last call, so each call first clears
+// the parts that must start at zero. Calls whose work overlaps on the GPU (two
+// host threads, or two streams, at the same time) race on it.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr size_t kNoAllocChunkBytes = sizeof(float) * rom::kMaxChunks * 16;   // 8 KiB
+constexpr size_t kNoAllocMaxOff = kNoAllocChunkBytes;                           // 4 x u64
+constexpr size_t kNoAllocBarOff = kNoAllocMaxOff + 4 * sizeof(unsigned long long);
+constexpr size_t kNoAllocStatusOff = kNoAllocBarOff + sizeof(rom::GridBarrier);  // status, iters
+constexpr size_t kNoAllocUsed = kNoAllocStatusOff + 2 * sizeof(int);
+constexpr size_t kNoAllocScratchBytes = 8448;
+static_assert(kNoAllocUsed <= kNoAllocScratchBytes, "scratch layout exceeds the array");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device. Looked up once per
+// device (with that device current) and cached; in host code the array's name
+// is only a stand-in, not a device address.
+cudaError_t noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" rom_status rom_fom_step_noalloc_dev(int32_t problem, int64_t n_cells, double nu,
+                                               double gamma, double h, double newton_tol,
+                                               int32_t newton_max, const double* q_prev_dev,
+                                               double* q_dev, int32_t* iters_host, void* stream) {
+  const int64_t max_cells = (int64_t)rom::kMaxChunks * rom::kMaxChunkRows;
+  if (!q_prev_dev || !q_dev || q_prev_dev == q_dev || problem != ROM_BURGERS || n_cells < 2 ||
+      n_cells > max_cells || !(h > 0.0) || newton_max < 1 || !(newton_tol > 0.0))
+    return ROM_EINVAL;
+  unsigned char* base = nullptr;
+  if (noalloc_scratch(&base) != cudaSuccess) return ROM_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  rom::FomScratch sc;
+  sc.chunk = reinterpret_cast<float*>(base);
+  sc.maxbuf = reinterpret_cast<unsigned long long*>(base + kNoAllocMaxOff);
+  sc.bar = reinterpret_cast<rom::GridBarrier*>(base + kNoAllocBarOff);
+  sc.status = reinterpret_cast<int*>(base + kNoAllocStatusOff);
+  sc.iters = sc.status + 1;
+  rom::FomParams p;
+  p.problem = problem; p.n_cells = n_cells; p.nu = nu; p.gamma = gamma; p.h = h;
+  p.tol = newton_tol; p.max_iter = newton_max;
+  // maxima, barrier, status and iteration count must start at zero
+  cudaError_t e = cudaMemsetAsync(base + kNoAllocMaxOff, 0, kNoAllocUsed - kNoAllocMaxOff, s);
+  if (e == cudaSuccess) e = rom::launch_fom_step(p, q_prev_dev, q_dev, sc, s);
+  int hv[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hv, sc.status, sizeof(hv), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return ROM_ECUDA;
+  if (iters_host) *iters_host = hv[1];
+  switch (hv[0]) {
+    case rom::kStOK: return ROM_OK;
+    case rom::kStNoConv: return ROM_ENOCONV;
+    case rom::kStNonFinite: return ROM_ENONFINITE;
+    case rom::kStTimeout: return ROM_ETIMEOUT;
+    default: return ROM_ECUDA;
+  }
+}
