@@ -217,21 +217,26 @@ burgers_newton_kernel(BurgersNewtonArgs A) {
       u += delta;
       A.q[i] = u;
     }
-    double dmax = block_max(active ? fabs(delta) : 0.0, red);
-    double umax = block_max(active ? fabs(u) : 0.0, red);
-    bool bad = !(isfinite(dmax) && isfinite(umax));
+    // maxima of |delta| (an FP32 value already) and |u| rounded to FP32 (it
+    // only scales the tolerance), compared as integer keys; NaN/Inf map to
+    // keys >= 0x7f800000
+    unsigned int kdl = active ? (__float_as_uint(fabsf((float)delta))) : 0u;
+    unsigned int kul = active ? (__float_as_uint(fabsf((float)u))) : 0u;
+    if (active && !isfinite(u)) kul = 0x7fc00000u;
+    kdl = block_max_u32(kdl, reinterpret_cast<unsigned int*>(red));
+    kul = block_max_u32(kul, reinterpret_cast<unsigned int*>(red));
     if (t == 0) {
-      atomicMax(&A.maxbuf[2 * par], bad ? 0x7ff8000000000000ull : nonneg_key(dmax));
-      atomicMax(&A.maxbuf[2 * par + 1], bad ? 0x7ff8000000000000ull : nonneg_key(umax));
+      atomicMax(&A.maxbuf[2 * par], (unsigned long long)kdl);
+      atomicMax(&A.maxbuf[2 * par + 1], (unsigned long long)kul);
     }
     if (!grid_sync(A.bar, A.status)) return;
-    unsigned long long kd = __ldcg(&A.maxbuf[2 * par]);
-    unsigned long long ku = __ldcg(&A.maxbuf[2 * par + 1]);
-    if (kd >= 0x7ff0000000000000ull || ku >= 0x7ff0000000000000ull) {
+    unsigned int kd = (unsigned int)__ldcg(&A.maxbuf[2 * par]);
+    unsigned int ku = (unsigned int)__ldcg(&A.maxbuf[2 * par + 1]);
+    if (kd >= 0x7f800000u || ku >= 0x7f800000u) {
       if (c == 0 && t == 0) record_status(A.status, kStNonFinite);
       return;
     }
-    if (key_to_double(kd) <= A.tol * (1.0 + key_to_double(ku))) done = true;
+    if ((double)__uint_as_float(kd) <= A.tol * (1.0 + (double)__uint_as_float(ku))) done = true;
   }
   if (c == 0 && t == 0) {
     *A.iters = it - 1;

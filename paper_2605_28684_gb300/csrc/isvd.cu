@@ -19,6 +19,7 @@
 //     (exact because q/||q|| is orthogonal to Phi_old).
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 
 #include "rom_internal.cuh"
 #include "rom_kernels.cuh"
@@ -92,56 +93,109 @@ __device__ void secular_setup(SecularSetup& S, int n, const double* d_desc, cons
   S.znorm2 = zz;
 }
 
-// Warp-level evaluation of g(tau) and g'(tau) for origin o.
-__device__ __forceinline__ void secular_eval(const SecularSetup& S, int o, double tau, double& g,
-                                             double& gp) {
-  const int lane = threadIdx.x & 31;
-  const double Do = S.D[o];
-  double sg = 0.0, sgp = 0.0;
-  for (int i = lane; i < S.k2; i += 32) {
-    double A = (S.D[i] - Do) - tau;
-    double B = (S.D[i] + Do) + tau;
-    double AB = A * B;
-    double z2 = S.Z[i] * S.Z[i];
-    sg += z2 / AB;
-    sgp += z2 * (B - A) / (AB * AB);
-  }
-  g = 1.0 + warp_sum(sg);
-  gp = warp_sum(sgp);
-}
-
 // Root j (0-based, ascending) of the secular equation by one warp.
+//
+// Work in the shifted eigenvalue variable nu = s^2 - D_o^2 around the nearer
+// pole D_o: f(nu) = 1 + sum_i z_i^2 / (Delta_i - nu), Delta_i = (D_i - D_o)(D_i + D_o),
+// whose poles are all simple. Each update fits f ~ b - c/nu (the origin pole
+// plus a constant) to f and f' at the current point, which is exact for one
+// pole and converges fast near it; the bracket [lo, hi] between the poles
+// guards every step (bisection otherwise). The iteration runs in FP32 on
+// rescaled data first (cheap) and is finished by a few FP64 steps; a
+// dependent FP64 operation costs tens of cycles on this part, so the
+// number of FP64 steps is what sets the time.
 __device__ void secular_root(const SecularSetup& S, int j, int& o_out, double& tau_out) {
   const int k2 = S.k2;
+  const int lane = threadIdx.x & 31;
   int o;
   double lo, hi;
   if (j < k2 - 1) {
     double mid = 0.5 * (S.D[j] + S.D[j + 1]);
-    const int lane = threadIdx.x & 31;
     double s = 0.0;
     for (int i = lane; i < k2; i += 32) s += S.Z[i] * S.Z[i] / ((S.D[i] - mid) * (S.D[i] + mid));
     double fm = 1.0 + warp_sum(s);
-    if (fm >= 0.0) { o = j; lo = 0.0; hi = mid - S.D[j]; }
-    else { o = j + 1; lo = mid - S.D[j + 1]; hi = 0.0; }
+    if (fm >= 0.0) {
+      o = j;
+      lo = 0.0;
+      hi = (mid - S.D[j]) * (mid + S.D[j]);
+    } else {
+      o = j + 1;
+      lo = (mid - S.D[j + 1]) * (mid + S.D[j + 1]);
+      hi = 0.0;
+    }
   } else {
     o = k2 - 1;
-    double Do = S.D[o];
     lo = 0.0;
-    hi = S.znorm2 / (Do + sqrt(Do * Do + S.znorm2));
+    hi = S.znorm2;
   }
-  double tau = 0.5 * (lo + hi);
-  for (int it = 0; it < 400; ++it) {
-    double g, gp;
-    secular_eval(S, o, tau, g, gp);
-    if (g == 0.0) break;
-    if (g < 0.0) lo = tau; else hi = tau;
-    double tn = tau - g / gp;
-    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
-    bool stop = fabs(tn - tau) <= 2.0 * DBL_EPSILON * fabs(tn) ||
-                (hi - lo) <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi));
-    tau = tn;
+  const double Do = S.D[o];
+  // per-lane terms (k2 <= 65: at most three per lane); the FP32 phase has
+  // converged in at most a handful of steps and the FP64 finish in two or
+  // three on the cores this method produces
+  double dl[3], z2[3];
+  int nt = 0;
+  for (int i = lane; i < k2; i += 32, ++nt) {
+    dl[nt] = (S.D[i] - Do) * (S.D[i] + Do);
+    z2[nt] = S.Z[i] * S.Z[i];
+  }
+  // ---- FP32 phase on data scaled by 1 / ||z||^2 ----
+  const double sc = 1.0 / S.znorm2;
+  float dlf[3], z2f[3];
+  for (int q = 0; q < nt; ++q) { dlf[q] = (float)(dl[q] * sc); z2f[q] = (float)(z2[q] * sc); }
+  float flo = (float)(lo * sc), fhi = (float)(hi * sc);
+  float nu = 0.5f * (flo + fhi);
+  for (int it = 0; it < 60; ++it) {
+    float f = 0.f, fp = 0.f, em = 0.f;
+    for (int q = 0; q < nt; ++q) {
+      float r = 1.0f / (dlf[q] - nu);
+      float tq = z2f[q] * r;
+      f += tq;
+      fp += tq * r;
+      em += fabsf(tq);
+    }
+    f = 1.0f + warp_sumf(f);
+    fp = warp_sumf(fp);
+    em = warp_sumf(em);
+    if (fabsf(f) <= 8.0f * FLT_EPSILON * (1.0f + em)) break;   // root to working precision
+    if (f < 0.f) flo = nu; else fhi = nu;
+    // one-pole rational step, else Newton, else bisection (kept inside the bracket)
+    float c = fp * nu * nu, bb = f + fp * nu;
+    float nn = (bb != 0.f) ? c / bb : flo - 1.0f;
+    if (!(nn > flo && nn < fhi)) nn = nu - f / fp;
+    if (!(nn > flo && nn < fhi)) nn = 0.5f * (flo + fhi);
+    bool stop = fabsf(nn - nu) <= 4.0f * FLT_EPSILON * fabsf(nn) || !(fhi > flo);
+    nu = nn;
     if (stop) break;
   }
+  // ---- FP64 finish ----
+  double v = (double)nu / sc;
+  if (!(v > lo && v < hi)) v = 0.5 * (lo + hi);
+  for (int it = 0; it < 40; ++it) {
+    double f = 0.0, fp = 0.0, em = 0.0;
+    for (int q = 0; q < nt; ++q) {
+      double r = 1.0 / (dl[q] - v);
+      double tq = z2[q] * r;
+      f += tq;
+      fp += tq * r;
+      em += fabs(tq);
+    }
+    f = 1.0 + warp_sum(f);
+    fp = warp_sum(fp);
+    em = warp_sum(em);
+    // stop once f is at the level of its own rounding error
+    if (fabs(f) <= 8.0 * DBL_EPSILON * (1.0 + em)) break;
+    if (f < 0.0) lo = v; else hi = v;
+    double c = fp * v * v, bb = f + fp * v;
+    double nn = (bb != 0.0) ? c / bb : lo - 1.0;
+    if (!(nn > lo && nn < hi)) nn = v - f / fp;
+    if (!(nn > lo && nn < hi)) nn = 0.5 * (lo + hi);
+    bool stop = fabs(nn - v) <= 2.0 * DBL_EPSILON * fabs(nn) ||
+                (hi - lo) <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi));
+    v = nn;
+    if (stop) break;
+  }
+  // s = D_o + tau with tau (2 D_o + tau) = nu
+  const double tau = v / (Do + sqrt(Do * Do + v));
   o_out = o;
   tau_out = tau;
 }
@@ -178,6 +232,17 @@ struct EventSmem {
 // --------------------------------------------------------------------------
 // Row-parallel pieces (templated on the register budget KM >= k+1).
 // --------------------------------------------------------------------------
+
+// Calls f(std::integral_constant<int, KB>) with the smallest register budget
+// KB in {9, 17, 33, 65} (capped at KM) that holds k+1 entries, so that loops
+// over the rank are sized for the actual rank rather than the maximum.
+template <int KM, typename F>
+__device__ __forceinline__ void with_rank_bucket(int kp1, F&& f) {
+  if (KM <= 9 || kp1 <= 9) f(std::integral_constant<int, (KM < 9 ? KM : 9)>{});
+  else if (KM <= 17 || kp1 <= 17) f(std::integral_constant<int, (KM < 17 ? KM : 17)>{});
+  else if (KM <= 33 || kp1 <= 33) f(std::integral_constant<int, (KM < 33 ? KM : 33)>{});
+  else f(std::integral_constant<int, KM>{});
+}
 
 template <int KM>
 __device__ __forceinline__ void block_reduce_vec(double (&acc)[KM], int k, double* red, double* out) {
@@ -218,10 +283,11 @@ __global__ void __launch_bounds__(kBlock) isvd_event_kernel(EventArgs A) {
   double* ws = A.core;
 
   // ---- P1: yhat and p1 = Phi^T yhat, ||yhat||^2 ----
-  {
-    double acc[KM];
+  with_rank_bucket<KM>(n, [&](auto kb) {
+    constexpr int KB = decltype(kb)::value;
+    double acc[KB];
 #pragma unroll
-    for (int j = 0; j < KM; ++j) acc[j] = 0.0;
+    for (int j = 0; j < KB; ++j) acc[j] = 0.0;
     double yy = 0.0;
     for (int64_t i = beg + t; i < end; i += blockDim.x) {
       double yh;
@@ -233,37 +299,41 @@ __global__ void __launch_bounds__(kBlock) isvd_event_kernel(EventArgs A) {
       }
       yy = fma(yh, yh, yy);
 #pragma unroll
-      for (int j = 0; j < KM; ++j)
+      for (int j = 0; j < KB; ++j)
         if (j < k) acc[j] = fma(A.phi[j * ld + i], yh, acc[j]);
     }
-    block_reduce_vec<KM>(acc, k, sm.red, sm.p1);
+    block_reduce_vec<KB>(acc, k, sm.red, sm.p1);
     double yys = block_sum(yy, sm.red);
     for (int j = t; j < k; j += blockDim.x) part0[(size_t)b * stride + j] = sm.p1[j];
     if (t == 0) part0[(size_t)b * stride + KM] = yys;
-  }
+  });
   if (!grid_sync(A.bar, A.status)) return;
   grid_reduce_vec(part0, G, stride, k, sm.p1);
   grid_reduce_cols(part0 + KM, G, stride, 1, &sm.sc[0]);     // ||yhat||^2
 
   const double* yv = A.preprocess ? A.yhat : A.y;
   // ---- P2: q1 = yhat - Phi p1 ; p2 = Phi^T q1 ----
-  {
-    double acc[KM];
+  with_rank_bucket<KM>(n, [&](auto kb) {
+    constexpr int KB = decltype(kb)::value;
+    double acc[KB];
 #pragma unroll
-    for (int j = 0; j < KM; ++j) acc[j] = 0.0;
+    for (int j = 0; j < KB; ++j) acc[j] = 0.0;
     for (int64_t i = beg + t; i < end; i += blockDim.x) {
-      double v = A.preprocess ? __ldcg(&yv[i]) : yv[i];
+      double x[KB];
 #pragma unroll
-      for (int j = 0; j < KM; ++j)
-        if (j < k) v = fma(-A.phi[j * ld + i], sm.p1[j], v);
+      for (int j = 0; j < KB; ++j) x[j] = (j < k) ? A.phi[j * ld + i] : 0.0;
+      double v = yv[i];
+#pragma unroll
+      for (int j = 0; j < KB; ++j)
+        if (j < k) v = fma(-x[j], sm.p1[j], v);
       A.qres[i] = v;
 #pragma unroll
-      for (int j = 0; j < KM; ++j)
-        if (j < k) acc[j] = fma(A.phi[j * ld + i], v, acc[j]);
+      for (int j = 0; j < KB; ++j)
+        if (j < k) acc[j] = fma(x[j], v, acc[j]);
     }
-    block_reduce_vec<KM>(acc, k, sm.red, sm.p2);
+    block_reduce_vec<KB>(acc, k, sm.red, sm.p2);
     for (int j = t; j < k; j += blockDim.x) part1[(size_t)b * stride + j] = sm.p2[j];
-  }
+  });
   if (!grid_sync(A.bar, A.status)) return;
   grid_reduce_vec(part1, G, stride, k, sm.p2);
   // ---- P3: q = q1 - Phi p2, ||q||^2 ----
@@ -271,9 +341,7 @@ __global__ void __launch_bounds__(kBlock) isvd_event_kernel(EventArgs A) {
     double qq = 0.0;
     for (int64_t i = beg + t; i < end; i += blockDim.x) {
       double v = A.qres[i];
-#pragma unroll
-      for (int j = 0; j < KM; ++j)
-        if (j < k) v = fma(-A.phi[j * ld + i], sm.p2[j], v);
+      for (int j = 0; j < k; ++j) v = fma(-A.phi[j * ld + i], sm.p2[j], v);
       A.qres[i] = v;
       qq = fma(v, v, qq);
     }
@@ -442,24 +510,27 @@ __global__ void __launch_bounds__(kBlock) isvd_event_kernel(EventArgs A) {
     for (int j = t; j < k; j += blockDim.x) sm.a_old[j] = A.a ? A.a[j] : 0.0;
   __syncthreads();
   const double qinv = sm.sc[2];
-  for (int64_t i = beg + t; i < end; i += blockDim.x) {
-    double x[KM];
+  with_rank_bucket<KM>(n, [&](auto kb) {
+    constexpr int KB = decltype(kb)::value;
+    for (int64_t i = beg + t; i < end; i += blockDim.x) {
+      double x[KB];
 #pragma unroll
-    for (int j = 0; j < KM; ++j) x[j] = (j < k) ? A.phi[j * ld + i] : 0.0;
-    double qh = A.qres[i] * qinv;
+      for (int j = 0; j < KB; ++j) x[j] = (j < k) ? A.phi[j * ld + i] : 0.0;
+      double qh = A.qres[i] * qinv;
 #pragma unroll
-    for (int c = 0; c < KM; ++c) {
-      if (c < knew) {
-        double v = qh * sm.U[k * kMaxCore + c];
+      for (int c = 0; c < KB; ++c) {
+        if (c < knew) {
+          double v = qh * sm.U[k * kMaxCore + c];
 #pragma unroll
-        for (int j = 0; j < KM; ++j)
-          if (j < k) v = fma(x[j], sm.U[j * kMaxCore + c], v);
-        A.phi[c * ld + i] = v;
-      } else if (c < k) {
-        A.phi[c * ld + i] = 0.0;
+          for (int j = 0; j < KB; ++j)
+            if (j < k) v = fma(x[j], sm.U[j * kMaxCore + c], v);
+          A.phi[c * ld + i] = v;
+        } else if (c < k) {
+          A.phi[c * ld + i] = 0.0;
+        }
       }
     }
-  }
+  });
   if (b == 0) {
     // sigma, state transfer and the new rank (other CTAs read none of these)
     if (t < A.r) {

@@ -272,17 +272,23 @@ __global__ void __launch_bounds__(kBlock) galerkin_steps_kernel(StepArgs A) {
       }
       __syncthreads();
       lu_solve(s_J, s_piv, s_x, k);
-      if (t == 0) {
-        double dm = 0.0, am = 0.0;
+      if (t < 32) {
+        unsigned int kd = 0u, ka = 0u;
         bool bad = false;
-        for (int j = 0; j < k; ++j) {
-          double d = (double)s_x[j];
-          s_a[j] += d;
-          dm = fmax(dm, fabs(d));
-          am = fmax(am, fabs(s_a[j]));
-          bad = bad || !isfinite(s_a[j]);
+        for (int j = (t & 31); j < k; j += 32) {
+          float d = s_x[j];
+          double an = s_a[j] + (double)d;
+          s_a[j] = an;
+          kd = max(kd, __float_as_uint(fabsf(d)));
+          ka = max(ka, __float_as_uint(fabsf((float)an)));
+          bad = bad || !isfinite(an);
         }
-        s_sc[0] = bad ? -1.0 : ((dm <= A.tol * (1.0 + am)) ? 1.0 : 0.0);
+        kd = warp_max_u32(kd);
+        ka = warp_max_u32(ka);
+        bad = __any_sync(0xffffffffu, bad);
+        if (t == 0)
+          s_sc[0] = bad ? -1.0
+                        : (((double)__uint_as_float(kd) <= A.tol * (1.0 + (double)__uint_as_float(ka))) ? 1.0 : 0.0);
       }
       __syncthreads();
       if (s_sc[0] < 0.0) {
@@ -305,95 +311,123 @@ __global__ void __launch_bounds__(kBlock) galerkin_steps_kernel(StepArgs A) {
 
 // ----------------------------------------------------------------------------
 // DEIM-Galerkin: one CTA on the sample mesh.
+//
+// The stencil mesh (3 n_s rows of Phi, q_ref and 1/D) is staged in shared
+// memory once; every FP64 loop runs over the actual rank k with all lanes busy:
+// the lift is one thread per mesh row, the residual M (D f) is one warp per
+// reduced coordinate with lanes over the samples.
 // ----------------------------------------------------------------------------
 
 template <int KM>
 __global__ void __launch_bounds__(kBlock) hyper_steps_kernel(StepArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
   const int k = *A.rank;
   const int ns = A.n_s;
+  const int nm = 3 * ns;
   const double inv_dx = (double)A.n;
-  double* s_a = reinterpret_cast<double*>(smem_raw);   // KM
-  double* s_ap = s_a + KM;
-  double* s_sc = s_ap + KM;                             // 8
-  double* s_qt = s_sc + 8;                              // 3 ns
-  double* s_f = s_qt + 3 * ns;                          // ns (d f at samples)
-  float* s_J = reinterpret_cast<float*>(s_f + ns);      // kMaxR * kMaxR
-  float* s_x = s_J + kMaxR * kMaxR;                     // kMaxR
-  int* s_piv = reinterpret_cast<int*>(s_x + kMaxR);     // kMaxR
-  float* s_jr3 = reinterpret_cast<float*>(s_piv + kMaxR);  // 3 ns  (J_f row)
-  float* s_As = s_jr3 + 3 * ns;                         // ns x KM (FP32)
-  double* s_dinv = reinterpret_cast<double*>(s_As + ns * KM + (ns * KM) % 2);  // 3 ns
+  double* s_mesh = reinterpret_cast<double*>(smem_raw);  // nm x k
+  double* s_qr = s_mesh + (size_t)nm * k;                // nm
+  double* s_di = s_qr + nm;                              // nm (1/d)
+  double* s_qt = s_di + nm;                              // nm (lifted)
+  double* s_f = s_qt + nm;                               // ns (d f at samples)
+  double* s_dc = s_f + ns;                               // ns (d at samples)
+  double* s_a = s_dc + ns;                               // KM
+  double* s_ap = s_a + KM;                               // KM
+  double* s_sc = s_ap + KM;                              // 8
+  float* s_J = reinterpret_cast<float*>(s_sc + 8);       // kMaxR * kMaxR
+  float* s_x = s_J + kMaxR * kMaxR;                      // kMaxR
+  int* s_piv = reinterpret_cast<int*>(s_x + kMaxR);      // kMaxR
+  float* s_jr3 = reinterpret_cast<float*>(s_piv + kMaxR);  // nm
+  float* s_As = s_jr3 + nm;                              // ns x k (FP32)
+  float* s_mf = s_As + ns * k;                           // nm x k: Phi row / d (FP32)
+  float* s_Mf = s_mf + nm * k;                           // k x ns: (P^T Phi)^+ (FP32)
+  float* s_dcf = s_Mf + k * ns;                          // ns: d at samples (FP32)
 
-  for (int e = t; e < 3 * ns; e += blockDim.x)
-    s_dinv[e] = 1.0 / A.mesh[(size_t)e * kMeshStride + kMaxR + 1];
+  for (int e = t; e < nm * k; e += blockDim.x) {
+    int row = e / k, j = e % k;
+    s_mesh[e] = A.mesh[(size_t)row * kMeshStride + j];
+  }
+  for (int e = t; e < nm; e += blockDim.x) {
+    s_qr[e] = A.mesh[(size_t)e * kMeshStride + kMaxR];
+    s_di[e] = 1.0 / A.mesh[(size_t)e * kMeshStride + kMaxR + 1];
+  }
+  for (int q = t; q < ns; q += blockDim.x) s_dc[q] = A.mesh[(size_t)(3 * q + 1) * kMeshStride + kMaxR + 1];
+  __syncthreads();
+  // FP32 copies for the Jacobian, converted once per launch
+  for (int e = t; e < nm * k; e += blockDim.x) s_mf[e] = (float)(s_mesh[e] * s_di[e / k]);
+  for (int e = t; e < k * ns; e += blockDim.x) s_Mf[e] = (float)A.minv[e];
+  for (int q = t; q < ns; q += blockDim.x) s_dcf[q] = (float)s_dc[q];
   for (int j = t; j < KM; j += blockDim.x) s_a[j] = (j < k) ? A.a[j] : 0.0;
   __syncthreads();
   int it_total = 0;
   for (int step = 0; step < A.nsteps; ++step) {
-    for (int j = t; j < KM; j += blockDim.x) s_ap[j] = s_a[j];
+    for (int j = t; j < k; j += blockDim.x) s_ap[j] = s_a[j];
     __syncthreads();
     bool conv = false;
     int it;
     for (it = 1; it <= A.max_iter; ++it) {
       // lift at the 3 stencil rows of every sample
-      for (int e = t; e < 3 * ns; e += blockDim.x) {
-        const double* row = A.mesh + (size_t)e * kMeshStride;
+      for (int e = t; e < nm; e += blockDim.x) {
+        const double* row = s_mesh + (size_t)e * k;
         double s = 0.0;
-#pragma unroll
-        for (int j = 0; j < KM; ++j)
-          if (j < k) s = fma(row[j], s_a[j], s);
-        s_qt[e] = row[kMaxR] + s * s_dinv[e];
+        for (int j = 0; j < k; ++j) s = fma(row[j], s_a[j], s);
+        s_qt[e] = s_qr[e] + s * s_di[e];
       }
       __syncthreads();
       for (int q = t; q < ns; q += blockDim.x) {
         RowF rf = burgers_f_row(s_qt[3 * q], s_qt[3 * q + 1], s_qt[3 * q + 2], A.nu, inv_dx);
-        const double dq = A.mesh[(size_t)(3 * q + 1) * kMeshStride + kMaxR + 1];
-        s_f[q] = dq * rf.f;
+        s_f[q] = s_dc[q] * rf.f;                          // d f at the sample
         s_jr3[3 * q] = rf.dl; s_jr3[3 * q + 1] = rf.dc; s_jr3[3 * q + 2] = rf.dr;
       }
       __syncthreads();
       if (it == 1) {
-        // sampled rows of D J_f D^-1 Phi (FP32)
+        // sampled rows of D J_f D^-1 Phi (FP32), then J = I - dt M A (FP32)
         for (int e = t; e < ns * k; e += blockDim.x) {
           int q = e / k, l = e % k;
           float s = 0.f;
-          for (int o = 0; o < 3; ++o) {
-            const double* row = A.mesh + (size_t)(3 * q + o) * kMeshStride;
-            s += s_jr3[3 * q + o] * (float)row[l] * (float)s_dinv[3 * q + o];
-          }
-          s_As[q * KM + l] = s * (float)A.mesh[(size_t)(3 * q + 1) * kMeshStride + kMaxR + 1];
+          for (int o = 0; o < 3; ++o) s += s_jr3[3 * q + o] * s_mf[(size_t)(3 * q + o) * k + l];
+          s_As[q * k + l] = s * s_dcf[q];
         }
         __syncthreads();
-        for (int e = t; e < k * k; e += blockDim.x) {
+        for (int e = wid; e < k * k; e += nw) {
           int j = e / k, l = e % k;
           float s = 0.f;
-          for (int q = 0; q < ns; ++q) s += (float)A.minv[(size_t)j * ns + q] * s_As[q * KM + l];
-          s_J[j * kMaxR + l] = (j == l ? 1.0f : 0.0f) - (float)A.dt * s;
+          for (int q = lane; q < ns; q += 32) s += s_Mf[(size_t)j * ns + q] * s_As[q * k + l];
+          s = warp_sumf(s);
+          if (lane == 0) s_J[j * kMaxR + l] = (j == l ? 1.0f : 0.0f) - (float)A.dt * s;
         }
         __syncthreads();
         lu_factor(s_J, s_piv, k);
       }
-      for (int j = t; j < k; j += blockDim.x) {
+      // residual g_j = a_j - a^n_j - dt sum_q M_jq (d f)_q: one warp per j
+      for (int j = wid; j < k; j += nw) {
         double s = 0.0;
-        for (int q = 0; q < ns; ++q) s = fma(A.minv[(size_t)j * ns + q], s_f[q], s);
-        double g = s_a[j] - s_ap[j] - A.dt * s;
-        s_x[j] = (float)(-g);
+        for (int q = lane; q < ns; q += 32) s = fma(A.minv[(size_t)j * ns + q], s_f[q], s);
+        s = warp_sum(s);
+        if (lane == 0) s_x[j] = (float)(-(s_a[j] - s_ap[j] - A.dt * s));
       }
       __syncthreads();
       lu_solve(s_J, s_piv, s_x, k);
-      if (t == 0) {
-        double dm = 0.0, am = 0.0;
+      if (t < 32) {
+        // max |delta| (an FP32 value) and max |a| rounded to FP32 (it only
+        // scales the tolerance), compared as integer keys
+        unsigned int kd = 0u, ka = 0u;
         bool bad = false;
-        for (int j = 0; j < k; ++j) {
-          double d = (double)s_x[j];
-          s_a[j] += d;
-          dm = fmax(dm, fabs(d));
-          am = fmax(am, fabs(s_a[j]));
-          bad = bad || !isfinite(s_a[j]);
+        for (int j = lane; j < k; j += 32) {
+          float d = s_x[j];
+          double an = s_a[j] + (double)d;
+          s_a[j] = an;
+          kd = max(kd, __float_as_uint(fabsf(d)));
+          ka = max(ka, __float_as_uint(fabsf((float)an)));
+          bad = bad || !isfinite(an);
         }
-        s_sc[0] = bad ? -1.0 : ((dm <= A.tol * (1.0 + am)) ? 1.0 : 0.0);
+        kd = warp_max_u32(kd);
+        ka = warp_max_u32(ka);
+        bad = __any_sync(0xffffffffu, bad);
+        if (lane == 0)
+          s_sc[0] = bad ? -1.0
+                        : (((double)__uint_as_float(kd) <= A.tol * (1.0 + (double)__uint_as_float(ka))) ? 1.0 : 0.0);
       }
       __syncthreads();
       if (s_sc[0] < 0.0) {
@@ -468,9 +502,11 @@ cudaError_t launch_galerkin_steps(const StepArgs& A, int km, int grid, cudaStrea
 
 template <int KM>
 static cudaError_t launch_hyper_t(const StepArgs& A, cudaStream_t s) {
-  int ns = A.n_s;
-  size_t smem = sizeof(double) * (2 * KM + 8 + 3 * ns + ns) + sizeof(float) * (kMaxR * kMaxR + kMaxR) +
-                sizeof(int) * kMaxR + sizeof(float) * (3 * ns + ns * KM + 1) + sizeof(double) * 3 * ns + 64;
+  // sized for the largest rank the context can reach (k <= r <= KM - 1)
+  const size_t ns = A.n_s, nm = 3 * ns, kmax = KM - 1;
+  size_t smem = sizeof(double) * (nm * kmax + 3 * nm + 2 * ns + 2 * KM + 8) +
+                sizeof(float) * (kMaxR * kMaxR + kMaxR) + sizeof(int) * kMaxR +
+                sizeof(float) * (nm + ns * kmax + nm * kmax + kmax * ns + ns) + 64;
   cudaError_t e = cudaFuncSetAttribute(hyper_steps_kernel<KM>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -113,6 +113,36 @@ __device__ __forceinline__ double block_max(double v, double* scratch) {
   return r;
 }
 
+// Integer comparisons of non-negative floating-point values. On this part a
+// dependent FP64 instruction costs tens of cycles, so maxima and argmax
+// reductions compare the IEEE bit patterns (which order like the values for
+// non-negative numbers) on the integer pipe instead.
+__device__ __forceinline__ unsigned int warp_max_u32(unsigned int v) {
+  return __reduce_max_sync(0xffffffffu, v);
+}
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+// Block-wide maximum of a 32-bit key; every thread gets the result.
+__device__ __forceinline__ unsigned int block_max_u32(unsigned int v, unsigned int* scratch) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_max_u32(v);
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  unsigned int t = (threadIdx.x < nw) ? scratch[threadIdx.x] : 0u;
+  if (wid == 0) t = warp_max_u32(t);
+  if (threadIdx.x == 0) scratch[0] = t;
+  __syncthreads();
+  unsigned int r = scratch[0];
+  __syncthreads();
+  return r;
+}
+
 // Order-preserving key of a non-negative double for atomicMax.
 __device__ __forceinline__ unsigned long long nonneg_key(double x) {
   return (unsigned long long)__double_as_longlong(x);
@@ -126,8 +156,16 @@ struct ArgMax {
   double v;
   int i;
 };
+// Larger value first, then lower index. Values are non-negative or negative
+// sentinels; negative values map below every non-negative one. The test runs
+// on integer keys (see above).
+__device__ __forceinline__ long long argmax_key(double v) {
+  long long b = __double_as_longlong(v);
+  return b < 0 ? -1 - (b & 0x7fffffffffffffffLL) : b;
+}
 __device__ __forceinline__ bool argmax_better(double v1, int i1, double v2, int i2) {
-  return (v1 > v2) || (v1 == v2 && i1 < i2);
+  long long k1 = argmax_key(v1), k2 = argmax_key(v2);
+  return (k1 > k2) || (k1 == k2 && i1 < i2);
 }
 __device__ __forceinline__ ArgMax warp_argmax(ArgMax a) {
   for (int o = 16; o > 0; o >>= 1) {

@@ -35,6 +35,7 @@ struct SampleSmem {
   int piv[kMaxNs];
   double cv[512];
   int ci[512];
+  double X[256 * kMaxR];     // (P^T Phi)^+ columns being solved (n_s <= 256)
 };
 
 // Bitonic sort (descending value, ascending index) of 512 (value, index) pairs.
@@ -72,71 +73,92 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
   const int lane = t & 31;
 
   // ---- initial residual norms and first local argmax ----
+  // Each thread owns at most kRowsPerThread rows of this CTA's range and keeps
+  // their remaining norms and chosen flags in registers across the pivots.
+  constexpr int kRowsPerThread = 4;
+  double res[kRowsPerThread];
+  bool taken[kRowsPerThread];
   ArgMax best{-1.0, 0x7fffffff};
-  for (int64_t i = beg + t; i < end; i += blockDim.x) {
-    double s = 0.0;
 #pragma unroll
-    for (int j = 0; j < KM; ++j)
-      if (j < k) { double x = A.phi[j * ld + i]; s = fma(x, x, s); }
-    A.resid[i] = s;
-    A.chosen[i] = 0;
-    if (argmax_better(s, (int)i, best.v, best.i)) { best.v = s; best.i = (int)i; }
+  for (int r = 0; r < kRowsPerThread; ++r) {
+    const int64_t i = beg + t + (int64_t)r * blockDim.x;
+    res[r] = -1.0;
+    taken[r] = false;
+    if (i < end) {
+      double s = 0.0;
+      for (int j = 0; j < k; ++j) { double x = A.phi[j * ld + i]; s = fma(x, x, s); }
+      res[r] = s;
+      if (argmax_better(s, (int)i, best.v, best.i)) { best.v = s; best.i = (int)i; }
+    }
   }
   best = block_argmax(best, sm.red, sm.redi);
   if (t == 0) { A.cand_v[(size_t)b * kMaxNs] = best.v; A.cand_i[(size_t)b * kMaxNs] = best.i; }
   if (!grid_sync(A.bar, A.status)) return;
 
+  // Candidate slots are double-buffered by step parity, so one grid barrier
+  // per pivot suffices: step s reads slot s&1 and writes slot (s+1)&1.
+  const int wid = t >> 5, nwarp = blockDim.x >> 5;
   for (int step = 0; step < kq; ++step) {
+    const size_t rd = (size_t)(step & 1), wr = (size_t)((step + 1) & 1);
     // global pivot (every CTA, same fixed-order reduction)
     ArgMax g{-1.0, 0x7fffffff};
     for (int bb = t; bb < G; bb += blockDim.x) {
-      double v = __ldcg(&A.cand_v[(size_t)bb * kMaxNs]);
-      int i = __ldcg(&A.cand_i[(size_t)bb * kMaxNs]);
+      double v = __ldcg(&A.cand_v[(size_t)bb * kMaxNs + rd]);
+      int i = __ldcg(&A.cand_i[(size_t)bb * kMaxNs + rd]);
       if (argmax_better(v, i, g.v, g.i)) { g.v = v; g.i = i; }
     }
     g = block_argmax(g, sm.red, sm.redi);
     const int p = g.i;
     if (t == 0) sm.piv[step] = p;
-    // residual direction of row p against the previous directions (CGS twice)
-    if (t < 32) {
-      for (int j = lane; j < k; j += 32) sm.v[j] = A.phi[j * ld + p];
-      __syncwarp();
-      for (int pass = 0; pass < 2; ++pass) {
-        for (int l = 0; l < step; ++l) {
-          double s = 0.0;
-          for (int j = lane; j < k; j += 32) s += sm.v[j] * sm.q[l * kMaxR + j];
-          s = warp_sum(s);
-          for (int j = lane; j < k; j += 32) sm.v[j] -= s * sm.q[l * kMaxR + j];
-          __syncwarp();
-        }
+    // residual direction of row p against the previous directions: classical
+    // Gram-Schmidt twice, the dot products of one pass computed by all warps
+    for (int j = t; j < k; j += blockDim.x) sm.v[j] = A.phi[j * ld + p];
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int l = wid; l < step; l += nwarp) {
+        double s = 0.0;
+        for (int j = lane; j < k; j += 32) s = fma(sm.v[j], sm.q[l * kMaxR + j], s);
+        s = warp_sum(s);
+        if (lane == 0) sm.w[l] = s;
       }
+      __syncthreads();
+      for (int j = t; j < k; j += blockDim.x) {
+        double x = sm.v[j];
+        for (int l = 0; l < step; ++l) x = fma(-sm.w[l], sm.q[l * kMaxR + j], x);
+        sm.v[j] = x;
+      }
+      __syncthreads();
+    }
+    if (t < 32) {
       double s = 0.0;
-      for (int j = lane; j < k; j += 32) s += sm.v[j] * sm.v[j];
+      for (int j = lane; j < k; j += 32) s = fma(sm.v[j], sm.v[j], s);
       s = warp_sum(s);
       double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
       for (int j = lane; j < k; j += 32) sm.q[step * kMaxR + j] = sm.v[j] * inv;
     }
     __syncthreads();
+    if (step + 1 == kq) break;        // the last pivot needs no further update
     // update residual norms, mark the pivot, next local argmax
     best = ArgMax{-1.0, 0x7fffffff};
-    for (int64_t i = beg + t; i < end; i += blockDim.x) {
-      double c = 0.0;
 #pragma unroll
-      for (int j = 0; j < KM; ++j)
-        if (j < k) c = fma(A.phi[j * ld + i], sm.q[step * kMaxR + j], c);
-      double r = A.resid[i] - c * c;
-      A.resid[i] = r;
-      if (i == p) A.chosen[i] = 1;
-      if (!A.chosen[i] && argmax_better(r, (int)i, best.v, best.i)) { best.v = r; best.i = (int)i; }
+    for (int r = 0; r < kRowsPerThread; ++r) {
+      const int64_t i = beg + t + (int64_t)r * blockDim.x;
+      if (i < end) {
+        double c = 0.0;
+        for (int j = 0; j < k; ++j) c = fma(A.phi[j * ld + i], sm.q[step * kMaxR + j], c);
+        res[r] = fma(-c, c, res[r]);
+        if (i == p) taken[r] = true;
+        if (!taken[r] && argmax_better(res[r], (int)i, best.v, best.i)) { best.v = res[r]; best.i = (int)i; }
+      }
     }
     best = block_argmax(best, sm.red, sm.redi);
-    if (!grid_sync(A.bar, A.status)) return;    // everyone has read the old candidates
-    if (t == 0) { A.cand_v[(size_t)b * kMaxNs] = best.v; A.cand_i[(size_t)b * kMaxNs] = best.i; }
+    if (t == 0) { A.cand_v[(size_t)b * kMaxNs + wr] = best.v; A.cand_i[(size_t)b * kMaxNs + wr] = best.i; }
     if (!grid_sync(A.bar, A.status)) return;
   }
 
   // ---- feature-guided points: local top-m by (y_{i+1} - y_i)^2 ----
   const int m = A.n_s - kq;
+  if (kq > 0 && !grid_sync(A.bar, A.status)) return;   // all CTAs have read the last slot
   if (m > 0) {
     for (int e = t; e < 512; e += blockDim.x) { sm.cv[e] = -1.0; sm.ci[e] = 0x7fffffff; }
     __syncthreads();
@@ -254,21 +276,26 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
     row[kMaxR + 1] = A.drow[i];
   }
   __syncthreads();
-  // ---- G = A^T A with A = P^T Phi (k x k), FP64 ----
-  for (int e = t; e < k * k; e += blockDim.x) {
-    int r = e / k, c = e % k;
-    double s = 0.0;
-    for (int q = 0; q < ns; ++q)
-      s = fma(A.mesh[(size_t)(3 * q + 1) * kMeshStride + r], A.mesh[(size_t)(3 * q + 1) * kMeshStride + c], s);
-    sm.G[r * kMaxR + c] = s;
+  // ---- G = A^T A with A = P^T Phi (k x k), FP64: one warp per entry ----
+  {
+    const int wid = t >> 5, nw = blockDim.x >> 5;
+    for (int e = wid; e < k * k; e += nw) {
+      int r = e / k, c = e % k;
+      double s = 0.0;
+      for (int q = lane; q < ns; q += 32)
+        s = fma(A.mesh[(size_t)(3 * q + 1) * kMeshStride + r], A.mesh[(size_t)(3 * q + 1) * kMeshStride + c], s);
+      s = warp_sum(s);
+      if (lane == 0) sm.G[r * kMaxR + c] = s;
+    }
   }
   __syncthreads();
   // Cholesky (lower), one column at a time
   for (int j = 0; j < k; ++j) {
-    if (t == 0) {
-      double s = sm.G[j * kMaxR + j];
-      for (int l = 0; l < j; ++l) s -= sm.G[j * kMaxR + l] * sm.G[j * kMaxR + l];
-      sm.G[j * kMaxR + j] = sqrt(fmax(s, DBL_MIN));
+    if (t < 32) {
+      double s = 0.0;
+      for (int l = lane; l < j; l += 32) s += sm.G[j * kMaxR + l] * sm.G[j * kMaxR + l];
+      s = warp_sum(s);
+      if (lane == 0) sm.G[j * kMaxR + j] = sqrt(fmax(sm.G[j * kMaxR + j] - s, DBL_MIN));
     }
     __syncthreads();
     for (int i = j + 1 + t; i < k; i += blockDim.x) {
@@ -278,20 +305,25 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
     }
     __syncthreads();
   }
-  // M = G^{-1} A^T: for each sample column q solve L L^T x = A(q, :)^T
+  // M = G^{-1} A^T: each sample column q solves L L^T x = A(q, :)^T, with x in
+  // shared memory (X[q * k + i])
+  double* X = sm.X;
   for (int q = t; q < ns; q += blockDim.x) {
-    double x[kMaxR];
     for (int i = 0; i < k; ++i) {
       double s = A.mesh[(size_t)(3 * q + 1) * kMeshStride + i];
-      for (int l = 0; l < i; ++l) s -= sm.G[i * kMaxR + l] * x[l];
-      x[i] = s / sm.G[i * kMaxR + i];
+      for (int l = 0; l < i; ++l) s -= sm.G[i * kMaxR + l] * X[q * k + l];
+      X[q * k + i] = s / sm.G[i * kMaxR + i];
     }
     for (int i = k - 1; i >= 0; --i) {
-      double s = x[i];
-      for (int l = i + 1; l < k; ++l) s -= sm.G[l * kMaxR + i] * x[l];
-      x[i] = s / sm.G[i * kMaxR + i];
+      double s = X[q * k + i];
+      for (int l = i + 1; l < k; ++l) s -= sm.G[l * kMaxR + i] * X[q * k + l];
+      X[q * k + i] = s / sm.G[i * kMaxR + i];
     }
-    for (int i = 0; i < A.r; ++i) A.minv[(size_t)i * ns + q] = (i < k) ? x[i] : 0.0;
+  }
+  __syncthreads();
+  for (int e = t; e < A.r * ns; e += blockDim.x) {
+    int i = e / ns, q = e % ns;
+    A.minv[e] = (i < k) ? X[q * k + i] : 0.0;
   }
 }
 
@@ -308,6 +340,8 @@ static cudaError_t launch_sampling_t(const SampleArgs& A, int grid, cudaStream_t
 }
 
 cudaError_t launch_sampling(const SampleArgs& A, int km, int grid, cudaStream_t s) {
+  // each thread keeps the QDEIM norms of at most 4 rows in registers
+  if ((A.n + grid - 1) / grid > 4 * kBlock) return cudaErrorInvalidValue;
   switch (km) {
     case 9: return launch_sampling_t<9>(A, grid, s);
     case 17: return launch_sampling_t<17>(A, grid, s);
