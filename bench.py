@@ -52,13 +52,19 @@ WORKLOAD = "burgers-deim-N16384-r32-ns96-z5-lambda0.5-fp64"
 # 2 flop x 2.07 GHz (the nominal 1.25 TFLOP/s of the part).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 
-# DRAM traffic per launch of the dominant kernel from one ncu capture, valid
-# only while the kernel source is unchanged (sha1 of the file).
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch from
+# one ncu capture of each kernel on this workload (profiles/
+# kernels_burgers_deim_n16384.md); reported only while the kernel's source file
+# is unchanged (sha1).
 TRAFFIC = {
-    "isvd_update": {"bytes": None, "src": "paper_2605_28684_gb300/csrc/isvd.cu", "sha1": None},
-    "coarse_fom": {"bytes": None, "src": "paper_2605_28684_gb300/csrc/fom.cu", "sha1": None},
-    "reduced_steps": {"bytes": None, "src": "paper_2605_28684_gb300/csrc/reduced.cu", "sha1": None},
-    "sampling": {"bytes": None, "src": "paper_2605_28684_gb300/csrc/sampling.cu", "sha1": None},
+    "isvd_update": {"bytes": 1719040, "src": "paper_2605_28684_gb300/csrc/isvd.cu",
+                    "sha1": "256ac5fb22147b5cd1dee92d65d9bb886a0da3c2"},
+    "coarse_fom": {"bytes": 162304, "src": "paper_2605_28684_gb300/csrc/fom.cu",
+                   "sha1": "41fe1123cf55dbaaea5c55bb118f0ef5e1516c8a"},
+    "reduced_steps": {"bytes": 106752, "src": "paper_2605_28684_gb300/csrc/reduced.cu",
+                      "sha1": "19040aafdb6138cd9e10904b67f14c28959d3ac8"},
+    "sampling": {"bytes": 1356032, "src": "paper_2605_28684_gb300/csrc/sampling.cu",
+                 "sha1": "141560cfbfee019dec07f138e1e9ac08cdd08cd0"},
 }
 
 
