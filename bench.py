@@ -53,9 +53,8 @@ WORKLOAD = "burgers-deim-N16384-r32-ns96-z5-lambda0.5-fp64"
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch from
-# one ncu capture of each kernel on this workload (profiles/
-# kernels_burgers_deim_n16384.md); reported only while the kernel's source file
-# is unchanged (sha1).
+# one ncu capture of each kernel on this workload (summarised under profiles/);
+# reported only while the kernel's source file is unchanged (sha1).
 TRAFFIC = {
     "isvd_update": {"bytes": 1719040, "src": "paper_2605_28684_gb300/csrc/isvd.cu",
                     "sha1": "256ac5fb22147b5cd1dee92d65d9bb886a0da3c2"},
@@ -269,39 +268,64 @@ def main():
     cfg = workload_config()
     q0 = synth.initial_state(cfg)
     stream = torch.cuda.current_stream()
-    rom = g.AdaptiveROM(cfg, q0, stream=stream.cuda_stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    for _ in range(args.warmup):
-        rom.step(cfg.z)
+    def timed_cycles(c, sampler=None):
+        """W warm-up cycles, then K timed cycles (CUDA events on the ROM's
+        stream around each cycle, L2 flushed before each); returns the summed
+        device time, the per-phase profile and the final rank/Newton counts."""
+        rom = g.AdaptiveROM(c, q0, stream=stream.cuda_stream)
+        for _ in range(args.warmup):
+            rom.step(c.z)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if sampler is not None:
+            sampler.start()
+        rom.profile(True)
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            starts[i].record(stream)
+            rom.step(c.z)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        prof = rom.profile_read()
+        rom.profile(False)
+        if dist is not None:
+            dist.barrier()
+        clk = sampler.stop() if sampler is not None else None
+        total = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
+        info = rom.info()
+        rom.close()
+        return total, prof, info, clk
 
     sampler = ClockSampler(local)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    rom.profile(True)
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        starts[i].record(stream)
-        rom.step(cfg.z)
-        ends[i].record(stream)
-    torch.cuda.synchronize()
-    prof = rom.profile_read()
-    rom.profile(False)
-    if dist is not None:
-        dist.barrier()
-    clocks = sampler.stop()
-    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    total_ms, prof, info, clocks = timed_cycles(cfg, sampler)
     t_max = total_ms
     if dist is not None:
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_max = float(t.item())
-    info = rom.info()
     value = world * args.steps * cfg.z / (t_max / 1e3)
+
+    # the mixed-precision form of the same workload (FP32 basis and projections)
+    mcfg = workload_config()
+    mcfg.precision = 1
+    m_ms, m_prof, m_info, _ = timed_cycles(mcfg)
+    if dist is not None:
+        t = torch.tensor([m_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        m_ms = float(t.item())
+    forms = {
+        "fp64": {"value": value, "ms_per_step": t_max / args.steps, "rank_k": info["rank"]},
+        "mixed_fp32": {"value": world * args.steps * mcfg.z / (m_ms / 1e3),
+                       "ms_per_step": m_ms / args.steps, "rank_k": m_info["rank"],
+                       "rank_tol": 1e-5,
+                       "phases_avg_us": {p: m_prof[p]["ms"] * 1e3 / max(1, m_prof[p]["launches"])
+                                         for p in m_prof}},
+    }
 
     # roofline of the dominant kernel (largest device time in the timed region)
     dom = max(prof, key=lambda p: prof[p]["ms"])
@@ -352,13 +376,12 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
-    rom.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config_json(cfg), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": gpu_launches, "clocks": clocks, "phases": phases,
+                "gpu_launches": gpu_launches, "clocks": clocks, "phases": phases, "forms": forms,
                 "rank_k": info["rank"], "newton_iters": {"rom": info["rom_newton_iters"],
                                                          "fom": info["fom_newton_iters"]}}
         print(json.dumps(line), flush=True)

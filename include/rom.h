@@ -58,8 +58,10 @@ typedef enum { ROM_FP64 = 0, ROM_MIXED_FP32 = 1 } rom_precision;
  *  problem     ROM_BURGERS: u_t + (u^2/2)_x = nu u_xx, periodic, Godunov flux,
  *              centred diffusion. ROM_EULER: 1D Euler, ideal gas (gamma),
  *              Rusanov flux, zero-gradient ghost cells (App. B).
- *  precision   ROM_FP64, or ROM_MIXED_FP32 (FP32 basis storage, FP32
- *              projections with FP32 accumulation; FP64 core SVD and residuals).
+ *  precision   ROM_FP64, or ROM_MIXED_FP32 (FP32 basis storage; FP32 lift,
+ *              projections and rotation with FP32 accumulation; FP64 core SVD,
+ *              FP64 re-orthonormalisation of the basis after every update, FP64
+ *              full-order model).
  *  n_cells     cells of the uniform grid on [0, 1]; n_var = 1 (Burgers) or 3.
  *  r           maximum reduced dimension (1 <= r <= 64, r <= w_init, r < N).
  *  n_s         0: plain Galerkin. > 0: DEIM-Galerkin with n_s sampled cells
@@ -73,7 +75,10 @@ typedef enum { ROM_FP64 = 0, ROM_MIXED_FP32 = 1 } rom_precision;
  *  newton_max, newton_tol  Newton stops once max|delta| <= tol (1 + max|x|);
  *              newton_max iterations without that -> ROM_ENOCONV.
  *  rank_tol    singular directions with sigma_j <= rank_tol * sigma_1 are
- *              numerically null and kept as zero columns (<= 0 selects 1e-10).
+ *              numerically null and kept as zero columns; a new iSVD direction
+ *              enters only if ||q|| > rank_tol * max(||y||, sigma_1). <= 0 selects
+ *              the precision's default: 1e-10 (FP64), 1e-5 (mixed; FP32
+ *              projections cannot resolve smaller residuals).
  */
 typedef struct {
     int32_t problem;

@@ -68,7 +68,6 @@ rom_status validate(const rom_config* c) {
   if (c->problem == ROM_BURGERS && c->n_var != 1) return ROM_EINVAL;
   if (c->problem == ROM_EULER && c->n_var != 3) return ROM_EINVAL;
   if (c->problem == ROM_EULER) return ROM_EINVAL;            // not built yet
-  if (c->precision != ROM_FP64) return ROM_EINVAL;           // not built yet
   if (c->n_cells < 8 || c->n_cells > (int64_t)kMaxChunks * kMaxChunkRows) return ROM_EINVAL;
   int64_t N = c->n_cells * c->n_var;
   if (c->r < 1 || c->r > kMaxR || c->r >= N || c->r > c->w_init) return ROM_EINVAL;
@@ -109,6 +108,9 @@ rom_status finish(rom_ctx* ctx) {
 }
 
 int km_of(const rom_ctx* ctx) { return km_bucket(ctx->cfg.r + 1); }
+
+bool mixed(const rom_ctx* ctx) { return ctx->cfg.precision == ROM_MIXED_FP32; }
+float* basis32(const rom_ctx* ctx) { return mixed(ctx) ? ctx->d.phi32 : nullptr; }
 
 // Accumulate the recorded event pairs into the per-phase totals.
 cudaError_t prof_flush(rom_ctx* ctx) {
@@ -169,7 +171,7 @@ cudaError_t fom_step(rom_ctx* ctx, const double* q_prev, double* q, double h) {
 }
 
 EventArgs event_args(rom_ctx* ctx, const double* y, int preprocess, double lambda, double rank_tol,
-                     int r_cap, int transfer) {
+                     int r_cap, int transfer, bool online = true) {
   EventArgs A;
   A.n = ctx->N;
   A.ld = ctx->N;
@@ -178,6 +180,8 @@ EventArgs event_args(rom_ctx* ctx, const double* y, int preprocess, double lambd
   A.lambda = lambda;
   A.rank_tol = rank_tol;
   A.phi = ctx->d.phi;
+  A.phi32 = online ? basis32(ctx) : nullptr;   // the offline POD runs in FP64
+  A.gram = ctx->d.gram;
   A.sigma = ctx->d.sigma;
   A.a = transfer ? ctx->d.a : nullptr;
   A.transfer = transfer;
@@ -203,6 +207,7 @@ SampleArgs sample_args(rom_ctx* ctx) {
   S.n_s = ctx->cfg.n_s;
   S.rank = ctx->d.rank;
   S.phi = ctx->d.phi;
+  S.phi32 = basis32(ctx);
   S.y = ctx->d.y_corr;
   S.q_ref = ctx->d.q_ref;
   S.drow = ctx->d.drow;
@@ -226,6 +231,7 @@ StepArgs step_args(rom_ctx* ctx, int nsteps) {
   A.r = ctx->cfg.r;
   A.rank = ctx->d.rank;
   A.phi = ctx->d.phi;
+  A.phi32 = basis32(ctx);
   A.q_ref = ctx->d.q_ref;
   A.drow = ctx->d.drow;
   A.dinv = ctx->d.dinv;
@@ -318,6 +324,12 @@ __global__ void scale_final_kernel(const double* partial, int nb, int64_t n_cell
   }
 }
 
+__global__ void to_fp32_kernel(const double* in, float* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
 __global__ void drow_kernel(const double* dvals, int64_t n_cells, int64_t N, double* drow,
                             double* dinv) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
@@ -330,7 +342,7 @@ __global__ void drow_kernel(const double* dvals, int64_t n_cells, int64_t N, dou
 void free_state(rom_ctx* ctx) {
   DevState& d = ctx->d;
   void* ptrs[] = {d.q_ref, d.y_corr, d.y_tmp, d.yhat, d.qres, d.lifted, d.dvals, d.drow, d.dinv, d.phi,
-                  d.phi32, d.sigma, d.a, d.a_prev, d.rank, d.core, d.ubar, d.partials,
+                  d.phi32, d.gram, d.sigma, d.a, d.a_prev, d.rank, d.core, d.ubar, d.partials,
                   d.jpartials, d.jac, d.samples, d.chosen, d.resid_norm, d.qdeim_q, d.cand_v,
                   d.cand_i, d.mesh, d.minv, d.bar, d.status, d.iters_rom, d.iters_fom, d.maxbuf,
                   d.fom_chunk, ctx->q_train};
@@ -382,7 +394,10 @@ rom_status rom_init(const rom_config* cfg_in, const double* q0_host, void* strea
   ctx->prof_ev_made = 0;
   for (int p = 0; p < kPhases; ++p) { ctx->prof_ms[p] = 0.0; ctx->prof_cnt[p] = 0; }
   ctx->cfg = *cfg_in;
-  if (!(ctx->cfg.rank_tol > 0.0)) ctx->cfg.rank_tol = 1e-10;
+  // numerical-rank tolerance: what the working precision of the projections
+  // can resolve (FP64: 1e-10; FP32 projections of the mixed form: 1e-5)
+  if (!(ctx->cfg.rank_tol > 0.0))
+    ctx->cfg.rank_tol = (ctx->cfg.precision == ROM_MIXED_FP32) ? 1e-5 : 1e-10;
   ctx->stream = (cudaStream_t)stream;
   ctx->N = ctx->cfg.n_cells * ctx->cfg.n_var;
   ctx->step = 0;
@@ -410,6 +425,10 @@ rom_status rom_init(const rom_config* cfg_in, const double* q0_host, void* strea
   ALLOC(d.minv, (size_t)kMaxR * ns); ALLOC(d.bar, 1); ALLOC(d.status, 1); ALLOC(d.iters_rom, 1);
   ALLOC(d.iters_fom, 1); ALLOC(d.maxbuf, 4); ALLOC(d.fom_chunk, fom_chunk_floats());
   ALLOC(ctx->q_train, (size_t)N * w);
+  if (ctx->cfg.precision == ROM_MIXED_FP32) {
+    ALLOC(d.phi32, (size_t)N * r);
+    ALLOC(d.gram, (size_t)G * kMaxR * kMaxR);
+  }
 #undef ALLOC
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -450,7 +469,7 @@ rom_status rom_init(const rom_config* cfg_in, const double* q0_host, void* strea
   {
     const int km = km_bucket(r_grow + 1);
     for (int j = 0; j < w; ++j) {
-      EventArgs A = event_args(ctx, ctx->q_train + (size_t)j * N, 1, 1.0, kGrowRankTol, r_grow, 0);
+      EventArgs A = event_args(ctx, ctx->q_train + (size_t)j * N, 1, 1.0, kGrowRankTol, r_grow, 0, false);
       RCK(launch_event(A, km, G, s));
     }
     st = finish(ctx);
@@ -465,13 +484,17 @@ rom_status rom_init(const rom_config* cfg_in, const double* q0_host, void* strea
       RCK(cudaMemsetAsync(d.sigma + k, 0, sizeof(double) * (kMaxR + 1 - k), s));
     }
     RCK(cudaMemcpyAsync(d.rank, &k, sizeof(int), cudaMemcpyHostToDevice, s));
+    if (mixed(ctx)) {   // the online basis of the mixed form is the FP32 rounding of the POD
+      to_fp32_kernel<<<512, 256, 0, s>>>(d.phi, d.phi32, (int64_t)N * r);
+      RCK(cudaGetLastError());
+    }
     RCK(cudaStreamSynchronize(s));
   }
   // initial reduced state and first coarse correction state
   {
     const double* qlast = ctx->q_train + (size_t)(w - 1) * N;
     ProjectArgs P;
-    P.n = N; P.ld = N; P.r = r; P.rank = d.rank; P.phi = d.phi; P.v = qlast; P.q_ref = d.q_ref;
+    P.n = N; P.ld = N; P.r = r; P.rank = d.rank; P.phi = d.phi; P.phi32 = basis32(ctx); P.v = qlast; P.q_ref = d.q_ref;
     P.drow = d.drow; P.a = d.a; P.partials = d.partials; P.bar = d.bar; P.status = d.status;
     RCK(launch_project(P, km_of(ctx), G, s));
     RCK(fom_step(ctx, qlast, d.y_corr, ctx->cfg.z * ctx->cfg.dt));
@@ -528,7 +551,7 @@ rom_status rom_state(rom_ctx* ctx, double* q_tilde, double* a, double* sigma, do
   cudaStream_t s = ctx->stream;
   if (q_tilde) {
     LiftArgs L;
-    L.n = N; L.ld = N; L.rank = ctx->d.rank; L.phi = ctx->d.phi; L.q_ref = ctx->d.q_ref;
+    L.n = N; L.ld = N; L.rank = ctx->d.rank; L.phi = ctx->d.phi; L.phi32 = basis32(ctx); L.q_ref = ctx->d.q_ref;
     L.drow = ctx->d.drow; L.dinv = ctx->d.dinv; L.a = ctx->d.a; L.out = ctx->d.lifted;
     RCK(launch_lift(L, km_of(ctx), s));
     RCK(cudaMemcpyAsync(q_tilde, ctx->d.lifted, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
@@ -536,10 +559,18 @@ rom_status rom_state(rom_ctx* ctx, double* q_tilde, double* a, double* sigma, do
   std::vector<double> ha(r), hphi;
   RCK(cudaMemcpyAsync(ha.data(), ctx->d.a, sizeof(double) * r, cudaMemcpyDeviceToHost, s));
   if (sigma) RCK(cudaMemcpyAsync(sigma, ctx->d.sigma, sizeof(double) * r, cudaMemcpyDeviceToHost, s));
-  if (phi) RCK(cudaMemcpyAsync(phi, ctx->d.phi, sizeof(double) * N * r, cudaMemcpyDeviceToHost, s));
+  std::vector<float> phi32h;
+  if (phi && mixed(ctx)) {
+    phi32h.resize((size_t)N * r);
+    RCK(cudaMemcpyAsync(phi32h.data(), ctx->d.phi32, sizeof(float) * N * r, cudaMemcpyDeviceToHost, s));
+  } else if (phi) {
+    RCK(cudaMemcpyAsync(phi, ctx->d.phi, sizeof(double) * N * r, cudaMemcpyDeviceToHost, s));
+  }
   if (y_corr) RCK(cudaMemcpyAsync(y_corr, ctx->d.y_corr, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
   rom_status st = finish(ctx);
   if (st != ROM_OK) return st;
+  if (phi && mixed(ctx))
+    for (size_t e = 0; e < phi32h.size(); ++e) phi[e] = (double)phi32h[e];
   // sign convention of the exported basis: largest-magnitude entry positive
   if (phi) {
     for (int j = 0; j < r; ++j) {
@@ -569,7 +600,14 @@ rom_status rom_load_state(rom_ctx* ctx, const double* phi, const double* sigma, 
   for (int j = 0; j < r; ++j)
     if (sigma[j] > 0.0) k = j + 1;
   cudaStream_t s = ctx->stream;
-  RCK(cudaMemcpyAsync(ctx->d.phi, phi, sizeof(double) * N * r, cudaMemcpyHostToDevice, s));
+  std::vector<float> phi32h;
+  if (mixed(ctx)) {
+    phi32h.resize((size_t)N * r);
+    for (size_t e = 0; e < phi32h.size(); ++e) phi32h[e] = (float)phi[e];
+    RCK(cudaMemcpyAsync(ctx->d.phi32, phi32h.data(), sizeof(float) * N * r, cudaMemcpyHostToDevice, s));
+  } else {
+    RCK(cudaMemcpyAsync(ctx->d.phi, phi, sizeof(double) * N * r, cudaMemcpyHostToDevice, s));
+  }
   RCK(cudaMemsetAsync(ctx->d.sigma, 0, sizeof(double) * (kMaxR + 1), s));
   RCK(cudaMemcpyAsync(ctx->d.sigma, sigma, sizeof(double) * r, cudaMemcpyHostToDevice, s));
   RCK(cudaMemsetAsync(ctx->d.a, 0, sizeof(double) * (kMaxR + 1), s));
@@ -577,7 +615,7 @@ rom_status rom_load_state(rom_ctx* ctx, const double* phi, const double* sigma, 
   RCK(cudaMemcpyAsync(ctx->d.y_corr, y_corr, sizeof(double) * N, cudaMemcpyHostToDevice, s));
   RCK(cudaMemcpyAsync(ctx->d.rank, &k, sizeof(int), cudaMemcpyHostToDevice, s));
   if (ctx->cfg.n_s > 0) RCK(launch_sampling(sample_args(ctx), km_of(ctx), ctx->grid, s));
-  rom_status st = finish(ctx);
+  rom_status st = finish(ctx);   // (also waits for the staged host copies above)
   if (st == ROM_OK) ctx->step = step;
   return st;
 }
@@ -719,7 +757,8 @@ rom_status rom_isvd_update_dev(int64_t n, int32_t r, double lambda, double rank_
   }
   EventArgs A;
   A.n = n; A.ld = n; A.r = r; A.rank = ints + 1; A.lambda = lambda; A.rank_tol = rank_tol;
-  A.phi = phi_dev; A.sigma = sigma_dev; A.a = nullptr; A.transfer = 0; A.y = y_dev;
+  A.phi = phi_dev; A.phi32 = nullptr; A.gram = nullptr; A.sigma = sigma_dev; A.a = nullptr;
+  A.transfer = 0; A.y = y_dev;
   A.q_ref = nullptr; A.drow = nullptr; A.preprocess = 0; A.yhat = nullptr; A.qres = qres;
   A.partials = partials; A.core = core; A.ubar = ubar; A.bar = bar; A.status = ints;
   rom_status result = ROM_OK;

@@ -225,6 +225,11 @@ struct EventSmem {
   double a_old[kMaxR];
   int order[kMaxCore];              // position (descending value) of each eigenpair
   double val[kMaxCore];
+  // mixed precision: FP32 copies of p1, p2 and U, the FP64 Gram matrix
+  float p1f[kMaxCore];
+  float p2f[kMaxCore];
+  float Uf[kMaxCore * kMaxCore];
+  double Gm[kMaxR * kMaxR];
 };
 
 }  // namespace
@@ -267,10 +272,17 @@ __device__ __forceinline__ void grid_reduce_vec(const double* partials, int G, i
   grid_reduce_cols(partials, G, stride, k, out);
 }
 
-template <int KM>
+// TPhi is the storage type of the basis: double (FP64 form) or float (mixed
+// form: FP32 projections with FP32 accumulation, FP64 core SVD, and an FP64
+// CholQR re-orthonormalisation of the rotated basis).
+template <int KM, typename TPhi>
 __global__ void __launch_bounds__(kBlock) isvd_event_kernel(EventArgs A) {
+  using Acc = TPhi;
+  constexpr bool kMixed = std::is_same<TPhi, float>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   EventSmem& sm = *reinterpret_cast<EventSmem*>(smem_raw);
+  const TPhi* phi = basis<TPhi>(A);
+  TPhi* phiw = const_cast<TPhi*>(phi);
   const int G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
   const int64_t N = A.n, ld = A.ld;
   const int64_t beg = (int64_t)b * N / G, end = (int64_t)(b + 1) * N / G;
@@ -285,9 +297,9 @@ __global__ void __launch_bounds__(kBlock) isvd_event_kernel(EventArgs A) {
   // ---- P1: yhat and p1 = Phi^T yhat, ||yhat||^2 ----
   with_rank_bucket<KM>(n, [&](auto kb) {
     constexpr int KB = decltype(kb)::value;
-    double acc[KB];
+    Acc acc[KB];
 #pragma unroll
-    for (int j = 0; j < KB; ++j) acc[j] = 0.0;
+    for (int j = 0; j < KB; ++j) acc[j] = Acc(0);
     double yy = 0.0;
     for (int64_t i = beg + t; i < end; i += blockDim.x) {
       double yh;
@@ -298,11 +310,19 @@ __global__ void __launch_bounds__(kBlock) isvd_event_kernel(EventArgs A) {
         yh = A.y[i];
       }
       yy = fma(yh, yh, yy);
+      const Acc ya = (Acc)yh;
 #pragma unroll
       for (int j = 0; j < KB; ++j)
-        if (j < k) acc[j] = fma(A.phi[j * ld + i], yh, acc[j]);
+        if (j < k) acc[j] = fma((Acc)phi[j * ld + i], ya, acc[j]);
     }
-    block_reduce_vec<KB>(acc, k, sm.red, sm.p1);
+    if constexpr (kMixed) {
+      double accd[KB];
+#pragma unroll
+      for (int j = 0; j < KB; ++j) accd[j] = (double)acc[j];
+      block_reduce_vec<KB>(accd, k, sm.red, sm.p1);
+    } else {
+      block_reduce_vec<KB>(acc, k, sm.red, sm.p1);
+    }
     double yys = block_sum(yy, sm.red);
     for (int j = t; j < k; j += blockDim.x) part0[(size_t)b * stride + j] = sm.p1[j];
     if (t == 0) part0[(size_t)b * stride + KM] = yys;
@@ -310,42 +330,54 @@ __global__ void __launch_bounds__(kBlock) isvd_event_kernel(EventArgs A) {
   if (!grid_sync(A.bar, A.status)) return;
   grid_reduce_vec(part0, G, stride, k, sm.p1);
   grid_reduce_cols(part0 + KM, G, stride, 1, &sm.sc[0]);     // ||yhat||^2
+  for (int j = t; j < k; j += blockDim.x) sm.p1f[j] = (float)sm.p1[j];
+  __syncthreads();
 
   const double* yv = A.preprocess ? A.yhat : A.y;
   // ---- P2: q1 = yhat - Phi p1 ; p2 = Phi^T q1 ----
   with_rank_bucket<KM>(n, [&](auto kb) {
     constexpr int KB = decltype(kb)::value;
-    double acc[KB];
+    Acc acc[KB];
 #pragma unroll
-    for (int j = 0; j < KB; ++j) acc[j] = 0.0;
+    for (int j = 0; j < KB; ++j) acc[j] = Acc(0);
     for (int64_t i = beg + t; i < end; i += blockDim.x) {
-      double x[KB];
+      Acc x[KB];
 #pragma unroll
-      for (int j = 0; j < KB; ++j) x[j] = (j < k) ? A.phi[j * ld + i] : 0.0;
-      double v = yv[i];
+      for (int j = 0; j < KB; ++j) x[j] = (j < k) ? (Acc)phi[j * ld + i] : Acc(0);
+      Acc v = (Acc)yv[i];
 #pragma unroll
       for (int j = 0; j < KB; ++j)
-        if (j < k) v = fma(-x[j], sm.p1[j], v);
-      A.qres[i] = v;
+        if (j < k) v = fma(-x[j], kMixed ? (Acc)sm.p1f[j] : (Acc)sm.p1[j], v);
+      A.qres[i] = (double)v;
 #pragma unroll
       for (int j = 0; j < KB; ++j)
         if (j < k) acc[j] = fma(x[j], v, acc[j]);
     }
-    block_reduce_vec<KB>(acc, k, sm.red, sm.p2);
+    if constexpr (kMixed) {
+      double accd[KB];
+#pragma unroll
+      for (int j = 0; j < KB; ++j) accd[j] = (double)acc[j];
+      block_reduce_vec<KB>(accd, k, sm.red, sm.p2);
+    } else {
+      block_reduce_vec<KB>(acc, k, sm.red, sm.p2);
+    }
     for (int j = t; j < k; j += blockDim.x) part1[(size_t)b * stride + j] = sm.p2[j];
   });
   if (!grid_sync(A.bar, A.status)) return;
   grid_reduce_vec(part1, G, stride, k, sm.p2);
+  for (int j = t; j < k; j += blockDim.x) sm.p2f[j] = (float)sm.p2[j];
+  __syncthreads();
   // ---- P3: q = q1 - Phi p2, ||q||^2 ----
   {
-    double qq = 0.0;
+    Acc qq = Acc(0);
     for (int64_t i = beg + t; i < end; i += blockDim.x) {
-      double v = A.qres[i];
-      for (int j = 0; j < k; ++j) v = fma(-A.phi[j * ld + i], sm.p2[j], v);
-      A.qres[i] = v;
+      Acc v = (Acc)A.qres[i];
+      for (int j = 0; j < k; ++j)
+        v = fma(-(Acc)phi[j * ld + i], kMixed ? (Acc)sm.p2f[j] : (Acc)sm.p2[j], v);
+      A.qres[i] = (double)v;
       qq = fma(v, v, qq);
     }
-    double qs = block_sum(qq, sm.red);
+    double qs = block_sum((double)qq, sm.red);
     if (t == 0) part2[(size_t)b * stride] = qs;
   }
   if (!grid_sync(A.bar, A.status)) return;
@@ -504,7 +536,9 @@ __global__ void __launch_bounds__(kBlock) isvd_event_kernel(EventArgs A) {
   }
   for (int e = t; e < n * knew; e += blockDim.x) {
     int col = e / n, row = e % n;
-    sm.U[row * kMaxCore + col] = __ldcg(&A.ubar[(size_t)col * n + row]);
+    double u = __ldcg(&A.ubar[(size_t)col * n + row]);
+    sm.U[row * kMaxCore + col] = u;
+    sm.Uf[row * kMaxCore + col] = (float)u;
   }
   if (b == 0)
     for (int j = t; j < k; j += blockDim.x) sm.a_old[j] = A.a ? A.a[j] : 0.0;
@@ -512,25 +546,77 @@ __global__ void __launch_bounds__(kBlock) isvd_event_kernel(EventArgs A) {
   const double qinv = sm.sc[2];
   with_rank_bucket<KM>(n, [&](auto kb) {
     constexpr int KB = decltype(kb)::value;
+    const Acc* Us = kMixed ? (const Acc*)(const void*)sm.Uf : (const Acc*)(const void*)sm.U;
     for (int64_t i = beg + t; i < end; i += blockDim.x) {
-      double x[KB];
+      Acc x[KB];
 #pragma unroll
-      for (int j = 0; j < KB; ++j) x[j] = (j < k) ? A.phi[j * ld + i] : 0.0;
-      double qh = A.qres[i] * qinv;
+      for (int j = 0; j < KB; ++j) x[j] = (j < k) ? (Acc)phi[j * ld + i] : Acc(0);
+      Acc qh = (Acc)(A.qres[i] * qinv);
 #pragma unroll
       for (int c = 0; c < KB; ++c) {
         if (c < knew) {
-          double v = qh * sm.U[k * kMaxCore + c];
+          Acc v = qh * Us[k * kMaxCore + c];
 #pragma unroll
           for (int j = 0; j < KB; ++j)
-            if (j < k) v = fma(x[j], sm.U[j * kMaxCore + c], v);
-          A.phi[c * ld + i] = v;
+            if (j < k) v = fma(x[j], Us[j * kMaxCore + c], v);
+          phiw[c * ld + i] = (TPhi)v;
         } else if (c < k) {
-          A.phi[c * ld + i] = 0.0;
+          phiw[c * ld + i] = TPhi(0);
         }
       }
     }
   });
+  if constexpr (kMixed) {
+    // ---- FP64 re-orthonormalisation of the FP32 basis (CholQR): G = Phi^T Phi
+    // accumulated in FP64 (products of FP32 numbers are exact in FP64),
+    // G = R^T R, Phi <- Phi R^-1, and a <- R a so that q~ is unchanged ----
+    if (!grid_sync(A.bar, A.status)) return;
+    const int kk = knew;
+    for (int e = t; e < kk * kk; e += blockDim.x) {
+      int j = e / kk, l = e % kk;
+      double s = 0.0;
+      if (l >= j)
+        for (int64_t i = beg; i < end; ++i) s = fma((double)phi[j * ld + i], (double)phi[l * ld + i], s);
+      A.gram[(size_t)b * kMaxR * kMaxR + j * kMaxR + l] = s;
+    }
+    if (!grid_sync(A.bar, A.status)) return;
+    {
+      const int lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+      for (int e = wid; e < kk * kk; e += nw) {
+        int j = e / kk, l = e % kk;
+        double s = 0.0;
+        if (l >= j)
+          for (int bb = lane; bb < G; bb += 32) s += __ldcg(&A.gram[(size_t)bb * kMaxR * kMaxR + j * kMaxR + l]);
+        s = warp_sum(s);
+        if (lane == 0) sm.Gm[j * kMaxR + l] = s;
+      }
+    }
+    __syncthreads();
+    if (t == 0) {   // upper Cholesky factor R (in place, row-major, upper triangle)
+      for (int j = 0; j < kk; ++j) {
+        double d = sm.Gm[j * kMaxR + j];
+        for (int l = 0; l < j; ++l) d -= sm.Gm[l * kMaxR + j] * sm.Gm[l * kMaxR + j];
+        d = sqrt(fmax(d, DBL_MIN));
+        sm.Gm[j * kMaxR + j] = d;
+        const double inv = 1.0 / d;
+        for (int c = j + 1; c < kk; ++c) {
+          double v = sm.Gm[j * kMaxR + c];
+          for (int l = 0; l < j; ++l) v -= sm.Gm[l * kMaxR + j] * sm.Gm[l * kMaxR + c];
+          sm.Gm[j * kMaxR + c] = v * inv;
+        }
+      }
+    }
+    __syncthreads();
+    for (int64_t i = beg + t; i < end; i += blockDim.x) {   // y R = x, row by row
+      double y[kMaxR];
+      for (int j = 0; j < kk; ++j) {
+        double v = (double)phi[j * ld + i];
+        for (int l = 0; l < j; ++l) v -= y[l] * sm.Gm[l * kMaxR + j];
+        y[j] = v / sm.Gm[j * kMaxR + j];
+      }
+      for (int j = 0; j < kk; ++j) phiw[j * ld + i] = (TPhi)y[j];
+    }
+  }
   if (b == 0) {
     // sigma, state transfer and the new rank (other CTAs read none of these)
     if (t < A.r) {
@@ -539,8 +625,20 @@ __global__ void __launch_bounds__(kBlock) isvd_event_kernel(EventArgs A) {
         double v = 0.0;
         if (t < knew)
           for (int j = 0; j < k; ++j) v = fma(sm.U[j * kMaxCore + t], sm.a_old[j], v);
-        A.a[t] = v;
+        sm.a_old[kMaxR - 1 - t] = v;   // staged (a_old is no longer needed)
       }
+    }
+    __syncthreads();
+    if (t < A.r && A.a && A.transfer) {
+      double v = sm.a_old[kMaxR - 1 - t];
+      if constexpr (kMixed) {      // a <- R a
+        if (t < knew) {
+          double w = 0.0;
+          for (int c = t; c < knew; ++c) w = fma(sm.Gm[t * kMaxR + c], sm.a_old[kMaxR - 1 - c], w);
+          v = w;
+        }
+      }
+      A.a[t] = v;
     }
     __syncthreads();
     if (t == 0) *A.rank = knew;
@@ -551,8 +649,9 @@ __global__ void __launch_bounds__(kBlock) isvd_event_kernel(EventArgs A) {
 // Projection a = Phi^T D (v - q_ref) (offline initial state).
 // --------------------------------------------------------------------------
 
-template <int KM>
+template <int KM, typename TPhi>
 __global__ void __launch_bounds__(kBlock) project_kernel(ProjectArgs A) {
+  const TPhi* phi = basis<TPhi>(A);
   __shared__ double red[32 * KM];
   __shared__ double out[KM];
   const int G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
@@ -567,7 +666,7 @@ __global__ void __launch_bounds__(kBlock) project_kernel(ProjectArgs A) {
     double v = A.drow[i] * (A.v[i] - A.q_ref[i]);
 #pragma unroll
     for (int j = 0; j < KM; ++j)
-      if (j < k) acc[j] = fma(A.phi[j * ld + i], v, acc[j]);
+      if (j < k) acc[j] = fma((double)phi[j * ld + i], v, acc[j]);
   }
   block_reduce_vec<KM>(acc, k, red, out);
   for (int j = t; j < k; j += blockDim.x) A.partials[(size_t)b * stride + j] = out[j];
@@ -585,16 +684,21 @@ __global__ void __launch_bounds__(kBlock) project_kernel(ProjectArgs A) {
 size_t event_smem_bytes() { return sizeof(EventSmem); }
 size_t core_ws_doubles() { return kWsSize; }
 
-template <int KM>
-static cudaError_t launch_event_t(const EventArgs& A, int grid, cudaStream_t s) {
+template <int KM, typename TPhi>
+static cudaError_t launch_event_tt(const EventArgs& A, int grid, cudaStream_t s) {
   size_t smem = sizeof(EventSmem);
-  cudaError_t e = cudaFuncSetAttribute(isvd_event_kernel<KM>,
+  cudaError_t e = cudaFuncSetAttribute(isvd_event_kernel<KM, TPhi>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   EventArgs a = A;
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel((const void*)isvd_event_kernel<KM>, dim3(grid), dim3(kBlock),
-                                     args, smem, s);
+  return cudaLaunchCooperativeKernel((const void*)isvd_event_kernel<KM, TPhi>, dim3(grid),
+                                     dim3(kBlock), args, smem, s);
+}
+
+template <int KM>
+static cudaError_t launch_event_t(const EventArgs& A, int grid, cudaStream_t s) {
+  return A.phi32 ? launch_event_tt<KM, float>(A, grid, s) : launch_event_tt<KM, double>(A, grid, s);
 }
 
 cudaError_t launch_event(const EventArgs& A, int km, int grid, cudaStream_t s) {
@@ -610,8 +714,11 @@ template <int KM>
 static cudaError_t launch_project_t(const ProjectArgs& A, int grid, cudaStream_t s) {
   ProjectArgs a = A;
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel((const void*)project_kernel<KM>, dim3(grid), dim3(kBlock),
-                                     args, 0, s);
+  if (A.phi32)
+    return cudaLaunchCooperativeKernel((const void*)project_kernel<KM, float>, dim3(grid),
+                                       dim3(kBlock), args, 0, s);
+  return cudaLaunchCooperativeKernel((const void*)project_kernel<KM, double>, dim3(grid),
+                                     dim3(kBlock), args, 0, s);
 }
 
 cudaError_t launch_project(const ProjectArgs& A, int km, int grid, cudaStream_t s) {

@@ -12,6 +12,7 @@
 // max|delta| <= tol (1 + max|a|).
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 
 #include "rom_internal.cuh"
 #include "rom_kernels.cuh"
@@ -118,9 +119,11 @@ __device__ void lu_solve(const float* J, const int* piv, float* x, int k) {
 // Plain Galerkin: cooperative kernel over all rows.
 // ----------------------------------------------------------------------------
 
-template <int KM>
+template <int KM, typename TPhi>
 __global__ void __launch_bounds__(kBlock) galerkin_steps_kernel(StepArgs A) {
+  using Acc = TPhi;   // FP32 lift and projections with FP32 accumulation in the mixed form
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const TPhi* phi = basis<TPhi>(A);
   const int G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
   const int64_t N = A.n, ld = A.ld;
   const int64_t beg = (int64_t)b * N / G, end = (int64_t)(b + 1) * N / G;
@@ -159,25 +162,25 @@ __global__ void __launch_bounds__(kBlock) galerkin_steps_kernel(StepArgs A) {
       // lift q~ on rows beg-1 .. end (with the periodic halo)
       for (int e = t; e < rows + 2; e += blockDim.x) {
         int64_t i = (beg - 1 + e + N) % N;
-        double s = 0.0;
+        Acc s = Acc(0);
 #pragma unroll
         for (int j = 0; j < KM; ++j)
-          if (j < k) s = fma(A.phi[j * ld + i], s_a[j], s);
-        s_qt[e] = A.q_ref[i] + s * A.dinv[i];
+          if (j < k) s = fma((Acc)phi[j * ld + i], (Acc)s_a[j], s);
+        s_qt[e] = A.q_ref[i] + (double)s * A.dinv[i];
       }
       __syncthreads();
       // f and D f, projected: partial g_j = sum_i Phi_ij d_i f_i
-      double acc[KM];
+      Acc acc[KM];
 #pragma unroll
-      for (int j = 0; j < KM; ++j) acc[j] = 0.0;
+      for (int j = 0; j < KM; ++j) acc[j] = Acc(0);
       for (int e = t; e < rows; e += blockDim.x) {
         int64_t i = beg + e;
         RowF rf = burgers_f_row(s_qt[e], s_qt[e + 1], s_qt[e + 2], A.nu, inv_dx);
-        double w = A.drow[i] * rf.f;
+        Acc w = (Acc)(A.drow[i] * rf.f);
         s_jl[e] = rf.dl; s_jc[e] = rf.dc; s_jr[e] = rf.dr;
 #pragma unroll
         for (int j = 0; j < KM; ++j)
-          if (j < k) acc[j] = fma(A.phi[j * ld + i], w, acc[j]);
+          if (j < k) acc[j] = fma((Acc)phi[j * ld + i], w, acc[j]);
       }
       double* part = A.partials + (size_t)par * G * stride;
       {
@@ -186,7 +189,7 @@ __global__ void __launch_bounds__(kBlock) galerkin_steps_kernel(StepArgs A) {
         const int lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
 #pragma unroll
         for (int j = 0; j < KM; ++j) {
-          double v = warp_sum(acc[j]);
+          double v = warp_sum((double)acc[j]);
           if (lane == 0 && j < k) red[wid * KM + j] = v;
         }
         __syncthreads();
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(kBlock) galerkin_steps_kernel(StepArgs A) {
           for (int e = t; e < (cr + 2) * k; e += blockDim.x) {
             int rr = e / k, j = e % k;
             int64_t i = (beg + c0 - 1 + rr + N) % N;
-            s_phi[rr * KM + j] = (float)A.phi[j * ld + i] * (float)A.dinv[i];
+            s_phi[rr * KM + j] = (float)phi[j * ld + i] * (float)A.dinv[i];
           }
           __syncthreads();
           for (int e = t; e < cr * k; e += blockDim.x) {
@@ -286,9 +289,11 @@ __global__ void __launch_bounds__(kBlock) galerkin_steps_kernel(StepArgs A) {
         kd = warp_max_u32(kd);
         ka = warp_max_u32(ka);
         bad = __any_sync(0xffffffffu, bad);
+        // the mixed form's residual carries FP32 rounding: stop at that level
+        const double tol = std::is_same<TPhi, float>::value ? fmax(A.tol, 1e-7) : A.tol;
         if (t == 0)
           s_sc[0] = bad ? -1.0
-                        : (((double)__uint_as_float(kd) <= A.tol * (1.0 + (double)__uint_as_float(ka))) ? 1.0 : 0.0);
+                        : (((double)__uint_as_float(kd) <= tol * (1.0 + (double)__uint_as_float(ka))) ? 1.0 : 0.0);
       }
       __syncthreads();
       if (s_sc[0] < 0.0) {
@@ -450,8 +455,9 @@ __global__ void __launch_bounds__(kBlock) hyper_steps_kernel(StepArgs A) {
 // q~ = q_ref + D^-1 Phi a
 // ----------------------------------------------------------------------------
 
-template <int KM>
+template <int KM, typename TPhi>
 __global__ void lift_kernel(LiftArgs A) {
+  const TPhi* phi = basis<TPhi>(A);
   const int k = *A.rank;
   __shared__ double s_a[KM];
   for (int j = threadIdx.x; j < KM; j += blockDim.x) s_a[j] = (j < k) ? A.a[j] : 0.0;
@@ -461,7 +467,7 @@ __global__ void lift_kernel(LiftArgs A) {
     double s = 0.0;
 #pragma unroll
     for (int j = 0; j < KM; ++j)
-      if (j < k) s = fma(A.phi[j * A.ld + i], s_a[j], s);
+      if (j < k) s = fma((double)phi[j * A.ld + i], s_a[j], s);
     A.out[i] = A.q_ref[i] + s * A.dinv[i];
   }
 }
@@ -479,16 +485,21 @@ static size_t galerkin_smem(int64_t n, int grid) {
   return bytes;
 }
 
-template <int KM>
-static cudaError_t launch_galerkin_t(const StepArgs& A, int grid, cudaStream_t s) {
+template <int KM, typename TPhi>
+static cudaError_t launch_galerkin_tt(const StepArgs& A, int grid, cudaStream_t s) {
   size_t smem = galerkin_smem<KM>(A.n, grid);
-  cudaError_t e = cudaFuncSetAttribute(galerkin_steps_kernel<KM>,
+  cudaError_t e = cudaFuncSetAttribute(galerkin_steps_kernel<KM, TPhi>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   StepArgs a = A;
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel((const void*)galerkin_steps_kernel<KM>, dim3(grid),
+  return cudaLaunchCooperativeKernel((const void*)galerkin_steps_kernel<KM, TPhi>, dim3(grid),
                                      dim3(kBlock), args, smem, s);
+}
+
+template <int KM>
+static cudaError_t launch_galerkin_t(const StepArgs& A, int grid, cudaStream_t s) {
+  return A.phi32 ? launch_galerkin_tt<KM, float>(A, grid, s) : launch_galerkin_tt<KM, double>(A, grid, s);
 }
 
 cudaError_t launch_galerkin_steps(const StepArgs& A, int km, int grid, cudaStream_t s) {
@@ -527,7 +538,8 @@ template <int KM>
 static cudaError_t launch_lift_t(const LiftArgs& A, cudaStream_t s) {
   int blocks = (int)((A.n + 255) / 256);
   if (blocks > 1024) blocks = 1024;
-  lift_kernel<KM><<<blocks, 256, 0, s>>>(A);
+  if (A.phi32) lift_kernel<KM, float><<<blocks, 256, 0, s>>>(A);
+  else lift_kernel<KM, double><<<blocks, 256, 0, s>>>(A);
   return cudaGetLastError();
 }
 

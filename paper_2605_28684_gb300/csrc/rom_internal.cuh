@@ -249,7 +249,8 @@ struct DevState {
   double* dinv;         // 1 / drow (N)
   // basis
   double* phi;          // N x r (ld = N)
-  float* phi32;         // FP32 copy (mixed precision)
+  float* phi32;         // FP32 basis, N x r (mixed precision only)
+  double* gram;         // mixed precision: Gram partial sums (grid * kMaxR * kMaxR)
   double* sigma;        // r
   double* a;            // r
   double* a_prev;       // r

@@ -12,6 +12,8 @@ struct EventArgs {
   int* rank;
   double lambda, rank_tol;
   double* phi;
+  float* phi32;         // FP32 basis (mixed precision); null in the FP64 form
+  double* gram;         // mixed precision: grid * kMaxR * kMaxR Gram partial sums
   double* sigma;
   double* a;            // reduced state to transfer (may be null)
   int transfer;
@@ -33,6 +35,7 @@ struct ProjectArgs {
   int r;
   const int* rank;
   const double* phi;
+  const float* phi32;
   const double* v;
   const double* q_ref;
   const double* drow;
@@ -54,6 +57,7 @@ struct StepArgs {
   int r;
   const int* rank;
   const double* phi;
+  const float* phi32;
   const double* q_ref;
   const double* drow;
   const double* dinv;
@@ -81,6 +85,7 @@ struct LiftArgs {
   int64_t n, ld;
   const int* rank;
   const double* phi;
+  const float* phi32;
   const double* q_ref;
   const double* drow;
   const double* dinv;
@@ -95,6 +100,7 @@ struct SampleArgs {
   int r, n_s;
   const int* rank;
   const double* phi;
+  const float* phi32;
   const double* y;      // correction snapshot (feature-guided points)
   const double* q_ref;
   const double* drow;
@@ -112,5 +118,29 @@ struct SampleArgs {
 cudaError_t launch_sampling(const SampleArgs& A, int km, int grid, cudaStream_t s);
 
 constexpr int kMeshStride = kMaxR + 2;   // per stencil row: k basis entries, q_ref, d
+
+// Basis pointer of the storage type a kernel instance was compiled for.
+template <typename TPhi, typename Args>
+__device__ __forceinline__ const TPhi* basis(const Args& A);
+template <>
+__device__ __forceinline__ const double* basis<double>(const EventArgs& A) { return A.phi; }
+template <>
+__device__ __forceinline__ const float* basis<float>(const EventArgs& A) { return A.phi32; }
+template <>
+__device__ __forceinline__ const double* basis<double>(const ProjectArgs& A) { return A.phi; }
+template <>
+__device__ __forceinline__ const float* basis<float>(const ProjectArgs& A) { return A.phi32; }
+template <>
+__device__ __forceinline__ const double* basis<double>(const StepArgs& A) { return A.phi; }
+template <>
+__device__ __forceinline__ const float* basis<float>(const StepArgs& A) { return A.phi32; }
+template <>
+__device__ __forceinline__ const double* basis<double>(const LiftArgs& A) { return A.phi; }
+template <>
+__device__ __forceinline__ const float* basis<float>(const LiftArgs& A) { return A.phi32; }
+template <>
+__device__ __forceinline__ const double* basis<double>(const SampleArgs& A) { return A.phi; }
+template <>
+__device__ __forceinline__ const float* basis<float>(const SampleArgs& A) { return A.phi32; }
 
 }  // namespace rom

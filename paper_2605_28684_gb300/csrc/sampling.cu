@@ -61,8 +61,9 @@ __device__ void block_sort512(double* v, int* idx) {
 
 }  // namespace
 
-template <int KM>
+template <int KM, typename TPhi>
 __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
+  const TPhi* phi = basis<TPhi>(A);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SampleSmem& sm = *reinterpret_cast<SampleSmem*>(smem_raw);
   const int G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
     taken[r] = false;
     if (i < end) {
       double s = 0.0;
-      for (int j = 0; j < k; ++j) { double x = A.phi[j * ld + i]; s = fma(x, x, s); }
+      for (int j = 0; j < k; ++j) { double x = (double)phi[j * ld + i]; s = fma(x, x, s); }
       res[r] = s;
       if (argmax_better(s, (int)i, best.v, best.i)) { best.v = s; best.i = (int)i; }
     }
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
     if (t == 0) sm.piv[step] = p;
     // residual direction of row p against the previous directions: classical
     // Gram-Schmidt twice, the dot products of one pass computed by all warps
-    for (int j = t; j < k; j += blockDim.x) sm.v[j] = A.phi[j * ld + p];
+    for (int j = t; j < k; j += blockDim.x) sm.v[j] = (double)phi[j * ld + p];
     __syncthreads();
     for (int pass = 0; pass < 2; ++pass) {
       for (int l = wid; l < step; l += nwarp) {
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
       const int64_t i = beg + t + (int64_t)r * blockDim.x;
       if (i < end) {
         double c = 0.0;
-        for (int j = 0; j < k; ++j) c = fma(A.phi[j * ld + i], sm.q[step * kMaxR + j], c);
+        for (int j = 0; j < k; ++j) c = fma((double)phi[j * ld + i], sm.q[step * kMaxR + j], c);
         res[r] = fma(-c, c, res[r]);
         if (i == p) taken[r] = true;
         if (!taken[r] && argmax_better(res[r], (int)i, best.v, best.i)) { best.v = res[r]; best.i = (int)i; }
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
     int s = e / 3, o = e % 3;
     int64_t i = ((int64_t)sm.piv[s] + (o - 1) + N) % N;
     double* row = A.mesh + (size_t)e * kMeshStride;
-    for (int j = 0; j < kMaxR; ++j) row[j] = (j < k) ? A.phi[j * ld + i] : 0.0;
+    for (int j = 0; j < kMaxR; ++j) row[j] = (j < k) ? (double)phi[j * ld + i] : 0.0;
     row[kMaxR] = A.q_ref[i];
     row[kMaxR + 1] = A.drow[i];
   }
@@ -327,16 +328,21 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
   }
 }
 
-template <int KM>
-static cudaError_t launch_sampling_t(const SampleArgs& A, int grid, cudaStream_t s) {
+template <int KM, typename TPhi>
+static cudaError_t launch_sampling_tt(const SampleArgs& A, int grid, cudaStream_t s) {
   size_t smem = sizeof(SampleSmem);
-  cudaError_t e = cudaFuncSetAttribute(sampling_kernel<KM>,
+  cudaError_t e = cudaFuncSetAttribute(sampling_kernel<KM, TPhi>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   SampleArgs a = A;
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel((const void*)sampling_kernel<KM>, dim3(grid), dim3(kBlock),
-                                     args, smem, s);
+  return cudaLaunchCooperativeKernel((const void*)sampling_kernel<KM, TPhi>, dim3(grid),
+                                     dim3(kBlock), args, smem, s);
+}
+
+template <int KM>
+static cudaError_t launch_sampling_t(const SampleArgs& A, int grid, cudaStream_t s) {
+  return A.phi32 ? launch_sampling_tt<KM, float>(A, grid, s) : launch_sampling_tt<KM, double>(A, grid, s);
 }
 
 cudaError_t launch_sampling(const SampleArgs& A, int km, int grid, cudaStream_t s) {
