@@ -194,6 +194,7 @@ const char* rom_status_string(rom_status s);
  * rom_fom_step_dev: one backward-Euler step q - q_prev - h f(q) = 0 solved by
  *   Newton from q_prev (Eq. be_residual_rom_section); writes q_dev (N doubles,
  *   may not alias q_prev_dev) and, if iters_host is not NULL, the Newton count.
+ *   Limits: Burgers n_cells <= 131072; Euler 8 <= n_cells <= 32768.
  * Errors: ROM_EINVAL, ROM_ENOMEM, ROM_ECUDA, ROM_ENOCONV, ROM_ENONFINITE,
  * ROM_ETIMEOUT.
  */

@@ -67,7 +67,8 @@ rom_status validate(const rom_config* c) {
   if (c->precision != ROM_FP64 && c->precision != ROM_MIXED_FP32) return ROM_EINVAL;
   if (c->problem == ROM_BURGERS && c->n_var != 1) return ROM_EINVAL;
   if (c->problem == ROM_EULER && c->n_var != 3) return ROM_EINVAL;
-  if (c->problem == ROM_EULER) return ROM_EINVAL;            // not built yet
+  if (c->problem == ROM_EULER && c->n_s > 0) return ROM_EINVAL;   // DEIM: Burgers only
+  if (c->problem == ROM_EULER && c->n_cells > 128 * 256) return ROM_EINVAL;
   if (c->n_cells < 8 || c->n_cells > (int64_t)kMaxChunks * kMaxChunkRows) return ROM_EINVAL;
   int64_t N = c->n_cells * c->n_var;
   if (c->r < 1 || c->r > kMaxR || c->r >= N || c->r > c->w_init) return ROM_EINVAL;
@@ -237,6 +238,7 @@ StepArgs step_args(rom_ctx* ctx, int nsteps) {
   A.dinv = ctx->d.dinv;
   A.a = ctx->d.a;
   A.nu = ctx->cfg.nu;
+  A.gamma = ctx->cfg.gamma;
   A.dt = ctx->cfg.dt;
   A.tol = ctx->cfg.newton_tol;
   A.max_iter = ctx->cfg.newton_max;
@@ -259,6 +261,7 @@ cudaError_t run_steps(rom_ctx* ctx, int nsteps) {
   cudaError_t e = prof_mark(ctx, 0, true);
   if (e != cudaSuccess) return e;
   if (ctx->cfg.n_s > 0) e = launch_hyper_steps(A, km_of(ctx), ctx->stream);
+  else if (ctx->cfg.problem == ROM_EULER) e = launch_euler_galerkin_steps(A, km_of(ctx), ctx->grid, ctx->stream);
   else e = launch_galerkin_steps(A, km_of(ctx), ctx->grid, ctx->stream);
   if (e != cudaSuccess) return e;
   return prof_mark(ctx, 0, false);
@@ -679,7 +682,8 @@ rom_status rom_profile_read(rom_ctx* ctx, double* ms_total, int64_t* launches) {
 rom_status rom_fom_rhs_dev(int32_t problem, int64_t n_cells, double nu, double gamma,
                            const double* q_dev, double* f_dev, void* stream) {
   rom_ctx* ctx = nullptr;
-  if (!q_dev || !f_dev || n_cells < 2 || problem != ROM_BURGERS) return ROM_EINVAL;
+  if (!q_dev || !f_dev || n_cells < 2 || (problem != ROM_BURGERS && problem != ROM_EULER))
+    return ROM_EINVAL;
   if (!device_ok()) return ROM_ECUDA;
   FomParams p;
   p.problem = problem; p.n_cells = n_cells; p.nu = nu; p.gamma = gamma; p.h = 0; p.tol = 0; p.max_iter = 0;
@@ -692,10 +696,12 @@ rom_status rom_fom_step_dev(int32_t problem, int64_t n_cells, double nu, double 
                             double newton_tol, int32_t newton_max, const double* q_prev_dev,
                             double* q_dev, int32_t* iters_host, void* stream) {
   rom_ctx* ctx = nullptr;
-  if (!q_prev_dev || !q_dev || q_prev_dev == q_dev || problem != ROM_BURGERS || n_cells < 2 ||
-      n_cells > (int64_t)kMaxChunks * kMaxChunkRows || !(h > 0.0) || newton_max < 1 ||
-      !(newton_tol > 0.0))
+  if (!q_prev_dev || !q_dev || q_prev_dev == q_dev || n_cells < 2 || !(h > 0.0) ||
+      newton_max < 1 || !(newton_tol > 0.0))
     return ROM_EINVAL;
+  if (problem == ROM_BURGERS && n_cells > (int64_t)kMaxChunks * kMaxChunkRows) return ROM_EINVAL;
+  if (problem == ROM_EULER && (n_cells < 8 || n_cells > 128 * 256)) return ROM_EINVAL;
+  if (problem != ROM_BURGERS && problem != ROM_EULER) return ROM_EINVAL;
   if (!device_ok()) return ROM_ECUDA;
   cudaStream_t s = (cudaStream_t)stream;
   FomScratch sc;

@@ -252,9 +252,13 @@ int choose_chunks(int64_t n) {
 
 }  // namespace
 
-size_t fom_chunk_floats() { return (size_t)kMaxChunks * kChunkStride; }
+size_t fom_chunk_floats() {
+  size_t a = (size_t)kMaxChunks * kChunkStride, b = euler_chunk_floats();
+  return a > b ? a : b;
+}
 
 cudaError_t launch_fom_rhs(const FomParams& p, const double* q, double* f, cudaStream_t s) {
+  if (p.problem == ROM_EULER) return launch_euler_rhs(p.n_cells, p.gamma, q, f, s);
   if (p.problem != ROM_BURGERS) return cudaErrorInvalidValue;
   int64_t n = p.n_cells;
   int blocks = (int)((n + 255) / 256);
@@ -265,12 +269,15 @@ cudaError_t launch_fom_rhs(const FomParams& p, const double* q, double* f, cudaS
 
 cudaError_t launch_fom_step(const FomParams& p, const double* q_prev, double* q,
                             const FomScratch& sc, cudaStream_t s) {
+  if (p.problem == ROM_EULER) return launch_euler_step(p, q_prev, q, sc, s);
   if (p.problem != ROM_BURGERS) return cudaErrorInvalidValue;
   int64_t n = p.n_cells;
   int C = choose_chunks(n);
   int64_t mmax = (n + C - 1) / C;
   if (mmax > kMaxChunkRows || n < 2) return cudaErrorInvalidValue;
+  // one thread per row, and at least one per chunk for the separator system
   int threads = (int)((mmax + 31) / 32 * 32);
+  if (threads < C) threads = C;
   BurgersNewtonArgs A;
   A.q_prev = q_prev; A.q = q; A.n = n; A.nu = p.nu; A.h = p.h; A.tol = p.tol;
   A.max_iter = p.max_iter; A.C = C; A.chunk = sc.chunk; A.maxbuf = sc.maxbuf;

@@ -223,6 +223,7 @@ struct EventSmem {
   double red[32 * kMaxCore];
   double U[kMaxCore * kMaxCore];    // U(:, 0:k') for the rotation
   double a_old[kMaxR];
+  double a_new[kMaxR];
   int order[kMaxCore];              // position (descending value) of each eigenpair
   double val[kMaxCore];
   // mixed precision: FP32 copies of p1, p2 and U, the FP64 Gram matrix
@@ -625,16 +626,16 @@ __global__ void __launch_bounds__(kBlock) isvd_event_kernel(EventArgs A) {
         double v = 0.0;
         if (t < knew)
           for (int j = 0; j < k; ++j) v = fma(sm.U[j * kMaxCore + t], sm.a_old[j], v);
-        sm.a_old[kMaxR - 1 - t] = v;   // staged (a_old is no longer needed)
+        sm.a_new[t] = v;               // staged: other threads still read a_old
       }
     }
     __syncthreads();
     if (t < A.r && A.a && A.transfer) {
-      double v = sm.a_old[kMaxR - 1 - t];
+      double v = sm.a_new[t];
       if constexpr (kMixed) {      // a <- R a
         if (t < knew) {
           double w = 0.0;
-          for (int c = t; c < knew; ++c) w = fma(sm.Gm[t * kMaxR + c], sm.a_old[kMaxR - 1 - c], w);
+          for (int c = t; c < knew; ++c) w = fma(sm.Gm[t * kMaxR + c], sm.a_new[c], w);
           v = w;
         }
       }

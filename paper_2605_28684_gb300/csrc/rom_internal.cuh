@@ -210,6 +210,71 @@ __device__ __forceinline__ void record_status(int* status, int code) {
   atomicCAS(status, kStOK, code);
 }
 
+// In-place LU with partial pivoting of a k x k FP32 matrix (row-major, ld
+// kMaxR) by one block.
+__device__ __forceinline__ void lu_factor(float* J, int* piv, int k) {
+  __shared__ int s_p;
+  for (int c = 0; c < k; ++c) {
+    if (threadIdx.x == 0) {
+      int p = c;
+      float best = fabsf(J[c * kMaxR + c]);
+      for (int r = c + 1; r < k; ++r) {
+        float v = fabsf(J[r * kMaxR + c]);
+        if (v > best) { best = v; p = r; }
+      }
+      piv[c] = p;
+      s_p = p;
+    }
+    __syncthreads();
+    int p = s_p;
+    if (p != c)
+      for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        float tmp = J[c * kMaxR + j];
+        J[c * kMaxR + j] = J[p * kMaxR + j];
+        J[p * kMaxR + j] = tmp;
+      }
+    __syncthreads();
+    float inv = 1.0f / J[c * kMaxR + c];
+    for (int r = c + 1 + threadIdx.x; r < k; r += blockDim.x) J[r * kMaxR + c] *= inv;
+    __syncthreads();
+    const int rem = k - c - 1;
+    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+      int r = c + 1 + e / rem, j = c + 1 + e % rem;
+      J[r * kMaxR + j] -= J[r * kMaxR + c] * J[c * kMaxR + j];
+    }
+    __syncthreads();
+  }
+}
+
+// Solve (LU) x = b for the RHS in x (FP32), by warp 0.
+__device__ __forceinline__ void lu_solve(const float* J, const int* piv, float* x, int k) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    if (lane == 0)
+      for (int c = 0; c < k; ++c) {
+        int p = piv[c];
+        if (p != c) { float tmp = x[c]; x[c] = x[p]; x[p] = tmp; }
+      }
+    __syncwarp();
+    for (int i = 0; i < k; ++i) {          // L y = b (unit lower)
+      float s = 0.f;
+      for (int l = lane; l < i; l += 32) s += J[i * kMaxR + l] * x[l];
+      s = warp_sumf(s);
+      if (lane == 0) x[i] -= s;
+      __syncwarp();
+    }
+    for (int i = k - 1; i >= 0; --i) {     // U x = y
+      float s = 0.f;
+      for (int l = i + 1 + lane; l < k; l += 32) s += J[i * kMaxR + l] * x[l];
+      s = warp_sumf(s);
+      if (lane == 0) x[i] = (x[i] - s) / J[i * kMaxR + i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+
 // ------------------------------------------------------------ FOM kernels --
 
 struct FomParams {
@@ -233,6 +298,12 @@ cudaError_t launch_fom_rhs(const FomParams& p, const double* q, double* f, cudaS
 cudaError_t launch_fom_step(const FomParams& p, const double* q_prev, double* q,
                             const FomScratch& sc, cudaStream_t s);
 size_t fom_chunk_floats();
+// Euler system (euler.cu)
+cudaError_t launch_euler_rhs(int64_t n_cells, double gamma, const double* q, double* f,
+                             cudaStream_t s);
+cudaError_t launch_euler_step(const FomParams& p, const double* q_prev, double* q,
+                              const FomScratch& sc, cudaStream_t s);
+size_t euler_chunk_floats();
 
 // ------------------------------------------------------------- ROM context --
 

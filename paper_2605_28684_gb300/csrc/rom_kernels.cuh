@@ -62,7 +62,7 @@ struct StepArgs {
   const double* drow;
   const double* dinv;
   double* a;
-  double nu, dt, tol;
+  double nu, gamma, dt, tol;
   int max_iter;
   int nsteps;
   double* partials;     // 2 * grid * (KM + 2)
@@ -79,6 +79,7 @@ struct StepArgs {
 };
 
 cudaError_t launch_galerkin_steps(const StepArgs& A, int km, int grid, cudaStream_t s);
+cudaError_t launch_euler_galerkin_steps(const StepArgs& A, int km, int grid, cudaStream_t s);
 cudaError_t launch_hyper_steps(const StepArgs& A, int km, cudaStream_t s);
 
 struct LiftArgs {

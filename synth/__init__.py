@@ -157,9 +157,10 @@ def sod_dt(n_cells: int, seed: int, gamma: float = 1.4, cfl: float = 0.4,
 
 
 def config_sod(n_cells: int = 8192, seed: int = 2) -> RomConfig:
-    """Sod, 3N state, r=40, z=10, lambda=0.01, fixed CFL-0.4 step to t=0.2."""
+    """Sod, 3N state, r=40, z=10, lambda=0.01, fixed CFL-0.4 step to t=0.2;
+    training window w_init = r = 40 (the method's default window)."""
     dt, n_steps = sod_dt(n_cells, seed)
-    w_init = 100
+    w_init = 40
     return RomConfig(problem=EULER, n_cells=n_cells, n_var=3, r=40, n_s=0,
                      w_init=w_init, z=10, dt=dt, nu=0.0, gamma=1.4, lam=0.01,
                      n_online=n_steps - w_init, seed=seed)

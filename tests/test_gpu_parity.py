@@ -67,7 +67,8 @@ def test_fom_rhs_parity(g, n):
     assert np.max(np.abs(fd.cpu().numpy() - f_or)) <= 1e-13 * np.max(np.abs(f_or))
 
 
-@pytest.mark.parametrize("n,h,nu", [(512, 1e-3, 0.01), (2053, 5e-4, 2e-3), (16384, 5e-4, 2e-3),
+@pytest.mark.parametrize("n,h,nu", [(512, 1e-3, 0.01), (2053, 5e-4, 2e-3), (8192, 5e-4, 2e-3),
+                                    (12000, 5e-4, 2e-3), (16384, 5e-4, 2e-3),
                                     (65536, 1e-3, 5e-3), (100, 1e-2, 0.01)])
 def test_fom_be_step_parity(g, n, h, nu):
     q0 = synth.burgers_ic(n, 7)
