@@ -227,6 +227,52 @@ def src_sha1(rel):
         return hashlib.sha1(f.read()).hexdigest()
 
 
+# --------------------------------------------------------------- batched ---
+
+def timed_batch(g, args, stream, dist, world):
+    """Aggregate ROM-steps/s of the 256-instance batch and the HBM roofline of
+    its reduced-step kernel (each Newton iteration streams every active
+    instance's FP32 basis and q_ref once)."""
+    import torch
+    cfgs = synth.config_batch(256)
+    q0s = [synth.initial_state(c) for c in cfgs]
+    b = g.Batch(cfgs, q0s, stream=stream.cuda_stream)
+    n_steps = 5 * args.steps
+    b.step(5 * args.warmup)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    b.profile(True)
+    start.record(stream)
+    b.step(n_steps)
+    end.record(stream)
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    prof = b.profile_read()
+    work = b.work()
+    lay = b.layout()
+    b.profile(False)
+    b.close()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    pk = peaks()
+    step_s = prof["reduced_steps"]["ms"] / 1e3
+    gbs = work["sweep_bytes"] / step_s / 1e9
+    return {"value": world * len(cfgs) * n_steps / (ms / 1e3), "unit": "ROM-steps/s",
+            "instances": len(cfgs), "steps": n_steps, "ms_per_step": ms / n_steps,
+            "basis_bytes": lay["basis_bytes"], "rows": lay["rows"], "tiles": lay["tiles"],
+            "newton_iters_per_instance_step": work["newton_iters"] / (len(cfgs) * n_steps),
+            "phases_ms": {p: prof[p]["ms"] for p in prof},
+            "launches": {p: prof[p]["launches"] for p in prof},
+            "roofline": {"bound": "hbm", "kernel": "batch_steps_kernel", "achieved": gbs,
+                         "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+                         "peak_source": pk["source"], "algorithmic_bytes": work["sweep_bytes"],
+                         "traffic": None}}
+
+
 # ------------------------------------------------------------------- main ---
 
 def main():
@@ -326,6 +372,11 @@ def main():
                        "phases_avg_us": {p: m_prof[p]["ms"] * 1e3 / max(1, m_prof[p]["launches"])
                                          for p in m_prof}},
     }
+
+    # the batched form: 256 independent Burgers ROMs of uneven size (N
+    # log-uniform in [2048, 65536], r in 8..48, z in {5, 10, 20}) advanced in
+    # lockstep; ~0.5 GB of FP32 bases, larger than L2, so no flush is needed
+    forms["batched_256"] = timed_batch(g, args, stream, dist, world)
 
     # roofline of the dominant kernel (largest device time in the timed region)
     dom = max(prof, key=lambda p: prof[p]["ms"])

@@ -9,7 +9,7 @@
  * coarse_fom_backward_euler) yields a correction snapshot y, whose
  * preprocessed form D (y - q_ref) updates the basis by Brand's rank-one
  * incremental SVD with forgetting factor lambda (Algorithm 2); the sampling
- * points and the reduced state are then refreshed (Algorithm 1, lines 13-18).
+ * points and the reduced state are then refreshed (the adaptation event of Algorithm 1).
  *
  * Conventions common to every entry point
  *  - Host pointers are read or written during the call only; the library never
@@ -99,7 +99,7 @@ typedef struct {
 } rom_config;
 
 /*
- * Offline stage of Algorithm 1 (lines 2-8): w_init fine backward-Euler FOM
+ * Offline stage of Algorithm 1: w_init fine backward-Euler FOM
  * steps from q0, preprocessing (q_ref = q0, D_v = 1/phi_v with phi_v the mean
  * square of the centred training field of variable v; Eqs.
  * scaling_matrix_local_block, variable_normalization), POD of
@@ -115,7 +115,7 @@ rom_status rom_init(const rom_config* cfg, const double* q0_host, void* stream,
                     rom_ctx** out);
 
 /*
- * n_steps iterations of the online loop of Algorithm 1 (lines 9-19): one
+ * n_steps iterations of the online loop of Algorithm 1: one
  * backward-Euler reduced step each, and an adaptation event (coarse FOM step,
  * iSVD update, sampling refresh, state transfer) after every step with
  * mod(n + 1 - w_init, z) = 0. The state stays on the device.
@@ -125,7 +125,7 @@ rom_status rom_init(const rom_config* cfg, const double* q0_host, void* stream,
 rom_status rom_step(rom_ctx* ctx, int64_t n_steps);
 
 /*
- * One adaptation event now (Algorithm 1 lines 13-18 with Algorithm 2): the
+ * One adaptation event now (the adaptation event of Algorithm 1 with Algorithm 2): the
  * correction snapshot is y_host (N doubles, a raw full-order state, which also
  * replaces the stored coarse state) or, if y_host is NULL, one coarse FOM step
  * of the stored coarse state. It is preprocessed as D (y - q_ref), the basis is
@@ -242,6 +242,81 @@ rom_status rom_fom_step_noalloc_dev(int32_t problem, int64_t n_cells, double nu,
 rom_status rom_isvd_update_dev(int64_t n, int32_t r, double lambda, double rank_tol,
                                double* phi_dev, double* sigma_dev, const double* y_dev,
                                double* ubar_host, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batched execution of many independent ROMs.
+ *
+ * A batch holds `count` independent Burgers ROMs (Algorithm 1 with the plain
+ * Galerkin step and the iSVD of Algorithm 2), each with its own n_cells, r,
+ * nu, dt, z, lambda and initial state. It runs the mixed form only: FP32
+ * basis, FP32 lift, projections and rotation with FP32 accumulation; FP64
+ * residual, coarse FOM step, core SVD, Cholesky re-orthonormalisation and
+ * reduced state. The instances advance in lockstep: every call to
+ * rom_batch_step advances each of them by n_steps steps (with its own
+ * adaptation events), and all data of the batch stays in device memory.
+ * ------------------------------------------------------------------------ */
+typedef struct rom_batch rom_batch;
+
+/*
+ * Offline stage of every instance (as rom_init), then packs the instances
+ * into one device layout: bases back to back (FP32, column-major per
+ * instance), N-vectors back to back, row tiles and FOM chunks.
+ *  cfgs     count configurations: problem ROM_BURGERS, precision
+ *           ROM_MIXED_FP32, n_var 1, n_s 0, 1 <= r <= 64,
+ *           256 <= n_cells <= 131072, z >= 1 (others as rom_init).
+ *  q0s      count host pointers, q0s[i] holding n_cells doubles (copied).
+ *  count    1 .. 4096.
+ *  stream   cudaStream_t or NULL; every batch call is ordered on it.
+ *  out      receives the batch, which owns all its device memory.
+ * Errors: ROM_EINVAL (a configuration outside the above), ROM_ENOMEM,
+ * ROM_ECUDA, and the errors of rom_init for an instance.
+ */
+rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int32_t count,
+                          void* stream, rom_batch** out);
+
+/*
+ * n_steps online steps of every instance. An instance i adapts (coarse FOM
+ * step, iSVD update, state transfer) after each of its steps n with
+ * (n + 1 - w_init_i) mod z_i == 0. Errors: ROM_EINVAL (n_steps < 0),
+ * ROM_ENOCONV / ROM_ENONFINITE (some instance's Newton solve), ROM_ETIMEOUT,
+ * ROM_ECUDA; after any of these the batch is poisoned (ROM_ESTATE on further
+ * calls except rom_batch_destroy).
+ */
+rom_status rom_batch_step(rom_batch* b, int64_t n_steps);
+
+/*
+ * State of instance i, as rom_state: q_tilde (n_cells), a (r), sigma (r),
+ * phi (n_cells x r column-major, sign convention applied, a adjusted to
+ * match), y_corr (n_cells), step; each output may be NULL.
+ * Errors: ROM_EINVAL (i out of range), ROM_ESTATE, ROM_ECUDA.
+ */
+rom_status rom_batch_state(rom_batch* b, int32_t i, double* q_tilde, double* a, double* sigma,
+                           double* phi, double* y_corr, int64_t* step);
+
+/* Rank of instance i and the Newton iterations of its last reduced step and
+ * of its last coarse FOM step. */
+rom_status rom_batch_info(rom_batch* b, int32_t i, int32_t* rank, int32_t* rom_iters,
+                          int32_t* fom_iters);
+
+/* Layout of the batch: total FP32 basis bytes (sum of n_cells * r * 4), total
+ * rows (sum of n_cells), number of row tiles, CTAs of the sweep kernels. Any
+ * output may be NULL. */
+rom_status rom_batch_layout(rom_batch* b, int64_t* basis_bytes, int64_t* rows, int32_t* tiles,
+                            int32_t* grid);
+
+/* Per-phase device timing (as rom_profile): phases 0 reduced steps, 1 coarse
+ * FOM, 2 iSVD update; ms_total and launches hold 3 entries each. */
+rom_status rom_batch_profile(rom_batch* b, int32_t enable);
+rom_status rom_batch_profile_read(rom_batch* b, double* ms_total, int64_t* launches);
+
+/* Work of the reduced steps since the last rom_batch_profile call (or init):
+ * Newton iterations summed over the instances, and the algorithmic bytes
+ * they stream (each iteration reads the instance's FP32 basis and q_ref
+ * once: 4 n_cells r + 8 n_cells bytes). Either output may be NULL. */
+rom_status rom_batch_work(rom_batch* b, int64_t* newton_iters, double* sweep_bytes);
+
+/* Releases the batch and all its device memory (NULL is ignored). */
+void rom_batch_destroy(rom_batch* b);
 
 #ifdef __cplusplus
 }

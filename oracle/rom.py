@@ -282,9 +282,9 @@ def isvd_update(Phi, sigma, yhat, lam, r, return_core=False):
 class AdaptiveROM:
     """History-aware adaptive ROM (Algorithm 1) with the iSVD update.
 
-    Offline (lines 2-8): w_init fine FOM steps, preprocessing, POD, initial
+    Offline stage: w_init fine FOM steps, preprocessing, POD, initial
     reduced state, first coarse correction state, initial sampling points.
-    Online (lines 9-20): one reduced BE step per call of ``step``; every z
+    Online loop: one reduced BE step per call of ``step``; every z
     steps an adaptation event advances the coarse FOM by z*dt, updates the
     basis by iSVD, refreshes the sampling points and transfers the state.
     """
@@ -331,7 +331,7 @@ class AdaptiveROM:
         return (n + 1 - self.cfg.w_init) % self.cfg.z == 0
 
     def adapt(self, q_tilde):
-        """Lines 13-18 of Algorithm 1 for the reconstructed state q_tilde."""
+        """The adaptation event of Algorithm 1 for the reconstructed state q_tilde."""
         c = self.cfg
         self.y_corr = self.coarse_step(self.y_corr)
         yhat = self.d * (self.y_corr - self.q_ref)

@@ -136,6 +136,91 @@ class AdaptiveROM:
             pass
 
 
+class Batch:
+    """Many independent Burgers ROMs advanced together on the GPU (mixed form)."""
+
+    PHASES = ("reduced_steps", "coarse_fom", "isvd_update")
+
+    def __init__(self, cfgs, q0s, stream: int | None = None):
+        self._lib = _lib.load()
+        self.cfgs = list(cfgs)
+        n = len(self.cfgs)
+        arr = (_lib.RomConfigC * n)()
+        for i, c in enumerate(self.cfgs):
+            arr[i] = make_config(c)
+        self._q0 = [np.ascontiguousarray(q, dtype=np.float64) for q in q0s]
+        for c, q in zip(self.cfgs, self._q0):
+            if q.shape != (int(c.n_cells),):
+                raise ValueError("each q0 must have n_cells entries")
+        ptrs = (_DP * n)(*[_dptr(q) for q in self._q0])
+        self._b = ctypes.c_void_p()
+        _lib.check(self._lib.rom_batch_init(arr, ptrs, n, ctypes.c_void_p(stream or 0),
+                                            ctypes.byref(self._b)), "rom_batch_init")
+        self.count = n
+
+    def step(self, n_steps: int = 1):
+        _lib.check(self._lib.rom_batch_step(self._b, int(n_steps)), "rom_batch_step")
+
+    def state(self, i: int, q_tilde=True, phi=False, y_corr=False):
+        c = self.cfgs[i]
+        N, r = int(c.n_cells), int(c.r)
+        qt = np.empty(N) if q_tilde else None
+        a = np.empty(r)
+        s = np.empty(r)
+        ph = np.empty((r, N)) if phi else None
+        yc = np.empty(N) if y_corr else None
+        step = ctypes.c_int64()
+        _lib.check(self._lib.rom_batch_state(self._b, int(i), None if qt is None else _dptr(qt),
+                                             _dptr(a), _dptr(s), None if ph is None else _dptr(ph),
+                                             None if yc is None else _dptr(yc), ctypes.byref(step)),
+                   "rom_batch_state")
+        return dict(q_tilde=qt, a=a, sigma=s, phi=None if ph is None else ph.T.copy(),
+                    y_corr=yc, step=step.value)
+
+    def q_tilde(self, i: int):
+        return self.state(i)["q_tilde"]
+
+    def info(self, i: int):
+        v = [ctypes.c_int32() for _ in range(3)]
+        _lib.check(self._lib.rom_batch_info(self._b, int(i), *[ctypes.byref(x) for x in v]),
+                   "rom_batch_info")
+        return dict(rank=v[0].value, rom_newton_iters=v[1].value, fom_newton_iters=v[2].value)
+
+    def layout(self):
+        bb, rows = ctypes.c_int64(), ctypes.c_int64()
+        tiles, grid = ctypes.c_int32(), ctypes.c_int32()
+        _lib.check(self._lib.rom_batch_layout(self._b, ctypes.byref(bb), ctypes.byref(rows),
+                                              ctypes.byref(tiles), ctypes.byref(grid)),
+                   "rom_batch_layout")
+        return dict(basis_bytes=bb.value, rows=rows.value, tiles=tiles.value, grid=grid.value)
+
+    def profile(self, enable: bool):
+        _lib.check(self._lib.rom_batch_profile(self._b, 1 if enable else 0), "rom_batch_profile")
+
+    def profile_read(self):
+        ms = (ctypes.c_double * 3)()
+        cnt = (ctypes.c_int64 * 3)()
+        _lib.check(self._lib.rom_batch_profile_read(self._b, ms, cnt), "rom_batch_profile_read")
+        return {p: dict(ms=ms[i], launches=cnt[i]) for i, p in enumerate(self.PHASES)}
+
+    def work(self):
+        it, by = ctypes.c_int64(), ctypes.c_double()
+        _lib.check(self._lib.rom_batch_work(self._b, ctypes.byref(it), ctypes.byref(by)),
+                   "rom_batch_work")
+        return dict(newton_iters=it.value, sweep_bytes=by.value)
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            self._lib.rom_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def fom_rhs_dev(problem, n_cells, nu, gamma, q_ptr: int, f_ptr: int, stream: int = 0):
     lib = _lib.load()
     _lib.check(lib.rom_fom_rhs_dev(problem, n_cells, nu, gamma, ctypes.c_void_p(q_ptr),

@@ -13,6 +13,8 @@ EXPORTED = [
     "rom_init", "rom_step", "rom_update_basis", "rom_state", "rom_load_state", "rom_samples",
     "rom_info", "rom_destroy", "rom_status_string", "rom_fom_rhs_dev", "rom_fom_step_dev",
     "rom_isvd_update_dev", "rom_profile", "rom_profile_read", "rom_fom_step_noalloc_dev",
+    "rom_batch_init", "rom_batch_step", "rom_batch_state", "rom_batch_info", "rom_batch_layout",
+    "rom_batch_profile", "rom_batch_profile_read", "rom_batch_destroy", "rom_batch_work",
 ]
 
 
@@ -79,7 +81,21 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                         ctypes.c_double, P, P, P, D, P]
     lib.rom_profile.argtypes = [P, ctypes.c_int32]
     lib.rom_profile_read.argtypes = [P, D, ctypes.POINTER(ctypes.c_int64)]
-    for name in ["rom_fom_step_noalloc_dev", "rom_profile", "rom_profile_read", "rom_init", "rom_step", "rom_update_basis", "rom_state", "rom_load_state",
+    I64P = ctypes.POINTER(ctypes.c_int64)
+    lib.rom_batch_init.argtypes = [ctypes.POINTER(RomConfigC), ctypes.POINTER(D), ctypes.c_int32, P,
+                                   ctypes.POINTER(P)]
+    lib.rom_batch_step.argtypes = [P, ctypes.c_int64]
+    lib.rom_batch_state.argtypes = [P, ctypes.c_int32, D, D, D, D, D, I64P]
+    lib.rom_batch_info.argtypes = [P, ctypes.c_int32, I32P, I32P, I32P]
+    lib.rom_batch_layout.argtypes = [P, I64P, I64P, I32P, I32P]
+    lib.rom_batch_profile.argtypes = [P, ctypes.c_int32]
+    lib.rom_batch_profile_read.argtypes = [P, D, I64P]
+    lib.rom_batch_work.argtypes = [P, I64P, D]
+    lib.rom_batch_destroy.argtypes = [P]
+    lib.rom_batch_destroy.restype = None
+    for name in ["rom_batch_init", "rom_batch_step", "rom_batch_state", "rom_batch_info",
+                 "rom_batch_layout", "rom_batch_profile", "rom_batch_profile_read", "rom_batch_work",
+                 "rom_fom_step_noalloc_dev", "rom_profile", "rom_profile_read", "rom_init", "rom_step", "rom_update_basis", "rom_state", "rom_load_state",
                  "rom_samples", "rom_info", "rom_fom_rhs_dev", "rom_fom_step_dev",
                  "rom_isvd_update_dev"]:
         getattr(lib, name).restype = ctypes.c_int

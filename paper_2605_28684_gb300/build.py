@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librom.so")
-SOURCES = ["api.cu", "fom.cu", "euler.cu", "isvd.cu", "reduced.cu", "sampling.cu"]
+SOURCES = ["api.cu", "fom.cu", "euler.cu", "isvd.cu", "reduced.cu", "sampling.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -3,7 +3,7 @@
 // The context owns every device buffer. All launches go to the context's
 // stream; every entry point synchronises that stream once at the end and then
 // reads the device status word (4 bytes), so the only host round trip per
-// call is that status. The offline stage (Algorithm 1, lines 2-8) is:
+// call is that status. The offline stage of Algorithm 1 is:
 // w_init fine FOM steps -> per-variable scaling -> POD as a rank-growing iSVD
 // with forgetting factor 1 (equal to the thin SVD of the training matrix
 // while its numerical rank stays within kMaxR) -> initial reduced state ->
@@ -21,7 +21,13 @@ using namespace rom;
 
 namespace {
 
-constexpr double kGrowRankTol = 1e-15;   // null-direction test while the POD grows
+// Null-direction test while the POD grows (new direction kept only if
+// rho > tol * max(|yhat|, sigma_1); singular values <= tol * sigma_1 dropped).
+// A residual rho much below 1e-13 |yhat| is set by rounding and by the basis'
+// own orthonormality error, not by the data: a direction normalised from it is
+// not orthogonal to the basis, and the error compounds over the updates. The
+// directions it drops lie far below the final truncation at rank_tol.
+constexpr double kGrowRankTol = 1e-13;
 
 #define RCK(call)                                  \
   do {                                             \
@@ -267,7 +273,7 @@ cudaError_t run_steps(rom_ctx* ctx, int nsteps) {
   return prof_mark(ctx, 0, false);
 }
 
-// Lines 13-18 of Algorithm 1 on the current y_corr.
+// The adaptation event of Algorithm 1 on the current y_corr.
 cudaError_t run_event(rom_ctx* ctx) {
   EventArgs A = event_args(ctx, ctx->d.y_corr, 1, ctx->cfg.lambda, ctx->cfg.rank_tol, ctx->cfg.r, 1);
   cudaError_t e = prof_mark(ctx, 2, true);

@@ -1,0 +1,1648 @@
+// Batched execution of many independent adaptive ROMs: Burgers instances of
+// uneven size (N, r, nu, z, lambda per instance) in the mixed form (FP32 basis
+// with FP32 lift, projections and rotation; FP64 residual, coarse FOM, core
+// SVD and re-orthonormalisation). Every instance runs the online loop of
+// Algorithm 1 with the plain Galerkin step and the iSVD of Algorithm 2.
+//
+// All instances advance in lockstep, one time step at a time, so that one
+// pass over the bases serves every instance: a Newton iteration streams the
+// FP32 bases of the whole batch once (about 0.5 GB for 256 instances of
+// N ~ 18k, r ~ 28), which makes the batch HBM-bound where a single small ROM
+// is latency-bound. Work is cut into row tiles (instance, first row, last
+// row); CTAs take tiles from a queue ordered by decreasing cost, and per-tile
+// partial sums are combined per instance in tile order, so results do not
+// depend on which CTA took which tile. Three persistent cooperative kernels:
+//   batch_steps_kernel  BE Galerkin steps: per iteration a sweep over the
+//                       tiles (lift, FP64 residual, FP32 projection, FP32
+//                       reduced Jacobian when due) and an instance phase
+//                       (Newton update with the FP32 LU factors).
+//   batch_fom_kernel    the coarse FOM step (Eq. coarse_fom_backward_euler)
+//                       of the instances that adapt now: Newton with the
+//                       chunked PCR solver of fom.cu over (instance, chunk)
+//                       work items.
+//   batch_event_kernel  Algorithm 2 for those instances: projections, one CTA
+//                       per instance for the core SVD, rotation with a fused
+//                       Gram matrix, FP64 Cholesky, basis <- basis R^-1.
+//
+// The reduced Jacobian I - dt Phi^T J_f Phi (D is a scalar for Burgers, so
+// D and D^-1 cancel) is formed at the first step after every basis change
+// and kept (a chord iteration); it is refreshed at the current iterate after
+// every 8 iterations without convergence. The root is fixed by the residual.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <climits>
+#include <cstddef>
+#include <cstring>
+#include <type_traits>
+#include <vector>
+
+#include "rom_internal.cuh"
+#include "secular.cuh"
+
+namespace rom {
+
+namespace {
+
+constexpr int kBT = 256;          // threads of the sweep kernels
+constexpr int kFomT = 1024;       // threads of the FOM kernel (one row each)
+constexpr int kPS = kMaxR + 4;    // stride of the per-tile partial vectors
+constexpr int kMaxBatch = 4096;   // instances per batch
+constexpr int kTileRows = 2048;   // rows per tile
+constexpr int kFomChunkStride = 16;
+
+// Per-instance constants (device array, written once at init).
+struct Inst {
+  long long phi_off;   // offset (floats) of the FP32 basis, N x r column-major
+  long long vec_off;   // offset (doubles) of the N-vectors of this instance
+  int n, r, z, maxit;
+  int tile0, tile1;    // row tiles [tile0, tile1)
+  int chunk0, nchunk;  // FOM chunks [chunk0, chunk0 + nchunk)
+  double nu, dt, lam, d, dinv, tol, rank_tol;
+};
+
+struct BArgs {
+  int count, ntiles, nchunks, nsteps, fom_maxit;
+  const Inst* inst;
+  const int* tile_inst;
+  const int* tile_r0;
+  const int* tile_r1;
+  const int* order;        // queue order of the tiles (decreasing cost)
+  const int* chunk_inst;
+  const int* chunk_c;
+  float* phi;
+  const double* q_ref;
+  double* y_corr;          // correction snapshot (previous coarse FOM state)
+  double* y_new;           // coarse FOM iterate / new snapshot
+  double* a;               // count x kMaxR: reduced state
+  double* an;              // count x kMaxR: reduced state at the start of the step
+  double* sigma;           // count x kMaxR
+  int* rank;
+  int* need_jac;
+  int* active;
+  int* iters_rom;
+  int* iters_fom;
+  long long* sweeps;       // count: Newton iterations (sweeps over the basis) since reset
+  float* jlu;              // count x kMaxR x kMaxR: LU factors of the reduced Jacobian
+  int* jpiv;               // count x kMaxR
+  double* gpart;           // ntiles x kPS
+  double* gpart2;          // ntiles x kPS
+  float* mpart;            // ntiles x kMaxR x kMaxR (Jacobian or Gram partials)
+  float* fom_row;          // 3 floats per row (PCR y, v, w)
+  float* fom_chunk;        // nchunks x kFomChunkStride
+  float* fom_sep;          // nchunks: separator values
+  unsigned int* fom_keys;  // count x 4
+  double* ev_p;            // count x kMaxCore: p1, then p = p1 + p2
+  double* ev_p2;           // count x kMaxCore: p2 (second Gram-Schmidt pass)
+  float* qres;             // q1 = yhat - Phi p1 per row (FP32), packed like the N-vectors
+  double* ev_sc;           // count x 8: |yhat|^2, 1/rho, k', k
+  float* ev_u;             // count x kMaxCore x kMaxR: rotation U(:, 0:k') (FP32)
+  double* ev_anew;         // count x kMaxR: transferred state before a <- R a
+  float* ev_r;             // count x kMaxR x kMaxR: Cholesky factor R (FP32 copy)
+  unsigned int* ctl;       // [0..3] tile queues, [4..5] active counts (host-zeroed)
+  long long* M;            // online steps done by every instance
+  GridBarrier* bar;
+  int* status;
+};
+
+__device__ __forceinline__ bool is_event(const Inst& I, long long M) {
+  return M > 0 && (M % I.z) == 0;
+}
+
+// ------------------------------------------------------------- Burgers ---
+
+// Godunov flux F(uL, uR) = max(max(uL,0)^2, min(uR,0)^2) / 2 (tie -> left) as
+// the selected state s (F = s^2 / 2). The branch is chosen on the magnitudes,
+// which order the same way as the squares, using integer tests on the bit
+// patterns; only the square is FP64 arithmetic.
+struct Sel {
+  double s;
+  bool left;
+};
+__device__ __forceinline__ Sel godunov_sel(double uL, double uR) {
+  const long long bl = __double_as_longlong(uL), br = __double_as_longlong(uR);
+  const double lp = (bl > 0) ? uL : 0.0;     // max(uL, 0); a positive NaN stays
+  const double rm = (br < 0) ? uR : 0.0;     // min(uR, 0); a negative NaN stays
+  const long long ml = __double_as_longlong(lp) & 0x7fffffffffffffffLL;
+  const long long mr = __double_as_longlong(rm) & 0x7fffffffffffffffLL;
+  Sel o;
+  o.left = ml >= mr;
+  o.s = o.left ? lp : rm;
+  return o;
+}
+
+// f_i = -(F_{i+1/2} - F_{i-1/2}) / dx + nu (u_{i+1} - 2 u_i + u_{i-1}) / dx^2.
+__device__ __forceinline__ double burgers_f(double ul, double u, double ur, double nu, double inv_dx) {
+  const Sel a = godunov_sel(ul, u), b = godunov_sel(u, ur);
+  const double adv = (-0.5 * inv_dx) * (b.s * b.s - a.s * a.s);
+  return fma(nu * inv_dx * inv_dx, fma(-2.0, u, ur + ul), adv);
+}
+
+// Tridiagonal row of J_f (FP32): df_i/du_{i-1}, df_i/du_i, df_i/du_{i+1}.
+__device__ __forceinline__ void burgers_band(double ul, double u, double ur, float nu_f, float inv_dx_f,
+                                             float& dl, float& dc, float& dr) {
+  const Sel a = godunov_sel(ul, u), b = godunov_sel(u, ur);
+  const float c2 = nu_f * inv_dx_f * inv_dx_f;
+  const float sa = (float)a.s, sb = (float)b.s;
+  dl = (a.left ? sa : 0.f) * inv_dx_f + c2;
+  dc = ((a.left ? 0.f : sa) - (b.left ? sb : 0.f)) * inv_dx_f - 2.f * c2;
+  dr = -(b.left ? 0.f : sb) * inv_dx_f + c2;
+}
+
+// --------------------------------------------------------- small helpers ---
+
+// Rank bucket (register budget) of an instance: loops are sized for the
+// bucket and guarded by the actual rank.
+__host__ __device__ __forceinline__ int bucket_of(int r) {
+  return r <= 8 ? 8 : r <= 16 ? 16 : r <= 32 ? 32 : r <= 48 ? 48 : 64;
+}
+
+// Calls f(integral_constant<KB>) for the bucket of r.
+template <typename F>
+__device__ __forceinline__ void with_bucket(int r, F&& f) {
+  switch (bucket_of(r)) {
+    case 8: f(std::integral_constant<int, 8>{}); break;
+    case 16: f(std::integral_constant<int, 16>{}); break;
+    case 32: f(std::integral_constant<int, 32>{}); break;
+    case 48: f(std::integral_constant<int, 48>{}); break;
+    default: f(std::integral_constant<int, 64>{}); break;
+  }
+}
+
+// Rows per thread: keeps about 64 basis loads in flight per thread.
+template <int KB>
+struct Rpt {
+  static constexpr int v = KB <= 8 ? 8 : KB <= 16 ? 4 : KB <= 32 ? 2 : 1;
+};
+
+// Next tile of a queue; -1 when empty. All threads call it.
+__device__ __forceinline__ int next_tile(unsigned int* ctr, int ntiles, int* s_q) {
+  __syncthreads();
+  if (threadIdx.x == 0) *s_q = (int)atomicAdd(ctr, 1u);
+  __syncthreads();
+  const int q = *s_q;
+  return q < ntiles ? q : -1;
+}
+
+// Sum of per-tile partial vectors of one instance, fixed order: warps over
+// entries, lanes over tiles.
+__device__ __forceinline__ void sum_tiles(const double* part, int tile0, int tile1, int nent, int off,
+                                          double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = wid; j < nent; j += nw) {
+    double s = 0.0;
+    for (int tt = tile0 + lane; tt < tile1; tt += 32) s += __ldcg(&part[(size_t)tt * kPS + off + j]);
+    s = warp_sum(s);
+    if (lane == 0) out[j] = s;
+  }
+}
+
+// Block reduction of per-thread FP32 accumulators into FP64 per-tile partials.
+template <int KB>
+__device__ __forceinline__ void tile_reduce(const float (&acc)[KB], int k, float* red, double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int j = 0; j < KB; ++j) {
+    float v = warp_sumf(acc[j]);
+    if (lane == 0) red[wid * KB + j] = v;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += (double)red[w * KB + j];
+    out[j] = s;
+  }
+}
+
+// Register-blocked accumulation of  M += sum_rows A_row^T B_row  for k x k
+// (4 x 4 blocks per thread, rows split over groups of threads when the
+// blocks are fewer than the threads). A, B: rows x KB, row-major in shared.
+template <int KB>
+struct Blk {
+  static constexpr int nb = KB / 4;
+  static constexpr int nblk = nb * nb;
+  static constexpr int groups = kBT / nblk > 0 ? kBT / nblk : 1;
+};
+
+template <int KB>
+__device__ __forceinline__ void blk_accum(const float* A, const float* B, int rows, float (&m)[16]) {
+  const int t = threadIdx.x;
+  const int g = t / Blk<KB>::nblk, bi = t % Blk<KB>::nblk;
+  if (g >= Blk<KB>::groups) return;
+  const int jb = bi / Blk<KB>::nb, lb = bi % Blk<KB>::nb;
+  for (int rr = g; rr < rows; rr += Blk<KB>::groups) {
+    const float4 av = *reinterpret_cast<const float4*>(A + rr * KB + 4 * jb);
+    const float4 bv = *reinterpret_cast<const float4*>(B + rr * KB + 4 * lb);
+    const float ar[4] = {av.x, av.y, av.z, av.w};
+    const float br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) m[p * 4 + q] = fmaf(ar[p], br[q], m[p * 4 + q]);
+  }
+}
+
+// Adds the per-thread blocks into a k x k FP32 matrix (row-major, ld k) in
+// shared memory that the caller zeroed.
+template <int KB>
+__device__ __forceinline__ void blk_flush(const float (&m)[16], int k, float* out) {
+  const int t = threadIdx.x;
+  const int g = t / Blk<KB>::nblk, bi = t % Blk<KB>::nblk;
+  if (g >= Blk<KB>::groups) return;
+  const int jb = bi / Blk<KB>::nb, lb = bi % Blk<KB>::nb;
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = 4 * jb + p, l = 4 * lb + q;
+      if (j < k && l < k) atomicAdd(&out[j * k + l], m[p * 4 + q]);
+    }
+}
+
+// ---------------------------------------------------- shared-memory plans ---
+
+struct StepSmem {
+  double qt[kTileRows + 2];          // lifted state of a chunk (+ halo)
+  alignas(16) float P[66 * kMaxR];   // basis rows of a 64-row sub-chunk (+ halo)
+  alignas(16) float W[64 * kMaxR];   // J_f Phi rows; tile Jacobian at the end
+  float red[8 * kMaxR];
+  float af[kMaxR];
+  float hx[2 * kMaxR];               // basis rows of the chunk halo
+  // instance phase
+  float J[kMaxR * kMaxR];
+  double g[kMaxR];
+  float x[kMaxR];
+  int piv[kMaxR];
+  double sc[4];
+  int q;
+};
+
+struct CoreSmem {
+  SecularSetup S;
+  double d_desc[kMaxCore], z[kMaxCore];
+  double tau[kMaxCore], orig[kMaxCore], zhat[kMaxCore];
+  double val[kMaxCore], sbar[kMaxCore];
+  int order[kMaxCore], pos[kMaxCore], defp[kMaxCore];
+  double pv[8][kMaxCore];
+  double U[kMaxCore * kMaxCore];      // row-major [row][col], ld kMaxCore
+  double aold[kMaxR];
+  double sc[8];
+};
+
+struct SweepSmem {
+  double dred[32];                   // FP64 block-reduction scratch
+  alignas(16) float P[kBT * 64];     // new basis rows of a chunk (Gram)
+  float U[kMaxCore * kMaxR];         // rotation (FP32), row-major [row][col]
+  float R[kMaxR * kMaxR];            // Cholesky factor (FP32), row-major
+  float Rd[kMaxR];                   // 1 / R_jj
+  float pf[kMaxCore];
+  float red[8 * kMaxR];
+  float Gt[kMaxR * kMaxR];           // tile Gram
+  double sc[4];
+  int q;
+};
+
+// float4 reads of the staged rows need 16-byte alignment
+static_assert(offsetof(StepSmem, P) % 16 == 0 && offsetof(StepSmem, W) % 16 == 0, "alignment");
+static_assert(offsetof(SweepSmem, P) % 16 == 0 && offsetof(SweepSmem, dred) % 8 == 0, "alignment");
+
+struct CholSmem {
+  double G[kMaxR * kMaxR];           // Gram, then R in its upper triangle
+  double anew[kMaxR];
+  double d;
+};
+
+// ======================================================== steps kernel ===
+
+template <int KB>
+__device__ void step_tile(const BArgs& A, StepSmem& sm, int tile, int i, bool jac) {
+  constexpr int RPT = Rpt<KB>::v;
+  constexpr int CR = kBT * RPT;
+  const Inst I = A.inst[i];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int k = A.rank[i];
+  const int N = I.n;
+  const float* phi = A.phi + I.phi_off;
+  const double* qref = A.q_ref + I.vec_off;
+  const int r0 = A.tile_r0[tile], r1 = A.tile_r1[tile];
+  const double inv_dx = (double)N;
+  const float d_f = (float)I.d;
+  const float nu_f = (float)I.nu, inv_dx_f = (float)N;
+  for (int j = t; j < KB; j += kBT) sm.af[j] = (j < k) ? (float)__ldcg(&A.a[(size_t)i * kMaxR + j]) : 0.f;
+  float acc[KB];
+#pragma unroll
+  for (int j = 0; j < KB; ++j) acc[j] = 0.f;
+  float m[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) m[q] = 0.f;
+  __syncthreads();
+  for (int c0 = r0; c0 < r1; c0 += CR) {
+    const int rows = min(CR, r1 - c0);
+    float x[RPT][KB];
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr) {
+      const int e = rr * kBT + t;
+#pragma unroll
+      for (int j = 0; j < KB; ++j) x[rr][j] = (e < rows && j < k) ? __ldg(&phi[(size_t)j * N + c0 + e]) : 0.f;
+    }
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr) {
+      const int e = rr * kBT + t;
+      float s = 0.f;
+#pragma unroll
+      for (int j = 0; j < KB; ++j) s = fmaf(x[rr][j], sm.af[j], s);
+      if (e < rows) sm.qt[1 + e] = fma(I.dinv, (double)s, qref[c0 + e]);
+    }
+    if (wid < 2) {   // periodic halo rows: warp 0 left, warp 1 right
+      const int h = (wid == 0) ? (c0 - 1 + N) % N : (c0 + rows) % N;
+      float s = 0.f;
+      for (int j = lane; j < KB; j += 32) {
+        const float v = (j < k) ? __ldg(&phi[(size_t)j * N + h]) : 0.f;
+        sm.hx[wid * kMaxR + j] = v;
+        s = fmaf(v, sm.af[j], s);
+      }
+      s = warp_sumf(s);
+      if (lane == 0) sm.qt[wid == 0 ? 0 : rows + 1] = fma(I.dinv, (double)s, qref[h]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr) {
+      const int e = rr * kBT + t;
+      if (e < rows) {
+        const double f = burgers_f(sm.qt[e], sm.qt[e + 1], sm.qt[e + 2], I.nu, inv_dx);
+        const float w = (float)f * d_f;
+#pragma unroll
+        for (int j = 0; j < KB; ++j) acc[j] = fmaf(x[rr][j], w, acc[j]);
+      }
+    }
+    if (jac) {
+      // Phi^T J_f Phi over 64-row sub-chunks: stage basis rows (+ halo),
+      // W = J_f Phi, then the blocked rank-64 update.
+      for (int s0 = 0; s0 < rows; s0 += 64) {
+        const int sr = min(64, rows - s0);
+#pragma unroll
+        for (int rr = 0; rr < RPT; ++rr) {
+          const int e = rr * kBT + t;
+          if (e < rows && e >= s0 - 1 && e <= s0 + sr) {
+#pragma unroll
+            for (int j = 0; j < KB; ++j) sm.P[(e - s0 + 1) * KB + j] = x[rr][j];
+          }
+        }
+        if (s0 == 0)
+          for (int j = t; j < KB; j += kBT) sm.P[j] = sm.hx[j];
+        if (s0 + sr == rows)
+          for (int j = t; j < KB; j += kBT) sm.P[(sr + 1) * KB + j] = sm.hx[kMaxR + j];
+        __syncthreads();
+        for (int e = t; e < sr * KB; e += kBT) {
+          const int rl = e / KB, l = e % KB;
+          float dl, dc, dr;
+          burgers_band(sm.qt[s0 + rl], sm.qt[s0 + rl + 1], sm.qt[s0 + rl + 2], nu_f, inv_dx_f, dl, dc, dr);
+          sm.W[rl * KB + l] = dl * sm.P[rl * KB + l] + dc * sm.P[(rl + 1) * KB + l] + dr * sm.P[(rl + 2) * KB + l];
+        }
+        __syncthreads();
+        blk_accum<KB>(sm.P + KB, sm.W, sr, m);
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+  }
+  double* gp = A.gpart + (size_t)tile * kPS;
+  tile_reduce<KB>(acc, k, sm.red, gp);
+  if (jac) {
+    __syncthreads();
+    for (int e = t; e < k * k; e += kBT) sm.W[e] = 0.f;
+    __syncthreads();
+    blk_flush<KB>(m, k, sm.W);
+    __syncthreads();
+    float* mp = A.mpart + (size_t)tile * kMaxR * kMaxR;
+    for (int e = t; e < k * k; e += kBT) mp[e] = sm.W[e];
+  }
+}
+
+// Newton update of instance i after a sweep (one CTA).
+__device__ void step_instance(const BArgs& A, StepSmem& sm, int i, int it, unsigned int* nact) {
+  const Inst I = A.inst[i];
+  const int t = threadIdx.x;
+  const int k = A.rank[i];
+  const int jac = A.need_jac[i];
+  sum_tiles(A.gpart, I.tile0, I.tile1, k, 0, sm.g);
+  __syncthreads();
+  float* J = sm.J;
+  if (jac) {
+    for (int e = t; e < k * k; e += blockDim.x) {
+      float s = 0.f;
+      for (int tt = I.tile0; tt < I.tile1; ++tt) s += __ldcg(&A.mpart[(size_t)tt * kMaxR * kMaxR + e]);
+      const int j = e / k, l = e % k;
+      J[j * kMaxR + l] = (j == l ? 1.f : 0.f) - (float)I.dt * s;
+    }
+    __syncthreads();
+    lu_factor(J, sm.piv, k);
+    float* jg = A.jlu + (size_t)i * kMaxR * kMaxR;
+    for (int e = t; e < k * kMaxR; e += blockDim.x) jg[e] = J[e];
+    for (int j = t; j < k; j += blockDim.x) A.jpiv[(size_t)i * kMaxR + j] = sm.piv[j];
+    if (t == 0) A.need_jac[i] = 0;
+  } else {
+    const float* jg = A.jlu + (size_t)i * kMaxR * kMaxR;
+    for (int e = t; e < k * kMaxR; e += blockDim.x) J[e] = __ldcg(&jg[e]);
+    for (int j = t; j < k; j += blockDim.x) sm.piv[j] = __ldcg(&A.jpiv[(size_t)i * kMaxR + j]);
+  }
+  double* a = A.a + (size_t)i * kMaxR;
+  const double* an = A.an + (size_t)i * kMaxR;
+  for (int j = t; j < k; j += blockDim.x) sm.x[j] = (float)(-(a[j] - an[j] - I.dt * sm.g[j]));
+  __syncthreads();
+  lu_solve(J, sm.piv, sm.x, k);
+  if (t < 32) {
+    unsigned int kd = 0u, ka = 0u;
+    bool bad = false;
+    for (int j = t; j < k; j += 32) {
+      const float dlt = sm.x[j];
+      const double v = a[j] + (double)dlt;
+      a[j] = v;
+      kd = max(kd, __float_as_uint(fabsf(dlt)));
+      ka = max(ka, __float_as_uint(fabsf((float)v)));
+      bad = bad || !isfinite(v);
+    }
+    kd = warp_max_u32(kd);
+    ka = warp_max_u32(ka);
+    bad = __any_sync(0xffffffffu, bad);
+    // FP32 projections: stop at their rounding level
+    const double tol = fmax(I.tol, 1e-7);
+    if (t == 0) {
+      const bool conv = (double)__uint_as_float(kd) <= tol * (1.0 + (double)__uint_as_float(ka));
+      if (bad) {
+        record_status(A.status, kStNonFinite);
+      } else if (conv) {
+        A.active[i] = 0;
+        A.iters_rom[i] = it;
+        A.sweeps[i] += it;
+      } else if (it >= I.maxit) {
+        record_status(A.status, kStNoConv);
+      } else {
+        A.active[i] = 1;
+        if (it % 8 == 0) A.need_jac[i] = 1;    // stale Jacobian: refresh at this iterate
+        atomicAdd(nact, 1u);
+      }
+      sm.sc[0] = conv ? 1.0 : 0.0;
+    }
+  }
+  __syncthreads();
+  if (sm.sc[0] > 0.0)
+    for (int j = t; j < k; j += blockDim.x) A.an[(size_t)i * kMaxR + j] = a[j];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBT, 1) batch_steps_kernel(BArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StepSmem& sm = *reinterpret_cast<StepSmem*>(smem_raw);
+  const int G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
+  for (int i = b; i < A.count; i += G)
+    for (int j = t; j < kMaxR; j += blockDim.x) A.an[(size_t)i * kMaxR + j] = A.a[(size_t)i * kMaxR + j];
+  int gi = 0;   // iteration counter over the whole launch (queue parity)
+  for (int step = 0; step < A.nsteps; ++step) {
+    for (int it = 1;; ++it, ++gi) {
+      const int par = gi & 1;
+      int q;
+      while ((q = next_tile(&A.ctl[par], A.ntiles, &sm.q)) >= 0) {
+        const int tile = A.order[q];
+        const int i = A.tile_inst[tile];
+        if (it > 1 && !__ldcg(&A.active[i])) continue;
+        const bool jac = __ldcg(&A.need_jac[i]) != 0;
+        with_bucket(A.inst[i].r, [&](auto kb) { step_tile<decltype(kb)::value>(A, sm, tile, i, jac); });
+      }
+      if (!grid_sync(A.bar, A.status)) return;
+      if (b == 0 && t == 0) {
+        A.ctl[par ^ 1] = 0u;
+        A.ctl[4 + (par ^ 1)] = 0u;
+      }
+      for (int i = b; i < A.count; i += G) {
+        if (it > 1 && !__ldcg(&A.active[i])) continue;
+        step_instance(A, sm, i, it, &A.ctl[4 + par]);
+      }
+      if (!grid_sync(A.bar, A.status)) return;
+      if (__ldcg(A.status) != 0) return;
+      if (__ldcg(&A.ctl[4 + par]) == 0u) { ++gi; break; }
+    }
+  }
+  if (b == 0 && t == 0) *A.M += A.nsteps;
+}
+
+// ========================================================== FOM kernel ===
+
+__device__ __forceinline__ int64_t fchunk_begin(int c, int C, int64_t n) { return (int64_t)c * n / C; }
+
+__global__ void __launch_bounds__(kFomT, 1) batch_fom_kernel(BArgs A) {
+  __shared__ float sa[kFomT], sb[kFomT], sc[kFomT], sd0[kFomT], sd1[kFomT], sd2[kFomT];
+  __shared__ float ra[kMaxChunks], rb[kMaxChunks], rc[kMaxChunks], rd[kMaxChunks];
+  __shared__ double su[kFomT];
+  __shared__ unsigned int redu[32];
+  __shared__ unsigned char s_done[kMaxBatch];
+  const int G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
+  const long long M = *A.M;
+  for (int i = t; i < A.count; i += blockDim.x) s_done[i] = is_event(A.inst[i], M) ? 0 : 1;
+  if (b == 0)
+    for (int e = t; e < 4 * A.count; e += blockDim.x) A.fom_keys[e] = 0u;
+  __syncthreads();
+  for (int it = 1; it <= A.fom_maxit; ++it) {
+    const int par = it & 1;
+    // ---- A: residual (FP64), Jacobian rows (FP32), interior PCR per chunk ----
+    for (int q = b; q < A.nchunks; q += G) {
+      const int i = A.chunk_inst[q];
+      if (s_done[i]) continue;
+      const Inst I = A.inst[i];
+      const int C = I.nchunk, c = A.chunk_c[q];
+      const int64_t n = I.n;
+      const int64_t beg = fchunk_begin(c, C, n);
+      const int m = (int)(fchunk_begin(c + 1, C, n) - beg);
+      const int mi = m - 1;
+      const double* ucur = (it == 1 ? A.y_corr : A.y_new) + I.vec_off;
+      const double* uprev = A.y_corr + I.vec_off;
+      const double h = (double)I.z * I.dt;
+      const double inv_dx = (double)n;
+      const float nu_f = (float)I.nu, inv_dx_f = (float)n, h_f = (float)h;
+      __syncthreads();
+      const bool act = t < m;
+      double u = act ? __ldcg(&ucur[beg + t]) : 0.0;
+      su[t] = u;
+      __syncthreads();
+      float a_t = 0.f, b_t = 1.f, c_t = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
+      if (act) {
+        const double ul = (t > 0) ? su[t - 1] : __ldcg(&ucur[(beg - 1 + n) % n]);
+        const double ur = (t < m - 1) ? su[t + 1] : __ldcg(&ucur[(beg + m) % n]);
+        const double f = burgers_f(ul, u, ur, I.nu, inv_dx);
+        const double res = u - uprev[beg + t] - h * f;
+        float dl, dc, dr;
+        burgers_band(ul, u, ur, nu_f, inv_dx_f, dl, dc, dr);
+        a_t = -h_f * dl;
+        b_t = 1.f - h_f * dc;
+        c_t = -h_f * dr;
+        d0 = (float)(-res);
+      }
+      float* ch = A.fom_chunk + (size_t)q * kFomChunkStride;
+      if (t == m - 1) { ch[0] = a_t; ch[1] = b_t; ch[2] = c_t; ch[3] = d0; }
+      if (t < mi) {
+        if (t == 0) { d1 = -a_t; a_t = 0.f; }
+        if (t == mi - 1) { d2 = -c_t; c_t = 0.f; }
+      } else {
+        a_t = 0.f; b_t = 1.f; c_t = 0.f; d0 = d1 = d2 = 0.f;
+      }
+      sa[t] = a_t; sb[t] = b_t; sc[t] = c_t; sd0[t] = d0; sd1[t] = d1; sd2[t] = d2;
+      __syncthreads();
+      for (int s = 1; s < mi; s <<= 1) {
+        float na = a_t, nb = b_t, nc = c_t, n0 = d0, n1 = d1, n2 = d2;
+        if (t < mi) {
+          const int tm = t - s, tp = t + s;
+          float am = 0.f, bm = 1.f, cm = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f;
+          float ap = 0.f, bp = 1.f, cp = 0.f, p0 = 0.f, p1 = 0.f, p2 = 0.f;
+          if (tm >= 0) { am = sa[tm]; bm = sb[tm]; cm = sc[tm]; m0 = sd0[tm]; m1 = sd1[tm]; m2 = sd2[tm]; }
+          if (tp < mi) { ap = sa[tp]; bp = sb[tp]; cp = sc[tp]; p0 = sd0[tp]; p1 = sd1[tp]; p2 = sd2[tp]; }
+          const float al = -a_t / bm, ga = -c_t / bp;
+          na = al * am;
+          nc = ga * cp;
+          nb = b_t + al * cm + ga * ap;
+          n0 = d0 + al * m0 + ga * p0;
+          n1 = d1 + al * m1 + ga * p1;
+          n2 = d2 + al * m2 + ga * p2;
+        }
+        __syncthreads();
+        a_t = na; b_t = nb; c_t = nc; d0 = n0; d1 = n1; d2 = n2;
+        sa[t] = a_t; sb[t] = b_t; sc[t] = c_t; sd0[t] = d0; sd1[t] = d1; sd2[t] = d2;
+        __syncthreads();
+      }
+      if (t < mi) {
+        const float yv = d0 / b_t, vv = d1 / b_t, wv = d2 / b_t;
+        float* row = A.fom_row + 3 * (size_t)(I.vec_off + beg + t);
+        row[0] = yv; row[1] = vv; row[2] = wv;
+        if (t == 0) { ch[4] = yv; ch[5] = vv; ch[6] = wv; }
+        if (t == mi - 1) { ch[7] = yv; ch[8] = vv; ch[9] = wv; }
+      }
+    }
+    if (!grid_sync(A.bar, A.status)) return;
+    // ---- B: cyclic separator system of each instance (order C) ----
+    if (b == 0)   // every CTA read the other parity's keys before the barrier above
+      for (int e = t; e < A.count; e += blockDim.x) {
+        A.fom_keys[4 * e + 2 * (par ^ 1)] = 0u;
+        A.fom_keys[4 * e + 2 * (par ^ 1) + 1] = 0u;
+      }
+    for (int i = b; i < A.count; i += G) {
+      if (s_done[i]) continue;
+      const Inst I = A.inst[i];
+      const int C = I.nchunk;
+      __syncthreads();
+      if (t < C) {
+        const float* ch = A.fom_chunk + (size_t)(I.chunk0 + t) * kFomChunkStride;
+        const float* nx = A.fom_chunk + (size_t)(I.chunk0 + (t + 1) % C) * kFomChunkStride;
+        const float as_ = __ldcg(ch + 0), bs_ = __ldcg(ch + 1), cs_ = __ldcg(ch + 2), ds_ = __ldcg(ch + 3);
+        const float yL = __ldcg(ch + 7), vL = __ldcg(ch + 8), wL = __ldcg(ch + 9);
+        const float y0 = __ldcg(nx + 4), v0 = __ldcg(nx + 5), w0 = __ldcg(nx + 6);
+        ra[t] = as_ * vL;
+        rb[t] = bs_ + as_ * wL + cs_ * v0;
+        rc[t] = cs_ * w0;
+        rd[t] = ds_ - as_ * yL - cs_ * y0;
+      }
+      __syncthreads();
+      for (int s = 1; s < C; s <<= 1) {
+        float na = 0.f, nb = 0.f, nc = 0.f, nd = 0.f;
+        if (t < C) {
+          const int tm = (t - s + C) % C, tp = (t + s) % C;
+          const float al = -ra[t] / rb[tm], ga = -rc[t] / rb[tp];
+          na = al * ra[tm];
+          nc = ga * rc[tp];
+          nb = rb[t] + al * rc[tm] + ga * ra[tp];
+          nd = rd[t] + al * rd[tm] + ga * rd[tp];
+        }
+        __syncthreads();
+        if (t < C) { ra[t] = na; rb[t] = nb; rc[t] = nc; rd[t] = nd; }
+        __syncthreads();
+      }
+      if (t < C) A.fom_sep[I.chunk0 + t] = rd[t] / (ra[t] + rb[t] + rc[t]);
+    }
+    if (!grid_sync(A.bar, A.status)) return;
+    // ---- C: update and per-instance maxima ----
+    for (int q = b; q < A.nchunks; q += G) {
+      const int i = A.chunk_inst[q];
+      if (s_done[i]) continue;
+      const Inst I = A.inst[i];
+      const int C = I.nchunk, c = A.chunk_c[q];
+      const int64_t n = I.n;
+      const int64_t beg = fchunk_begin(c, C, n);
+      const int m = (int)(fchunk_begin(c + 1, C, n) - beg);
+      const int mi = m - 1;
+      const float s_left = __ldcg(&A.fom_sep[I.chunk0 + (c - 1 + C) % C]);
+      const float s_self = __ldcg(&A.fom_sep[I.chunk0 + c]);
+      unsigned int kd = 0u, ku = 0u;
+      if (t < m) {
+        float dl;
+        if (t < mi) {
+          const float* row = A.fom_row + 3 * (size_t)(I.vec_off + beg + t);
+          dl = __ldcg(row) + __ldcg(row + 1) * s_left + __ldcg(row + 2) * s_self;
+        } else {
+          dl = s_self;
+        }
+        const double* ucur = (it == 1 ? A.y_corr : A.y_new) + I.vec_off;
+        const double u = __ldcg(&ucur[beg + t]) + (double)dl;
+        A.y_new[I.vec_off + beg + t] = u;
+        kd = __float_as_uint(fabsf(dl));
+        ku = isfinite(u) ? __float_as_uint(fabsf((float)u)) : 0x7fc00000u;
+        if (!isfinite(dl)) kd = 0x7fc00000u;
+      }
+      kd = block_max_u32(kd, redu);
+      ku = block_max_u32(ku, redu);
+      if (t == 0) {
+        atomicMax(&A.fom_keys[4 * i + 2 * par], kd);
+        atomicMax(&A.fom_keys[4 * i + 2 * par + 1], ku);
+      }
+    }
+    if (!grid_sync(A.bar, A.status)) return;
+    // ---- convergence (every CTA takes the same decisions from the same keys) ----
+    int any = 0, fail = 0;
+    for (int i = t; i < A.count; i += blockDim.x) {
+      if (s_done[i]) continue;
+      const Inst I = A.inst[i];
+      const unsigned int kd = __ldcg(&A.fom_keys[4 * i + 2 * par]);
+      const unsigned int ku = __ldcg(&A.fom_keys[4 * i + 2 * par + 1]);
+      if (kd >= 0x7f800000u || ku >= 0x7f800000u) {
+        if (b == 0) record_status(A.status, kStNonFinite);
+        fail = 1;
+      } else if ((double)__uint_as_float(kd) <= I.tol * (1.0 + (double)__uint_as_float(ku))) {
+        s_done[i] = 1;
+        if (b == 0) A.iters_fom[i] = it;
+      } else if (it >= I.maxit) {
+        if (b == 0) record_status(A.status, kStNoConv);
+        fail = 1;
+      } else {
+        any = 1;
+      }
+    }
+    fail = __syncthreads_or(fail);
+    any = __syncthreads_or(any);
+    if (fail || !any) return;
+  }
+}
+
+// ======================================================== event kernel ===
+
+// P1: yhat = d (y - q_ref) (and y_corr <- y), p1 partial = Phi^T yhat,
+// |yhat|^2 partial.
+template <int KB>
+__device__ void ev_p1_tile(const BArgs& A, SweepSmem& sm, int tile, int i) {
+  constexpr int RPT = Rpt<KB>::v;
+  constexpr int CR = kBT * RPT;
+  const Inst I = A.inst[i];
+  const int t = threadIdx.x;
+  const int k = A.rank[i];
+  const int N = I.n;
+  const float* phi = A.phi + I.phi_off;
+  const int r0 = A.tile_r0[tile], r1 = A.tile_r1[tile];
+  float acc[KB];
+#pragma unroll
+  for (int j = 0; j < KB; ++j) acc[j] = 0.f;
+  double yy = 0.0;
+  for (int c0 = r0; c0 < r1; c0 += CR) {
+    const int rows = min(CR, r1 - c0);
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr) {
+      const int e = rr * kBT + t;
+      if (e < rows) {
+        const size_t gi = (size_t)I.vec_off + c0 + e;
+        const double yn = __ldcg(&A.y_new[gi]);
+        A.y_corr[gi] = yn;
+        const double yh = I.d * (yn - A.q_ref[gi]);
+        yy = fma(yh, yh, yy);
+        const float yf = (float)yh;
+#pragma unroll
+        for (int j = 0; j < KB; ++j)
+          if (j < k) acc[j] = fmaf(__ldg(&phi[(size_t)j * N + c0 + e]), yf, acc[j]);
+      }
+    }
+  }
+  double* gp = A.gpart + (size_t)tile * kPS;
+  tile_reduce<KB>(acc, k, sm.red, gp);
+  __syncthreads();
+  const double ys = block_sum(yy, sm.dred);
+  if (t == 0) gp[kMaxR] = ys;
+}
+
+// P2: q1 = yhat - Phi p1, p2 partial = Phi^T q1, |q1|^2 partial.
+template <int KB>
+__device__ void ev_p2_tile(const BArgs& A, SweepSmem& sm, int tile, int i) {
+  constexpr int RPT = Rpt<KB>::v;
+  constexpr int CR = kBT * RPT;
+  const Inst I = A.inst[i];
+  const int t = threadIdx.x;
+  const int k = A.rank[i];
+  const int N = I.n;
+  const float* phi = A.phi + I.phi_off;
+  const int r0 = A.tile_r0[tile], r1 = A.tile_r1[tile];
+  for (int j = t; j < KB; j += kBT) sm.pf[j] = (j < k) ? (float)__ldcg(&A.ev_p[(size_t)i * kMaxCore + j]) : 0.f;
+  __syncthreads();
+  float acc[KB];
+#pragma unroll
+  for (int j = 0; j < KB; ++j) acc[j] = 0.f;
+  float qq = 0.f;
+  for (int c0 = r0; c0 < r1; c0 += CR) {
+    const int rows = min(CR, r1 - c0);
+    float x[RPT][KB];
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr) {
+      const int e = rr * kBT + t;
+#pragma unroll
+      for (int j = 0; j < KB; ++j) x[rr][j] = (e < rows && j < k) ? __ldg(&phi[(size_t)j * N + c0 + e]) : 0.f;
+    }
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr) {
+      const int e = rr * kBT + t;
+      if (e < rows) {
+        const size_t gi = (size_t)I.vec_off + c0 + e;
+        float v = (float)(I.d * (__ldcg(&A.y_corr[gi]) - A.q_ref[gi]));
+#pragma unroll
+        for (int j = 0; j < KB; ++j) v = fmaf(-x[rr][j], sm.pf[j], v);
+        A.qres[gi] = v;
+        qq = fmaf(v, v, qq);
+#pragma unroll
+        for (int j = 0; j < KB; ++j) acc[j] = fmaf(x[rr][j], v, acc[j]);
+      }
+    }
+  }
+  double* gp = A.gpart2 + (size_t)tile * kPS;
+  tile_reduce<KB>(acc, k, sm.red, gp);
+  __syncthreads();
+  const double qs = block_sum((double)qq, sm.dred);
+  if (t == 0) gp[kMaxR] = qs;
+}
+
+// Rotation Phi <- [Phi, q/rho] U(:, 0:k') with q = q1 - Phi p2 (the second
+// pass of classical Gram-Schmidt, which keeps q orthogonal to Phi at the
+// working precision even when yhat lies almost in span(Phi)), and the Gram
+// partial of the rotated rows.
+template <int KB>
+__device__ void ev_rot_tile(const BArgs& A, SweepSmem& sm, int tile, int i) {
+  constexpr int RPT = Rpt<KB>::v;
+  constexpr int CR = kBT * RPT;
+  const Inst I = A.inst[i];
+  const int t = threadIdx.x;
+  const double* esc = A.ev_sc + (size_t)i * 8;
+  const float qinv = (float)__ldcg(&esc[1]);
+  const int kn = (int)__ldcg(&esc[2]);
+  const int k = (int)__ldcg(&esc[3]);
+  const int N = I.n;
+  float* phi = A.phi + I.phi_off;
+  const int r0 = A.tile_r0[tile], r1 = A.tile_r1[tile];
+  for (int j = t; j < KB; j += kBT) sm.pf[j] = (j < k) ? (float)__ldcg(&A.ev_p2[(size_t)i * kMaxCore + j]) : 0.f;
+  const float* ug = A.ev_u + (size_t)i * kMaxCore * kMaxR;
+  for (int e = t; e < (KB + 1) * KB; e += kBT) {     // rows 0..KB; rows past k are zero
+    const int row = e / KB, col = e % KB;
+    sm.U[row * KB + col] = (row <= k && col < kn) ? __ldcg(&ug[row * kMaxR + col]) : 0.f;
+  }
+  float m[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) m[q] = 0.f;
+  __syncthreads();
+  for (int c0 = r0; c0 < r1; c0 += CR) {
+    const int rows = min(CR, r1 - c0);
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr) {
+      const int e = rr * kBT + t;
+      float x[KB];
+#pragma unroll
+      for (int j = 0; j < KB; ++j) x[j] = (e < rows && j < k) ? phi[(size_t)j * N + c0 + e] : 0.f;
+      if (e < rows) {
+        const size_t gi = (size_t)I.vec_off + c0 + e;
+        float q = __ldcg(&A.qres[gi]);
+#pragma unroll
+        for (int j = 0; j < KB; ++j) q = fmaf(-x[j], sm.pf[j], q);
+        const float qh = q * qinv;
+#pragma unroll
+        for (int c = 0; c < KB; ++c) {
+          float v = qh * sm.U[k * KB + c];
+#pragma unroll
+          for (int j = 0; j < KB; ++j) v = fmaf(x[j], sm.U[j * KB + c], v);
+          if (c < kn) {
+            phi[(size_t)c * N + c0 + e] = v;
+            sm.P[e * KB + c] = v;
+          } else {
+            if (c < k) phi[(size_t)c * N + c0 + e] = 0.f;
+            sm.P[e * KB + c] = 0.f;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    blk_accum<KB>(sm.P, sm.P, rows, m);
+    __syncthreads();
+  }
+  for (int e = t; e < kn * kn; e += kBT) sm.Gt[e] = 0.f;
+  __syncthreads();
+  blk_flush<KB>(m, kn, sm.Gt);
+  __syncthreads();
+  float* mp = A.mpart + (size_t)tile * kMaxR * kMaxR;
+  for (int e = t; e < kn * kn; e += kBT) mp[e] = sm.Gt[e];
+}
+
+// Phi <- Phi R^-1: each row y solves y R = x (FP32, R from the FP64 Cholesky).
+template <int KB>
+__device__ void ev_apply_tile(const BArgs& A, SweepSmem& sm, int tile, int i) {
+  constexpr int RPT = Rpt<KB>::v;
+  constexpr int CR = kBT * RPT;
+  const Inst I = A.inst[i];
+  const int t = threadIdx.x;
+  const int kn = (int)__ldcg(&A.ev_sc[(size_t)i * 8 + 2]);
+  const int N = I.n;
+  float* phi = A.phi + I.phi_off;
+  const int r0 = A.tile_r0[tile], r1 = A.tile_r1[tile];
+  const float* rg = A.ev_r + (size_t)i * kMaxR * kMaxR;
+  for (int e = t; e < KB * KB; e += kBT) {
+    const int j = e / KB, c = e % KB;
+    sm.R[j * KB + c] = (j < kn && c < kn) ? __ldcg(&rg[j * kMaxR + c]) : 0.f;
+  }
+  for (int j = t; j < KB; j += kBT) sm.Rd[j] = (j < kn) ? 1.f / __ldcg(&rg[j * kMaxR + j]) : 0.f;
+  __syncthreads();
+  for (int c0 = r0; c0 < r1; c0 += CR) {
+    const int rows = min(CR, r1 - c0);
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr) {
+      const int e = rr * kBT + t;
+      if (e < rows) {
+        float y[KB];
+#pragma unroll
+        for (int j = 0; j < KB; ++j) y[j] = (j < kn) ? __ldcg(&phi[(size_t)j * N + c0 + e]) : 0.f;
+#pragma unroll
+        for (int j = 0; j < KB; ++j) {
+          float v = y[j];
+#pragma unroll
+          for (int l = 0; l < j; ++l) v = fmaf(-y[l], sm.R[l * KB + j], v);
+          y[j] = v * sm.Rd[j];
+        }
+#pragma unroll
+        for (int j = 0; j < KB; ++j)
+          if (j < kn) phi[(size_t)j * N + c0 + e] = y[j];
+      }
+    }
+  }
+}
+
+// Core SVD of instance i in one CTA: K = [[lam Sigma, p], [0, rho]], roots of
+// the secular equation one per warp, zhat (Gu-Eisenstat), vectors, sorted;
+// then truncation, sigma, and the transferred state U(0:k, 0:k')^T a.
+__device__ void ev_core(const BArgs& A, CoreSmem& sm, int i) {
+  const Inst I = A.inst[i];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+  const int k = A.rank[i];
+  const int n = k + 1;
+  double* pv = A.ev_p + (size_t)i * kMaxCore;
+  double* esc = A.ev_sc + (size_t)i * 8;
+  // p2 and |q1|^2, then p = p1 + p2, rho^2 = |q1|^2 - |p2|^2
+  sum_tiles(A.gpart2, I.tile0, I.tile1, k, 0, sm.z);   // p2
+  __syncthreads();
+  // |q1|^2 (offset kMaxR of each tile vector)
+  sum_tiles(A.gpart2, I.tile0, I.tile1, 1, kMaxR, &sm.sc[0]);
+  __syncthreads();
+  if (t == 0) {
+    double p2n = 0.0;
+    for (int j = 0; j < k; ++j) p2n += sm.z[j] * sm.z[j];
+    double rho2 = sm.sc[0] - p2n;
+    double rho = sqrt(fmax(rho2, 0.0));
+    const double ynorm = sqrt(__ldcg(&esc[0]));
+    const double s1 = (k > 0) ? A.sigma[(size_t)i * kMaxR] : 0.0;
+    const bool keep = rho > I.rank_tol * fmax(ynorm, s1);
+    if (!keep) rho = 0.0;
+    for (int j = 0; j < k; ++j) {
+      const double p = __ldcg(&pv[j]) + sm.z[j];
+      A.ev_p2[(size_t)i * kMaxCore + j] = sm.z[j];
+      pv[j] = p;
+      sm.z[j] = p;
+      sm.d_desc[j] = I.lam * A.sigma[(size_t)i * kMaxR + j];
+    }
+    sm.d_desc[k] = 0.0;
+    sm.z[k] = rho;
+    esc[1] = keep ? 1.0 / rho : 0.0;
+    secular_setup(sm.S, n, sm.d_desc, sm.z);
+  }
+  for (int j = t; j < k; j += blockDim.x) sm.aold[j] = A.a[(size_t)i * kMaxR + j];
+  __syncthreads();
+  const SecularSetup& S = sm.S;
+  const int k2 = S.k2;
+  for (int j = wid; j < k2; j += nw) {
+    int o;
+    double tau;
+    secular_root(S, j, o, tau);
+    if (lane == 0) { sm.tau[j] = tau; sm.orig[j] = (double)o; }
+  }
+  __syncthreads();
+  for (int ii = wid; ii < k2; ii += nw) {
+    double pr = 1.0;
+    for (int j = lane; j < k2; j += 32) {
+      const int o = (int)sm.orig[j];
+      const double tau = sm.tau[j];
+      const double num = root_minus(S, o, tau, ii) * root_plus(S, o, tau, ii);
+      double den;
+      if (j == k2 - 1) den = 1.0;
+      else if (j < ii) den = (S.D[j] - S.D[ii]) * (S.D[j] + S.D[ii]);
+      else den = (S.D[j + 1] - S.D[ii]) * (S.D[j + 1] + S.D[ii]);
+      pr *= num / den;
+    }
+    pr = warp_prod(pr);
+    if (lane == 0) sm.zhat[ii] = copysign(sqrt(fabs(pr)), S.Z[ii]);
+  }
+  if (t == 0) {
+    for (int e = 0; e < k2; ++e) sm.val[e] = S.D[(int)sm.orig[e]] + sm.tau[e];
+    int c = k2;
+    for (int p = 0; p < n; ++p)
+      if (S.defl[p]) { sm.val[c] = S.dpos[p]; sm.order[c] = p; ++c; }
+  }
+  __syncthreads();
+  if (t < n) {
+    const double v = sm.val[t];
+    int ps = 0;
+    for (int e = 0; e < n; ++e) {
+      const double w = sm.val[e];
+      if (w > v || (w == v && e < t)) ++ps;
+    }
+    sm.pos[t] = ps;
+    sm.defp[t] = (t >= k2) ? sm.order[t] : -1;
+  }
+  __syncthreads();
+  for (int e = wid; e < n; e += nw) {
+    double* pw = sm.pv[wid];
+    for (int p = lane; p < n; p += 32) pw[p] = 0.0;
+    __syncwarp();
+    if (e < k2) {
+      const int o = (int)sm.orig[e];
+      const double tau = sm.tau[e];
+      double vec[3];
+      double ss = 0.0;
+      for (int mm = 0; mm < 3; ++mm) {
+        const int ci = lane + 32 * mm;
+        vec[mm] = 0.0;
+        if (ci < k2) {
+          const double den = -(root_minus(S, o, tau, ci)) * root_plus(S, o, tau, ci);
+          const double u = sm.zhat[ci] / den;
+          vec[mm] = u;
+          ss += u * u;
+        }
+      }
+      ss = warp_sum(ss);
+      const double inv = 1.0 / sqrt(ss);
+      for (int mm = 0; mm < 3; ++mm) {
+        const int ci = lane + 32 * mm;
+        if (ci < k2) pw[S.cidx[ci]] = vec[mm] * inv;
+      }
+    } else if (lane == 0) {
+      pw[sm.defp[e]] = 1.0;
+    }
+    __syncwarp();
+    if (lane == 0)
+      for (int q = S.nrot - 1; q >= 0; --q) {
+        const int pa = S.rot_a[q], pb = S.rot_b[q];
+        const double c = S.rot_c[q], s = S.rot_s[q];
+        const double xa = pw[pa], xb = pw[pb];
+        pw[pa] = c * xa + s * xb;
+        pw[pb] = -s * xa + c * xb;
+      }
+    __syncwarp();
+    const int col = sm.pos[e];
+    for (int p = lane; p < n; p += 32) sm.U[(n - 1 - p) * kMaxCore + col] = pw[p];
+    if (lane == 0) sm.sbar[col] = sm.val[e];
+    __syncwarp();
+  }
+  __syncthreads();
+  // truncation: singular values above rank_tol * s_1, at most r
+  int kn = 0;
+  {
+    const double s0 = sm.sbar[0];
+    for (int j = 0; j < n && j < I.r; ++j)
+      if (s0 > 0.0 && sm.sbar[j] > I.rank_tol * s0) ++kn;
+  }
+  float* ug = A.ev_u + (size_t)i * kMaxCore * kMaxR;
+  for (int e = t; e < n * kn; e += blockDim.x) {
+    const int row = e / kn, col = e % kn;
+    ug[row * kMaxR + col] = (float)sm.U[row * kMaxCore + col];
+  }
+  if (t < I.r) {
+    A.sigma[(size_t)i * kMaxR + t] = (t < kn) ? sm.sbar[t] : 0.0;
+    double v = 0.0;
+    if (t < kn)
+      for (int j = 0; j < k; ++j) v = fma(sm.U[j * kMaxCore + t], sm.aold[j], v);
+    A.ev_anew[(size_t)i * kMaxR + t] = v;
+  }
+  if (t == 0) { esc[2] = (double)kn; esc[3] = (double)k; }
+  __syncthreads();
+}
+
+// Gram matrix of the rotated basis, FP64 Cholesky G = R^T R (R upper), the
+// state a <- R a_new, rank and sigma bookkeeping.
+__device__ void ev_chol(const BArgs& A, CholSmem& sm, int i) {
+  const Inst I = A.inst[i];
+  const int t = threadIdx.x;
+  const int kn = (int)__ldcg(&A.ev_sc[(size_t)i * 8 + 2]);
+  for (int e = t; e < kn * kn; e += blockDim.x) {
+    double s = 0.0;
+    for (int tt = I.tile0; tt < I.tile1; ++tt) s += (double)__ldcg(&A.mpart[(size_t)tt * kMaxR * kMaxR + e]);
+    const int j = e / kn, l = e % kn;
+    sm.G[j * kMaxR + l] = s;
+  }
+  for (int j = t; j < kn; j += blockDim.x) sm.anew[j] = __ldcg(&A.ev_anew[(size_t)i * kMaxR + j]);
+  __syncthreads();
+  // right-looking Cholesky on the upper triangle (row j of R = row j of G / d)
+  for (int j = 0; j < kn; ++j) {
+    if (t == 0) sm.d = sqrt(fmax(sm.G[j * kMaxR + j], DBL_MIN));
+    __syncthreads();
+    const double d = sm.d, inv = 1.0 / d;
+    for (int c = j + t; c < kn; c += blockDim.x) sm.G[j * kMaxR + c] = (c == j) ? d : sm.G[j * kMaxR + c] * inv;
+    __syncthreads();
+    const int rem = kn - j - 1;
+    for (int e = t; e < rem * rem; e += blockDim.x) {
+      const int l = j + 1 + e / rem, c = j + 1 + e % rem;
+      if (c >= l) sm.G[l * kMaxR + c] -= sm.G[j * kMaxR + l] * sm.G[j * kMaxR + c];
+    }
+    __syncthreads();
+  }
+  float* rg = A.ev_r + (size_t)i * kMaxR * kMaxR;
+  for (int e = t; e < kn * kn; e += blockDim.x) {
+    const int j = e / kn, c = e % kn;
+    rg[j * kMaxR + c] = (c >= j) ? (float)sm.G[j * kMaxR + c] : 0.f;
+  }
+  if (t < I.r) {
+    double v = 0.0;
+    if (t < kn)
+      for (int c = t; c < kn; ++c) v = fma(sm.G[t * kMaxR + c], sm.anew[c], v);
+    A.a[(size_t)i * kMaxR + t] = v;
+  }
+  if (t == 0) {
+    A.rank[i] = kn;
+    A.need_jac[i] = 1;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBT, 1) batch_event_kernel(BArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SweepSmem& sw = *reinterpret_cast<SweepSmem*>(smem_raw);
+  CoreSmem& cs = *reinterpret_cast<CoreSmem*>(smem_raw);
+  CholSmem& ch = *reinterpret_cast<CholSmem*>(smem_raw);
+  const int G = gridDim.x, b = blockIdx.x;
+  const long long M = *A.M;
+  int q;
+  // ---- P1 ----
+  while ((q = next_tile(&A.ctl[0], A.ntiles, &sw.q)) >= 0) {
+    const int tile = A.order[q], i = A.tile_inst[tile];
+    if (!is_event(A.inst[i], M)) continue;
+    with_bucket(A.inst[i].r, [&](auto kb) { ev_p1_tile<decltype(kb)::value>(A, sw, tile, i); });
+  }
+  if (!grid_sync(A.bar, A.status)) return;
+  // ---- p1 and |yhat|^2 per instance ----
+  for (int i = b; i < A.count; i += G) {
+    const Inst I = A.inst[i];
+    if (!is_event(I, M)) continue;
+    __syncthreads();
+    sum_tiles(A.gpart, I.tile0, I.tile1, A.rank[i], 0, A.ev_p + (size_t)i * kMaxCore);
+    sum_tiles(A.gpart, I.tile0, I.tile1, 1, kMaxR, A.ev_sc + (size_t)i * 8);
+  }
+  if (!grid_sync(A.bar, A.status)) return;
+  // ---- P2 ----
+  while ((q = next_tile(&A.ctl[1], A.ntiles, &sw.q)) >= 0) {
+    const int tile = A.order[q], i = A.tile_inst[tile];
+    if (!is_event(A.inst[i], M)) continue;
+    with_bucket(A.inst[i].r, [&](auto kb) { ev_p2_tile<decltype(kb)::value>(A, sw, tile, i); });
+  }
+  if (!grid_sync(A.bar, A.status)) return;
+  // ---- core SVD per instance ----
+  for (int i = b; i < A.count; i += G) {
+    if (!is_event(A.inst[i], M)) continue;
+    __syncthreads();
+    ev_core(A, cs, i);
+  }
+  if (!grid_sync(A.bar, A.status)) return;
+  // ---- rotation + Gram ----
+  while ((q = next_tile(&A.ctl[2], A.ntiles, &sw.q)) >= 0) {
+    const int tile = A.order[q], i = A.tile_inst[tile];
+    if (!is_event(A.inst[i], M)) continue;
+    with_bucket(A.inst[i].r, [&](auto kb) { ev_rot_tile<decltype(kb)::value>(A, sw, tile, i); });
+  }
+  if (!grid_sync(A.bar, A.status)) return;
+  // ---- Cholesky per instance ----
+  for (int i = b; i < A.count; i += G) {
+    if (!is_event(A.inst[i], M)) continue;
+    __syncthreads();
+    ev_chol(A, ch, i);
+  }
+  if (!grid_sync(A.bar, A.status)) return;
+  // ---- Phi <- Phi R^-1 ----
+  while ((q = next_tile(&A.ctl[3], A.ntiles, &sw.q)) >= 0) {
+    const int tile = A.order[q], i = A.tile_inst[tile];
+    if (!is_event(A.inst[i], M)) continue;
+    with_bucket(A.inst[i].r, [&](auto kb) { ev_apply_tile<decltype(kb)::value>(A, sw, tile, i); });
+  }
+}
+
+// Lift of one instance: out = q_ref + d^-1 Phi a.
+__global__ void batch_lift_kernel(const float* phi, const double* q_ref, const double* a, int n, int k,
+                                  double dinv, double* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int j = 0; j < k; ++j) s = fmaf(phi[(size_t)j * n + i], (float)a[j], s);
+    out[i] = fma(dinv, (double)s, q_ref[i]);
+  }
+}
+
+}  // namespace
+}  // namespace rom
+
+// ============================================================= host side ===
+
+using namespace rom;
+
+struct rom_batch {
+  int count;
+  cudaStream_t stream;
+  int grid_sweep, grid_fom;
+  long long M;                 // online steps done by every instance
+  int ntiles, nchunks, fom_maxit;
+  int poisoned;
+  std::vector<Inst> hinst;
+  std::vector<rom_config> cfg;
+  std::vector<long long> w_init;
+  BArgs A;                     // device pointers
+  double* lift;                // lifted state of one instance (max N)
+  std::vector<void*> allocs;
+  // per-phase timing: 0 steps, 1 coarse FOM, 2 iSVD
+  int prof_on;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_phase;
+  double prof_ms[3];
+  long long prof_cnt[3];
+};
+
+namespace {
+
+#define BCK(x)                                      \
+  do {                                              \
+    cudaError_t e_ = (x);                           \
+    if (e_ != cudaSuccess) {                        \
+      cudaGetLastError();                           \
+      return ROM_ECUDA;                             \
+    }                                               \
+  } while (0)
+
+template <typename T>
+cudaError_t balloc(rom_batch* B, T** p, size_t n) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+  if (e != cudaSuccess) return e;
+  B->allocs.push_back(v);
+  *p = static_cast<T*>(v);
+  return cudaSuccess;
+}
+
+void batch_free(rom_batch* B) {
+  for (void* p : B->allocs) cudaFree(p);
+  B->allocs.clear();
+  for (cudaEvent_t e : B->ev) cudaEventDestroy(e);
+  B->ev.clear();
+}
+
+rom_status batch_finish(rom_batch* B) {
+  cudaError_t e = cudaStreamSynchronize(B->stream);
+  if (e != cudaSuccess) { B->poisoned = 1; return ROM_ECUDA; }
+  int st = 0;
+  e = cudaMemcpy(&st, B->A.status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) { B->poisoned = 1; return ROM_ECUDA; }
+  if (st != 0) {
+    cudaMemset(B->A.status, 0, sizeof(int));
+    cudaMemset(B->A.bar, 0, sizeof(GridBarrier));
+    B->poisoned = 1;   // instances may have stopped mid-step
+  }
+  switch (st) {
+    case 0: return ROM_OK;
+    case kStNoConv: return ROM_ENOCONV;
+    case kStNonFinite: return ROM_ENONFINITE;
+    case kStTimeout: return ROM_ETIMEOUT;
+    default: return ROM_ECUDA;
+  }
+}
+
+cudaError_t prof_mark(rom_batch* B, int phase) {
+  if (!B->prof_on) return cudaSuccess;
+  cudaEvent_t e;
+  cudaError_t r = cudaEventCreate(&e);
+  if (r != cudaSuccess) return r;
+  B->ev.push_back(e);
+  B->ev_phase.push_back(phase);
+  return cudaEventRecord(e, B->stream);
+}
+
+cudaError_t prof_collect(rom_batch* B) {
+  cudaError_t r = cudaStreamSynchronize(B->stream);
+  if (r != cudaSuccess) return r;
+  for (size_t e = 0; e + 1 < B->ev.size(); e += 2) {
+    float ms = 0.f;
+    r = cudaEventElapsedTime(&ms, B->ev[e], B->ev[e + 1]);
+    if (r != cudaSuccess) return r;
+    B->prof_ms[B->ev_phase[e]] += ms;
+    B->prof_cnt[B->ev_phase[e]] += 1;
+  }
+  for (cudaEvent_t e : B->ev) cudaEventDestroy(e);
+  B->ev.clear();
+  B->ev_phase.clear();
+  return cudaSuccess;
+}
+
+cudaError_t launch_coop(const void* fn, int grid, int block, size_t smem, BArgs& A, cudaStream_t s) {
+  void* args[] = {&A};
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, s);
+}
+
+cudaError_t run_steps(rom_batch* B, int nsteps) {
+  cudaError_t e = cudaMemsetAsync(B->A.ctl, 0, 8 * sizeof(unsigned int), B->stream);
+  if (e != cudaSuccess) return e;
+  B->A.nsteps = nsteps;
+  if ((e = prof_mark(B, 0)) != cudaSuccess) return e;
+  e = launch_coop((const void*)batch_steps_kernel, B->grid_sweep, kBT, sizeof(StepSmem), B->A, B->stream);
+  if (e != cudaSuccess) return e;
+  return prof_mark(B, 0);
+}
+
+cudaError_t run_event(rom_batch* B) {
+  cudaError_t e = prof_mark(B, 1);
+  if (e != cudaSuccess) return e;
+  e = launch_coop((const void*)batch_fom_kernel, B->grid_fom, kFomT, 0, B->A, B->stream);
+  if (e != cudaSuccess) return e;
+  if ((e = prof_mark(B, 1)) != cudaSuccess) return e;
+  e = cudaMemsetAsync(B->A.ctl, 0, 8 * sizeof(unsigned int), B->stream);
+  if (e != cudaSuccess) return e;
+  if ((e = prof_mark(B, 2)) != cudaSuccess) return e;
+  size_t smem = std::max(sizeof(SweepSmem), std::max(sizeof(CoreSmem), sizeof(CholSmem)));
+  e = launch_coop((const void*)batch_event_kernel, B->grid_sweep, kBT, smem, B->A, B->stream);
+  if (e != cudaSuccess) return e;
+  return prof_mark(B, 2);
+}
+
+size_t event_smem() { return std::max(sizeof(SweepSmem), std::max(sizeof(CoreSmem), sizeof(CholSmem))); }
+
+}  // namespace
+
+extern "C" {
+
+rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int32_t count, void* stream,
+                          rom_batch** out) {
+  if (!out) return ROM_EINVAL;
+  *out = nullptr;
+  if (!cfgs || !q0s || count < 1 || count > kMaxBatch) return ROM_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    const rom_config& c = cfgs[i];
+    if (c.problem != ROM_BURGERS || c.precision != ROM_MIXED_FP32 || c.n_s != 0 || c.n_var != 1 ||
+        c.r < 1 || c.r > kMaxR || c.n_cells < 256 || c.n_cells > 131072 || c.z < 1 || !q0s[i])
+      return ROM_EINVAL;
+  }
+  int dev = 0;
+  BCK(cudaGetDevice(&dev));
+  rom_batch* B = new rom_batch;
+  B->count = count;
+  B->stream = (cudaStream_t)stream;
+  B->M = 0;
+  B->poisoned = 0;
+  B->prof_on = 0;
+  for (int p = 0; p < 3; ++p) { B->prof_ms[p] = 0.0; B->prof_cnt[p] = 0; }
+  B->cfg.assign(cfgs, cfgs + count);
+  memset(&B->A, 0, sizeof(BArgs));
+  // ---- layout: packed bases and vectors, tiles, FOM chunks ----
+  std::vector<int> tinst, tr0, tr1, cinst, cc;
+  long long phi_tot = 0, vec_tot = 0, nmax = 1;
+  int fom_maxit = 1;
+  B->hinst.resize(count);
+  for (int i = 0; i < count; ++i) {
+    const rom_config& c = cfgs[i];
+    Inst& I = B->hinst[i];
+    I.n = (int)c.n_cells;
+    I.r = c.r;
+    I.z = c.z;
+    I.maxit = c.newton_max;
+    I.nu = c.nu;
+    I.dt = c.dt;
+    I.lam = c.lambda;
+    I.tol = c.newton_tol;
+    I.rank_tol = c.rank_tol > 0.0 ? c.rank_tol : 1e-5;
+    I.phi_off = phi_tot;
+    nmax = std::max(nmax, (long long)I.n);
+    I.vec_off = vec_tot;
+    phi_tot += ((long long)I.n * I.r + 63) / 64 * 64;
+    vec_tot += ((long long)I.n + 31) / 32 * 32;
+    I.tile0 = (int)tinst.size();
+    for (int r0 = 0; r0 < I.n; r0 += kTileRows) {
+      tinst.push_back(i);
+      tr0.push_back(r0);
+      tr1.push_back(std::min(I.n, r0 + kTileRows));
+    }
+    I.tile1 = (int)tinst.size();
+    int C = 4;
+    while ((I.n + C - 1) / C > kFomT && C < kMaxChunks) C *= 2;
+    if ((I.n + C - 1) / C > kFomT) { delete B; return ROM_EINVAL; }
+    I.chunk0 = (int)cinst.size();
+    I.nchunk = C;
+    for (int q = 0; q < C; ++q) { cinst.push_back(i); cc.push_back(q); }
+    fom_maxit = std::max(fom_maxit, c.newton_max);
+  }
+  B->ntiles = (int)tinst.size();
+  B->nchunks = (int)cinst.size();
+  B->fom_maxit = fom_maxit;
+  // queue order: decreasing cost (rows x rank bucket), ties by tile id
+  std::vector<int> order(B->ntiles);
+  for (int q = 0; q < B->ntiles; ++q) order[q] = q;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const long long cx = (long long)(tr1[x] - tr0[x]) * bucket_of(B->hinst[tinst[x]].r);
+    const long long cy = (long long)(tr1[y] - tr0[y]) * bucket_of(B->hinst[tinst[y]].r);
+    return cx > cy;
+  });
+  BArgs& A = B->A;
+  A.count = count;
+  A.ntiles = B->ntiles;
+  A.nchunks = B->nchunks;
+  A.fom_maxit = fom_maxit;
+  cudaError_t e = cudaSuccess;
+  Inst* d_inst = nullptr;
+  int *d_ti = nullptr, *d_r0 = nullptr, *d_r1 = nullptr, *d_order = nullptr, *d_ci = nullptr, *d_cc = nullptr;
+#define BA(p, n) \
+  if (e == cudaSuccess) e = balloc(B, &(p), (size_t)(n))
+  BA(d_inst, count); BA(d_ti, B->ntiles); BA(d_r0, B->ntiles); BA(d_r1, B->ntiles); BA(d_order, B->ntiles);
+  BA(d_ci, B->nchunks); BA(d_cc, B->nchunks);
+  BA(A.phi, phi_tot); BA(A.q_ref, vec_tot); BA(A.y_corr, vec_tot); BA(A.y_new, vec_tot);
+  BA(A.a, (size_t)count * kMaxR); BA(A.an, (size_t)count * kMaxR); BA(A.sigma, (size_t)count * kMaxR);
+  BA(A.sweeps, count); BA(A.rank, count); BA(A.need_jac, count); BA(A.active, count); BA(A.iters_rom, count); BA(A.iters_fom, count);
+  BA(A.jlu, (size_t)count * kMaxR * kMaxR); BA(A.jpiv, (size_t)count * kMaxR);
+  BA(A.gpart, (size_t)B->ntiles * kPS); BA(A.gpart2, (size_t)B->ntiles * kPS);
+  BA(A.mpart, (size_t)B->ntiles * kMaxR * kMaxR);
+  BA(A.fom_row, 3 * (size_t)vec_tot); BA(A.fom_chunk, (size_t)B->nchunks * kFomChunkStride);
+  BA(A.fom_sep, B->nchunks); BA(A.fom_keys, 4 * (size_t)count);
+  BA(A.ev_p, (size_t)count * kMaxCore); BA(A.ev_p2, (size_t)count * kMaxCore); BA(A.ev_sc, (size_t)count * 8);
+  BA(A.qres, vec_tot);
+  BA(A.ev_u, (size_t)count * kMaxCore * kMaxR); BA(A.ev_anew, (size_t)count * kMaxR);
+  BA(A.ev_r, (size_t)count * kMaxR * kMaxR); BA(A.ctl, 8); BA(A.M, 1); BA(A.bar, 1); BA(A.status, 1);
+  BA(B->lift, nmax);
+#undef BA
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    batch_free(B);
+    delete B;
+    return ROM_ENOMEM;
+  }
+  A.inst = d_inst;
+  A.tile_inst = d_ti; A.tile_r0 = d_r0; A.tile_r1 = d_r1; A.order = d_order;
+  A.chunk_inst = d_ci; A.chunk_c = d_cc;
+  cudaStream_t s = B->stream;
+  auto fail = [&](rom_status st) {
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    batch_free(B);
+    delete B;
+    return st;
+  };
+  const double* qref_d = A.q_ref;
+  if (cudaMemsetAsync(A.phi, 0, sizeof(float) * phi_tot, s) != cudaSuccess ||
+      cudaMemsetAsync(A.a, 0, sizeof(double) * count * kMaxR, s) != cudaSuccess ||
+      cudaMemsetAsync(A.sigma, 0, sizeof(double) * count * kMaxR, s) != cudaSuccess ||
+      cudaMemsetAsync(A.need_jac, 0, sizeof(int) * count, s) != cudaSuccess ||
+      cudaMemsetAsync(A.iters_rom, 0, sizeof(int) * count, s) != cudaSuccess ||
+      cudaMemsetAsync(A.iters_fom, 0, sizeof(int) * count, s) != cudaSuccess ||
+      cudaMemsetAsync(A.sweeps, 0, sizeof(long long) * count, s) != cudaSuccess ||
+      cudaMemsetAsync(A.M, 0, sizeof(long long), s) != cudaSuccess ||
+      cudaMemsetAsync(A.bar, 0, sizeof(GridBarrier), s) != cudaSuccess ||
+      cudaMemsetAsync(A.status, 0, sizeof(int), s) != cudaSuccess)
+    return fail(ROM_ECUDA);
+  // ---- offline stage of every instance (training FOM, POD, initial state,
+  //      first correction snapshot) through the single-instance path ----
+  B->w_init.resize(count);
+  for (int i = 0; i < count; ++i) {
+    rom_ctx* ctx = nullptr;
+    rom_status st = rom_init(&cfgs[i], q0s[i], stream, &ctx);
+    if (st != ROM_OK) return fail(st);
+    Inst& I = B->hinst[i];
+    const size_t N = (size_t)I.n;
+    double dv = 1.0;
+    bool ok = cudaMemcpyAsync(A.phi + I.phi_off, ctx->d.phi32, sizeof(float) * N * I.r, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+              cudaMemcpyAsync(const_cast<double*>(qref_d) + I.vec_off, ctx->d.q_ref, sizeof(double) * N, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+              cudaMemcpyAsync(A.y_corr + I.vec_off, ctx->d.y_corr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+              cudaMemcpyAsync(A.a + (size_t)i * kMaxR, ctx->d.a, sizeof(double) * I.r, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+              cudaMemcpyAsync(A.sigma + (size_t)i * kMaxR, ctx->d.sigma, sizeof(double) * I.r, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+              cudaMemcpyAsync(A.rank + i, ctx->d.rank, sizeof(int), cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+              cudaMemcpyAsync(&dv, ctx->d.dvals, sizeof(double), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+              cudaStreamSynchronize(s) == cudaSuccess;
+    I.rank_tol = ctx->cfg.rank_tol;
+    B->w_init[i] = ctx->step;
+    rom_destroy(ctx);
+    if (!ok) return fail(ROM_ECUDA);
+    I.d = dv;
+    I.dinv = 1.0 / dv;
+  }
+  {
+    std::vector<int> ones(count, 1);
+    if (cudaMemcpyAsync(A.need_jac, ones.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_inst, B->hinst.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_ti, tinst.data(), sizeof(int) * B->ntiles, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_r0, tr0.data(), sizeof(int) * B->ntiles, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_r1, tr1.data(), sizeof(int) * B->ntiles, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_order, order.data(), sizeof(int) * B->ntiles, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_ci, cinst.data(), sizeof(int) * B->nchunks, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_cc, cc.data(), sizeof(int) * B->nchunks, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return fail(ROM_ECUDA);
+  }
+  // ---- cooperative grids ----
+  int sms = 0, nb = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return fail(ROM_ECUDA);
+  if (cudaFuncSetAttribute((const void*)batch_steps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(StepSmem)) != cudaSuccess ||
+      cudaFuncSetAttribute((const void*)batch_event_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)event_smem()) != cudaSuccess)
+    return fail(ROM_ECUDA);
+  int g1 = 0, g2 = 0, g3 = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)batch_steps_kernel, kBT, sizeof(StepSmem)) != cudaSuccess) return fail(ROM_ECUDA);
+  g1 = nb;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)batch_event_kernel, kBT, event_smem()) != cudaSuccess) return fail(ROM_ECUDA);
+  g2 = nb;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)batch_fom_kernel, kFomT, 0) != cudaSuccess) return fail(ROM_ECUDA);
+  g3 = nb;
+  if (g1 < 1 || g2 < 1 || g3 < 1) return fail(ROM_ECUDA);
+  B->grid_sweep = sms * std::min(g1, g2);
+  B->grid_fom = sms * g3;
+  *out = B;
+  return ROM_OK;
+}
+
+rom_status rom_batch_step(rom_batch* B, int64_t n_steps) {
+  if (!B || n_steps < 0) return ROM_EINVAL;
+  if (B->poisoned) return ROM_ESTATE;
+  while (n_steps > 0) {
+    long long to_event = LLONG_MAX;
+    for (int i = 0; i < B->count; ++i) {
+      const long long z = B->hinst[i].z;
+      to_event = std::min(to_event, z - (B->M % z));
+    }
+    const long long seg = std::min<long long>(n_steps, to_event);
+    if (run_steps(B, (int)seg) != cudaSuccess) { B->poisoned = 1; cudaGetLastError(); return ROM_ECUDA; }
+    B->M += seg;
+    n_steps -= seg;
+    bool any = false;
+    for (int i = 0; i < B->count && !any; ++i) any = (B->M % B->hinst[i].z) == 0;
+    if (any && run_event(B) != cudaSuccess) { B->poisoned = 1; cudaGetLastError(); return ROM_ECUDA; }
+  }
+  rom_status st = batch_finish(B);
+  if (st == ROM_OK && B->prof_on && prof_collect(B) != cudaSuccess) return ROM_ECUDA;
+  return st;
+}
+
+rom_status rom_batch_state(rom_batch* B, int32_t i, double* q_tilde, double* a, double* sigma, double* phi,
+                           double* y_corr, int64_t* step) {
+  if (!B || i < 0 || i >= B->count) return ROM_EINVAL;
+  if (B->poisoned) return ROM_ESTATE;
+  const Inst& I = B->hinst[i];
+  const size_t N = (size_t)I.n;
+  cudaStream_t s = B->stream;
+  int k = 0;
+  BCK(cudaMemcpyAsync(&k, B->A.rank + i, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BCK(cudaStreamSynchronize(s));
+  std::vector<double> ha(I.r);
+  BCK(cudaMemcpyAsync(ha.data(), B->A.a + (size_t)i * kMaxR, sizeof(double) * I.r, cudaMemcpyDeviceToHost, s));
+  if (q_tilde) {
+    batch_lift_kernel<<<256, 256, 0, s>>>(B->A.phi + I.phi_off, B->A.q_ref + I.vec_off, B->A.a + (size_t)i * kMaxR,
+                                          I.n, k, I.dinv, B->lift);
+    BCK(cudaGetLastError());
+    BCK(cudaMemcpyAsync(q_tilde, B->lift, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  }
+  if (sigma) BCK(cudaMemcpyAsync(sigma, B->A.sigma + (size_t)i * kMaxR, sizeof(double) * I.r, cudaMemcpyDeviceToHost, s));
+  std::vector<float> p32;
+  if (phi) {
+    p32.resize(N * I.r);
+    BCK(cudaMemcpyAsync(p32.data(), B->A.phi + I.phi_off, sizeof(float) * N * I.r, cudaMemcpyDeviceToHost, s));
+  }
+  if (y_corr) BCK(cudaMemcpyAsync(y_corr, B->A.y_corr + I.vec_off, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  BCK(cudaStreamSynchronize(s));
+  if (phi) {
+    for (size_t e = 0; e < p32.size(); ++e) phi[e] = (double)p32[e];
+    for (int j = 0; j < I.r; ++j) {   // sign convention: largest-magnitude entry positive
+      double* col = phi + (size_t)j * N;
+      size_t im = 0;
+      double best = -1.0;
+      for (size_t r = 0; r < N; ++r)
+        if (fabs(col[r]) > best) { best = fabs(col[r]); im = r; }
+      if (col[im] < 0.0) {
+        for (size_t r = 0; r < N; ++r) col[r] = -col[r];
+        ha[j] = -ha[j];
+      }
+    }
+  }
+  if (a) memcpy(a, ha.data(), sizeof(double) * I.r);
+  if (step) *step = B->w_init[i] + B->M;
+  return ROM_OK;
+}
+
+rom_status rom_batch_info(rom_batch* B, int32_t i, int32_t* rank, int32_t* rom_iters, int32_t* fom_iters) {
+  if (!B || i < 0 || i >= B->count) return ROM_EINVAL;
+  if (B->poisoned) return ROM_ESTATE;
+  int v[3] = {0, 0, 0};
+  BCK(cudaMemcpyAsync(&v[0], B->A.rank + i, sizeof(int), cudaMemcpyDeviceToHost, B->stream));
+  BCK(cudaMemcpyAsync(&v[1], B->A.iters_rom + i, sizeof(int), cudaMemcpyDeviceToHost, B->stream));
+  BCK(cudaMemcpyAsync(&v[2], B->A.iters_fom + i, sizeof(int), cudaMemcpyDeviceToHost, B->stream));
+  BCK(cudaStreamSynchronize(B->stream));
+  if (rank) *rank = v[0];
+  if (rom_iters) *rom_iters = v[1];
+  if (fom_iters) *fom_iters = v[2];
+  return ROM_OK;
+}
+
+rom_status rom_batch_layout(rom_batch* B, int64_t* basis_bytes, int64_t* rows, int32_t* tiles,
+                            int32_t* grid) {
+  if (!B) return ROM_EINVAL;
+  long long bb = 0, nr = 0;
+  for (const Inst& I : B->hinst) {
+    bb += (long long)I.n * I.r * (long long)sizeof(float);
+    nr += I.n;
+  }
+  if (basis_bytes) *basis_bytes = bb;
+  if (rows) *rows = nr;
+  if (tiles) *tiles = B->ntiles;
+  if (grid) *grid = B->grid_sweep;
+  return ROM_OK;
+}
+
+rom_status rom_batch_profile(rom_batch* B, int32_t enable) {
+  if (!B) return ROM_EINVAL;
+  if (B->poisoned) return ROM_ESTATE;
+  B->prof_on = enable ? 1 : 0;
+  for (int p = 0; p < 3; ++p) { B->prof_ms[p] = 0.0; B->prof_cnt[p] = 0; }
+  BCK(cudaMemsetAsync(B->A.sweeps, 0, sizeof(long long) * B->count, B->stream));
+  BCK(cudaStreamSynchronize(B->stream));
+  return ROM_OK;
+}
+
+rom_status rom_batch_work(rom_batch* B, int64_t* newton_iters, double* sweep_bytes) {
+  if (!B) return ROM_EINVAL;
+  if (B->poisoned) return ROM_ESTATE;
+  std::vector<long long> sw(B->count);
+  BCK(cudaMemcpyAsync(sw.data(), B->A.sweeps, sizeof(long long) * B->count, cudaMemcpyDeviceToHost, B->stream));
+  BCK(cudaStreamSynchronize(B->stream));
+  long long it = 0;
+  double by = 0.0;
+  for (int i = 0; i < B->count; ++i) {
+    const Inst& I = B->hinst[i];
+    it += sw[i];
+    // one sweep reads the FP32 basis (N x r) and q_ref (N doubles) once
+    by += (double)sw[i] * ((double)I.n * I.r * 4.0 + (double)I.n * 8.0);
+  }
+  if (newton_iters) *newton_iters = it;
+  if (sweep_bytes) *sweep_bytes = by;
+  return ROM_OK;
+}
+
+rom_status rom_batch_profile_read(rom_batch* B, double* ms_total, int64_t* launches) {
+  if (!B || !ms_total || !launches) return ROM_EINVAL;
+  for (int p = 0; p < 3; ++p) { ms_total[p] = B->prof_ms[p]; launches[p] = B->prof_cnt[p]; }
+  return ROM_OK;
+}
+
+void rom_batch_destroy(rom_batch* B) {
+  if (!B) return;
+  cudaStreamSynchronize(B->stream);
+  batch_free(B);
+  delete B;
+}
+
+}  // extern "C"

@@ -1,4 +1,4 @@
-// Reduced backward-Euler steps (Algorithm 1 line 10) and the lift of the
+// Reduced backward-Euler steps of the online loop of Algorithm 1 and the lift of the
 // reduced state (Eq. trial_approximation).
 //
 // Plain Galerkin (Eq. galerkin_continuous_rom discretised by backward Euler):

@@ -58,3 +58,33 @@ def test_invalid_configs_rejected(lib):
     assert lib.rom_state(None, None, None, None, None, None, None) == 1
     lib.rom_destroy(None)
     assert lib.rom_status_string(4) == b"Newton iteration did not converge"
+
+
+def test_invalid_batches_rejected(lib):
+    """The batched engine runs Burgers in the mixed form without hyper-reduction;
+    anything else is refused before any device work."""
+    import paper_2605_28684_gb300 as g
+    good = synth.config_batch(2)
+    q0s = [synth.initial_state(c) for c in good]
+    D = ctypes.POINTER(ctypes.c_double)
+
+    def init(cfgs, count=None):
+        n = len(cfgs)
+        arr = (g._lib.RomConfigC * n)(*[g.make_config(c) for c in cfgs])
+        ptrs = (D * n)(*[q.ctypes.data_as(D) for q in q0s[:n]])
+        out = ctypes.c_void_p()
+        rc = lib.rom_batch_init(arr, ptrs, n if count is None else count, None, ctypes.byref(out))
+        return rc, out.value
+
+    for field, val in [("precision", 0), ("problem", 1), ("n_s", 4), ("r", 65), ("n_cells", 128),
+                       ("z", 0)]:
+        cfgs = synth.config_batch(2)
+        setattr(cfgs[1], field, val)
+        rc, out = init(cfgs)
+        assert rc == 1 and not out, field
+    rc, out = init(good, count=0)
+    assert rc == 1 and not out
+    assert lib.rom_batch_step(None, 1) == 1
+    assert lib.rom_batch_state(None, 0, None, None, None, None, None, None) == 1
+    assert lib.rom_batch_info(None, 0, None, None, None) == 1
+    lib.rom_batch_destroy(None)

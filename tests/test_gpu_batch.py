@@ -1,0 +1,163 @@
+"""GPU parity of the batched engine (many independent Burgers ROMs advanced in
+lockstep, mixed form) through the C ABI.
+
+Each instance of a batch must follow its own FP64 oracle trajectory within the
+mixed-form tolerance (relative L2 of q~ <= 1e-5 at every event, the oracle
+run with the numerical-rank tolerance 1e-5 that FP32 projections resolve),
+exactly as a single mixed-form ROM does; batching only changes how the work
+is scheduled. Cases: uneven N (including sizes that leave ragged row tiles
+and FOM chunks), uneven r and z, and sampled instances of the full
+256-instance workload."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import rom as orom
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_28684_gb300 as pkg
+    from paper_2605_28684_gb300 import build
+    build.build()
+    return pkg
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def small_batch():
+    """Uneven instances: N not multiples of the tile or chunk sizes, r in each
+    rank bucket, every update interval."""
+    spec = [(300, 8, 5, 4e-3), (777, 13, 10, 2e-3), (2048, 24, 20, 7e-3), (4100, 40, 5, 1e-3),
+            (2500, 33, 10, 5e-3), (1500, 48, 5, 9e-3)]
+    cfgs = []
+    for i, (n, r, z, nu) in enumerate(spec):
+        cfgs.append(synth.RomConfig(problem=synth.BURGERS, n_cells=n, r=r, n_s=0, w_init=100, z=z,
+                                    dt=1e-4, nu=nu, lam=synth.LAMBDA_BY_Z[z], n_online=200,
+                                    seed=2000 + i, precision=1))
+    return cfgs
+
+
+def run_oracles(cfgs, q0s, n_steps, check_every, gpu=None):
+    saved = orom.RANK_TOL
+    orom.RANK_TOL = 1e-5
+    try:
+        refs = [orom.AdaptiveROM(c, q) for c, q in zip(cfgs, q0s)]
+        worst = np.zeros(len(cfgs))
+        for m in range(1, n_steps + 1):
+            for ref in refs:
+                ref.step()
+            if gpu is not None and m % check_every == 0:
+                gpu.step(check_every)
+                for i, ref in enumerate(refs):
+                    worst[i] = max(worst[i], rel(gpu.q_tilde(i), ref.lifted()))
+    finally:
+        orom.RANK_TOL = saved
+    return refs, worst
+
+
+def test_batch_small_trajectories_against_oracle(g):
+    cfgs = small_batch()
+    q0s = [synth.initial_state(c) for c in cfgs]
+    b = g.Batch(cfgs, q0s)
+    refs, worst = run_oracles(cfgs, q0s, 200, 5, gpu=b)
+    print("batched vs FP64 oracle, worst relative error per instance:", worst)
+    for i, ref in enumerate(refs):
+        st = b.state(i, phi=True)
+        k = b.info(i)["rank"]
+        kr = orom.numerical_rank(ref.Phi)
+        if k != kr:
+            # a direction at the numerical-rank threshold (1e-5 sigma_1) may fall
+            # on either side of it under FP32 projections; the trajectory check
+            # below still bounds its effect
+            lo = min(k, kr)
+            s_edge = max(st["sigma"][lo], ref.sigma[lo]) / ref.sigma[0]
+            assert abs(k - kr) == 1 and 1e-5 / 3 <= s_edge <= 3e-5, (i, k, kr, s_edge)
+        P = st["phi"][:, :k]
+        assert np.max(np.abs(P.T @ P - np.eye(k))) <= 1e-6, i     # FP32 basis stays orthonormal
+        assert st["step"] == ref.n
+    assert np.all(worst <= 1e-5), worst
+    b.close()
+
+
+def test_batch_matches_single_instance_mixed_path(g):
+    """The batched schedule against the single-ROM mixed path on the GPU: the
+    same method, different summation orders and Newton iterates."""
+    cfgs = small_batch()[:3]
+    q0s = [synth.initial_state(c) for c in cfgs]
+    b = g.Batch(cfgs, q0s)
+    singles = [g.AdaptiveROM(c, q) for c, q in zip(cfgs, q0s)]
+    worst = 0.0
+    for _ in range(20):
+        b.step(5)
+        for i, s in enumerate(singles):
+            s.step(5)
+            worst = max(worst, rel(b.q_tilde(i), s.q_tilde()))
+    print(f"batched vs single-instance mixed path: worst {worst:.2e}")
+    assert worst <= 1e-6, worst
+    for s in singles:
+        s.close()
+    b.close()
+
+
+def test_batch_single_instance_and_odd_steps(g):
+    """A batch of one, advanced by step counts that cut across its events."""
+    cfg = small_batch()[1]
+    q0 = synth.initial_state(cfg)
+    b = g.Batch([cfg], [q0])
+    saved = orom.RANK_TOL
+    orom.RANK_TOL = 1e-5
+    try:
+        ref = orom.AdaptiveROM(cfg, q0)
+        worst = 0.0
+        for n in (3, 7, 1, 12, 17):
+            b.step(n)
+            for _ in range(n):
+                ref.step()
+            worst = max(worst, rel(b.q_tilde(0), ref.lifted()))
+    finally:
+        orom.RANK_TOL = saved
+    assert b.state(0)["step"] == ref.n
+    assert worst <= 1e-5, worst
+    b.close()
+
+
+def test_batch_full_workload_sampled_instances(g):
+    """The 256-instance workload: 20 steps of every instance (events of every
+    interval), then the smallest, the largest and the highest-rank instances
+    against their oracles."""
+    cfgs = synth.config_batch(256)
+    q0s = [synth.initial_state(c) for c in cfgs]
+    b = g.Batch(cfgs, q0s)
+    lay = b.layout()
+    assert lay["rows"] == sum(c.n_cells for c in cfgs)
+    assert lay["basis_bytes"] == sum(4 * c.n_cells * c.r for c in cfgs)
+    b.step(20)
+    ns = [c.n_cells for c in cfgs]
+    rs = [c.r for c in cfgs]
+    picks = sorted({int(np.argmin(ns)), int(np.argmax(ns)), int(np.argmax(rs))})
+    sub = [cfgs[i] for i in picks]
+    refs, _ = run_oracles(sub, [q0s[i] for i in picks], 20, 20)
+    for i, ref in zip(picks, refs):
+        e = rel(b.q_tilde(i), ref.lifted())
+        print(f"instance {i}: N={cfgs[i].n_cells} r={cfgs[i].r} z={cfgs[i].z} error {e:.2e}")
+        assert e <= 1e-5, (i, e)
+    b.close()
+
+
+def test_batch_nonconvergence_reported_and_poisons(g):
+    cfgs = small_batch()[:2]
+    cfgs[1].newton_max = 1          # the reduced Newton solve cannot converge in one iteration
+    q0s = [synth.initial_state(c) for c in cfgs]
+    with pytest.raises(g.RomError) as ei:
+        b = g.Batch(cfgs, q0s)      # the offline FOM already needs more than one iteration
+        b.step(1)
+    assert ei.value.code == 4
