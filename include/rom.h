@@ -311,8 +311,9 @@ rom_status rom_batch_profile_read(rom_batch* b, double* ms_total, int64_t* launc
 
 /* Work of the reduced steps since the last rom_batch_profile call (or init):
  * Newton iterations summed over the instances, and the algorithmic bytes
- * they stream (each iteration reads the instance's FP32 basis and q_ref
- * once: 4 n_cells r + 8 n_cells bytes). Either output may be NULL. */
+ * they stream (each iteration reads the k live columns of the instance's FP32
+ * basis and three FP32 words of reference-state data per row: 4 n_cells k +
+ * 12 n_cells bytes, k the rank at that step). Either output may be NULL. */
 rom_status rom_batch_work(rom_batch* b, int64_t* newton_iters, double* sweep_bytes);
 
 /* Releases the batch and all its device memory (NULL is ignored). */

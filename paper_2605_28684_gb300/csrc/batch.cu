@@ -45,7 +45,8 @@ namespace rom {
 namespace {
 
 constexpr int kBT = 256;          // threads of the sweep kernels
-constexpr int kFomT = 1024;       // threads of the FOM kernel (one row each)
+constexpr int kFomT = 512;        // threads of the FOM kernel (one row each; two CTAs per SM)
+constexpr int kFomMaxChunks = 256; // FOM chunks per instance (power of two)
 constexpr int kPS = kMaxR + 4;    // stride of the per-tile partial vectors
 constexpr int kMaxBatch = 4096;   // instances per batch
 constexpr int kTileRows = 2048;   // rows per tile
@@ -72,6 +73,9 @@ struct BArgs {
   const int* chunk_c;
   float* phi;
   const double* q_ref;
+  float* qr32;             // q_ref rounded to FP32, packed like the N-vectors
+  float* dq32;             // q_ref(i+1) - q_ref(i) (periodic), FP64 difference rounded
+  float* lq32;             // q_ref(i+1) - 2 q_ref(i) + q_ref(i-1), likewise
   double* y_corr;          // correction snapshot (previous coarse FOM state)
   double* y_new;           // coarse FOM iterate / new snapshot
   double* a;               // count x kMaxR: reduced state
@@ -83,11 +87,13 @@ struct BArgs {
   int* iters_rom;
   int* iters_fom;
   long long* sweeps;       // count: Newton iterations (sweeps over the basis) since reset
+  long long* sweep_cols;   // count: basis columns streamed by those sweeps (rank each time)
   float* jlu;              // count x kMaxR x kMaxR: LU factors of the reduced Jacobian
   int* jpiv;               // count x kMaxR
   double* gpart;           // ntiles x kPS
   double* gpart2;          // ntiles x kPS
-  float* mpart;            // ntiles x kMaxR x kMaxR (Jacobian or Gram partials)
+  float* mpart;            // ntiles x kMaxR x kMaxR: reduced Jacobian partials (FP32)
+  double* gram_part;       // ntiles x kMaxR x kMaxR: Gram partials of the rotated basis (FP64)
   float* fom_row;          // 3 floats per row (PCR y, v, w)
   float* fom_chunk;        // nchunks x kFomChunkStride
   float* fom_sep;          // nchunks: separator values
@@ -147,6 +153,51 @@ __device__ __forceinline__ void burgers_band(double ul, double u, double ur, flo
   dl = (a.left ? sa : 0.f) * inv_dx_f + c2;
   dc = ((a.left ? 0.f : sa) - (b.left ? sb : 0.f)) * inv_dx_f - 2.f * c2;
   dr = -(b.left ? 0.f : sb) * inv_dx_f + c2;
+}
+
+// FP32 form of f for the lifted state u = q_ref + delta (the mixed form's
+// batched sweep). Differences of u are taken as differences of q_ref
+// (computed in FP64 and rounded once) plus differences of delta: FP32
+// subtraction of the nearly equal delta values is exact, so f carries the
+// rounding of delta itself and one FP32 rounding, the same as evaluating f in
+// FP64 on the FP32 lift and rounding it to FP32 for the FP32 projection.
+//  qm, q0, qp: q_ref(i-1), q_ref(i), q_ref(i+1) (FP32); dm, d0, dp: delta;
+//  em = q_ref(i) - q_ref(i-1), ep = q_ref(i+1) - q_ref(i);
+//  lr = q_ref(i+1) - 2 q_ref(i) + q_ref(i-1).
+__device__ __forceinline__ float burgers_f32(float qm, float q0, float qp, float dm, float d0, float dp,
+                                             float em, float ep, float lr, float inv_dx, float c2) {
+  const float um = qm + dm, u0 = q0 + d0, up = qp + dp;
+  const float gm = em + (d0 - dm);          // u0 - um
+  const float gp = ep + (dp - d0);          // up - u0
+  // left interface (um, u0): 1 -> um, 2 -> u0, 0 -> zero; right (u0, up): 2 -> u0, 3 -> up
+  const float lpL = um > 0.f ? um : 0.f, rmL = u0 < 0.f ? u0 : 0.f;
+  const bool selL = fabsf(lpL) >= fabsf(rmL);
+  const int iL = selL ? (um > 0.f ? 1 : 0) : (u0 < 0.f ? 2 : 0);
+  const float sL = selL ? lpL : rmL;
+  const float lpR = u0 > 0.f ? u0 : 0.f, rmR = up < 0.f ? up : 0.f;
+  const bool selR = fabsf(lpR) >= fabsf(rmR);
+  const int iR = selR ? (u0 > 0.f ? 2 : 0) : (up < 0.f ? 3 : 0);
+  const float sR = selR ? lpR : rmR;
+  float diff;                               // sR - sL without cancellation
+  if (iL == 1 && iR == 2) diff = gm;
+  else if (iL == 1 && iR == 3) diff = gm + gp;
+  else if (iL == 2 && iR == 2) diff = 0.f;
+  else if (iL == 2 && iR == 3) diff = gp;
+  else diff = sR - sL;
+  const float lap = lr + ((dp - d0) - (d0 - dm));
+  return fmaf(c2, lap, -0.5f * inv_dx * diff * (sR + sL));
+}
+
+// Tridiagonal row of J_f in FP32 from FP32 states.
+__device__ __forceinline__ void burgers_band32(float ul, float u, float ur, float inv_dx, float c2,
+                                               float& dl, float& dc, float& dr) {
+  const float lpL = ul > 0.f ? ul : 0.f, rmL = u < 0.f ? u : 0.f;
+  const bool selL = fabsf(lpL) >= fabsf(rmL);
+  const float lpR = u > 0.f ? u : 0.f, rmR = ur < 0.f ? ur : 0.f;
+  const bool selR = fabsf(lpR) >= fabsf(rmR);
+  dl = (selL ? lpL : 0.f) * inv_dx + c2;
+  dc = ((selL ? 0.f : rmL) - (selR ? lpR : 0.f)) * inv_dx - 2.f * c2;
+  dr = -(selR ? 0.f : rmR) * inv_dx + c2;
 }
 
 // --------------------------------------------------------- small helpers ---
@@ -262,7 +313,9 @@ __device__ __forceinline__ void blk_flush(const float (&m)[16], int k, float* ou
 // ---------------------------------------------------- shared-memory plans ---
 
 struct StepSmem {
-  double qt[kTileRows + 2];          // lifted state of a chunk (+ halo)
+  float sd[kTileRows + 2];           // delta = D^-1 Phi a of a chunk (+ halo)
+  float su[kTileRows + 2];           // q_ref (FP32) of the same rows
+  float sdq[kTileRows + 2];          // q_ref(i+1) - q_ref(i), from row c0 - 1
   alignas(16) float P[66 * kMaxR];   // basis rows of a 64-row sub-chunk (+ halo)
   alignas(16) float W[64 * kMaxR];   // J_f Phi rows; tile Jacobian at the end
   float red[8 * kMaxR];
@@ -297,7 +350,7 @@ struct SweepSmem {
   float Rd[kMaxR];                   // 1 / R_jj
   float pf[kMaxCore];
   float red[8 * kMaxR];
-  float Gt[kMaxR * kMaxR];           // tile Gram
+  double Gd[kBT * 16];               // per-thread FP64 Gram blocks (4 x 4 each)
   double sc[4];
   int q;
 };
@@ -323,11 +376,13 @@ __device__ void step_tile(const BArgs& A, StepSmem& sm, int tile, int i, bool ja
   const int k = A.rank[i];
   const int N = I.n;
   const float* phi = A.phi + I.phi_off;
-  const double* qref = A.q_ref + I.vec_off;
+  const float* qr = A.qr32 + I.vec_off;
+  const float* dq = A.dq32 + I.vec_off;
+  const float* lq = A.lq32 + I.vec_off;
   const int r0 = A.tile_r0[tile], r1 = A.tile_r1[tile];
-  const double inv_dx = (double)N;
-  const float d_f = (float)I.d;
-  const float nu_f = (float)I.nu, inv_dx_f = (float)N;
+  const float inv_dx = (float)N;
+  const float c2 = (float)I.nu * inv_dx * inv_dx;
+  const float d_f = (float)I.d, dinv_f = (float)I.dinv;
   for (int j = t; j < KB; j += kBT) sm.af[j] = (j < k) ? (float)__ldcg(&A.a[(size_t)i * kMaxR + j]) : 0.f;
   float acc[KB];
 #pragma unroll
@@ -338,39 +393,58 @@ __device__ void step_tile(const BArgs& A, StepSmem& sm, int tile, int i, bool ja
   __syncthreads();
   for (int c0 = r0; c0 < r1; c0 += CR) {
     const int rows = min(CR, r1 - c0);
+    // periodic halo rows (warp 0: left, warp 1: right); their loads go out
+    // first so that they overlap the main loads
+    const int h = (wid == 0) ? (c0 - 1 + N) % N : (c0 + rows) % N;
+    float hv0 = 0.f, hv1 = 0.f, hq = 0.f, hd = 0.f;
+    if (wid < 2) {
+      if (lane < k && lane < KB) hv0 = __ldg(&phi[(size_t)lane * N + h]);
+      if (lane + 32 < k && lane + 32 < KB) hv1 = __ldg(&phi[(size_t)(lane + 32) * N + h]);
+      if (lane == 0) { hq = qr[h]; hd = dq[h]; }
+    }
     float x[RPT][KB];
+    float lqv[RPT];
 #pragma unroll
     for (int rr = 0; rr < RPT; ++rr) {
       const int e = rr * kBT + t;
 #pragma unroll
       for (int j = 0; j < KB; ++j) x[rr][j] = (e < rows && j < k) ? __ldg(&phi[(size_t)j * N + c0 + e]) : 0.f;
+      if (e < rows) {
+        sm.su[1 + e] = qr[c0 + e];
+        sm.sdq[1 + e] = dq[c0 + e];
+        lqv[rr] = lq[c0 + e];
+      }
     }
+    // lift: delta = D^-1 Phi a (FP32)
 #pragma unroll
     for (int rr = 0; rr < RPT; ++rr) {
       const int e = rr * kBT + t;
       float s = 0.f;
 #pragma unroll
       for (int j = 0; j < KB; ++j) s = fmaf(x[rr][j], sm.af[j], s);
-      if (e < rows) sm.qt[1 + e] = fma(I.dinv, (double)s, qref[c0 + e]);
+      if (e < rows) sm.sd[1 + e] = dinv_f * s;
     }
-    if (wid < 2) {   // periodic halo rows: warp 0 left, warp 1 right
-      const int h = (wid == 0) ? (c0 - 1 + N) % N : (c0 + rows) % N;
+    if (wid < 2) {
       float s = 0.f;
-      for (int j = lane; j < KB; j += 32) {
-        const float v = (j < k) ? __ldg(&phi[(size_t)j * N + h]) : 0.f;
-        sm.hx[wid * kMaxR + j] = v;
-        s = fmaf(v, sm.af[j], s);
-      }
+      if (lane < KB) { sm.hx[wid * kMaxR + lane] = hv0; s = hv0 * sm.af[lane]; }
+      if (lane + 32 < KB) { sm.hx[wid * kMaxR + lane + 32] = hv1; s = fmaf(hv1, sm.af[lane + 32], s); }
       s = warp_sumf(s);
-      if (lane == 0) sm.qt[wid == 0 ? 0 : rows + 1] = fma(I.dinv, (double)s, qref[h]);
+      if (lane == 0) {
+        const int e = (wid == 0) ? 0 : rows + 1;
+        sm.sd[e] = dinv_f * s;
+        sm.su[e] = hq;
+        if (wid == 0) sm.sdq[0] = hd;   // q_ref(c0) - q_ref(c0 - 1)
+      }
     }
     __syncthreads();
+    // f in FP32, difference form, and the projection
 #pragma unroll
     for (int rr = 0; rr < RPT; ++rr) {
       const int e = rr * kBT + t;
       if (e < rows) {
-        const double f = burgers_f(sm.qt[e], sm.qt[e + 1], sm.qt[e + 2], I.nu, inv_dx);
-        const float w = (float)f * d_f;
+        const float f = burgers_f32(sm.su[e], sm.su[e + 1], sm.su[e + 2], sm.sd[e], sm.sd[e + 1],
+                                    sm.sd[e + 2], sm.sdq[e], sm.sdq[e + 1], lqv[rr], inv_dx, c2);
+        const float w = f * d_f;
 #pragma unroll
         for (int j = 0; j < KB; ++j) acc[j] = fmaf(x[rr][j], w, acc[j]);
       }
@@ -395,8 +469,10 @@ __device__ void step_tile(const BArgs& A, StepSmem& sm, int tile, int i, bool ja
         __syncthreads();
         for (int e = t; e < sr * KB; e += kBT) {
           const int rl = e / KB, l = e % KB;
+          const int ee = s0 + rl;
           float dl, dc, dr;
-          burgers_band(sm.qt[s0 + rl], sm.qt[s0 + rl + 1], sm.qt[s0 + rl + 2], nu_f, inv_dx_f, dl, dc, dr);
+          burgers_band32(sm.su[ee] + sm.sd[ee], sm.su[ee + 1] + sm.sd[ee + 1], sm.su[ee + 2] + sm.sd[ee + 2],
+                         inv_dx, c2, dl, dc, dr);
           sm.W[rl * KB + l] = dl * sm.P[rl * KB + l] + dc * sm.P[(rl + 1) * KB + l] + dr * sm.P[(rl + 2) * KB + l];
         }
         __syncthreads();
@@ -475,6 +551,7 @@ __device__ void step_instance(const BArgs& A, StepSmem& sm, int i, int it, unsig
         A.active[i] = 0;
         A.iters_rom[i] = it;
         A.sweeps[i] += it;
+        A.sweep_cols[i] += (long long)it * k;
       } else if (it >= I.maxit) {
         record_status(A.status, kStNoConv);
       } else {
@@ -507,7 +584,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_steps_kernel(BArgs A) {
         const int i = A.tile_inst[tile];
         if (it > 1 && !__ldcg(&A.active[i])) continue;
         const bool jac = __ldcg(&A.need_jac[i]) != 0;
-        with_bucket(A.inst[i].r, [&](auto kb) { step_tile<decltype(kb)::value>(A, sm, tile, i, jac); });
+        with_bucket(A.rank[i], [&](auto kb) { step_tile<decltype(kb)::value>(A, sm, tile, i, jac); });
       }
       if (!grid_sync(A.bar, A.status)) return;
       if (b == 0 && t == 0) {
@@ -530,9 +607,9 @@ __global__ void __launch_bounds__(kBT, 1) batch_steps_kernel(BArgs A) {
 
 __device__ __forceinline__ int64_t fchunk_begin(int c, int C, int64_t n) { return (int64_t)c * n / C; }
 
-__global__ void __launch_bounds__(kFomT, 1) batch_fom_kernel(BArgs A) {
-  __shared__ float sa[kFomT], sb[kFomT], sc[kFomT], sd0[kFomT], sd1[kFomT], sd2[kFomT];
-  __shared__ float ra[kMaxChunks], rb[kMaxChunks], rc[kMaxChunks], rd[kMaxChunks];
+__global__ void __launch_bounds__(kFomT, 2) batch_fom_kernel(BArgs A) {
+  __shared__ float sa[kFomT], sc[kFomT], sd0[kFomT], sd1[kFomT], sd2[kFomT], sib[kFomT];
+  __shared__ float ra[kFomMaxChunks], rb[kFomMaxChunks], rc[kFomMaxChunks], rd[kFomMaxChunks];
   __shared__ double su[kFomT];
   __shared__ unsigned int redu[32];
   __shared__ unsigned char s_done[kMaxBatch];
@@ -561,15 +638,20 @@ __global__ void __launch_bounds__(kFomT, 1) batch_fom_kernel(BArgs A) {
       const float nu_f = (float)I.nu, inv_dx_f = (float)n, h_f = (float)h;
       __syncthreads();
       const bool act = t < m;
+      // the chunk's rows and its two halo rows (loaded together)
       double u = act ? __ldcg(&ucur[beg + t]) : 0.0;
+      const double un = act ? uprev[beg + t] : 0.0;
+      double hl = 0.0, hr = 0.0;
+      if (t == 0) hl = __ldcg(&ucur[(beg - 1 + n) % n]);
+      if (t == m - 1) hr = __ldcg(&ucur[(beg + m) % n]);
       su[t] = u;
       __syncthreads();
       float a_t = 0.f, b_t = 1.f, c_t = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
       if (act) {
-        const double ul = (t > 0) ? su[t - 1] : __ldcg(&ucur[(beg - 1 + n) % n]);
-        const double ur = (t < m - 1) ? su[t + 1] : __ldcg(&ucur[(beg + m) % n]);
+        const double ul = (t > 0) ? su[t - 1] : hl;
+        const double ur = (t < m - 1) ? su[t + 1] : hr;
         const double f = burgers_f(ul, u, ur, I.nu, inv_dx);
-        const double res = u - uprev[beg + t] - h * f;
+        const double res = u - un - h * f;
         float dl, dc, dr;
         burgers_band(ul, u, ur, nu_f, inv_dx_f, dl, dc, dr);
         a_t = -h_f * dl;
@@ -585,17 +667,19 @@ __global__ void __launch_bounds__(kFomT, 1) batch_fom_kernel(BArgs A) {
       } else {
         a_t = 0.f; b_t = 1.f; c_t = 0.f; d0 = d1 = d2 = 0.f;
       }
-      sa[t] = a_t; sb[t] = b_t; sc[t] = c_t; sd0[t] = d0; sd1[t] = d1; sd2[t] = d2;
+      // PCR (FP32: the solve only steers the iteration); each row publishes
+      // the reciprocal of its diagonal once per level
+      sa[t] = a_t; sc[t] = c_t; sd0[t] = d0; sd1[t] = d1; sd2[t] = d2; sib[t] = __frcp_rn(b_t);
       __syncthreads();
       for (int s = 1; s < mi; s <<= 1) {
         float na = a_t, nb = b_t, nc = c_t, n0 = d0, n1 = d1, n2 = d2;
         if (t < mi) {
           const int tm = t - s, tp = t + s;
-          float am = 0.f, bm = 1.f, cm = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f;
-          float ap = 0.f, bp = 1.f, cp = 0.f, p0 = 0.f, p1 = 0.f, p2 = 0.f;
-          if (tm >= 0) { am = sa[tm]; bm = sb[tm]; cm = sc[tm]; m0 = sd0[tm]; m1 = sd1[tm]; m2 = sd2[tm]; }
-          if (tp < mi) { ap = sa[tp]; bp = sb[tp]; cp = sc[tp]; p0 = sd0[tp]; p1 = sd1[tp]; p2 = sd2[tp]; }
-          const float al = -a_t / bm, ga = -c_t / bp;
+          float am = 0.f, ibm = 1.f, cm = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f;
+          float ap = 0.f, ibp = 1.f, cp = 0.f, p0 = 0.f, p1 = 0.f, p2 = 0.f;
+          if (tm >= 0) { am = sa[tm]; ibm = sib[tm]; cm = sc[tm]; m0 = sd0[tm]; m1 = sd1[tm]; m2 = sd2[tm]; }
+          if (tp < mi) { ap = sa[tp]; ibp = sib[tp]; cp = sc[tp]; p0 = sd0[tp]; p1 = sd1[tp]; p2 = sd2[tp]; }
+          const float al = -a_t * ibm, ga = -c_t * ibp;
           na = al * am;
           nc = ga * cp;
           nb = b_t + al * cm + ga * ap;
@@ -605,11 +689,12 @@ __global__ void __launch_bounds__(kFomT, 1) batch_fom_kernel(BArgs A) {
         }
         __syncthreads();
         a_t = na; b_t = nb; c_t = nc; d0 = n0; d1 = n1; d2 = n2;
-        sa[t] = a_t; sb[t] = b_t; sc[t] = c_t; sd0[t] = d0; sd1[t] = d1; sd2[t] = d2;
+        sa[t] = a_t; sc[t] = c_t; sd0[t] = d0; sd1[t] = d1; sd2[t] = d2; sib[t] = __frcp_rn(b_t);
         __syncthreads();
       }
       if (t < mi) {
-        const float yv = d0 / b_t, vv = d1 / b_t, wv = d2 / b_t;
+        const float ib = sib[t];
+        const float yv = d0 * ib, vv = d1 * ib, wv = d2 * ib;
         float* row = A.fom_row + 3 * (size_t)(I.vec_off + beg + t);
         row[0] = yv; row[1] = vv; row[2] = wv;
         if (t == 0) { ch[4] = yv; ch[5] = vv; ch[6] = wv; }
@@ -833,9 +918,7 @@ __device__ void ev_rot_tile(const BArgs& A, SweepSmem& sm, int tile, int i) {
     const int row = e / KB, col = e % KB;
     sm.U[row * KB + col] = (row <= k && col < kn) ? __ldcg(&ug[row * kMaxR + col]) : 0.f;
   }
-  float m[16];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) m[q] = 0.f;
+  for (int q = 0; q < 16; ++q) sm.Gd[t * 16 + q] = 0.0;
   __syncthreads();
   for (int c0 = r0; c0 < r1; c0 += CR) {
     const int rows = min(CR, r1 - c0);
@@ -867,15 +950,28 @@ __device__ void ev_rot_tile(const BArgs& A, SweepSmem& sm, int tile, int i) {
       }
     }
     __syncthreads();
-    blk_accum<KB>(sm.P, sm.P, rows, m);
+    // FP32 sums over runs of at most 64 rows (one group's share of them),
+    // added to this thread's FP64 slots: the Gram carries about eps * 8
+    // relative error per run instead of eps * sqrt(rows per tile)
+    for (int s0 = 0; s0 < rows; s0 += 64) {
+      float m[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) m[q] = 0.f;
+      blk_accum<KB>(sm.P + s0 * KB, sm.P + s0 * KB, min(64, rows - s0), m);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) sm.Gd[t * 16 + q] += (double)m[q];
+    }
     __syncthreads();
   }
-  for (int e = t; e < kn * kn; e += kBT) sm.Gt[e] = 0.f;
-  __syncthreads();
-  blk_flush<KB>(m, kn, sm.Gt);
-  __syncthreads();
-  float* mp = A.mpart + (size_t)tile * kMaxR * kMaxR;
-  for (int e = t; e < kn * kn; e += kBT) mp[e] = sm.Gt[e];
+  // fixed-order FP64 sum over the thread groups that share a 4 x 4 block
+  double* gp = A.gram_part + (size_t)tile * kMaxR * kMaxR;
+  for (int e = t; e < kn * kn; e += kBT) {
+    const int j = e / kn, l = e % kn;
+    const int bi = (j >> 2) * Blk<KB>::nb + (l >> 2), q = (j & 3) * 4 + (l & 3);
+    double v = 0.0;
+    for (int g = 0; g < Blk<KB>::groups; ++g) v += sm.Gd[(g * Blk<KB>::nblk + bi) * 16 + q];
+    gp[e] = v;
+  }
 }
 
 // Phi <- Phi R^-1: each row y solves y R = x (FP32, R from the FP64 Cholesky).
@@ -1076,7 +1172,7 @@ __device__ void ev_chol(const BArgs& A, CholSmem& sm, int i) {
   const int kn = (int)__ldcg(&A.ev_sc[(size_t)i * 8 + 2]);
   for (int e = t; e < kn * kn; e += blockDim.x) {
     double s = 0.0;
-    for (int tt = I.tile0; tt < I.tile1; ++tt) s += (double)__ldcg(&A.mpart[(size_t)tt * kMaxR * kMaxR + e]);
+    for (int tt = I.tile0; tt < I.tile1; ++tt) s += __ldcg(&A.gram_part[(size_t)tt * kMaxR * kMaxR + e]);
     const int j = e / kn, l = e % kn;
     sm.G[j * kMaxR + l] = s;
   }
@@ -1126,7 +1222,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_event_kernel(BArgs A) {
   while ((q = next_tile(&A.ctl[0], A.ntiles, &sw.q)) >= 0) {
     const int tile = A.order[q], i = A.tile_inst[tile];
     if (!is_event(A.inst[i], M)) continue;
-    with_bucket(A.inst[i].r, [&](auto kb) { ev_p1_tile<decltype(kb)::value>(A, sw, tile, i); });
+    with_bucket(A.rank[i], [&](auto kb) { ev_p1_tile<decltype(kb)::value>(A, sw, tile, i); });
   }
   if (!grid_sync(A.bar, A.status)) return;
   // ---- p1 and |yhat|^2 per instance ----
@@ -1142,7 +1238,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_event_kernel(BArgs A) {
   while ((q = next_tile(&A.ctl[1], A.ntiles, &sw.q)) >= 0) {
     const int tile = A.order[q], i = A.tile_inst[tile];
     if (!is_event(A.inst[i], M)) continue;
-    with_bucket(A.inst[i].r, [&](auto kb) { ev_p2_tile<decltype(kb)::value>(A, sw, tile, i); });
+    with_bucket(A.rank[i], [&](auto kb) { ev_p2_tile<decltype(kb)::value>(A, sw, tile, i); });
   }
   if (!grid_sync(A.bar, A.status)) return;
   // ---- core SVD per instance ----
@@ -1156,7 +1252,9 @@ __global__ void __launch_bounds__(kBT, 1) batch_event_kernel(BArgs A) {
   while ((q = next_tile(&A.ctl[2], A.ntiles, &sw.q)) >= 0) {
     const int tile = A.order[q], i = A.tile_inst[tile];
     if (!is_event(A.inst[i], M)) continue;
-    with_bucket(A.inst[i].r, [&](auto kb) { ev_rot_tile<decltype(kb)::value>(A, sw, tile, i); });
+    const double* esc = A.ev_sc + (size_t)i * 8;   // k' and k of this update
+    const int kb_cols = max((int)__ldcg(&esc[2]), (int)__ldcg(&esc[3]));
+    with_bucket(kb_cols, [&](auto kb) { ev_rot_tile<decltype(kb)::value>(A, sw, tile, i); });
   }
   if (!grid_sync(A.bar, A.status)) return;
   // ---- Cholesky per instance ----
@@ -1170,7 +1268,18 @@ __global__ void __launch_bounds__(kBT, 1) batch_event_kernel(BArgs A) {
   while ((q = next_tile(&A.ctl[3], A.ntiles, &sw.q)) >= 0) {
     const int tile = A.order[q], i = A.tile_inst[tile];
     if (!is_event(A.inst[i], M)) continue;
-    with_bucket(A.inst[i].r, [&](auto kb) { ev_apply_tile<decltype(kb)::value>(A, sw, tile, i); });
+    with_bucket((int)__ldcg(&A.ev_sc[(size_t)i * 8 + 2]), [&](auto kb) { ev_apply_tile<decltype(kb)::value>(A, sw, tile, i); });
+  }
+}
+
+// FP32 copies of q_ref and of its first and second differences (periodic),
+// differences taken in FP64.
+__global__ void batch_qref_kernel(const double* q_ref, int n, float* qr, float* dq, float* lq) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double qm = q_ref[(i - 1 + n) % n], q0 = q_ref[i], qp = q_ref[(i + 1) % n];
+    qr[i] = (float)q0;
+    dq[i] = (float)(qp - q0);
+    lq[i] = (float)((qp - q0) - (q0 - qm));
   }
 }
 
@@ -1374,7 +1483,7 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
     }
     I.tile1 = (int)tinst.size();
     int C = 4;
-    while ((I.n + C - 1) / C > kFomT && C < kMaxChunks) C *= 2;
+    while ((I.n + C - 1) / C > kFomT && C < kFomMaxChunks) C *= 2;
     if ((I.n + C - 1) / C > kFomT) { delete B; return ROM_EINVAL; }
     I.chunk0 = (int)cinst.size();
     I.nchunk = C;
@@ -1406,14 +1515,14 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
   BA(d_ci, B->nchunks); BA(d_cc, B->nchunks);
   BA(A.phi, phi_tot); BA(A.q_ref, vec_tot); BA(A.y_corr, vec_tot); BA(A.y_new, vec_tot);
   BA(A.a, (size_t)count * kMaxR); BA(A.an, (size_t)count * kMaxR); BA(A.sigma, (size_t)count * kMaxR);
-  BA(A.sweeps, count); BA(A.rank, count); BA(A.need_jac, count); BA(A.active, count); BA(A.iters_rom, count); BA(A.iters_fom, count);
+  BA(A.sweeps, count); BA(A.sweep_cols, count); BA(A.rank, count); BA(A.need_jac, count); BA(A.active, count); BA(A.iters_rom, count); BA(A.iters_fom, count);
   BA(A.jlu, (size_t)count * kMaxR * kMaxR); BA(A.jpiv, (size_t)count * kMaxR);
   BA(A.gpart, (size_t)B->ntiles * kPS); BA(A.gpart2, (size_t)B->ntiles * kPS);
-  BA(A.mpart, (size_t)B->ntiles * kMaxR * kMaxR);
+  BA(A.mpart, (size_t)B->ntiles * kMaxR * kMaxR); BA(A.gram_part, (size_t)B->ntiles * kMaxR * kMaxR);
   BA(A.fom_row, 3 * (size_t)vec_tot); BA(A.fom_chunk, (size_t)B->nchunks * kFomChunkStride);
   BA(A.fom_sep, B->nchunks); BA(A.fom_keys, 4 * (size_t)count);
   BA(A.ev_p, (size_t)count * kMaxCore); BA(A.ev_p2, (size_t)count * kMaxCore); BA(A.ev_sc, (size_t)count * 8);
-  BA(A.qres, vec_tot);
+  BA(A.qres, vec_tot); BA(A.qr32, vec_tot); BA(A.dq32, vec_tot); BA(A.lq32, vec_tot);
   BA(A.ev_u, (size_t)count * kMaxCore * kMaxR); BA(A.ev_anew, (size_t)count * kMaxR);
   BA(A.ev_r, (size_t)count * kMaxR * kMaxR); BA(A.ctl, 8); BA(A.M, 1); BA(A.bar, 1); BA(A.status, 1);
   BA(B->lift, nmax);
@@ -1443,6 +1552,7 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
       cudaMemsetAsync(A.iters_rom, 0, sizeof(int) * count, s) != cudaSuccess ||
       cudaMemsetAsync(A.iters_fom, 0, sizeof(int) * count, s) != cudaSuccess ||
       cudaMemsetAsync(A.sweeps, 0, sizeof(long long) * count, s) != cudaSuccess ||
+      cudaMemsetAsync(A.sweep_cols, 0, sizeof(long long) * count, s) != cudaSuccess ||
       cudaMemsetAsync(A.M, 0, sizeof(long long), s) != cudaSuccess ||
       cudaMemsetAsync(A.bar, 0, sizeof(GridBarrier), s) != cudaSuccess ||
       cudaMemsetAsync(A.status, 0, sizeof(int), s) != cudaSuccess)
@@ -1467,6 +1577,9 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
               cudaStreamSynchronize(s) == cudaSuccess;
     I.rank_tol = ctx->cfg.rank_tol;
     B->w_init[i] = ctx->step;
+    batch_qref_kernel<<<64, 256, 0, s>>>(qref_d + I.vec_off, I.n, A.qr32 + I.vec_off, A.dq32 + I.vec_off,
+                                         A.lq32 + I.vec_off);
+    ok = ok && cudaGetLastError() == cudaSuccess;
     rom_destroy(ctx);
     if (!ok) return fail(ROM_ECUDA);
     I.d = dv;
@@ -1609,6 +1722,7 @@ rom_status rom_batch_profile(rom_batch* B, int32_t enable) {
   B->prof_on = enable ? 1 : 0;
   for (int p = 0; p < 3; ++p) { B->prof_ms[p] = 0.0; B->prof_cnt[p] = 0; }
   BCK(cudaMemsetAsync(B->A.sweeps, 0, sizeof(long long) * B->count, B->stream));
+  BCK(cudaMemsetAsync(B->A.sweep_cols, 0, sizeof(long long) * B->count, B->stream));
   BCK(cudaStreamSynchronize(B->stream));
   return ROM_OK;
 }
@@ -1616,16 +1730,18 @@ rom_status rom_batch_profile(rom_batch* B, int32_t enable) {
 rom_status rom_batch_work(rom_batch* B, int64_t* newton_iters, double* sweep_bytes) {
   if (!B) return ROM_EINVAL;
   if (B->poisoned) return ROM_ESTATE;
-  std::vector<long long> sw(B->count);
+  std::vector<long long> sw(B->count), sc(B->count);
   BCK(cudaMemcpyAsync(sw.data(), B->A.sweeps, sizeof(long long) * B->count, cudaMemcpyDeviceToHost, B->stream));
+  BCK(cudaMemcpyAsync(sc.data(), B->A.sweep_cols, sizeof(long long) * B->count, cudaMemcpyDeviceToHost, B->stream));
   BCK(cudaStreamSynchronize(B->stream));
   long long it = 0;
   double by = 0.0;
   for (int i = 0; i < B->count; ++i) {
     const Inst& I = B->hinst[i];
     it += sw[i];
-    // one sweep reads the FP32 basis (N x r) and q_ref (N doubles) once
-    by += (double)sw[i] * ((double)I.n * I.r * 4.0 + (double)I.n * 8.0);
+    // a sweep reads the k live FP32 basis columns (zero columns are not
+    // read) and three FP32 words of q_ref data per row
+    by += (double)I.n * (4.0 * (double)sc[i] + 12.0 * (double)sw[i]);
   }
   if (newton_iters) *newton_iters = it;
   if (sweep_bytes) *sweep_bytes = by;
