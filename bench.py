@@ -16,7 +16,14 @@ through the public API from host buffers: the initial state goes up from
 pinned host memory (rom_init, amortised over the run) and q~ comes back to
 pinned host memory after every cycle.
 
+The line also carries the other forms of the method (``forms``): the
+mixed-precision form of the same workload, and the batched form, 256
+independent Burgers ROMs of uneven size (N log-uniform in [2048, 65536],
+r in 8..48, z in {5, 10, 20}) advanced together for 5 K steps, reported in
+aggregate ROM-steps/s with the HBM roofline of its reduced-step kernel.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                       [--only single|batched] [--batch-count B]
 Under torchrun each rank runs an independent replica (the path does not
 shard; weak scaling) and rank 0 prints one JSON line.
 """
@@ -56,14 +63,14 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # one ncu capture of each kernel on this workload (summarised under profiles/);
 # reported only while the kernel's source file is unchanged (sha1).
 TRAFFIC = {
-    "isvd_update": {"bytes": 1719040, "src": "paper_2605_28684_gb300/csrc/isvd.cu",
-                    "sha1": "256ac5fb22147b5cd1dee92d65d9bb886a0da3c2"},
-    "coarse_fom": {"bytes": 162304, "src": "paper_2605_28684_gb300/csrc/fom.cu",
-                   "sha1": "41fe1123cf55dbaaea5c55bb118f0ef5e1516c8a"},
-    "reduced_steps": {"bytes": 106752, "src": "paper_2605_28684_gb300/csrc/reduced.cu",
-                      "sha1": "19040aafdb6138cd9e10904b67f14c28959d3ac8"},
-    "sampling": {"bytes": 1356032, "src": "paper_2605_28684_gb300/csrc/sampling.cu",
-                 "sha1": "141560cfbfee019dec07f138e1e9ac08cdd08cd0"},
+    "isvd_update": {"bytes": 1726464, "src": "paper_2605_28684_gb300/csrc/isvd.cu",
+                    "sha1": "04d9a2f76a29ce18e5b2d85d3825c6ecfdd939c1"},
+    "coarse_fom": {"bytes": 164736, "src": "paper_2605_28684_gb300/csrc/fom.cu",
+                   "sha1": "9ac9def378168c9a4419c8e6d4a2ef53e7b328b9"},
+    "reduced_steps": {"bytes": 131328, "src": "paper_2605_28684_gb300/csrc/reduced.cu",
+                      "sha1": "4a2337f50f3eabb5166972928632f5977719e5d1"},
+    "sampling": {"bytes": 1358592, "src": "paper_2605_28684_gb300/csrc/sampling.cu",
+                 "sha1": "d1c431fe36a57bd4721be962d5d4c096560e0acf"},
 }
 
 
@@ -234,7 +241,7 @@ def timed_batch(g, args, stream, dist, world):
     its reduced-step kernel (each Newton iteration streams every active
     instance's FP32 basis and q_ref once)."""
     import torch
-    cfgs = synth.config_batch(256)
+    cfgs = synth.config_batch(args.batch_count)
     q0s = [synth.initial_state(c) for c in cfgs]
     b = g.Batch(cfgs, q0s, stream=stream.cuda_stream)
     n_steps = 5 * args.steps
@@ -283,6 +290,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--oracle-sample", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", default="all", choices=["all", "single", "batched"],
+                    help="single / batched: time only the single-ROM forms or only the "
+                         "batched form (for profiling runs)")
+    ap.add_argument("--batch-count", type=int, default=256,
+                    help="instances of the batched form (256 is the configured workload)")
     args = ap.parse_args()
 
     if args.oracle_sample is not None:
@@ -311,9 +323,16 @@ def main():
         dist.barrier()
     import paper_2605_28684_gb300 as g
 
+    stream = torch.cuda.current_stream()
+    if args.only == "batched":
+        line = timed_batch(g, args, stream, dist, world)
+        if rank == 0:
+            print(json.dumps({"form": "batched", **line}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     cfg = workload_config()
     q0 = synth.initial_state(cfg)
-    stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def timed_cycles(c, sampler=None):
@@ -376,7 +395,8 @@ def main():
     # the batched form: 256 independent Burgers ROMs of uneven size (N
     # log-uniform in [2048, 65536], r in 8..48, z in {5, 10, 20}) advanced in
     # lockstep; ~0.5 GB of FP32 bases, larger than L2, so no flush is needed
-    forms["batched_256"] = timed_batch(g, args, stream, dist, world)
+    if args.only == "all":
+        forms["batched_256"] = timed_batch(g, args, stream, dist, world)
 
     # roofline of the dominant kernel (largest device time in the timed region)
     dom = max(prof, key=lambda p: prof[p]["ms"])

@@ -49,7 +49,8 @@ constexpr int kFomT = 512;        // threads of the FOM kernel (one row each; tw
 constexpr int kFomMaxChunks = 256; // FOM chunks per instance (power of two)
 constexpr int kPS = kMaxR + 4;    // stride of the per-tile partial vectors
 constexpr int kMaxBatch = 4096;   // instances per batch
-constexpr int kTileRows = 2048;   // rows per tile
+constexpr int kTileRows = 8192;   // rows per tile (a multiple of every chunk size)
+constexpr int kChunkMax = 2048;   // rows per chunk of a sweep (256 threads x rows per thread)
 constexpr int kFomChunkStride = 16;
 
 // Per-instance constants (device array, written once at init).
@@ -101,6 +102,7 @@ struct BArgs {
   double* ev_p;            // count x kMaxCore: p1, then p = p1 + p2
   double* ev_p2;           // count x kMaxCore: p2 (second Gram-Schmidt pass)
   float* qres;             // q1 = yhat - Phi p1 per row (FP32), packed like the N-vectors
+  float* yhat32;           // yhat = D (y - q_ref) per row, formed in FP64 and rounded
   double* ev_sc;           // count x 8: |yhat|^2, 1/rho, k', k
   float* ev_u;             // count x kMaxCore x kMaxR: rotation U(:, 0:k') (FP32)
   double* ev_anew;         // count x kMaxR: transferred state before a <- R a
@@ -235,6 +237,24 @@ __device__ __forceinline__ int next_tile(unsigned int* ctr, int ntiles, int* s_q
   return q < ntiles ? q : -1;
 }
 
+// Runs body(q) for every queue slot q this CTA claims. The claim of the next
+// slot goes out before the current tile is processed, so its round trip to
+// L2 overlaps the work.
+template <typename F>
+__device__ __forceinline__ void for_each_tile(unsigned int* ctr, int ntiles, int* s_q, F&& body) {
+  int q = next_tile(ctr, ntiles, s_q);
+  while (q >= 0) {
+    unsigned int qn = 0u;
+    if (threadIdx.x == 0) qn = atomicAdd(ctr, 1u);
+    body(q);
+    __syncthreads();
+    if (threadIdx.x == 0) *s_q = (int)qn;
+    __syncthreads();
+    q = *s_q;
+    if (q >= ntiles) q = -1;
+  }
+}
+
 // Sum of per-tile partial vectors of one instance, fixed order: warps over
 // entries, lanes over tiles.
 __device__ __forceinline__ void sum_tiles(const double* part, int tile0, int tile1, int nent, int off,
@@ -313,9 +333,9 @@ __device__ __forceinline__ void blk_flush(const float (&m)[16], int k, float* ou
 // ---------------------------------------------------- shared-memory plans ---
 
 struct StepSmem {
-  float sd[kTileRows + 2];           // delta = D^-1 Phi a of a chunk (+ halo)
-  float su[kTileRows + 2];           // q_ref (FP32) of the same rows
-  float sdq[kTileRows + 2];          // q_ref(i+1) - q_ref(i), from row c0 - 1
+  float sd[kChunkMax + 2];           // delta = D^-1 Phi a of a chunk (+ halo)
+  float su[kChunkMax + 2];           // q_ref (FP32) of the same rows
+  float sdq[kChunkMax + 2];          // q_ref(i+1) - q_ref(i), from row c0 - 1
   alignas(16) float P[66 * kMaxR];   // basis rows of a 64-row sub-chunk (+ halo)
   alignas(16) float W[64 * kMaxR];   // J_f Phi rows; tile Jacobian at the end
   float red[8 * kMaxR];
@@ -367,22 +387,158 @@ struct CholSmem {
 
 // ======================================================== steps kernel ===
 
+// Registers of one chunk of a sweep tile: the chunk's basis rows and
+// reference-state data, and (warps 0 and 1) the two periodic halo rows.
+// Rows per thread of the step sweep: the small rank buckets keep two chunks
+// in flight (double-buffered registers), so each holds half as many rows.
+template <int KB>
+struct StepRpt {
+  static constexpr bool dbl = false;   // measured slower than one chunk in flight
+  static constexpr int v = dbl ? 32 / KB : Rpt<KB>::v;
+};
+
+template <int KB>
+struct ChunkRegs {
+  static constexpr int RPT = StepRpt<KB>::v;
+  float x[RPT][KB];
+  float qr[RPT], dq[RPT], lq[RPT];
+  float hv0, hv1, hq, hd;
+};
+
+struct TileCtx {
+  const float* phi;
+  const float* qr;
+  const float* dq;
+  const float* lq;
+  int N, k, r1;
+  float inv_dx, c2, d_f, dinv_f;
+};
+
+template <int KB>
+__device__ __forceinline__ void load_chunk(const TileCtx& T, int c0, ChunkRegs<KB>& R) {
+  constexpr int RPT = StepRpt<KB>::v;
+  constexpr int CR = kBT * RPT;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int rows = min(CR, T.r1 - c0);
+  const int h = (wid == 0) ? (c0 - 1 + T.N) % T.N : (c0 + rows) % T.N;
+  R.hv0 = R.hv1 = R.hq = R.hd = 0.f;
+  if (wid < 2) {
+    if (lane < T.k && lane < KB) R.hv0 = __ldg(&T.phi[(size_t)lane * T.N + h]);
+    if (lane + 32 < T.k && lane + 32 < KB) R.hv1 = __ldg(&T.phi[(size_t)(lane + 32) * T.N + h]);
+    if (lane == 0) { R.hq = T.qr[h]; R.hd = T.dq[h]; }
+  }
+#pragma unroll
+  for (int rr = 0; rr < RPT; ++rr) {
+    const int e = rr * kBT + t;
+#pragma unroll
+    for (int j = 0; j < KB; ++j) R.x[rr][j] = (e < rows && j < T.k) ? __ldg(&T.phi[(size_t)j * T.N + c0 + e]) : 0.f;
+    R.qr[rr] = (e < rows) ? T.qr[c0 + e] : 0.f;
+    R.dq[rr] = (e < rows) ? T.dq[c0 + e] : 0.f;
+    R.lq[rr] = (e < rows) ? T.lq[c0 + e] : 0.f;
+  }
+}
+
+// Lift, FP32 operator and projection of one chunk (and its part of the
+// reduced Jacobian when due).
+template <int KB>
+__device__ __forceinline__ void compute_chunk(const TileCtx& T, int c0, const ChunkRegs<KB>& R, StepSmem& sm,
+                                              bool jac, float (&acc)[KB], float (&m)[16]) {
+  constexpr int RPT = StepRpt<KB>::v;
+  constexpr int CR = kBT * RPT;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int rows = min(CR, T.r1 - c0);
+#pragma unroll
+  for (int rr = 0; rr < RPT; ++rr) {
+    const int e = rr * kBT + t;
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < KB; ++j) s = fmaf(R.x[rr][j], sm.af[j], s);
+    if (e < rows) {
+      sm.sd[1 + e] = T.dinv_f * s;
+      sm.su[1 + e] = R.qr[rr];
+      sm.sdq[1 + e] = R.dq[rr];
+    }
+  }
+  if (wid < 2) {
+    float s = 0.f;
+    if (lane < KB) { sm.hx[wid * kMaxR + lane] = R.hv0; s = R.hv0 * sm.af[lane]; }
+    if (lane + 32 < KB) { sm.hx[wid * kMaxR + lane + 32] = R.hv1; s = fmaf(R.hv1, sm.af[lane + 32], s); }
+    s = warp_sumf(s);
+    if (lane == 0) {
+      const int e = (wid == 0) ? 0 : rows + 1;
+      sm.sd[e] = T.dinv_f * s;
+      sm.su[e] = R.hq;
+      if (wid == 0) sm.sdq[0] = R.hd;   // q_ref(c0) - q_ref(c0 - 1)
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int rr = 0; rr < RPT; ++rr) {
+    const int e = rr * kBT + t;
+    if (e < rows) {
+      const float f = burgers_f32(sm.su[e], sm.su[e + 1], sm.su[e + 2], sm.sd[e], sm.sd[e + 1],
+                                  sm.sd[e + 2], sm.sdq[e], sm.sdq[e + 1], R.lq[rr], T.inv_dx, T.c2);
+      const float w = f * T.d_f;
+#pragma unroll
+      for (int j = 0; j < KB; ++j) acc[j] = fmaf(R.x[rr][j], w, acc[j]);
+    }
+  }
+  if (jac) {
+    // Phi^T J_f Phi over 64-row sub-chunks: stage basis rows (+ halo),
+    // W = J_f Phi, then the blocked rank-64 update.
+    for (int s0 = 0; s0 < rows; s0 += 64) {
+      const int sr = min(64, rows - s0);
+#pragma unroll
+      for (int rr = 0; rr < RPT; ++rr) {
+        const int e = rr * kBT + t;
+        if (e < rows && e >= s0 - 1 && e <= s0 + sr) {
+#pragma unroll
+          for (int j = 0; j < KB; ++j) sm.P[(e - s0 + 1) * KB + j] = R.x[rr][j];
+        }
+      }
+      if (s0 == 0)
+        for (int j = t; j < KB; j += kBT) sm.P[j] = sm.hx[j];
+      if (s0 + sr == rows)
+        for (int j = t; j < KB; j += kBT) sm.P[(sr + 1) * KB + j] = sm.hx[kMaxR + j];
+      __syncthreads();
+      for (int e = t; e < sr * KB; e += kBT) {
+        const int rl = e / KB, l = e % KB;
+        const int ee = s0 + rl;
+        float dl, dc, dr;
+        burgers_band32(sm.su[ee] + sm.sd[ee], sm.su[ee + 1] + sm.sd[ee + 1], sm.su[ee + 2] + sm.sd[ee + 2],
+                       T.inv_dx, T.c2, dl, dc, dr);
+        sm.W[rl * KB + l] = dl * sm.P[rl * KB + l] + dc * sm.P[(rl + 1) * KB + l] + dr * sm.P[(rl + 2) * KB + l];
+      }
+      __syncthreads();
+      blk_accum<KB>(sm.P + KB, sm.W, sr, m);
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+}
+
 template <int KB>
 __device__ void step_tile(const BArgs& A, StepSmem& sm, int tile, int i, bool jac) {
-  constexpr int RPT = Rpt<KB>::v;
+  constexpr int RPT = StepRpt<KB>::v;
   constexpr int CR = kBT * RPT;
+  // two chunks in flight for the small rank buckets (register budget)
+  constexpr bool kDouble = StepRpt<KB>::dbl;
   const Inst I = A.inst[i];
-  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int t = threadIdx.x;
   const int k = A.rank[i];
-  const int N = I.n;
-  const float* phi = A.phi + I.phi_off;
-  const float* qr = A.qr32 + I.vec_off;
-  const float* dq = A.dq32 + I.vec_off;
-  const float* lq = A.lq32 + I.vec_off;
-  const int r0 = A.tile_r0[tile], r1 = A.tile_r1[tile];
-  const float inv_dx = (float)N;
-  const float c2 = (float)I.nu * inv_dx * inv_dx;
-  const float d_f = (float)I.d, dinv_f = (float)I.dinv;
+  TileCtx T;
+  T.phi = A.phi + I.phi_off;
+  T.qr = A.qr32 + I.vec_off;
+  T.dq = A.dq32 + I.vec_off;
+  T.lq = A.lq32 + I.vec_off;
+  T.N = I.n;
+  T.k = k;
+  T.r1 = A.tile_r1[tile];
+  T.inv_dx = (float)I.n;
+  T.c2 = (float)I.nu * T.inv_dx * T.inv_dx;
+  T.d_f = (float)I.d;
+  T.dinv_f = (float)I.dinv;
+  const int r0 = A.tile_r0[tile], r1 = T.r1;
   for (int j = t; j < KB; j += kBT) sm.af[j] = (j < k) ? (float)__ldcg(&A.a[(size_t)i * kMaxR + j]) : 0.f;
   float acc[KB];
 #pragma unroll
@@ -390,97 +546,25 @@ __device__ void step_tile(const BArgs& A, StepSmem& sm, int tile, int i, bool ja
   float m[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) m[q] = 0.f;
+  ChunkRegs<KB> ra;
+  load_chunk<KB>(T, r0, ra);
   __syncthreads();
-  for (int c0 = r0; c0 < r1; c0 += CR) {
-    const int rows = min(CR, r1 - c0);
-    // periodic halo rows (warp 0: left, warp 1: right); their loads go out
-    // first so that they overlap the main loads
-    const int h = (wid == 0) ? (c0 - 1 + N) % N : (c0 + rows) % N;
-    float hv0 = 0.f, hv1 = 0.f, hq = 0.f, hd = 0.f;
-    if (wid < 2) {
-      if (lane < k && lane < KB) hv0 = __ldg(&phi[(size_t)lane * N + h]);
-      if (lane + 32 < k && lane + 32 < KB) hv1 = __ldg(&phi[(size_t)(lane + 32) * N + h]);
-      if (lane == 0) { hq = qr[h]; hd = dq[h]; }
-    }
-    float x[RPT][KB];
-    float lqv[RPT];
-#pragma unroll
-    for (int rr = 0; rr < RPT; ++rr) {
-      const int e = rr * kBT + t;
-#pragma unroll
-      for (int j = 0; j < KB; ++j) x[rr][j] = (e < rows && j < k) ? __ldg(&phi[(size_t)j * N + c0 + e]) : 0.f;
-      if (e < rows) {
-        sm.su[1 + e] = qr[c0 + e];
-        sm.sdq[1 + e] = dq[c0 + e];
-        lqv[rr] = lq[c0 + e];
+  if constexpr (kDouble) {
+    ChunkRegs<KB> rb;
+    for (int c0 = r0; c0 < r1; c0 += 2 * CR) {
+      const bool has_b = c0 + CR < r1;
+      if (has_b) load_chunk<KB>(T, c0 + CR, rb);
+      compute_chunk<KB>(T, c0, ra, sm, jac, acc, m);
+      if (has_b) {
+        if (c0 + 2 * CR < r1) load_chunk<KB>(T, c0 + 2 * CR, ra);
+        compute_chunk<KB>(T, c0 + CR, rb, sm, jac, acc, m);
       }
     }
-    // lift: delta = D^-1 Phi a (FP32)
-#pragma unroll
-    for (int rr = 0; rr < RPT; ++rr) {
-      const int e = rr * kBT + t;
-      float s = 0.f;
-#pragma unroll
-      for (int j = 0; j < KB; ++j) s = fmaf(x[rr][j], sm.af[j], s);
-      if (e < rows) sm.sd[1 + e] = dinv_f * s;
+  } else {
+    for (int c0 = r0; c0 < r1; c0 += CR) {
+      if (c0 > r0) load_chunk<KB>(T, c0, ra);
+      compute_chunk<KB>(T, c0, ra, sm, jac, acc, m);
     }
-    if (wid < 2) {
-      float s = 0.f;
-      if (lane < KB) { sm.hx[wid * kMaxR + lane] = hv0; s = hv0 * sm.af[lane]; }
-      if (lane + 32 < KB) { sm.hx[wid * kMaxR + lane + 32] = hv1; s = fmaf(hv1, sm.af[lane + 32], s); }
-      s = warp_sumf(s);
-      if (lane == 0) {
-        const int e = (wid == 0) ? 0 : rows + 1;
-        sm.sd[e] = dinv_f * s;
-        sm.su[e] = hq;
-        if (wid == 0) sm.sdq[0] = hd;   // q_ref(c0) - q_ref(c0 - 1)
-      }
-    }
-    __syncthreads();
-    // f in FP32, difference form, and the projection
-#pragma unroll
-    for (int rr = 0; rr < RPT; ++rr) {
-      const int e = rr * kBT + t;
-      if (e < rows) {
-        const float f = burgers_f32(sm.su[e], sm.su[e + 1], sm.su[e + 2], sm.sd[e], sm.sd[e + 1],
-                                    sm.sd[e + 2], sm.sdq[e], sm.sdq[e + 1], lqv[rr], inv_dx, c2);
-        const float w = f * d_f;
-#pragma unroll
-        for (int j = 0; j < KB; ++j) acc[j] = fmaf(x[rr][j], w, acc[j]);
-      }
-    }
-    if (jac) {
-      // Phi^T J_f Phi over 64-row sub-chunks: stage basis rows (+ halo),
-      // W = J_f Phi, then the blocked rank-64 update.
-      for (int s0 = 0; s0 < rows; s0 += 64) {
-        const int sr = min(64, rows - s0);
-#pragma unroll
-        for (int rr = 0; rr < RPT; ++rr) {
-          const int e = rr * kBT + t;
-          if (e < rows && e >= s0 - 1 && e <= s0 + sr) {
-#pragma unroll
-            for (int j = 0; j < KB; ++j) sm.P[(e - s0 + 1) * KB + j] = x[rr][j];
-          }
-        }
-        if (s0 == 0)
-          for (int j = t; j < KB; j += kBT) sm.P[j] = sm.hx[j];
-        if (s0 + sr == rows)
-          for (int j = t; j < KB; j += kBT) sm.P[(sr + 1) * KB + j] = sm.hx[kMaxR + j];
-        __syncthreads();
-        for (int e = t; e < sr * KB; e += kBT) {
-          const int rl = e / KB, l = e % KB;
-          const int ee = s0 + rl;
-          float dl, dc, dr;
-          burgers_band32(sm.su[ee] + sm.sd[ee], sm.su[ee + 1] + sm.sd[ee + 1], sm.su[ee + 2] + sm.sd[ee + 2],
-                         inv_dx, c2, dl, dc, dr);
-          sm.W[rl * KB + l] = dl * sm.P[rl * KB + l] + dc * sm.P[(rl + 1) * KB + l] + dr * sm.P[(rl + 2) * KB + l];
-        }
-        __syncthreads();
-        blk_accum<KB>(sm.P + KB, sm.W, sr, m);
-        __syncthreads();
-      }
-    }
-    __syncthreads();
   }
   double* gp = A.gpart + (size_t)tile * kPS;
   tile_reduce<KB>(acc, k, sm.red, gp);
@@ -568,24 +652,58 @@ __device__ void step_instance(const BArgs& A, StepSmem& sm, int i, int it, unsig
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kBT, 1) batch_steps_kernel(BArgs A) {
+// Largest current rank over the batch (every CTA computes the same value).
+__device__ int batch_max_rank(const BArgs& A) {
+  __shared__ int s_m;
+  if (threadIdx.x == 0) s_m = 0;
+  __syncthreads();
+  int m = 0;
+  for (int i = threadIdx.x; i < A.count; i += blockDim.x) m = max(m, A.rank[i]);
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0) atomicMax(&s_m, m);
+  __syncthreads();
+  return s_m;
+}
+
+// Calls f(integral_constant<KB>) for the bucket of r, among the buckets up to
+// MAXKB.
+template <int MAXKB, typename F>
+__device__ __forceinline__ void with_bucket_upto(int r, F&& f) {
+  const int kb = bucket_of(r);
+  if (kb <= 8) { f(std::integral_constant<int, 8>{}); return; }
+  if constexpr (MAXKB >= 16) { if (kb <= 16) { f(std::integral_constant<int, 16>{}); return; } }
+  if constexpr (MAXKB >= 32) { if (kb <= 32) { f(std::integral_constant<int, 32>{}); return; } }
+  if constexpr (MAXKB >= 48) { if (kb <= 48) { f(std::integral_constant<int, 48>{}); return; } }
+  if constexpr (MAXKB >= 64) { f(std::integral_constant<int, 64>{}); }
+}
+
+constexpr int kLowRank = 16;   // rank limit of the two-CTAs-per-SM instantiation
+
+// Two instantiations are launched back to back for every segment of steps:
+// MAXKB = kLowRank (two CTAs per SM; fewer registers) runs when every rank
+// is at most kLowRank, MAXKB = kMaxR otherwise; the other one returns at once.
+template <int MAXKB>
+__global__ void __launch_bounds__(kBT, MAXKB <= kLowRank ? 2 : 1) batch_steps_kernel(BArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StepSmem& sm = *reinterpret_cast<StepSmem*>(smem_raw);
   const int G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
+  {
+    const int mr = batch_max_rank(A);
+    if (MAXKB < kMaxR ? (mr > MAXKB) : (mr <= kLowRank)) return;
+  }
   for (int i = b; i < A.count; i += G)
     for (int j = t; j < kMaxR; j += blockDim.x) A.an[(size_t)i * kMaxR + j] = A.a[(size_t)i * kMaxR + j];
   int gi = 0;   // iteration counter over the whole launch (queue parity)
   for (int step = 0; step < A.nsteps; ++step) {
     for (int it = 1;; ++it, ++gi) {
       const int par = gi & 1;
-      int q;
-      while ((q = next_tile(&A.ctl[par], A.ntiles, &sm.q)) >= 0) {
+      for_each_tile(&A.ctl[par], A.ntiles, &sm.q, [&](int q) {
         const int tile = A.order[q];
         const int i = A.tile_inst[tile];
-        if (it > 1 && !__ldcg(&A.active[i])) continue;
+        if (it > 1 && !__ldcg(&A.active[i])) return;
         const bool jac = __ldcg(&A.need_jac[i]) != 0;
-        with_bucket(A.rank[i], [&](auto kb) { step_tile<decltype(kb)::value>(A, sm, tile, i, jac); });
-      }
+        with_bucket_upto<MAXKB>(A.rank[i], [&](auto kb) { step_tile<decltype(kb)::value>(A, sm, tile, i, jac); });
+      });
       if (!grid_sync(A.bar, A.status)) return;
       if (b == 0 && t == 0) {
         A.ctl[par ^ 1] = 0u;
@@ -821,7 +939,7 @@ __device__ void ev_p1_tile(const BArgs& A, SweepSmem& sm, int tile, int i) {
   float acc[KB];
 #pragma unroll
   for (int j = 0; j < KB; ++j) acc[j] = 0.f;
-  double yy = 0.0;
+  float yy = 0.f;
   for (int c0 = r0; c0 < r1; c0 += CR) {
     const int rows = min(CR, r1 - c0);
 #pragma unroll
@@ -831,9 +949,9 @@ __device__ void ev_p1_tile(const BArgs& A, SweepSmem& sm, int tile, int i) {
         const size_t gi = (size_t)I.vec_off + c0 + e;
         const double yn = __ldcg(&A.y_new[gi]);
         A.y_corr[gi] = yn;
-        const double yh = I.d * (yn - A.q_ref[gi]);
-        yy = fma(yh, yh, yy);
-        const float yf = (float)yh;
+        const float yf = (float)(I.d * (yn - A.q_ref[gi]));
+        A.yhat32[gi] = yf;
+        yy = fmaf(yf, yf, yy);
 #pragma unroll
         for (int j = 0; j < KB; ++j)
           if (j < k) acc[j] = fmaf(__ldg(&phi[(size_t)j * N + c0 + e]), yf, acc[j]);
@@ -843,7 +961,7 @@ __device__ void ev_p1_tile(const BArgs& A, SweepSmem& sm, int tile, int i) {
   double* gp = A.gpart + (size_t)tile * kPS;
   tile_reduce<KB>(acc, k, sm.red, gp);
   __syncthreads();
-  const double ys = block_sum(yy, sm.dred);
+  const double ys = block_sum((double)yy, sm.dred);
   if (t == 0) gp[kMaxR] = ys;
 }
 
@@ -878,7 +996,7 @@ __device__ void ev_p2_tile(const BArgs& A, SweepSmem& sm, int tile, int i) {
       const int e = rr * kBT + t;
       if (e < rows) {
         const size_t gi = (size_t)I.vec_off + c0 + e;
-        float v = (float)(I.d * (__ldcg(&A.y_corr[gi]) - A.q_ref[gi]));
+        float v = __ldcg(&A.yhat32[gi]);
 #pragma unroll
         for (int j = 0; j < KB; ++j) v = fmaf(-x[rr][j], sm.pf[j], v);
         A.qres[gi] = v;
@@ -950,14 +1068,16 @@ __device__ void ev_rot_tile(const BArgs& A, SweepSmem& sm, int tile, int i) {
       }
     }
     __syncthreads();
-    // FP32 sums over runs of at most 64 rows (one group's share of them),
-    // added to this thread's FP64 slots: the Gram carries about eps * 8
-    // relative error per run instead of eps * sqrt(rows per tile)
-    for (int s0 = 0; s0 < rows; s0 += 64) {
+    // FP32 sums over at most 64 of a thread's rows (its group takes every
+    // groups-th row of a run of 64 * groups), added to the thread's FP64
+    // slots: about eps * 8 relative error per run instead of
+    // eps * sqrt(rows per tile), at 16 FP64 adds per 64 rows
+    constexpr int kRun = 64 * Blk<KB>::groups;
+    for (int s0 = 0; s0 < rows; s0 += kRun) {
       float m[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) m[q] = 0.f;
-      blk_accum<KB>(sm.P + s0 * KB, sm.P + s0 * KB, min(64, rows - s0), m);
+      blk_accum<KB>(sm.P + s0 * KB, sm.P + s0 * KB, min(kRun, rows - s0), m);
 #pragma unroll
       for (int q = 0; q < 16; ++q) sm.Gd[t * 16 + q] += (double)m[q];
     }
@@ -1217,13 +1337,12 @@ __global__ void __launch_bounds__(kBT, 1) batch_event_kernel(BArgs A) {
   CholSmem& ch = *reinterpret_cast<CholSmem*>(smem_raw);
   const int G = gridDim.x, b = blockIdx.x;
   const long long M = *A.M;
-  int q;
   // ---- P1 ----
-  while ((q = next_tile(&A.ctl[0], A.ntiles, &sw.q)) >= 0) {
+  for_each_tile(&A.ctl[0], A.ntiles, &sw.q, [&](int q) {
     const int tile = A.order[q], i = A.tile_inst[tile];
-    if (!is_event(A.inst[i], M)) continue;
+    if (!is_event(A.inst[i], M)) return;
     with_bucket(A.rank[i], [&](auto kb) { ev_p1_tile<decltype(kb)::value>(A, sw, tile, i); });
-  }
+  });
   if (!grid_sync(A.bar, A.status)) return;
   // ---- p1 and |yhat|^2 per instance ----
   for (int i = b; i < A.count; i += G) {
@@ -1235,11 +1354,11 @@ __global__ void __launch_bounds__(kBT, 1) batch_event_kernel(BArgs A) {
   }
   if (!grid_sync(A.bar, A.status)) return;
   // ---- P2 ----
-  while ((q = next_tile(&A.ctl[1], A.ntiles, &sw.q)) >= 0) {
+  for_each_tile(&A.ctl[1], A.ntiles, &sw.q, [&](int q) {
     const int tile = A.order[q], i = A.tile_inst[tile];
-    if (!is_event(A.inst[i], M)) continue;
+    if (!is_event(A.inst[i], M)) return;
     with_bucket(A.rank[i], [&](auto kb) { ev_p2_tile<decltype(kb)::value>(A, sw, tile, i); });
-  }
+  });
   if (!grid_sync(A.bar, A.status)) return;
   // ---- core SVD per instance ----
   for (int i = b; i < A.count; i += G) {
@@ -1249,13 +1368,13 @@ __global__ void __launch_bounds__(kBT, 1) batch_event_kernel(BArgs A) {
   }
   if (!grid_sync(A.bar, A.status)) return;
   // ---- rotation + Gram ----
-  while ((q = next_tile(&A.ctl[2], A.ntiles, &sw.q)) >= 0) {
+  for_each_tile(&A.ctl[2], A.ntiles, &sw.q, [&](int q) {
     const int tile = A.order[q], i = A.tile_inst[tile];
-    if (!is_event(A.inst[i], M)) continue;
+    if (!is_event(A.inst[i], M)) return;
     const double* esc = A.ev_sc + (size_t)i * 8;   // k' and k of this update
     const int kb_cols = max((int)__ldcg(&esc[2]), (int)__ldcg(&esc[3]));
     with_bucket(kb_cols, [&](auto kb) { ev_rot_tile<decltype(kb)::value>(A, sw, tile, i); });
-  }
+  });
   if (!grid_sync(A.bar, A.status)) return;
   // ---- Cholesky per instance ----
   for (int i = b; i < A.count; i += G) {
@@ -1265,11 +1384,11 @@ __global__ void __launch_bounds__(kBT, 1) batch_event_kernel(BArgs A) {
   }
   if (!grid_sync(A.bar, A.status)) return;
   // ---- Phi <- Phi R^-1 ----
-  while ((q = next_tile(&A.ctl[3], A.ntiles, &sw.q)) >= 0) {
+  for_each_tile(&A.ctl[3], A.ntiles, &sw.q, [&](int q) {
     const int tile = A.order[q], i = A.tile_inst[tile];
-    if (!is_event(A.inst[i], M)) continue;
+    if (!is_event(A.inst[i], M)) return;
     with_bucket((int)__ldcg(&A.ev_sc[(size_t)i * 8 + 2]), [&](auto kb) { ev_apply_tile<decltype(kb)::value>(A, sw, tile, i); });
-  }
+  });
 }
 
 // FP32 copies of q_ref and of its first and second differences (periodic),
@@ -1303,7 +1422,7 @@ using namespace rom;
 struct rom_batch {
   int count;
   cudaStream_t stream;
-  int grid_sweep, grid_fom;
+  int grid_sweep, grid_fom, grid_lo;
   long long M;                 // online steps done by every instance
   int ntiles, nchunks, fom_maxit;
   int poisoned;
@@ -1405,7 +1524,9 @@ cudaError_t run_steps(rom_batch* B, int nsteps) {
   if (e != cudaSuccess) return e;
   B->A.nsteps = nsteps;
   if ((e = prof_mark(B, 0)) != cudaSuccess) return e;
-  e = launch_coop((const void*)batch_steps_kernel, B->grid_sweep, kBT, sizeof(StepSmem), B->A, B->stream);
+  e = launch_coop((const void*)batch_steps_kernel<kLowRank>, B->grid_lo, kBT, sizeof(StepSmem), B->A, B->stream);
+  if (e != cudaSuccess) return e;
+  e = launch_coop((const void*)batch_steps_kernel<kMaxR>, B->grid_sweep, kBT, sizeof(StepSmem), B->A, B->stream);
   if (e != cudaSuccess) return e;
   return prof_mark(B, 0);
 }
@@ -1522,7 +1643,7 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
   BA(A.fom_row, 3 * (size_t)vec_tot); BA(A.fom_chunk, (size_t)B->nchunks * kFomChunkStride);
   BA(A.fom_sep, B->nchunks); BA(A.fom_keys, 4 * (size_t)count);
   BA(A.ev_p, (size_t)count * kMaxCore); BA(A.ev_p2, (size_t)count * kMaxCore); BA(A.ev_sc, (size_t)count * 8);
-  BA(A.qres, vec_tot); BA(A.qr32, vec_tot); BA(A.dq32, vec_tot); BA(A.lq32, vec_tot);
+  BA(A.qres, vec_tot); BA(A.yhat32, vec_tot); BA(A.qr32, vec_tot); BA(A.dq32, vec_tot); BA(A.lq32, vec_tot);
   BA(A.ev_u, (size_t)count * kMaxCore * kMaxR); BA(A.ev_anew, (size_t)count * kMaxR);
   BA(A.ev_r, (size_t)count * kMaxR * kMaxR); BA(A.ctl, 8); BA(A.M, 1); BA(A.bar, 1); BA(A.status, 1);
   BA(B->lift, nmax);
@@ -1601,14 +1722,20 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
   // ---- cooperative grids ----
   int sms = 0, nb = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return fail(ROM_ECUDA);
-  if (cudaFuncSetAttribute((const void*)batch_steps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute((const void*)batch_steps_kernel<kMaxR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(StepSmem)) != cudaSuccess ||
+      cudaFuncSetAttribute((const void*)batch_steps_kernel<kLowRank>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sizeof(StepSmem)) != cudaSuccess ||
       cudaFuncSetAttribute((const void*)batch_event_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)event_smem()) != cudaSuccess)
     return fail(ROM_ECUDA);
   int g1 = 0, g2 = 0, g3 = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)batch_steps_kernel, kBT, sizeof(StepSmem)) != cudaSuccess) return fail(ROM_ECUDA);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)batch_steps_kernel<kMaxR>, kBT, sizeof(StepSmem)) != cudaSuccess) return fail(ROM_ECUDA);
   g1 = nb;
+  int g4 = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g4, (const void*)batch_steps_kernel<kLowRank>, kBT, sizeof(StepSmem)) != cudaSuccess) return fail(ROM_ECUDA);
+  if (g4 < 1) return fail(ROM_ECUDA);
+  B->grid_lo = sms * g4;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)batch_event_kernel, kBT, event_smem()) != cudaSuccess) return fail(ROM_ECUDA);
   g2 = nb;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)batch_fom_kernel, kFomT, 0) != cudaSuccess) return fail(ROM_ECUDA);
