@@ -265,7 +265,9 @@ typedef struct rom_batch rom_batch;
  *           ROM_MIXED_FP32, n_var 1, n_s 0, 1 <= r <= 64,
  *           256 <= n_cells <= 131072, z >= 1 (others as rom_init).
  *  q0s      count host pointers, q0s[i] holding n_cells doubles (copied).
- *  count    1 .. 4096.
+ *  count    1 .. 4096, with at most 256 coarse-FOM chunks per CTA of the FOM
+ *           grid in all (an instance has max(4, 2^ceil(log2(n_cells/512)))
+ *           chunks; the grid is two CTAs per SM): 77,824 on a 152-SM GPU.
  *  stream   cudaStream_t or NULL; every batch call is ordered on it.
  *  out      receives the batch, which owns all its device memory.
  * Errors: ROM_EINVAL (a configuration outside the above), ROM_ENOMEM,

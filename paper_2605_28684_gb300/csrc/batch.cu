@@ -47,6 +47,7 @@ namespace {
 constexpr int kBT = 256;          // threads of the sweep kernels
 constexpr int kFomT = 512;        // threads of the FOM kernel (one row each; two CTAs per SM)
 constexpr int kFomMaxChunks = 256; // FOM chunks per instance (power of two)
+constexpr int kFomItems = 256;     // FOM work items (chunks) per CTA
 constexpr int kPS = kMaxR + 4;    // stride of the per-tile partial vectors
 constexpr int kMaxBatch = 4096;   // instances per batch
 constexpr int kTileRows = 8192;   // rows per tile (a multiple of every chunk size)
@@ -731,29 +732,46 @@ __global__ void __launch_bounds__(kFomT, 2) batch_fom_kernel(BArgs A) {
   __shared__ double su[kFomT];
   __shared__ unsigned int redu[32];
   __shared__ unsigned char s_done[kMaxBatch];
+  // this CTA's work items (chunks q = b + G j), read once per launch
+  __shared__ int it_inst[kFomItems], it_c[kFomItems], it_C[kFomItems], it_beg[kFomItems], it_m[kFomItems];
+  __shared__ int it_n[kFomItems], it_chunk0[kFomItems];
+  __shared__ long long it_vec[kFomItems];
+  __shared__ double it_nu[kFomItems], it_h[kFomItems];
   const int G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
   const long long M = *A.M;
+  const int nitems = (A.nchunks - b + G - 1) / G;
   for (int i = t; i < A.count; i += blockDim.x) s_done[i] = is_event(A.inst[i], M) ? 0 : 1;
+  for (int j = t; j < nitems; j += blockDim.x) {
+    const int q = b + G * j;
+    const int i = A.chunk_inst[q];
+    const Inst& I = A.inst[i];
+    const int C = I.nchunk, c = A.chunk_c[q];
+    const int64_t beg = fchunk_begin(c, C, I.n);
+    it_inst[j] = i; it_c[j] = c; it_C[j] = C; it_beg[j] = (int)beg;
+    it_m[j] = (int)(fchunk_begin(c + 1, C, I.n) - beg);
+    it_n[j] = I.n; it_chunk0[j] = I.chunk0; it_vec[j] = I.vec_off;
+    it_nu[j] = I.nu; it_h[j] = (double)I.z * I.dt;
+  }
   if (b == 0)
     for (int e = t; e < 4 * A.count; e += blockDim.x) A.fom_keys[e] = 0u;
   __syncthreads();
   for (int it = 1; it <= A.fom_maxit; ++it) {
     const int par = it & 1;
     // ---- A: residual (FP64), Jacobian rows (FP32), interior PCR per chunk ----
-    for (int q = b; q < A.nchunks; q += G) {
-      const int i = A.chunk_inst[q];
+    for (int j = 0; j < nitems; ++j) {
+      const int i = it_inst[j];
       if (s_done[i]) continue;
-      const Inst I = A.inst[i];
-      const int C = I.nchunk, c = A.chunk_c[q];
-      const int64_t n = I.n;
-      const int64_t beg = fchunk_begin(c, C, n);
-      const int m = (int)(fchunk_begin(c + 1, C, n) - beg);
+      const int q = b + G * j;
+      const int64_t n = it_n[j];
+      const int64_t beg = it_beg[j];
+      const int m = it_m[j];
       const int mi = m - 1;
-      const double* ucur = (it == 1 ? A.y_corr : A.y_new) + I.vec_off;
-      const double* uprev = A.y_corr + I.vec_off;
-      const double h = (double)I.z * I.dt;
+      const double* ucur = (it == 1 ? A.y_corr : A.y_new) + it_vec[j];
+      const double* uprev = A.y_corr + it_vec[j];
+      const double h = it_h[j];
+      const double nu = it_nu[j];
       const double inv_dx = (double)n;
-      const float nu_f = (float)I.nu, inv_dx_f = (float)n, h_f = (float)h;
+      const float nu_f = (float)nu, inv_dx_f = (float)n, h_f = (float)h;
       __syncthreads();
       const bool act = t < m;
       // the chunk's rows and its two halo rows (loaded together)
@@ -768,7 +786,7 @@ __global__ void __launch_bounds__(kFomT, 2) batch_fom_kernel(BArgs A) {
       if (act) {
         const double ul = (t > 0) ? su[t - 1] : hl;
         const double ur = (t < m - 1) ? su[t + 1] : hr;
-        const double f = burgers_f(ul, u, ur, I.nu, inv_dx);
+        const double f = burgers_f(ul, u, ur, nu, inv_dx);
         const double res = u - un - h * f;
         float dl, dc, dr;
         burgers_band(ul, u, ur, nu_f, inv_dx_f, dl, dc, dr);
@@ -813,7 +831,7 @@ __global__ void __launch_bounds__(kFomT, 2) batch_fom_kernel(BArgs A) {
       if (t < mi) {
         const float ib = sib[t];
         const float yv = d0 * ib, vv = d1 * ib, wv = d2 * ib;
-        float* row = A.fom_row + 3 * (size_t)(I.vec_off + beg + t);
+        float* row = A.fom_row + 3 * (size_t)(it_vec[j] + beg + t);
         row[0] = yv; row[1] = vv; row[2] = wv;
         if (t == 0) { ch[4] = yv; ch[5] = vv; ch[6] = wv; }
         if (t == mi - 1) { ch[7] = yv; ch[8] = vv; ch[9] = wv; }
@@ -861,29 +879,28 @@ __global__ void __launch_bounds__(kFomT, 2) batch_fom_kernel(BArgs A) {
     }
     if (!grid_sync(A.bar, A.status)) return;
     // ---- C: update and per-instance maxima ----
-    for (int q = b; q < A.nchunks; q += G) {
-      const int i = A.chunk_inst[q];
+    for (int j = 0; j < nitems; ++j) {
+      const int i = it_inst[j];
       if (s_done[i]) continue;
-      const Inst I = A.inst[i];
-      const int C = I.nchunk, c = A.chunk_c[q];
-      const int64_t n = I.n;
-      const int64_t beg = fchunk_begin(c, C, n);
-      const int m = (int)(fchunk_begin(c + 1, C, n) - beg);
+      const int C = it_C[j], c = it_c[j];
+      const int64_t beg = it_beg[j];
+      const int m = it_m[j];
       const int mi = m - 1;
-      const float s_left = __ldcg(&A.fom_sep[I.chunk0 + (c - 1 + C) % C]);
-      const float s_self = __ldcg(&A.fom_sep[I.chunk0 + c]);
+      const long long vec_off = it_vec[j];
+      const float s_left = __ldcg(&A.fom_sep[it_chunk0[j] + (c - 1 + C) % C]);
+      const float s_self = __ldcg(&A.fom_sep[it_chunk0[j] + c]);
       unsigned int kd = 0u, ku = 0u;
       if (t < m) {
         float dl;
         if (t < mi) {
-          const float* row = A.fom_row + 3 * (size_t)(I.vec_off + beg + t);
+          const float* row = A.fom_row + 3 * (size_t)(vec_off + beg + t);
           dl = __ldcg(row) + __ldcg(row + 1) * s_left + __ldcg(row + 2) * s_self;
         } else {
           dl = s_self;
         }
-        const double* ucur = (it == 1 ? A.y_corr : A.y_new) + I.vec_off;
+        const double* ucur = (it == 1 ? A.y_corr : A.y_new) + vec_off;
         const double u = __ldcg(&ucur[beg + t]) + (double)dl;
-        A.y_new[I.vec_off + beg + t] = u;
+        A.y_new[vec_off + beg + t] = u;
         kd = __float_as_uint(fabsf(dl));
         ku = isfinite(u) ? __float_as_uint(fabsf((float)u)) : 0x7fc00000u;
         if (!isfinite(dl)) kd = 0x7fc00000u;
@@ -1743,6 +1760,8 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
   if (g1 < 1 || g2 < 1 || g3 < 1) return fail(ROM_ECUDA);
   B->grid_sweep = sms * std::min(g1, g2);
   B->grid_fom = sms * g3;
+  // every CTA of the FOM kernel keeps a table of its chunks in shared memory
+  if ((B->nchunks + B->grid_fom - 1) / B->grid_fom > kFomItems) return fail(ROM_EINVAL);
   *out = B;
   return ROM_OK;
 }
