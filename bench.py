@@ -236,6 +236,12 @@ def src_sha1(rel):
 
 # --------------------------------------------------------------- batched ---
 
+# DRAM traffic of one launch of the batched reduced-step kernel (5 steps) from
+# one ncu capture of the 256-instance workload (summarised under profiles/);
+# reported only while csrc/batch.cu is unchanged.
+TRAFFIC_BATCH = {"bytes": None, "src": "paper_2605_28684_gb300/csrc/batch.cu", "sha1": None}
+
+
 def timed_batch(g, args, stream, dist, world):
     """Aggregate ROM-steps/s of the 256-instance batch and the HBM roofline of
     its reduced-step kernel (each Newton iteration streams every active
@@ -268,6 +274,11 @@ def timed_batch(g, args, stream, dist, world):
     pk = peaks()
     step_s = prof["reduced_steps"]["ms"] / 1e3
     gbs = work["sweep_bytes"] / step_s / 1e9
+    launches = max(1, prof["reduced_steps"]["launches"])
+    traffic = None
+    if TRAFFIC_BATCH["bytes"] is not None and TRAFFIC_BATCH["sha1"] == src_sha1(TRAFFIC_BATCH["src"]) \
+            and len(cfgs) == 256:
+        traffic = TRAFFIC_BATCH["bytes"]
     return {"value": world * len(cfgs) * n_steps / (ms / 1e3), "unit": "ROM-steps/s",
             "instances": len(cfgs), "steps": n_steps, "ms_per_step": ms / n_steps,
             "basis_bytes": lay["basis_bytes"], "rows": lay["rows"], "tiles": lay["tiles"],
@@ -276,8 +287,10 @@ def timed_batch(g, args, stream, dist, world):
             "launches": {p: prof[p]["launches"] for p in prof},
             "roofline": {"bound": "hbm", "kernel": "batch_steps_kernel", "achieved": gbs,
                          "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
-                         "peak_source": pk["source"], "algorithmic_bytes": work["sweep_bytes"],
-                         "traffic": None}}
+                         "peak_source": pk["source"],
+                         "algorithmic_bytes": work["sweep_bytes"] / launches,
+                         "avg_launch_us": step_s / launches * 1e6, "traffic": traffic,
+                         "per": "launch (5 steps of every instance)"}}
 
 
 # ------------------------------------------------------------------- main ---

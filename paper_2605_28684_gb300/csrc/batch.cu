@@ -71,6 +71,7 @@ struct BArgs {
   const int* tile_r0;
   const int* tile_r1;
   const int* order;        // queue order of the tiles (decreasing cost)
+  const int4* qdesc;       // per queue slot: (tile, instance, first row, last row)
   const int* chunk_inst;
   const int* chunk_c;
   float* phi;
@@ -80,6 +81,7 @@ struct BArgs {
   float* lq32;             // q_ref(i+1) - 2 q_ref(i) + q_ref(i-1), likewise
   double* y_corr;          // correction snapshot (previous coarse FOM state)
   double* y_new;           // coarse FOM iterate / new snapshot
+  double* dy;              // last snapshot increment y_new - y_corr (initial guess of the next solve)
   double* a;               // count x kMaxR: reduced state
   double* an;              // count x kMaxR: reduced state at the start of the step
   double* sigma;           // count x kMaxR
@@ -699,8 +701,8 @@ __global__ void __launch_bounds__(kBT, MAXKB <= kLowRank ? 2 : 1) batch_steps_ke
     for (int it = 1;; ++it, ++gi) {
       const int par = gi & 1;
       for_each_tile(&A.ctl[par], A.ntiles, &sm.q, [&](int q) {
-        const int tile = A.order[q];
-        const int i = A.tile_inst[tile];
+        const int4 dsc = __ldg(&A.qdesc[q]);
+        const int tile = dsc.x, i = dsc.y;
         if (it > 1 && !__ldcg(&A.active[i])) return;
         const bool jac = __ldcg(&A.need_jac[i]) != 0;
         with_bucket_upto<MAXKB>(A.rank[i], [&](auto kb) { step_tile<decltype(kb)::value>(A, sm, tile, i, jac); });
@@ -766,7 +768,10 @@ __global__ void __launch_bounds__(kFomT, 2) batch_fom_kernel(BArgs A) {
       const int64_t beg = it_beg[j];
       const int m = it_m[j];
       const int mi = m - 1;
+      // iterate it-1: the previous snapshot extrapolated by the previous
+      // increment (it == 1), else y_new
       const double* ucur = (it == 1 ? A.y_corr : A.y_new) + it_vec[j];
+      const double* dy = A.dy + it_vec[j];
       const double* uprev = A.y_corr + it_vec[j];
       const double h = it_h[j];
       const double nu = it_nu[j];
@@ -778,8 +783,14 @@ __global__ void __launch_bounds__(kFomT, 2) batch_fom_kernel(BArgs A) {
       double u = act ? __ldcg(&ucur[beg + t]) : 0.0;
       const double un = act ? uprev[beg + t] : 0.0;
       double hl = 0.0, hr = 0.0;
-      if (t == 0) hl = __ldcg(&ucur[(beg - 1 + n) % n]);
-      if (t == m - 1) hr = __ldcg(&ucur[(beg + m) % n]);
+      const int64_t il = (beg - 1 + n) % n, ir = (beg + m) % n;
+      if (t == 0) hl = __ldcg(&ucur[il]);
+      if (t == m - 1) hr = __ldcg(&ucur[ir]);
+      if (it == 1) {
+        if (act) u += dy[beg + t];
+        if (t == 0) hl += dy[il];
+        if (t == m - 1) hr += dy[ir];
+      }
       su[t] = u;
       __syncthreads();
       float a_t = 0.f, b_t = 1.f, c_t = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
@@ -899,7 +910,8 @@ __global__ void __launch_bounds__(kFomT, 2) batch_fom_kernel(BArgs A) {
           dl = s_self;
         }
         const double* ucur = (it == 1 ? A.y_corr : A.y_new) + vec_off;
-        const double u = __ldcg(&ucur[beg + t]) + (double)dl;
+        double u = __ldcg(&ucur[beg + t]) + (double)dl;
+        if (it == 1) u += A.dy[vec_off + beg + t];
         A.y_new[vec_off + beg + t] = u;
         kd = __float_as_uint(fabsf(dl));
         ku = isfinite(u) ? __float_as_uint(fabsf((float)u)) : 0x7fc00000u;
@@ -965,6 +977,7 @@ __device__ void ev_p1_tile(const BArgs& A, SweepSmem& sm, int tile, int i) {
       if (e < rows) {
         const size_t gi = (size_t)I.vec_off + c0 + e;
         const double yn = __ldcg(&A.y_new[gi]);
+        A.dy[gi] = yn - A.y_corr[gi];
         A.y_corr[gi] = yn;
         const float yf = (float)(I.d * (yn - A.q_ref[gi]));
         A.yhat32[gi] = yf;
@@ -1356,7 +1369,8 @@ __global__ void __launch_bounds__(kBT, 1) batch_event_kernel(BArgs A) {
   const long long M = *A.M;
   // ---- P1 ----
   for_each_tile(&A.ctl[0], A.ntiles, &sw.q, [&](int q) {
-    const int tile = A.order[q], i = A.tile_inst[tile];
+    const int4 dsc = __ldg(&A.qdesc[q]);
+    const int tile = dsc.x, i = dsc.y;
     if (!is_event(A.inst[i], M)) return;
     with_bucket(A.rank[i], [&](auto kb) { ev_p1_tile<decltype(kb)::value>(A, sw, tile, i); });
   });
@@ -1372,7 +1386,8 @@ __global__ void __launch_bounds__(kBT, 1) batch_event_kernel(BArgs A) {
   if (!grid_sync(A.bar, A.status)) return;
   // ---- P2 ----
   for_each_tile(&A.ctl[1], A.ntiles, &sw.q, [&](int q) {
-    const int tile = A.order[q], i = A.tile_inst[tile];
+    const int4 dsc = __ldg(&A.qdesc[q]);
+    const int tile = dsc.x, i = dsc.y;
     if (!is_event(A.inst[i], M)) return;
     with_bucket(A.rank[i], [&](auto kb) { ev_p2_tile<decltype(kb)::value>(A, sw, tile, i); });
   });
@@ -1386,7 +1401,8 @@ __global__ void __launch_bounds__(kBT, 1) batch_event_kernel(BArgs A) {
   if (!grid_sync(A.bar, A.status)) return;
   // ---- rotation + Gram ----
   for_each_tile(&A.ctl[2], A.ntiles, &sw.q, [&](int q) {
-    const int tile = A.order[q], i = A.tile_inst[tile];
+    const int4 dsc = __ldg(&A.qdesc[q]);
+    const int tile = dsc.x, i = dsc.y;
     if (!is_event(A.inst[i], M)) return;
     const double* esc = A.ev_sc + (size_t)i * 8;   // k' and k of this update
     const int kb_cols = max((int)__ldcg(&esc[2]), (int)__ldcg(&esc[3]));
@@ -1402,7 +1418,8 @@ __global__ void __launch_bounds__(kBT, 1) batch_event_kernel(BArgs A) {
   if (!grid_sync(A.bar, A.status)) return;
   // ---- Phi <- Phi R^-1 ----
   for_each_tile(&A.ctl[3], A.ntiles, &sw.q, [&](int q) {
-    const int tile = A.order[q], i = A.tile_inst[tile];
+    const int4 dsc = __ldg(&A.qdesc[q]);
+    const int tile = dsc.x, i = dsc.y;
     if (!is_event(A.inst[i], M)) return;
     with_bucket((int)__ldcg(&A.ev_sc[(size_t)i * 8 + 2]), [&](auto kb) { ev_apply_tile<decltype(kb)::value>(A, sw, tile, i); });
   });
@@ -1647,11 +1664,12 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
   cudaError_t e = cudaSuccess;
   Inst* d_inst = nullptr;
   int *d_ti = nullptr, *d_r0 = nullptr, *d_r1 = nullptr, *d_order = nullptr, *d_ci = nullptr, *d_cc = nullptr;
+  int4* d_qdesc = nullptr;
 #define BA(p, n) \
   if (e == cudaSuccess) e = balloc(B, &(p), (size_t)(n))
   BA(d_inst, count); BA(d_ti, B->ntiles); BA(d_r0, B->ntiles); BA(d_r1, B->ntiles); BA(d_order, B->ntiles);
-  BA(d_ci, B->nchunks); BA(d_cc, B->nchunks);
-  BA(A.phi, phi_tot); BA(A.q_ref, vec_tot); BA(A.y_corr, vec_tot); BA(A.y_new, vec_tot);
+  BA(d_ci, B->nchunks); BA(d_cc, B->nchunks); BA(d_qdesc, B->ntiles);
+  BA(A.phi, phi_tot); BA(A.q_ref, vec_tot); BA(A.y_corr, vec_tot); BA(A.y_new, vec_tot); BA(A.dy, vec_tot);
   BA(A.a, (size_t)count * kMaxR); BA(A.an, (size_t)count * kMaxR); BA(A.sigma, (size_t)count * kMaxR);
   BA(A.sweeps, count); BA(A.sweep_cols, count); BA(A.rank, count); BA(A.need_jac, count); BA(A.active, count); BA(A.iters_rom, count); BA(A.iters_fom, count);
   BA(A.jlu, (size_t)count * kMaxR * kMaxR); BA(A.jpiv, (size_t)count * kMaxR);
@@ -1672,7 +1690,7 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
     return ROM_ENOMEM;
   }
   A.inst = d_inst;
-  A.tile_inst = d_ti; A.tile_r0 = d_r0; A.tile_r1 = d_r1; A.order = d_order;
+  A.tile_inst = d_ti; A.tile_r0 = d_r0; A.tile_r1 = d_r1; A.order = d_order; A.qdesc = d_qdesc;
   A.chunk_inst = d_ci; A.chunk_c = d_cc;
   cudaStream_t s = B->stream;
   auto fail = [&](rom_status st) {
@@ -1685,6 +1703,7 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
   const double* qref_d = A.q_ref;
   if (cudaMemsetAsync(A.phi, 0, sizeof(float) * phi_tot, s) != cudaSuccess ||
       cudaMemsetAsync(A.a, 0, sizeof(double) * count * kMaxR, s) != cudaSuccess ||
+      cudaMemsetAsync(A.dy, 0, sizeof(double) * vec_tot, s) != cudaSuccess ||
       cudaMemsetAsync(A.sigma, 0, sizeof(double) * count * kMaxR, s) != cudaSuccess ||
       cudaMemsetAsync(A.need_jac, 0, sizeof(int) * count, s) != cudaSuccess ||
       cudaMemsetAsync(A.iters_rom, 0, sizeof(int) * count, s) != cudaSuccess ||
@@ -1724,6 +1743,11 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
     I.dinv = 1.0 / dv;
   }
   {
+    std::vector<int4> qdesc(B->ntiles);
+    for (int q = 0; q < B->ntiles; ++q) {
+      const int tl = order[q];
+      qdesc[q] = make_int4(tl, tinst[tl], tr0[tl], tr1[tl]);
+    }
     std::vector<int> ones(count, 1);
     if (cudaMemcpyAsync(A.need_jac, ones.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(d_inst, B->hinst.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -1731,6 +1755,7 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
         cudaMemcpyAsync(d_r0, tr0.data(), sizeof(int) * B->ntiles, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(d_r1, tr1.data(), sizeof(int) * B->ntiles, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(d_order, order.data(), sizeof(int) * B->ntiles, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_qdesc, qdesc.data(), sizeof(int4) * B->ntiles, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(d_ci, cinst.data(), sizeof(int) * B->nchunks, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(d_cc, cc.data(), sizeof(int) * B->nchunks, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
