@@ -239,7 +239,8 @@ def src_sha1(rel):
 # DRAM traffic of one launch of the batched reduced-step kernel (5 steps) from
 # one ncu capture of the 256-instance workload (summarised under profiles/);
 # reported only while csrc/batch.cu is unchanged.
-TRAFFIC_BATCH = {"bytes": None, "src": "paper_2605_28684_gb300/csrc/batch.cu", "sha1": None}
+TRAFFIC_BATCH = {"bytes": 862447360, "src": "paper_2605_28684_gb300/csrc/batch.cu",
+                 "sha1": "13f97d6aae5672b0279e3004cab7b131ab90f48c"}
 
 
 def timed_batch(g, args, stream, dist, world):

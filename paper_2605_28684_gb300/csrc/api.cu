@@ -81,7 +81,7 @@ rom_status validate(const rom_config* c) {
   if (c->n_s < 0 || (c->n_s > 0 && (c->n_s < c->r || c->n_s > 256 || c->n_s > N))) return ROM_EINVAL;
   if (c->w_init < 1 || c->z < 1 || c->newton_max < 1) return ROM_EINVAL;
   if (c->n_s > 0) {   // the DEIM step stages the stencil mesh in shared memory
-    size_t need = (size_t)44 * c->n_s * c->r + (size_t)c->n_s * 44 + 17000;
+    size_t need = (size_t)44 * c->n_s * c->r + (size_t)c->n_s * 44 + 33500;
     if (need > 220000) return ROM_EINVAL;
   }
   if (!(c->dt > 0.0) || !(c->nu >= 0.0) || !(c->lambda >= 0.0 && c->lambda <= 1.0)) return ROM_EINVAL;

@@ -92,7 +92,7 @@ struct BArgs {
   int* iters_fom;
   long long* sweeps;       // count: Newton iterations (sweeps over the basis) since reset
   long long* sweep_cols;   // count: basis columns streamed by those sweeps (rank each time)
-  float* jlu;              // count x kMaxR x kMaxR: LU factors of the reduced Jacobian
+  float* jlu;              // count x kMaxR x kMaxR: inverse of the reduced Jacobian (FP32)
   int* jpiv;               // count x kMaxR
   double* gpart;           // ntiles x kPS
   double* gpart2;          // ntiles x kPS
@@ -346,6 +346,7 @@ struct StepSmem {
   float hx[2 * kMaxR];               // basis rows of the chunk halo
   // instance phase
   float J[kMaxR * kMaxR];
+  float Ji[kMaxR * kMaxR];           // inverse of the reduced Jacobian
   double g[kMaxR];
   float x[kMaxR];
   int piv[kMaxR];
@@ -600,20 +601,19 @@ __device__ void step_instance(const BArgs& A, StepSmem& sm, int i, int it, unsig
     }
     __syncthreads();
     lu_factor(J, sm.piv, k);
+    lu_inverse(J, sm.piv, sm.Ji, k);
     float* jg = A.jlu + (size_t)i * kMaxR * kMaxR;
-    for (int e = t; e < k * kMaxR; e += blockDim.x) jg[e] = J[e];
-    for (int j = t; j < k; j += blockDim.x) A.jpiv[(size_t)i * kMaxR + j] = sm.piv[j];
+    for (int e = t; e < k * kMaxR; e += blockDim.x) jg[e] = sm.Ji[e];
     if (t == 0) A.need_jac[i] = 0;
   } else {
     const float* jg = A.jlu + (size_t)i * kMaxR * kMaxR;
-    for (int e = t; e < k * kMaxR; e += blockDim.x) J[e] = __ldcg(&jg[e]);
-    for (int j = t; j < k; j += blockDim.x) sm.piv[j] = __ldcg(&A.jpiv[(size_t)i * kMaxR + j]);
+    for (int e = t; e < k * kMaxR; e += blockDim.x) sm.Ji[e] = __ldcg(&jg[e]);
   }
   double* a = A.a + (size_t)i * kMaxR;
   const double* an = A.an + (size_t)i * kMaxR;
   for (int j = t; j < k; j += blockDim.x) sm.x[j] = (float)(-(a[j] - an[j] - I.dt * sm.g[j]));
   __syncthreads();
-  lu_solve(J, sm.piv, sm.x, k);
+  inv_apply(sm.Ji, sm.x, k);
   if (t < 32) {
     unsigned int kd = 0u, ka = 0u;
     bool bad = false;

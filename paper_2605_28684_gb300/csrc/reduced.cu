@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(kBlock) galerkin_steps_kernel(StepArgs A) {
   float* s_jr = s_jc + rows;
   float* s_phi = s_jr + rows;                                  // 66 x KM  (FP32 tile)
   float* s_w = s_phi + 66 * KM;                                // 64 x KM
+  float* s_Ji = s_w + 64 * KM;                                 // kMaxR x kMaxR: inverse Jacobian
 
   for (int j = t; j < KM; j += blockDim.x) s_a[j] = (j < k) ? A.a[j] : 0.0;
   __syncthreads();
@@ -202,6 +203,7 @@ __global__ void __launch_bounds__(kBlock) galerkin_steps_kernel(StepArgs A) {
         }
         __syncthreads();
         lu_factor(s_J, s_piv, k);
+        lu_inverse(s_J, s_piv, s_Ji, k);
       }
       // residual g (every CTA, fixed-order sum) and Newton update
       grid_reduce_cols(part, G, stride, k, s_g);
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(kBlock) galerkin_steps_kernel(StepArgs A) {
         s_x[j] = (float)(-g);
       }
       __syncthreads();
-      lu_solve(s_J, s_piv, s_x, k);
+      inv_apply(s_Ji, s_x, k);
       if (t < 32) {
         unsigned int kd = 0u, ka = 0u;
         bool bad = false;
@@ -284,6 +286,7 @@ __global__ void __launch_bounds__(kBlock) hyper_steps_kernel(StepArgs A) {
   float* s_mf = s_As + ns * k;                           // nm x k: Phi row / d (FP32)
   float* s_Mf = s_mf + nm * k;                           // k x ns: (P^T Phi)^+ (FP32)
   float* s_dcf = s_Mf + k * ns;                          // ns: d at samples (FP32)
+  float* s_Ji = s_dcf + ns;                              // kMaxR * kMaxR: inverse Jacobian (FP32)
 
   for (int e = t; e < nm * k; e += blockDim.x) {
     int row = e / k, j = e % k;
@@ -340,6 +343,7 @@ __global__ void __launch_bounds__(kBlock) hyper_steps_kernel(StepArgs A) {
         }
         __syncthreads();
         lu_factor(s_J, s_piv, k);
+        lu_inverse(s_J, s_piv, s_Ji, k);
       }
       // residual g_j = a_j - a^n_j - dt sum_q M_jq (d f)_q: one warp per j
       for (int j = wid; j < k; j += nw) {
@@ -349,7 +353,7 @@ __global__ void __launch_bounds__(kBlock) hyper_steps_kernel(StepArgs A) {
         if (lane == 0) s_x[j] = (float)(-(s_a[j] - s_ap[j] - A.dt * s));
       }
       __syncthreads();
-      lu_solve(s_J, s_piv, s_x, k);
+      inv_apply(s_Ji, s_x, k);
       if (t < 32) {
         // max |delta| (an FP32 value) and max |a| rounded to FP32 (it only
         // scales the tolerance), compared as integer keys
@@ -417,7 +421,7 @@ static size_t galerkin_smem(int64_t n, int grid) {
   int rows = (int)((n + grid - 1) / grid) + 1;
   size_t bytes = sizeof(double) * (3 * KM + 32 * KM + 8) + sizeof(float) * (kMaxR * kMaxR + kMaxR) +
                  sizeof(int) * kMaxR + sizeof(double) * (rows + 2) + sizeof(float) * 3 * rows +
-                 sizeof(float) * (66 * KM + 64 * KM) + 64;
+                 sizeof(float) * (66 * KM + 64 * KM + kMaxR * kMaxR) + 64;
   return bytes;
 }
 
@@ -453,7 +457,7 @@ static cudaError_t launch_hyper_t(const StepArgs& A, cudaStream_t s) {
   const size_t ns = A.n_s, nm = 3 * ns, kmax = KM - 1;
   size_t smem = sizeof(double) * (nm * kmax + 3 * nm + 2 * ns + 2 * KM + 8) +
                 sizeof(float) * (kMaxR * kMaxR + kMaxR) + sizeof(int) * kMaxR +
-                sizeof(float) * (nm + ns * kmax + nm * kmax + kmax * ns + ns) + 64;
+                sizeof(float) * (nm + ns * kmax + nm * kmax + kmax * ns + ns + kMaxR * kMaxR) + 64;
   cudaError_t e = cudaFuncSetAttribute(hyper_steps_kernel<KM>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -246,6 +246,48 @@ __device__ __forceinline__ void lu_factor(float* J, int* piv, int k) {
   }
 }
 
+// Inverse of a k x k FP32 matrix factorised by lu_factor, into Ji (row-major,
+// ld kMaxR): thread l < k solves for column l (needs blockDim >= k). Newton
+// loops that keep one factorisation for several iterations form it once, so
+// that every iteration's solve is a k-thread matrix-vector product
+// (inv_apply) instead of 2k dependent warp reductions.
+__device__ __forceinline__ void lu_inverse(const float* J, const int* piv, float* Ji, int k) {
+  const int l = threadIdx.x;
+  if (l < k) {
+    for (int i = 0; i < k; ++i) Ji[i * kMaxR + l] = (i == l) ? 1.f : 0.f;
+    for (int c = 0; c < k; ++c) {        // the row swaps of the factorisation, in order
+      const int p = piv[c];
+      if (p != c) {
+        const float tmp = Ji[c * kMaxR + l];
+        Ji[c * kMaxR + l] = Ji[p * kMaxR + l];
+        Ji[p * kMaxR + l] = tmp;
+      }
+    }
+    for (int i = 0; i < k; ++i) {        // L y = P e_l (unit lower)
+      float s = Ji[i * kMaxR + l];
+      for (int m = 0; m < i; ++m) s = fmaf(-J[i * kMaxR + m], Ji[m * kMaxR + l], s);
+      Ji[i * kMaxR + l] = s;
+    }
+    for (int i = k - 1; i >= 0; --i) {   // U x = y
+      float s = Ji[i * kMaxR + l];
+      for (int m = i + 1; m < k; ++m) s = fmaf(-J[i * kMaxR + m], Ji[m * kMaxR + l], s);
+      Ji[i * kMaxR + l] = s / J[i * kMaxR + i];
+    }
+  }
+  __syncthreads();
+}
+
+// x <- Ji x for a k-vector x in shared memory (block-level).
+__device__ __forceinline__ void inv_apply(const float* Ji, float* x, int k) {
+  const int j = threadIdx.x;
+  float v = 0.f;
+  if (j < k)
+    for (int l = 0; l < k; ++l) v = fmaf(Ji[j * kMaxR + l], x[l], v);
+  __syncthreads();
+  if (j < k) x[j] = v;
+  __syncthreads();
+}
+
 // Solve (LU) x = b for the RHS in x (FP32), by warp 0.
 __device__ __forceinline__ void lu_solve(const float* J, const int* piv, float* x, int k) {
   if (threadIdx.x < 32) {
