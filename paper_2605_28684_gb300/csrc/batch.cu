@@ -1,25 +1,27 @@
 // Batched execution of many independent adaptive ROMs: Burgers instances of
 // uneven size (N, r, nu, z, lambda per instance) in the mixed form (FP32 basis
-// with FP32 lift, projections and rotation; FP64 residual, coarse FOM, core
-// SVD and re-orthonormalisation). Every instance runs the online loop of
-// Algorithm 1 with the plain Galerkin step and the iSVD of Algorithm 2.
+// with FP32 lift, projections and rotation; FP64 coarse FOM, core SVD and
+// re-orthonormalisation). Every instance runs the online loop of Algorithm 1
+// with the plain Galerkin step and the iSVD of Algorithm 2.
 //
 // All instances advance in lockstep, one time step at a time, so that one
 // pass over the bases serves every instance: a Newton iteration streams the
-// FP32 bases of the whole batch once (about 0.5 GB for 256 instances of
-// N ~ 18k, r ~ 28), which makes the batch HBM-bound where a single small ROM
-// is latency-bound. Work is cut into row tiles (instance, first row, last
-// row); CTAs take tiles from a queue ordered by decreasing cost, and per-tile
-// partial sums are combined per instance in tile order, so results do not
-// depend on which CTA took which tile. Three persistent cooperative kernels:
+// live columns of the FP32 bases of the whole batch once, and the batch is
+// limited by memory traffic and latency instead of running hundreds of small
+// latency-bound solves one after another. Work is cut into row tiles
+// (instance, first row, last row); CTAs take tiles from a queue ordered by
+// decreasing cost, and per-tile partial sums are combined per instance in tile
+// order, so results do not depend on which CTA took which tile. Three
+// persistent cooperative kernels:
 //   batch_steps_kernel  BE Galerkin steps: per iteration a sweep over the
-//                       tiles (lift, FP64 residual, FP32 projection, FP32
-//                       reduced Jacobian when due) and an instance phase
-//                       (Newton update with the FP32 LU factors).
+//                       tiles (FP32 lift, FP32 difference-form residual, FP32
+//                       projection, FP32 reduced Jacobian when due) and an
+//                       instance phase (Newton update with the inverse of the
+//                       reduced Jacobian).
 //   batch_fom_kernel    the coarse FOM step (Eq. coarse_fom_backward_euler)
-//                       of the instances that adapt now: Newton with the
-//                       chunked PCR solver of fom.cu over (instance, chunk)
-//                       work items.
+//                       of the instances that adapt now: Newton with FP64
+//                       residuals and a chunked PCR solver over (instance,
+//                       chunk) work items.
 //   batch_event_kernel  Algorithm 2 for those instances: projections, one CTA
 //                       per instance for the core SVD, rotation with a fused
 //                       Gram matrix, FP64 Cholesky, basis <- basis R^-1.
@@ -93,7 +95,6 @@ struct BArgs {
   long long* sweeps;       // count: Newton iterations (sweeps over the basis) since reset
   long long* sweep_cols;   // count: basis columns streamed by those sweeps (rank each time)
   float* jlu;              // count x kMaxR x kMaxR: inverse of the reduced Jacobian (FP32)
-  int* jpiv;               // count x kMaxR
   double* gpart;           // ntiles x kPS
   double* gpart2;          // ntiles x kPS
   float* mpart;            // ntiles x kMaxR x kMaxR: reduced Jacobian partials (FP32)
@@ -1672,7 +1673,7 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
   BA(A.phi, phi_tot); BA(A.q_ref, vec_tot); BA(A.y_corr, vec_tot); BA(A.y_new, vec_tot); BA(A.dy, vec_tot);
   BA(A.a, (size_t)count * kMaxR); BA(A.an, (size_t)count * kMaxR); BA(A.sigma, (size_t)count * kMaxR);
   BA(A.sweeps, count); BA(A.sweep_cols, count); BA(A.rank, count); BA(A.need_jac, count); BA(A.active, count); BA(A.iters_rom, count); BA(A.iters_fom, count);
-  BA(A.jlu, (size_t)count * kMaxR * kMaxR); BA(A.jpiv, (size_t)count * kMaxR);
+  BA(A.jlu, (size_t)count * kMaxR * kMaxR);
   BA(A.gpart, (size_t)B->ntiles * kPS); BA(A.gpart2, (size_t)B->ntiles * kPS);
   BA(A.mpart, (size_t)B->ntiles * kMaxR * kMaxR); BA(A.gram_part, (size_t)B->ntiles * kMaxR * kMaxR);
   BA(A.fom_row, 3 * (size_t)vec_tot); BA(A.fom_chunk, (size_t)B->nchunks * kFomChunkStride);
