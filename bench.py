@@ -240,7 +240,7 @@ def src_sha1(rel):
 # one ncu capture of the 256-instance workload (summarised under profiles/);
 # reported only while csrc/batch.cu is unchanged.
 TRAFFIC_BATCH = {"bytes": 862447360, "src": "paper_2605_28684_gb300/csrc/batch.cu",
-                 "sha1": "2a2943404ea672e31672c54f3d3974868668e92c"}
+                 "sha1": "ea1aecc6c133f3d33cc03f2ecd70ba22c6e22eea"}
 
 
 def timed_batch(g, args, stream, dist, world):
@@ -250,19 +250,24 @@ def timed_batch(g, args, stream, dist, world):
     import torch
     cfgs = synth.config_batch(args.batch_count)
     q0s = [synth.initial_state(c) for c in cfgs]
-    b = g.Batch(cfgs, q0s, stream=stream.cuda_stream)
+    bs = torch.cuda.Stream()      # a capturable stream: whole intervals replay a CUDA graph
+    b = g.Batch(cfgs, q0s, stream=bs.cuda_stream)
     n_steps = 5 * args.steps
     b.step(5 * args.warmup)
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    b.profile(True)
-    start.record(stream)
+    start.record(bs)
     b.step(n_steps)
-    end.record(stream)
+    end.record(bs)
     torch.cuda.synchronize()
     ms = start.elapsed_time(end)
+    graph_state = b.layout()["graph"]
+    # the same number of steps again with the per-phase timer on (no graph)
+    b.profile(True)
+    b.step(n_steps)
+    torch.cuda.synchronize()
     prof = b.profile_read()
     work = b.work()
     lay = b.layout()
@@ -285,6 +290,10 @@ def timed_batch(g, args, stream, dist, world):
             "basis_bytes": lay["basis_bytes"], "rows": lay["rows"], "tiles": lay["tiles"],
             "newton_iters_per_instance_step": work["newton_iters"] / (len(cfgs) * n_steps),
             "phases_ms": {p: prof[p]["ms"] for p in prof},
+            "graph": {"state": graph_state,
+                      "note": "1: each adaptation interval of the timed run replays one captured "
+                              "CUDA graph; the phase split comes from a second, profiled run "
+                              "of the same length"},
             "launches": {p: prof[p]["launches"] for p in prof},
             "roofline": {"bound": "hbm", "kernel": "batch_steps_kernel", "achieved": gbs,
                          "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],

@@ -285,6 +285,10 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
  * calls except rom_batch_destroy).
  */
 rom_status rom_batch_step(rom_batch* b, int64_t n_steps);
+/*   On a stream other than the legacy default stream, and while the per-phase
+ *   timer (rom_batch_profile) is off, the launches of one whole adaptation
+ *   interval are captured once into a CUDA graph and replayed for every
+ *   interval of the same length; otherwise they are launched one by one. */
 
 /*
  * State of instance i, as rom_state: q_tilde (n_cells), a (r), sigma (r),
@@ -301,10 +305,11 @@ rom_status rom_batch_info(rom_batch* b, int32_t i, int32_t* rank, int32_t* rom_i
                           int32_t* fom_iters);
 
 /* Layout of the batch: total FP32 basis bytes (sum of n_cells * r * 4), total
- * rows (sum of n_cells), number of row tiles, CTAs of the sweep kernels. Any
- * output may be NULL. */
+ * rows (sum of n_cells), number of row tiles, CTAs of the sweep kernels, and
+ * whether whole adaptation intervals replay a captured graph (1), have not
+ * been tried yet (0) or launch one by one (-1). Any output may be NULL. */
 rom_status rom_batch_layout(rom_batch* b, int64_t* basis_bytes, int64_t* rows, int32_t* tiles,
-                            int32_t* grid);
+                            int32_t* grid, int32_t* graph);
 
 /* Per-phase device timing (as rom_profile): phases 0 reduced steps, 1 coarse
  * FOM, 2 iSVD update; ms_total and launches hold 3 entries each. */

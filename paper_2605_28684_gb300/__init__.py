@@ -188,11 +188,13 @@ class Batch:
 
     def layout(self):
         bb, rows = ctypes.c_int64(), ctypes.c_int64()
-        tiles, grid = ctypes.c_int32(), ctypes.c_int32()
+        tiles, grid, graph = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         _lib.check(self._lib.rom_batch_layout(self._b, ctypes.byref(bb), ctypes.byref(rows),
-                                              ctypes.byref(tiles), ctypes.byref(grid)),
+                                              ctypes.byref(tiles), ctypes.byref(grid),
+                                              ctypes.byref(graph)),
                    "rom_batch_layout")
-        return dict(basis_bytes=bb.value, rows=rows.value, tiles=tiles.value, grid=grid.value)
+        return dict(basis_bytes=bb.value, rows=rows.value, tiles=tiles.value, grid=grid.value,
+                    graph=graph.value)
 
     def profile(self, enable: bool):
         _lib.check(self._lib.rom_batch_profile(self._b, 1 if enable else 0), "rom_batch_profile")

@@ -1467,6 +1467,10 @@ struct rom_batch {
   BArgs A;                     // device pointers
   double* lift;                // lifted state of one instance (max N)
   std::vector<void*> allocs;
+  // one adaptation interval (steps + coarse FOM + iSVD) captured as a graph
+  cudaGraphExec_t seg_graph;
+  long long seg_len;
+  int graph_state;             // 0 not tried, 1 captured, -1 unavailable
   // per-phase timing: 0 steps, 1 coarse FOM, 2 iSVD
   int prof_on;
   std::vector<cudaEvent_t> ev;
@@ -1497,6 +1501,8 @@ cudaError_t balloc(rom_batch* B, T** p, size_t n) {
 }
 
 void batch_free(rom_batch* B) {
+  if (B->seg_graph) cudaGraphExecDestroy(B->seg_graph);
+  B->seg_graph = nullptr;
   for (void* p : B->allocs) cudaFree(p);
   B->allocs.clear();
   for (cudaEvent_t e : B->ev) cudaEventDestroy(e);
@@ -1583,6 +1589,24 @@ cudaError_t run_event(rom_batch* B) {
 
 size_t event_smem() { return std::max(sizeof(SweepSmem), std::max(sizeof(CoreSmem), sizeof(CholSmem))); }
 
+// Captures the launches of one adaptation interval (seg steps, then the
+// coarse FOM and the iSVD update) into a graph. Every launch reads the step
+// counter and the ranks from device memory, so the same graph serves every
+// interval of that length. Fails (and nothing runs) on a stream that cannot
+// be captured, such as the legacy default stream.
+cudaError_t capture_interval(rom_batch* B, long long seg) {
+  cudaError_t e = cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t e1 = run_steps(B, (int)seg);
+  if (e1 == cudaSuccess) e1 = run_event(B);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(B->stream, &g);
+  if (e1 == cudaSuccess) e1 = e2;
+  if (e1 == cudaSuccess) e1 = cudaGraphInstantiate(&B->seg_graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  return e1;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1606,6 +1630,9 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
   B->M = 0;
   B->poisoned = 0;
   B->prof_on = 0;
+  B->seg_graph = nullptr;
+  B->seg_len = 0;
+  B->graph_state = 0;
   for (int p = 0; p < 3; ++p) { B->prof_ms[p] = 0.0; B->prof_cnt[p] = 0; }
   B->cfg.assign(cfgs, cfgs + count);
   memset(&B->A, 0, sizeof(BArgs));
@@ -1801,6 +1828,29 @@ rom_status rom_batch_step(rom_batch* B, int64_t n_steps) {
       const long long z = B->hinst[i].z;
       to_event = std::min(to_event, z - (B->M % z));
     }
+    // whole adaptation intervals replay one captured graph (not while the
+    // per-phase timer is on)
+    if (!B->prof_on && B->graph_state >= 0 && to_event <= n_steps) {
+      if (B->graph_state == 0) {
+        if (capture_interval(B, to_event) == cudaSuccess) {
+          B->graph_state = 1;
+          B->seg_len = to_event;
+        } else {
+          cudaGetLastError();
+          B->graph_state = -1;
+        }
+      }
+      if (B->graph_state == 1 && to_event == B->seg_len) {
+        if (cudaGraphLaunch(B->seg_graph, B->stream) != cudaSuccess) {
+          B->poisoned = 1;
+          cudaGetLastError();
+          return ROM_ECUDA;
+        }
+        B->M += to_event;
+        n_steps -= to_event;
+        continue;
+      }
+    }
     const long long seg = std::min<long long>(n_steps, to_event);
     if (run_steps(B, (int)seg) != cudaSuccess) { B->poisoned = 1; cudaGetLastError(); return ROM_ECUDA; }
     B->M += seg;
@@ -1874,8 +1924,9 @@ rom_status rom_batch_info(rom_batch* B, int32_t i, int32_t* rank, int32_t* rom_i
 }
 
 rom_status rom_batch_layout(rom_batch* B, int64_t* basis_bytes, int64_t* rows, int32_t* tiles,
-                            int32_t* grid) {
+                            int32_t* grid, int32_t* graph) {
   if (!B) return ROM_EINVAL;
+  if (graph) *graph = B->graph_state;
   long long bb = 0, nr = 0;
   for (const Inst& I : B->hinst) {
     bb += (long long)I.n * I.r * (long long)sizeof(float);

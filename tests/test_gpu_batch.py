@@ -161,3 +161,25 @@ def test_batch_nonconvergence_reported_and_poisons(g):
         b = g.Batch(cfgs, q0s)      # the offline FOM already needs more than one iteration
         b.step(1)
     assert ei.value.code == 4
+
+
+def test_batch_graph_replay_matches_direct_launches(g):
+    """On a capturable stream whole adaptation intervals replay one captured
+    CUDA graph; the trajectory equals the one launched kernel by kernel on the
+    default stream (up to the order of FP32 atomic adds in the reduced
+    Jacobian, which only steers Newton)."""
+    cfgs = small_batch()[:3]
+    q0s = [synth.initial_state(c) for c in cfgs]
+    side = torch.cuda.Stream()
+    bg = g.Batch(cfgs, q0s, stream=side.cuda_stream)
+    bd = g.Batch(cfgs, q0s)
+    bg.step(43)
+    bd.step(43)
+    torch.cuda.synchronize()
+    assert bg.layout()["graph"] == 1
+    assert bd.layout()["graph"] == -1          # the legacy default stream cannot be captured
+    for i in range(len(cfgs)):
+        assert rel(bg.q_tilde(i), bd.q_tilde(i)) <= 1e-8, i
+        assert bg.state(i)["step"] == bd.state(i)["step"] == 143
+    bg.close()
+    bd.close()
