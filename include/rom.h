@@ -305,11 +305,13 @@ rom_status rom_batch_info(rom_batch* b, int32_t i, int32_t* rank, int32_t* rom_i
                           int32_t* fom_iters);
 
 /* Layout of the batch: total FP32 basis bytes (sum of n_cells * r * 4), total
- * rows (sum of n_cells), number of row tiles, CTAs of the sweep kernels, and
+ * rows (sum of n_cells), number of row tiles and their size in rows (chosen by
+ * rom_batch_init: the fastest of 2048, 4096, 8192 and 16384 rows in a timed
+ * residual sweep over the instances' bases), CTAs of the sweep kernels, and
  * whether whole adaptation intervals replay a captured graph (1), have not
  * been tried yet (0) or launch one by one (-1). Any output may be NULL. */
 rom_status rom_batch_layout(rom_batch* b, int64_t* basis_bytes, int64_t* rows, int32_t* tiles,
-                            int32_t* grid, int32_t* graph);
+                            int32_t* tile_rows, int32_t* grid, int32_t* graph);
 
 /* Per-phase device timing (as rom_profile): phases 0 reduced steps, 1 coarse
  * FOM, 2 iSVD update; ms_total and launches hold 3 entries each. */

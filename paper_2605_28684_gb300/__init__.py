@@ -188,13 +188,14 @@ class Batch:
 
     def layout(self):
         bb, rows = ctypes.c_int64(), ctypes.c_int64()
-        tiles, grid, graph = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        tiles, tile_rows = ctypes.c_int32(), ctypes.c_int32()
+        grid, graph = ctypes.c_int32(), ctypes.c_int32()
         _lib.check(self._lib.rom_batch_layout(self._b, ctypes.byref(bb), ctypes.byref(rows),
-                                              ctypes.byref(tiles), ctypes.byref(grid),
-                                              ctypes.byref(graph)),
+                                              ctypes.byref(tiles), ctypes.byref(tile_rows),
+                                              ctypes.byref(grid), ctypes.byref(graph)),
                    "rom_batch_layout")
-        return dict(basis_bytes=bb.value, rows=rows.value, tiles=tiles.value, grid=grid.value,
-                    graph=graph.value)
+        return dict(basis_bytes=bb.value, rows=rows.value, tiles=tiles.value,
+                    tile_rows=tile_rows.value, grid=grid.value, graph=graph.value)
 
     def profile(self, enable: bool):
         _lib.check(self._lib.rom_batch_profile(self._b, 1 if enable else 0), "rom_batch_profile")

@@ -87,7 +87,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rom_batch_step.argtypes = [P, ctypes.c_int64]
     lib.rom_batch_state.argtypes = [P, ctypes.c_int32, D, D, D, D, D, I64P]
     lib.rom_batch_info.argtypes = [P, ctypes.c_int32, I32P, I32P, I32P]
-    lib.rom_batch_layout.argtypes = [P, I64P, I64P, I32P, I32P, I32P]
+    lib.rom_batch_layout.argtypes = [P, I64P, I64P, I32P, I32P, I32P, I32P]
     lib.rom_batch_profile.argtypes = [P, ctypes.c_int32]
     lib.rom_batch_profile_read.argtypes = [P, D, I64P]
     lib.rom_batch_work.argtypes = [P, I64P, D]

@@ -52,7 +52,8 @@ constexpr int kFomMaxChunks = 256; // FOM chunks per instance (power of two)
 constexpr int kFomItems = 256;     // FOM work items (chunks) per CTA
 constexpr int kPS = kMaxR + 4;    // stride of the per-tile partial vectors
 constexpr int kMaxBatch = 4096;   // instances per batch
-constexpr int kTileRows = 8192;   // rows per tile (a multiple of every chunk size)
+constexpr int kTileRowsMin = 2048;  // smallest tile the autotuner tries (a multiple of every chunk)
+constexpr int kTileCandidates[] = {2048, 4096, 8192, 16384};
 constexpr int kChunkMax = 2048;   // rows per chunk of a sweep (256 threads x rows per thread)
 constexpr int kFomChunkStride = 16;
 
@@ -723,6 +724,24 @@ __global__ void __launch_bounds__(kBT, MAXKB <= kLowRank ? 2 : 1) batch_steps_ke
     }
   }
   if (b == 0 && t == 0) *A.M += A.nsteps;
+}
+
+// One residual sweep over the tiles into the per-tile partials (scratch),
+// without a Newton update: the tile autotuner times it.
+template <int MAXKB>
+__global__ void __launch_bounds__(kBT, MAXKB <= kLowRank ? 2 : 1) batch_sweep_kernel(BArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StepSmem& sm = *reinterpret_cast<StepSmem*>(smem_raw);
+  {
+    const int mr = batch_max_rank(A);
+    if (MAXKB < kMaxR ? (mr > MAXKB) : (mr <= kLowRank)) return;
+  }
+  for_each_tile(&A.ctl[0], A.ntiles, &sm.q, [&](int q) {
+    const int4 dsc = __ldg(&A.qdesc[q]);
+    with_bucket_upto<MAXKB>(A.rank[dsc.y], [&](auto kb) {
+      step_tile<decltype(kb)::value>(A, sm, dsc.x, dsc.y, false);
+    });
+  });
 }
 
 // ========================================================== FOM kernel ===
@@ -1467,6 +1486,12 @@ struct rom_batch {
   BArgs A;                     // device pointers
   double* lift;                // lifted state of one instance (max N)
   std::vector<void*> allocs;
+  // tile tables (rebuilt by the autotuner) and their device copies
+  Inst* d_inst;
+  int *d_ti, *d_r0, *d_r1, *d_order;
+  int4* d_qdesc;
+  int tile_rows;
+  float tune_ms[4];            // timed residual sweep per candidate tile size
   // one adaptation interval (steps + coarse FOM + iSVD) captured as a graph
   cudaGraphExec_t seg_graph;
   long long seg_len;
@@ -1607,6 +1632,75 @@ cudaError_t capture_interval(rom_batch* B, long long seg) {
   return e1;
 }
 
+// Row tiles of tile_rows rows (the last one of an instance ragged), the queue
+// ordered by decreasing cost (rows x (rank + 3), the live columns plus the
+// reference data), uploaded with the instances' tile ranges.
+cudaError_t set_tiles(rom_batch* B, int tile_rows, const std::vector<int>& rank) {
+  std::vector<int> tinst, tr0, tr1;
+  for (int i = 0; i < B->count; ++i) {
+    Inst& I = B->hinst[i];
+    I.tile0 = (int)tinst.size();
+    for (int r0 = 0; r0 < I.n; r0 += tile_rows) {
+      tinst.push_back(i);
+      tr0.push_back(r0);
+      tr1.push_back(std::min(I.n, r0 + tile_rows));
+    }
+    I.tile1 = (int)tinst.size();
+  }
+  const int nt = (int)tinst.size();
+  std::vector<int> order(nt);
+  for (int q = 0; q < nt; ++q) order[q] = q;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const long long cx = (long long)(tr1[x] - tr0[x]) * (rank[tinst[x]] + 3);
+    const long long cy = (long long)(tr1[y] - tr0[y]) * (rank[tinst[y]] + 3);
+    return cx > cy;
+  });
+  std::vector<int4> qdesc(nt);
+  for (int q = 0; q < nt; ++q) {
+    const int tl = order[q];
+    qdesc[q] = make_int4(tl, tinst[tl], tr0[tl], tr1[tl]);
+  }
+  cudaStream_t s = B->stream;
+  cudaError_t e = cudaMemcpyAsync(B->d_ti, tinst.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(B->d_r0, tr0.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(B->d_r1, tr1.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(B->d_order, order.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(B->d_qdesc, qdesc.data(), sizeof(int4) * nt, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(B->d_inst, B->hinst.data(), sizeof(Inst) * B->count, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) {
+    B->ntiles = nt;
+    B->A.ntiles = nt;
+    B->tile_rows = tile_rows;
+  }
+  return e;
+}
+
+// Device time of one residual sweep over all tiles (mean of three, after one
+// untimed), without changing any state.
+cudaError_t time_dry_sweep(rom_batch* B, float* ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (int r = -1; r < 3 && e == cudaSuccess; ++r) {
+    if (r == 0) e = cudaEventRecord(e0, B->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B->A.ctl, 0, 8 * sizeof(unsigned int), B->stream);
+    if (e == cudaSuccess)
+      e = launch_coop((const void*)batch_sweep_kernel<kLowRank>, B->grid_lo, kBT, sizeof(StepSmem), B->A, B->stream);
+    if (e == cudaSuccess)
+      e = launch_coop((const void*)batch_sweep_kernel<kMaxR>, B->grid_sweep, kBT, sizeof(StepSmem), B->A, B->stream);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, B->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  *ms = t / 3.f;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1633,12 +1727,18 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
   B->seg_graph = nullptr;
   B->seg_len = 0;
   B->graph_state = 0;
+  B->d_inst = nullptr;
+  B->d_ti = B->d_r0 = B->d_r1 = B->d_order = nullptr;
+  B->d_qdesc = nullptr;
+  B->tile_rows = 0;
+  for (int c = 0; c < 4; ++c) B->tune_ms[c] = 0.f;
   for (int p = 0; p < 3; ++p) { B->prof_ms[p] = 0.0; B->prof_cnt[p] = 0; }
   B->cfg.assign(cfgs, cfgs + count);
   memset(&B->A, 0, sizeof(BArgs));
   // ---- layout: packed bases and vectors, tiles, FOM chunks ----
-  std::vector<int> tinst, tr0, tr1, cinst, cc;
+  std::vector<int> cinst, cc;
   long long phi_tot = 0, vec_tot = 0, nmax = 1;
+  int ntiles_max = 0;
   int fom_maxit = 1;
   B->hinst.resize(count);
   for (int i = 0; i < count; ++i) {
@@ -1658,13 +1758,7 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
     I.vec_off = vec_tot;
     phi_tot += ((long long)I.n * I.r + 63) / 64 * 64;
     vec_tot += ((long long)I.n + 31) / 32 * 32;
-    I.tile0 = (int)tinst.size();
-    for (int r0 = 0; r0 < I.n; r0 += kTileRows) {
-      tinst.push_back(i);
-      tr0.push_back(r0);
-      tr1.push_back(std::min(I.n, r0 + kTileRows));
-    }
-    I.tile1 = (int)tinst.size();
+    ntiles_max += (I.n + kTileRowsMin - 1) / kTileRowsMin;
     int C = 4;
     while ((I.n + C - 1) / C > kFomT && C < kFomMaxChunks) C *= 2;
     if ((I.n + C - 1) / C > kFomT) { delete B; return ROM_EINVAL; }
@@ -1673,17 +1767,9 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
     for (int q = 0; q < C; ++q) { cinst.push_back(i); cc.push_back(q); }
     fom_maxit = std::max(fom_maxit, c.newton_max);
   }
-  B->ntiles = (int)tinst.size();
+  B->ntiles = ntiles_max;
   B->nchunks = (int)cinst.size();
   B->fom_maxit = fom_maxit;
-  // queue order: decreasing cost (rows x rank bucket), ties by tile id
-  std::vector<int> order(B->ntiles);
-  for (int q = 0; q < B->ntiles; ++q) order[q] = q;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    const long long cx = (long long)(tr1[x] - tr0[x]) * bucket_of(B->hinst[tinst[x]].r);
-    const long long cy = (long long)(tr1[y] - tr0[y]) * bucket_of(B->hinst[tinst[y]].r);
-    return cx > cy;
-  });
   BArgs& A = B->A;
   A.count = count;
   A.ntiles = B->ntiles;
@@ -1770,23 +1856,17 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
     I.d = dv;
     I.dinv = 1.0 / dv;
   }
+  B->d_inst = d_inst; B->d_ti = d_ti; B->d_r0 = d_r0; B->d_r1 = d_r1; B->d_order = d_order;
+  B->d_qdesc = d_qdesc;
+  std::vector<int> rank0(count, 1);
   {
-    std::vector<int4> qdesc(B->ntiles);
-    for (int q = 0; q < B->ntiles; ++q) {
-      const int tl = order[q];
-      qdesc[q] = make_int4(tl, tinst[tl], tr0[tl], tr1[tl]);
-    }
     std::vector<int> ones(count, 1);
     if (cudaMemcpyAsync(A.need_jac, ones.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(d_inst, B->hinst.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(d_ti, tinst.data(), sizeof(int) * B->ntiles, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(d_r0, tr0.data(), sizeof(int) * B->ntiles, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(d_r1, tr1.data(), sizeof(int) * B->ntiles, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(d_order, order.data(), sizeof(int) * B->ntiles, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(d_qdesc, qdesc.data(), sizeof(int4) * B->ntiles, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(rank0.data(), A.rank, sizeof(int) * count, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(d_ci, cinst.data(), sizeof(int) * B->nchunks, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(d_cc, cc.data(), sizeof(int) * B->nchunks, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
+        cudaStreamSynchronize(s) != cudaSuccess ||
+        set_tiles(B, kTileCandidates[0], rank0) != cudaSuccess)
       return fail(ROM_ECUDA);
   }
   // ---- cooperative grids ----
@@ -1795,6 +1875,10 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
   if (cudaFuncSetAttribute((const void*)batch_steps_kernel<kMaxR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sizeof(StepSmem)) != cudaSuccess ||
       cudaFuncSetAttribute((const void*)batch_steps_kernel<kLowRank>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(StepSmem)) != cudaSuccess ||
+      cudaFuncSetAttribute((const void*)batch_sweep_kernel<kMaxR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(StepSmem)) != cudaSuccess ||
+      cudaFuncSetAttribute((const void*)batch_sweep_kernel<kLowRank>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sizeof(StepSmem)) != cudaSuccess ||
       cudaFuncSetAttribute((const void*)batch_event_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)event_smem()) != cudaSuccess)
@@ -1815,6 +1899,20 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
   B->grid_fom = sms * g3;
   // every CTA of the FOM kernel keeps a table of its chunks in shared memory
   if ((B->nchunks + B->grid_fom - 1) / B->grid_fom > kFomItems) return fail(ROM_EINVAL);
+  // tile autotuning: time a residual sweep over the actual bases for each
+  // candidate tile size and keep the fastest
+  {
+    int best = kTileCandidates[0];
+    float best_ms = 0.f;
+    for (int c = 0; c < (int)(sizeof(kTileCandidates) / sizeof(int)); ++c) {
+      float ms = 0.f;
+      if (set_tiles(B, kTileCandidates[c], rank0) != cudaSuccess || time_dry_sweep(B, &ms) != cudaSuccess)
+        return fail(ROM_ECUDA);
+      B->tune_ms[c] = ms;
+      if (c == 0 || ms < best_ms) { best = kTileCandidates[c]; best_ms = ms; }
+    }
+    if (set_tiles(B, best, rank0) != cudaSuccess) return fail(ROM_ECUDA);
+  }
   *out = B;
   return ROM_OK;
 }
@@ -1924,9 +2022,10 @@ rom_status rom_batch_info(rom_batch* B, int32_t i, int32_t* rank, int32_t* rom_i
 }
 
 rom_status rom_batch_layout(rom_batch* B, int64_t* basis_bytes, int64_t* rows, int32_t* tiles,
-                            int32_t* grid, int32_t* graph) {
+                            int32_t* tile_rows, int32_t* grid, int32_t* graph) {
   if (!B) return ROM_EINVAL;
   if (graph) *graph = B->graph_state;
+  if (tile_rows) *tile_rows = B->tile_rows;
   long long bb = 0, nr = 0;
   for (const Inst& I : B->hinst) {
     bb += (long long)I.n * I.r * (long long)sizeof(float);
