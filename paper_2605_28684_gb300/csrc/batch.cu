@@ -395,17 +395,9 @@ struct CholSmem {
 
 // Registers of one chunk of a sweep tile: the chunk's basis rows and
 // reference-state data, and (warps 0 and 1) the two periodic halo rows.
-// Rows per thread of the step sweep: the small rank buckets keep two chunks
-// in flight (double-buffered registers), so each holds half as many rows.
-template <int KB>
-struct StepRpt {
-  static constexpr bool dbl = false;   // measured slower than one chunk in flight
-  static constexpr int v = dbl ? 32 / KB : Rpt<KB>::v;
-};
-
 template <int KB>
 struct ChunkRegs {
-  static constexpr int RPT = StepRpt<KB>::v;
+  static constexpr int RPT = Rpt<KB>::v;
   float x[RPT][KB];
   float qr[RPT], dq[RPT], lq[RPT];
   float hv0, hv1, hq, hd;
@@ -422,7 +414,7 @@ struct TileCtx {
 
 template <int KB>
 __device__ __forceinline__ void load_chunk(const TileCtx& T, int c0, ChunkRegs<KB>& R) {
-  constexpr int RPT = StepRpt<KB>::v;
+  constexpr int RPT = Rpt<KB>::v;
   constexpr int CR = kBT * RPT;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int rows = min(CR, T.r1 - c0);
@@ -449,7 +441,7 @@ __device__ __forceinline__ void load_chunk(const TileCtx& T, int c0, ChunkRegs<K
 template <int KB>
 __device__ __forceinline__ void compute_chunk(const TileCtx& T, int c0, const ChunkRegs<KB>& R, StepSmem& sm,
                                               bool jac, float (&acc)[KB], float (&m)[16]) {
-  constexpr int RPT = StepRpt<KB>::v;
+  constexpr int RPT = Rpt<KB>::v;
   constexpr int CR = kBT * RPT;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int rows = min(CR, T.r1 - c0);
@@ -525,10 +517,8 @@ __device__ __forceinline__ void compute_chunk(const TileCtx& T, int c0, const Ch
 
 template <int KB>
 __device__ void step_tile(const BArgs& A, StepSmem& sm, int tile, int i, bool jac) {
-  constexpr int RPT = StepRpt<KB>::v;
+  constexpr int RPT = Rpt<KB>::v;
   constexpr int CR = kBT * RPT;
-  // two chunks in flight for the small rank buckets (register budget)
-  constexpr bool kDouble = StepRpt<KB>::dbl;
   const Inst I = A.inst[i];
   const int t = threadIdx.x;
   const int k = A.rank[i];
@@ -552,25 +542,13 @@ __device__ void step_tile(const BArgs& A, StepSmem& sm, int tile, int i, bool ja
   float m[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) m[q] = 0.f;
+  // (two chunks in flight, with double-buffered registers, measured slower)
   ChunkRegs<KB> ra;
   load_chunk<KB>(T, r0, ra);
   __syncthreads();
-  if constexpr (kDouble) {
-    ChunkRegs<KB> rb;
-    for (int c0 = r0; c0 < r1; c0 += 2 * CR) {
-      const bool has_b = c0 + CR < r1;
-      if (has_b) load_chunk<KB>(T, c0 + CR, rb);
-      compute_chunk<KB>(T, c0, ra, sm, jac, acc, m);
-      if (has_b) {
-        if (c0 + 2 * CR < r1) load_chunk<KB>(T, c0 + 2 * CR, ra);
-        compute_chunk<KB>(T, c0 + CR, rb, sm, jac, acc, m);
-      }
-    }
-  } else {
-    for (int c0 = r0; c0 < r1; c0 += CR) {
-      if (c0 > r0) load_chunk<KB>(T, c0, ra);
-      compute_chunk<KB>(T, c0, ra, sm, jac, acc, m);
-    }
+  for (int c0 = r0; c0 < r1; c0 += CR) {
+    if (c0 > r0) load_chunk<KB>(T, c0, ra);
+    compute_chunk<KB>(T, c0, ra, sm, jac, acc, m);
   }
   double* gp = A.gpart + (size_t)tile * kPS;
   tile_reduce<KB>(acc, k, sm.red, gp);
