@@ -17,10 +17,12 @@ pinned host memory (rom_init, amortised over the run) and q~ comes back to
 pinned host memory after every cycle.
 
 The line also carries the other forms of the method (``forms``): the
-mixed-precision form of the same workload, and the batched form, 256
+mixed-precision form of the same workload; the batched form, 256
 independent Burgers ROMs of uneven size (N log-uniform in [2048, 65536],
 r in 8..48, z in {5, 10, 20}) advanced together for 5 K steps, reported in
-aggregate ROM-steps/s with the HBM roofline of its reduced-step kernel.
+aggregate ROM-steps/s with the HBM roofline of its reduced-step kernel; and
+the two other single-ROM workloads (Burgers N=512, r=10, z=10, plain
+Galerkin; Sod shock tube, 8192 cells, r=40, z=10), both FP64.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                        [--only single|batched] [--batch-count B]
@@ -236,6 +238,30 @@ def src_sha1(rel):
 
 # --------------------------------------------------------------- batched ---
 
+def timed_single(g, cfg, n_steps):
+    """Online steps/s of one more single-ROM workload (device time of n_steps
+    steps on a side stream after 3 adaptation intervals of warm-up)."""
+    import torch
+    try:
+        q0 = synth.initial_state(cfg)
+        s = torch.cuda.Stream()
+        rom = g.AdaptiveROM(cfg, q0, stream=s.cuda_stream)
+        rom.step(3 * cfg.z)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        rom.step(n_steps)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        info = rom.info()
+        rom.close()
+        return {"value": n_steps / (ms / 1e3), "unit": "steps/s", "steps": n_steps,
+                "ms_per_step": ms / n_steps, "rank_k": info["rank"]}
+    except Exception as exc:       # an extra form must not cost the main line
+        return {"error": f"{type(exc).__name__}: {exc}"}
+
+
 # DRAM traffic of one launch of the batched reduced-step kernel (5 steps) from
 # one ncu capture of the 256-instance workload (summarised under profiles/);
 # reported only while csrc/batch.cu is unchanged.
@@ -421,6 +447,9 @@ def main():
     # lockstep; ~0.5 GB of FP32 bases, larger than L2, so no flush is needed
     if args.only == "all":
         forms["batched_256"] = timed_batch(g, args, stream, dist, world)
+        # the two other single-ROM workloads: Burgers N=512 plain Galerkin, and Sod
+        forms["burgers_n512_r10_z10_fp64"] = timed_single(g, synth.config_burgers_small(), 2000)
+        forms["sod_n8192_r40_z10_fp64"] = timed_single(g, synth.config_sod(), 500)
 
     # roofline of the dominant kernel (largest device time in the timed region)
     dom = max(prof, key=lambda p: prof[p]["ms"])
