@@ -15,6 +15,10 @@ riemann  exact solution of the Riemann problem (used only to pin the Euler FOM).
 rom      preprocessing, POD, Galerkin and DEIM-Galerkin reduced steps, QDEIM,
          feature-guided oversampling, the iSVD update (Algorithm 2) and the
          adaptive ROM driver (Algorithm 1).
+adjoint  gradient of a terminal misfit of the adaptive Burgers ROM with respect
+         to the viscosity and the initial-condition amplitude, in forward mode
+         and as a checkpointed reverse sweep (no paper counterpart; pinned by
+         finite differences of ``rom``).
 
 Parity status: every function here is pinned by a test in ``tests/`` against a
 closed form, an invariant, a library routine or brute force, except the
