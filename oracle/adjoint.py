@@ -11,8 +11,8 @@ Algorithm 2) and the state transfers. The loss is
 
     J = 1/2 || q~^{n_T} - q_target ||^2,
 
-q~^{n_T} the lifted ROM state returned by the last online step (before that
-step's own event, if it has one, which cannot change it). The parameters are
+q~^{n_T} the lifted ROM state returned by the last online step, i.e. computed
+before that step's adaptation event, if it has one. The parameters are
 the viscosity nu and the amplitude A of the initial condition
 u0 = 1 + A sin(2 pi x) + 0.1 S(x), so dq0/dA = sin(2 pi x) and q_ref = q0
 moves with A.
