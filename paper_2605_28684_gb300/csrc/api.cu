@@ -701,7 +701,6 @@ rom_status rom_fom_rhs_dev(int32_t problem, int64_t n_cells, double nu, double g
 rom_status rom_fom_step_dev(int32_t problem, int64_t n_cells, double nu, double gamma, double h,
                             double newton_tol, int32_t newton_max, const double* q_prev_dev,
                             double* q_dev, int32_t* iters_host, void* stream) {
-  rom_ctx* ctx = nullptr;
   if (!q_prev_dev || !q_dev || q_prev_dev == q_dev || n_cells < 2 || !(h > 0.0) ||
       newton_max < 1 || !(newton_tol > 0.0))
     return ROM_EINVAL;
@@ -743,7 +742,6 @@ rom_status rom_fom_step_dev(int32_t problem, int64_t n_cells, double nu, double 
 rom_status rom_isvd_update_dev(int64_t n, int32_t r, double lambda, double rank_tol, double* phi_dev,
                                double* sigma_dev, const double* y_dev, double* ubar_host,
                                void* stream) {
-  rom_ctx* ctx = nullptr;
   if (n < 2 || r < 1 || r > kMaxR || r >= n || !phi_dev || !sigma_dev || !y_dev ||
       !(lambda >= 0.0 && lambda <= 1.0))
     return ROM_EINVAL;
