@@ -88,3 +88,58 @@ def test_invalid_batches_rejected(lib):
     assert lib.rom_batch_state(None, 0, None, None, None, None, None, None) == 1
     assert lib.rom_batch_info(None, 0, None, None, None) == 1
     lib.rom_batch_destroy(None)
+
+
+def test_context_free_entry_points_reject_invalid_arguments(lib):
+    """Every case below fails the argument check, which comes before any
+    device call; the pointers are never dereferenced."""
+    P = ctypes.c_void_p
+    a, b = P(0x10000), P(0x20000)           # stand-ins for device buffers
+    EINVAL = 1
+    nan = float("nan")
+    # f(q): null buffers, too few cells, unknown problem
+    for args in [(0, 64, 0.01, 1.4, None, b), (0, 64, 0.01, 1.4, a, None), (0, 1, 0.01, 1.4, a, b),
+                 (2, 64, 0.01, 1.4, a, b)]:
+        assert lib.rom_fom_rhs_dev(*args, None) == EINVAL, args
+    # one BE step (both variants): buffers, aliasing, sizes, step, Newton controls, problem
+    step_cases = [
+        dict(q_prev=None), dict(q=a), dict(n=1), dict(h=0.0), dict(h=nan), dict(newton_max=0),
+        dict(tol=0.0), dict(problem=2), dict(n=1 << 40),
+    ]
+    base = dict(problem=0, n=512, nu=0.01, gamma=1.4, h=1e-3, tol=1e-12, newton_max=20, q_prev=a, q=b)
+    for fn in (lib.rom_fom_step_dev, lib.rom_fom_step_noalloc_dev):
+        for case in step_cases:
+            c = dict(base, **case)
+            rc = fn(c["problem"], c["n"], c["nu"], c["gamma"], c["h"], c["tol"], c["newton_max"],
+                    c["q_prev"], c["q"], None, None)
+            assert rc == EINVAL, (fn, case)
+    for n in (4, 40000):                     # the Euler step's cell range
+        assert lib.rom_fom_step_dev(1, n, 0.0, 1.4, 1e-4, 1e-12, 20, a, b, None, None) == EINVAL
+    # the allocation-free step serves Burgers only
+    assert lib.rom_fom_step_noalloc_dev(1, 512, 0.0, 1.4, 1e-4, 1e-12, 20, a, b, None, None) == EINVAL
+    # rank-one update: sizes, rank range, buffers, forgetting factor
+    for n, r, lam, phi in [(1, 1, 0.5, a), (64, 0, 0.5, a), (128, 65, 0.5, a), (16, 16, 0.5, a),
+                           (64, 8, 0.5, None), (64, 8, 1.5, a), (64, 8, -0.1, a), (64, 8, nan, a)]:
+        assert lib.rom_isvd_update_dev(n, r, lam, 1e-10, phi, b, b, None, None) == EINVAL, (n, r, lam)
+
+
+def test_context_calls_reject_a_null_context(lib):
+    D = ctypes.POINTER(ctypes.c_double)
+    buf = (ctypes.c_double * 64)()
+    i64 = (ctypes.c_int64 * 8)()
+    i32 = (ctypes.c_int32 * 8)()
+    dp = ctypes.cast(buf, D)
+    EINVAL = 1
+    assert lib.rom_step(None, -1) == EINVAL
+    assert lib.rom_update_basis(None, None) == EINVAL
+    assert lib.rom_load_state(None, dp, dp, dp, dp, 100) == EINVAL
+    assert lib.rom_samples(None, i32) == EINVAL
+    assert lib.rom_info(None, None, None, None) == EINVAL
+    assert lib.rom_profile(None, 1) == EINVAL
+    assert lib.rom_profile_read(None, dp, i64) == EINVAL
+    assert lib.rom_batch_layout(None, None, None, None, None, None, None) == EINVAL
+    assert lib.rom_batch_profile(None, 1) == EINVAL
+    assert lib.rom_batch_work(None, None, None) == EINVAL
+    assert lib.rom_batch_profile_read(None, dp, i64) == EINVAL
+    for code in range(8):
+        assert lib.rom_status_string(code)
