@@ -13,6 +13,9 @@ What fixes the gradient independently of the oracle's own formulas:
 * equality of the reverse sweep with forward mode, and its independence of the
   checkpoint interval (bit for bit).
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -312,3 +315,27 @@ def test_rejects_configurations_it_does_not_cover():
         adj.tangent_gradient(cfg, 1, np.zeros(cfg.n_cells))
     with pytest.raises(ValueError):
         adj.adjoint_gradient(cfg_small(), 1, np.zeros(64), ckpt_every=0)
+
+
+# ------------------------------------------------- stored full-size values ---
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                      "adjoint_burgers_n65536_r64.json")
+
+
+def test_stored_full_size_gradient_is_current_and_consistent():
+    """The stored gradient of the full-size workload (written by
+    tests/golden/make_adjoint_golden.py from the oracle alone) belongs to the
+    current workload definition, and its two routes and its central
+    differences agree."""
+    with open(GOLDEN) as f:
+        gold = json.load(f)
+    cfg = synth.config_adjoint()
+    assert gold["config"] == cfg.to_dict()
+    assert gold["n_steps"] == cfg.n_online
+    for name in ("nu", "A"):
+        fwd, rev = gold["grad_forward_mode"][name], gold["grad_reverse_sweep"][name]
+        assert abs(fwd - rev) <= 1e-8 * abs(fwd)        # measured 2e-9 and 9e-11
+        fd = gold["central_differences"]["value"][name]
+        assert abs(fwd - fd) <= 1e-6 * abs(fd)          # measured 1.3e-8 and 1e-9
+    assert gold["J"] > 0.0
