@@ -133,6 +133,16 @@ def cpu_baseline(seconds=15.0):
                       f"workload after the offline stage, {d['seconds']:.1f} s, one thread"}
 
 
+def max_over_ranks(x, dist, device="cuda"):
+    """The largest of every rank's x (a device time); x itself on one rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args):
     """The reference arm: the FP64 oracle on the host, same workload and metric."""
     rank = int(os.environ.get("RANK", "0"))
@@ -299,10 +309,7 @@ def timed_batch(g, args, stream, dist, world):
     lay = b.layout()
     b.profile(False)
     b.close()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     pk = peaks()
     step_s = prof["reduced_steps"]["ms"] / 1e3
     gbs = work["sweep_bytes"] / step_s / 1e9
@@ -418,21 +425,14 @@ def main():
 
     sampler = ClockSampler(local)
     total_ms, prof, info, clocks = timed_cycles(cfg, sampler)
-    t_max = total_ms
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(total_ms, dist)
     value = world * args.steps * cfg.z / (t_max / 1e3)
 
     # the mixed-precision form of the same workload (FP32 basis and projections)
     mcfg = workload_config()
     mcfg.precision = 1
     m_ms, m_prof, m_info, _ = timed_cycles(mcfg)
-    if dist is not None:
-        t = torch.tensor([m_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        m_ms = float(t.item())
+    m_ms = max_over_ranks(m_ms, dist)
     forms = {
         "fp64": {"value": value, "ms_per_step": t_max / args.steps, "rank_k": info["rank"]},
         "mixed_fp32": {"value": world * args.steps * mcfg.z / (m_ms / 1e3),
@@ -489,10 +489,7 @@ def main():
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     rom2.close()
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist)
     e2e = {"value": world * args.steps * cfg.z / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": 8 * cfg.n_cells / args.steps, "d2h_bytes_per_step": 8 * cfg.n_cells,
            "includes": "rom_init from host q0 (offline stage) + every cycle's q~ readback"}
