@@ -70,6 +70,8 @@ class AdaptiveROM:
             _lib.check(self._lib.rom_update_basis(self._ctx, None), "rom_update_basis")
         else:
             y = np.ascontiguousarray(y, dtype=np.float64)
+            if y.shape != (self.N,):
+                raise ValueError(f"y must have {self.N} entries")
             _lib.check(self._lib.rom_update_basis(self._ctx, _dptr(y)), "rom_update_basis")
 
     def state(self, q_tilde=True, phi=True, y_corr=True):
@@ -95,10 +97,17 @@ class AdaptiveROM:
         return qt
 
     def load_state(self, phi, sigma, a, y_corr, step):
-        ph = np.ascontiguousarray(np.asarray(phi, dtype=np.float64).T)   # column-major N x r
+        """Phi (N x r), sigma (r), a (r), y_corr (N) and the step count, as
+        ``state`` returns them; the library copies exactly these sizes."""
+        ph = np.asarray(phi, dtype=np.float64)
         s = np.ascontiguousarray(sigma, dtype=np.float64)
         av = np.ascontiguousarray(a, dtype=np.float64)
         yc = np.ascontiguousarray(y_corr, dtype=np.float64)
+        if ph.shape != (self.N, self.r) or s.shape != (self.r,) or av.shape != (self.r,) \
+                or yc.shape != (self.N,):
+            raise ValueError(f"expected phi ({self.N}, {self.r}), sigma and a ({self.r},), "
+                             f"y_corr ({self.N},)")
+        ph = np.ascontiguousarray(ph.T)                                  # column-major N x r
         _lib.check(self._lib.rom_load_state(self._ctx, _dptr(ph), _dptr(s), _dptr(av), _dptr(yc),
                                             int(step)), "rom_load_state")
 

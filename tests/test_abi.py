@@ -143,3 +143,20 @@ def test_context_calls_reject_a_null_context(lib):
     assert lib.rom_batch_profile_read(None, dp, i64) == EINVAL
     for code in range(8):
         assert lib.rom_status_string(code)
+
+
+def test_binding_checks_host_array_sizes_before_the_library():
+    """The library copies N (or N x r) doubles from host arrays; the binding
+    refuses arrays of other shapes before calling it (here on an object with
+    no context, so nothing else could run)."""
+    import paper_2605_28684_gb300 as g
+    rom = g.AdaptiveROM.__new__(g.AdaptiveROM)
+    rom.N, rom.r, rom._lib, rom._ctx = 12, 3, None, ctypes.c_void_p()
+    with pytest.raises(ValueError):
+        rom.update_basis(np.zeros(11))
+    good = dict(phi=np.zeros((12, 3)), sigma=np.zeros(3), a=np.zeros(3), y_corr=np.zeros(12))
+    for key, bad in [("phi", np.zeros((3, 12))), ("phi", np.zeros((12, 2))), ("sigma", np.zeros(4)),
+                     ("a", np.zeros(2)), ("y_corr", np.zeros(13))]:
+        args = dict(good, **{key: bad})
+        with pytest.raises(ValueError):
+            rom.load_state(args["phi"], args["sigma"], args["a"], args["y_corr"], 100)
