@@ -43,8 +43,17 @@ def test_invalid_configs_rejected(lib):
     q0 = synth.initial_state(base)
     bad = []
     for field, val in [("r", 0), ("r", 65), ("r", 200), ("z", 0), ("lam", 1.5), ("dt", 0.0),
-                       ("n_s", 5), ("w_init", 0), ("n_var", 3), ("newton_tol", 0.0)]:
+                       ("n_s", 5), ("w_init", 0), ("n_var", 3), ("newton_tol", 0.0),
+                       # sizes the FOM partitioning cannot hold (128 chunks x 1024 rows)
+                       ("n_cells", 4), ("n_cells", 128 * 1024 + 1),
+                       # r beyond the training window, too many samples, no BF16 form
+                       ("w_init", 5), ("n_s", 257), ("precision", 2),
+                       ("nu", -1e-3), ("dt", float("nan")), ("newton_max", 0)]:
         c = synth.config_burgers_small()
+        setattr(c, field, val)
+        bad.append(c)
+    for field, val in [("n_cells", 128 * 256 + 1), ("n_s", 60), ("n_var", 1)]:
+        c = synth.config_sod(256)
         setattr(c, field, val)
         bad.append(c)
     for c in bad:
