@@ -109,7 +109,9 @@ typedef struct {
  *  q0_host   host array of N doubles, the initial state.
  *  stream    cudaStream_t to order all work on (NULL: the legacy default stream).
  *  out       receives the new context on ROM_OK, NULL otherwise.
- * Errors: ROM_EINVAL, ROM_ENOMEM, ROM_ECUDA, ROM_ENOCONV, ROM_ENONFINITE.
+ * Errors: ROM_EINVAL, ROM_ENOMEM, ROM_ECUDA, ROM_ENOCONV, ROM_ENONFINITE (a
+ * NaN or Inf in q0_host is refused on the host before any device work; later
+ * the FOM Newton solves report a non-finite state).
  */
 rom_status rom_init(const rom_config* cfg, const double* q0_host, void* stream,
                     rom_ctx** out);
@@ -131,7 +133,8 @@ rom_status rom_step(rom_ctx* ctx, int64_t n_steps);
  * of the stored coarse state. It is preprocessed as D (y - q_ref), the basis is
  * updated by the rank-one iSVD with forgetting, the sampling points are
  * refreshed and the reduced state is transferred to the new basis.
- * Errors: as rom_step.
+ * Errors: as rom_step; a NaN or Inf in y_host returns ROM_ENONFINITE before
+ * any device work and leaves the context unchanged (not poisoned).
  */
 rom_status rom_update_basis(rom_ctx* ctx, const double* y_host);
 
@@ -154,7 +157,8 @@ rom_status rom_state(rom_ctx* ctx, double* q_tilde, double* a, double* sigma,
  * state exported by rom_state). phi: N*r column-major with orthonormal
  * non-zero columns; sigma: r; a: r; y_corr: N; step: time level. If n_s > 0
  * the sampling points are rebuilt from phi and y_corr.
- * Errors: ROM_EINVAL, ROM_ECUDA, ROM_ESTATE.
+ * Errors: ROM_EINVAL, ROM_ECUDA, ROM_ESTATE, ROM_ENONFINITE (a NaN or Inf in
+ * any input array; checked on the host, the context is unchanged).
  */
 rom_status rom_load_state(rom_ctx* ctx, const double* phi, const double* sigma,
                           const double* a, const double* y_corr, int64_t step);
@@ -211,14 +215,18 @@ rom_status rom_fom_step_dev(int32_t problem, int64_t n_cells, double nu, double 
  * allocate). Some callers cannot call cudaMalloc: a host application that owns
  * all device memory through its own pool allocator and forbids raw
  * allocations, or a time-critical loop that cannot afford cudaMalloc/cudaFree
- * (cudaFree waits for the whole device). This call runs the same Newton solve
- * with the same arguments, results and errors as rom_fom_step_dev, but
- * allocates nothing: its scratch is one fixed 8448-byte device array inside
- * the library, held by every GPU that loads it until the process exits.
+ * (cudaFree waits for the whole device). For the Burgers problem this call
+ * runs the same Newton solve with the same arguments, results and errors as
+ * rom_fom_step_dev, but allocates nothing: its scratch is one fixed 8448-byte
+ * device array inside the library, held by every GPU that loads it until the
+ * process exits.
+ *  Problems: ROM_BURGERS only; ROM_EULER (whose separator system needs more
+ *  scratch than the array holds) returns ROM_EINVAL.
  *  Limit: n_cells <= 131072 (larger values return ROM_EINVAL).
  *  The first call on a device looks up that array's device address
- *  (cudaGetSymbolAddress) and caches it; make that first call before any
- *  stream capture.
+ *  (cudaGetSymbolAddress) and caches it.
+ *  Every call synchronises `stream` and reads the status word back to the
+ *  host before it returns.
  *  All calls share the array, and each call clears what must start at zero;
  *  calls that overlap on the GPU (from several host threads or streams at once)
  *  race on it and must be serialised by the caller.
@@ -227,6 +235,18 @@ rom_status rom_fom_step_noalloc_dev(int32_t problem, int64_t n_cells, double nu,
                                     double gamma, double h, double newton_tol,
                                     int32_t newton_max, const double* q_prev_dev,
                                     double* q_dev, int32_t* iters_host, void* stream);
+
+/*
+ * Test hook (no counterpart in the paper): sets the bound, in SM clock
+ * cycles, of every device-side wait of the library's kernels (the software
+ * grid barrier between the phases of a cooperative launch). A kernel whose
+ * wait runs out records ROM_ETIMEOUT and returns; the call then reports
+ * ROM_ETIMEOUT and poisons its context. cycles <= 0 restores the default
+ * (4e9 cycles, about 2 s). The setting is process-wide and applies to the
+ * current device; change it only while none of the library's kernels runs.
+ * Errors: ROM_ECUDA.
+ */
+rom_status rom_debug_set_wait_limit(int64_t cycles);
 
 /*
  * Low-level iSVD update (Algorithm 2) on caller-owned device buffers.

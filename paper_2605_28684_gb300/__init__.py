@@ -258,3 +258,10 @@ def isvd_update_dev(n, r, lam, rank_tol, phi_ptr: int, sigma_ptr: int, y_ptr: in
                                        None if ub is None else _dptr(ub), ctypes.c_void_p(stream)),
                "rom_isvd_update_dev")
     return None if ub is None else ub.reshape(r + 1, r + 1).T
+
+
+def debug_set_wait_limit(cycles: int):
+    """Bound of every device-side wait of the library's kernels, in SM clock
+    cycles (a test hook; <= 0 restores the default of about 2 s)."""
+    lib = _lib.load()
+    _lib.check(lib.rom_debug_set_wait_limit(int(cycles)), "rom_debug_set_wait_limit")

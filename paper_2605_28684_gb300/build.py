@@ -11,6 +11,10 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librom.so")
 SOURCES = ["api.cu", "fom.cu", "euler.cu", "isvd.cu", "reduced.cu", "sampling.cu", "batch.cu"]
+# one object per rank bucket and basis type of the iSVD kernels, so that they compile in parallel
+BUCKETS = [("isvd_bucket.cu", f"isvd_b{km}_{t}.o",
+            [f"-DROM_ISVD_KM={km}", f"-DROM_ISVD_F32={int(t == 'f32')}"])
+           for km in (9, 17, 33, 65) for t in ("f64", "f32")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -35,12 +39,17 @@ def build(verbose: bool = False) -> str:
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".cuh")]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "rom.h"))
     nvcc = _nvcc()
+    units = [(src, src.replace(".cu", ".o"), []) for src in SOURCES] + BUCKETS
     jobs = []
-    for src in SOURCES:
+    objs = []
+    for src, obj, defs in units:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(BUILD, obj)
+        objs.append(o)
         if _stale(o, [s] + headers):
-            jobs.append([nvcc, *ARCH, *FLAGS, "-c", s, "-o", o])
+            jobs.append([nvcc, *ARCH, *FLAGS, *defs, "-c", s, "-o", o])
+    # longest first (the widest rank bucket), so the parallel build ends soonest
+    jobs.sort(key=lambda cmd: ("-DROM_ISVD_KM=65" not in cmd, "batch.cu" not in cmd[-3]))
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -49,9 +58,8 @@ def build(verbose: bool = False) -> str:
         if r.returncode != 0:
             raise RuntimeError("nvcc failed: " + " ".join(cmd))
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with ThreadPoolExecutor(max_workers=max(1, min(len(units), os.cpu_count() or 1))) as ex:
         list(ex.map(run, jobs))
-    objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
     if jobs or _stale(LIB, objs):
         run([nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"])
     return LIB

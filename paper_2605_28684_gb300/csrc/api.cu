@@ -348,6 +348,13 @@ __global__ void drow_kernel(const double* dvals, int64_t n_cells, int64_t N, dou
   }
 }
 
+// true if every one of the n host values is finite
+bool all_finite(const double* v, int64_t n) {
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
 void free_state(rom_ctx* ctx) {
   DevState& d = ctx->d;
   void* ptrs[] = {d.q_ref, d.y_corr, d.y_tmp, d.yhat, d.qres, d.lifted, d.dvals, d.drow, d.dinv, d.phi,
@@ -394,6 +401,7 @@ rom_status rom_init(const rom_config* cfg_in, const double* q0_host, void* strea
   rom_status vs = validate(cfg_in);
   if (vs != ROM_OK) return vs;
   if (!q0_host) return ROM_EINVAL;
+  if (!all_finite(q0_host, cfg_in->n_cells * cfg_in->n_var)) return ROM_ENONFINITE;
   if (!device_ok()) return ROM_ECUDA;
   rom_ctx* ctx = new rom_ctx;
   memset(&ctx->d, 0, sizeof(DevState));
@@ -541,6 +549,7 @@ rom_status rom_step(rom_ctx* ctx, int64_t n_steps) {
 rom_status rom_update_basis(rom_ctx* ctx, const double* y_host) {
   if (!ctx) return ROM_EINVAL;
   if (ctx->poisoned) return ROM_ESTATE;
+  if (y_host && !all_finite(y_host, ctx->N)) return ROM_ENONFINITE;
   if (y_host) {
     RCK(cudaMemcpyAsync(ctx->d.y_corr, y_host, sizeof(double) * ctx->N, cudaMemcpyHostToDevice,
                         ctx->stream));
@@ -605,6 +614,9 @@ rom_status rom_load_state(rom_ctx* ctx, const double* phi, const double* sigma, 
   if (ctx->poisoned) return ROM_ESTATE;
   const int64_t N = ctx->N;
   const int r = ctx->cfg.r;
+  if (!all_finite(phi, N * r) || !all_finite(sigma, r) || !all_finite(a, r) ||
+      !all_finite(y_corr, N))
+    return ROM_ENONFINITE;
   int k = 0;
   for (int j = 0; j < r; ++j)
     if (sigma[j] > 0.0) k = j + 1;
@@ -737,6 +749,16 @@ rom_status rom_fom_step_dev(int32_t problem, int64_t n_cells, double nu, double 
   if (iters_host) *iters_host = hv[1];
   cudaFree(chunk); cudaFree(maxbuf); cudaFree(bar); cudaFree(ints);
   return result;
+}
+
+rom_status rom_debug_set_wait_limit(int64_t cycles) {
+  const long long c = cycles > 0 ? (long long)cycles : kSpinLimitCycles;
+  cudaError_t (*setters[])(long long) = {set_wait_limit_fom, set_wait_limit_euler,
+                                         set_wait_limit_isvd, set_wait_limit_reduced,
+                                         set_wait_limit_sampling, set_wait_limit_batch};
+  for (auto f : setters)
+    if (f(c) != cudaSuccess) return ROM_ECUDA;
+  return ROM_OK;
 }
 
 rom_status rom_isvd_update_dev(int64_t n, int32_t r, double lambda, double rank_tol, double* phi_dev,

@@ -1445,6 +1445,9 @@ __global__ void batch_lift_kernel(const float* phi, const double* q_ref, const d
 }
 
 }  // namespace
+// Wait bound of this translation unit's kernels (see rom_internal.cuh).
+cudaError_t set_wait_limit_batch(long long cycles) { return set_wait_limit_here(cycles); }
+
 }  // namespace rom
 
 // ============================================================= host side ===

@@ -725,4 +725,7 @@ cudaError_t launch_euler_galerkin_steps(const StepArgs& A, int km, int grid, cud
   }
 }
 
+// Wait bound of this translation unit's kernels (see rom_internal.cuh).
+cudaError_t set_wait_limit_euler(long long cycles) { return set_wait_limit_here(cycles); }
+
 }  // namespace rom

@@ -287,6 +287,9 @@ cudaError_t launch_fom_step(const FomParams& p, const double* q_prev, double* q,
                                      dim3(threads), args, 0, s);
 }
 
+// Wait bound of this translation unit's kernels (see rom_internal.cuh).
+cudaError_t set_wait_limit_fom(long long cycles) { return set_wait_limit_here(cycles); }
+
 }  // namespace rom
 
 // ---------------------------------------------------------------------------

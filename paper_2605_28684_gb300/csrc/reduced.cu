@@ -492,4 +492,7 @@ cudaError_t launch_lift(const LiftArgs& A, int km, cudaStream_t s) {
   }
 }
 
+// Wait bound of this translation unit's kernels (see rom_internal.cuh).
+cudaError_t set_wait_limit_reduced(long long cycles) { return set_wait_limit_here(cycles); }
+
 }  // namespace rom

@@ -33,11 +33,26 @@ struct GridBarrier {
   unsigned int gen;
 };
 
+// Bound of every device-side wait, in SM clock cycles. Each translation unit
+// holds its own copy (no relocatable device code), so each one exports a
+// setter (set_wait_limit_<unit>) and rom_debug_set_wait_limit calls them all.
+static __constant__ long long c_wait_limit = kSpinLimitCycles;
+static inline cudaError_t set_wait_limit_here(long long cycles) {
+  return cudaMemcpyToSymbol(c_wait_limit, &cycles, sizeof(cycles));
+}
+cudaError_t set_wait_limit_fom(long long cycles);
+cudaError_t set_wait_limit_euler(long long cycles);
+cudaError_t set_wait_limit_isvd(long long cycles);
+cudaError_t set_wait_limit_reduced(long long cycles);
+cudaError_t set_wait_limit_sampling(long long cycles);
+cudaError_t set_wait_limit_batch(long long cycles);
+
 // ---------------------------------------------------------------- barrier --
 
 // All CTAs of a cooperative launch call this the same number of times.
-// Returns false (and records a timeout) if the other CTAs did not arrive in
-// kSpinLimitCycles; the caller must then return.
+// Returns false (and records a timeout) if the other CTAs did not arrive within
+// c_wait_limit cycles (kSpinLimitCycles unless a test lowered it); the caller
+// must then return.
 __device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status) {
   __syncthreads();
   __shared__ int s_ok;
@@ -52,9 +67,10 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status) {
       __threadfence();
       atomicAdd(&bar->gen, 1u);
     } else {
+      const long long limit = c_wait_limit;
       long long t0 = clock64();
       while (*vgen == g) {
-        if (clock64() - t0 > kSpinLimitCycles) {
+        if (clock64() - t0 > limit) {
           atomicExch(status, kStTimeout);
           ok = 0;
           break;

@@ -356,4 +356,7 @@ cudaError_t launch_sampling(const SampleArgs& A, int km, int grid, cudaStream_t 
   }
 }
 
+// Wait bound of this translation unit's kernels (see rom_internal.cuh).
+cudaError_t set_wait_limit_sampling(long long cycles) { return set_wait_limit_here(cycles); }
+
 }  // namespace rom

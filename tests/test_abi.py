@@ -169,3 +169,18 @@ def test_binding_checks_host_array_sizes_before_the_library():
         args = dict(good, **{key: bad})
         with pytest.raises(ValueError):
             rom.load_state(args["phi"], args["sigma"], args["a"], args["y_corr"], 100)
+
+
+def test_nonfinite_initial_state_refused_before_the_device(lib):
+    """A NaN or Inf in the host initial state is refused on the host
+    (ROM_ENONFINITE) before any device call, so no context is made."""
+    import paper_2605_28684_gb300 as g
+    cfg = synth.config_burgers_small()
+    D = ctypes.POINTER(ctypes.c_double)
+    for bad in (float("nan"), float("inf"), -float("inf")):
+        q0 = synth.initial_state(cfg)
+        q0[123] = bad
+        c = g.make_config(cfg)
+        ctx = ctypes.c_void_p()
+        rc = lib.rom_init(ctypes.byref(c), q0.ctypes.data_as(D), None, ctypes.byref(ctx))
+        assert rc == 5 and not ctx.value, bad       # ROM_ENONFINITE

@@ -139,16 +139,48 @@ def test_rank_truncation_zeroes_null_directions():
 
 # ------------------------------------------------------------ preprocess ---
 
-def test_preprocess_mean_square_scaling():
-    n_cells = 8
-    rng = np.random.default_rng(0)
-    q0 = rng.standard_normal(3 * n_cells)
-    Q = q0[:, None] + rng.standard_normal((3 * n_cells, 5)) * np.repeat([1.0, 2.0, 3.0], n_cells)[:, None]
+def test_preprocess_hand_worked_three_variables():
+    """Sec. 3.1, Eqs. scaling_matrix_local_block and variable_normalization,
+    worked by hand on 2 cells, 3 variables (blocked [rho0 rho1 m0 m1 E0 E1]),
+    2 snapshots. Centred on q_ref = q0, the blocks are
+        rho: [1, 0], [0, 2]   squares 1 0 0 4   mean 5/4  -> D = 0.8
+        m:   [1, 0], [0, 3]   squares 1 0 0 9   mean 10/4 -> D = 0.4
+        E:   [0, 2], [2, 0]   squares 0 4 4 0   mean 2    -> D = 0.5
+    The literals fail each plausible misreading: a mean over cells only
+    (rho 0.4), the RMS instead of the mean square (rho 0.894, E 0.707),
+    centring on the time mean instead of q_ref (rho 1.6), one mean over all
+    variables (0.522 each) and an interleaved layout."""
+    q0 = np.array([1.0, 2.0, 0.0, 0.0, 3.0, 4.0])
+    Q = np.array([[2.0, 1.0],
+                  [2.0, 4.0],
+                  [1.0, 0.0],
+                  [0.0, 3.0],
+                  [3.0, 5.0],
+                  [6.0, 4.0]])
     q_ref, d, Xhat = rom.preprocess(Q, q0, 3)
-    for v in range(3):
-        blk = (Q - q0[:, None])[v * n_cells:(v + 1) * n_cells]
-        assert np.allclose(d[v * n_cells:(v + 1) * n_cells], 1.0 / np.mean(blk**2))
-    assert np.allclose(Xhat, d[:, None] * (Q - q0[:, None]))
+    assert np.array_equal(q_ref, q0)
+    assert np.allclose(d, [0.8, 0.8, 0.4, 0.4, 0.5, 0.5], rtol=1e-15, atol=0)
+    expected = np.array([[0.8, 0.0],
+                         [0.0, 1.6],
+                         [0.4, 0.0],
+                         [0.0, 1.2],
+                         [0.0, 1.0],
+                         [1.0, 0.0]])
+    assert np.allclose(Xhat, expected, rtol=1e-15, atol=1e-15)
+
+
+def test_preprocess_constant_variable_is_left_unscaled():
+    """A variable that never leaves q_ref has phi_v = 0; the guard takes
+    D_v = 1 so that the block stays zero instead of becoming NaN."""
+    q0 = np.array([1.0, 2.0, 5.0, 5.0])
+    Q = np.array([[3.0, 1.0],
+                  [2.0, 4.0],
+                  [5.0, 5.0],
+                  [5.0, 5.0]])
+    _, d, Xhat = rom.preprocess(Q, q0, 2)
+    # variable 0: centred [2, 0], [0, 2] -> mean square 2 -> D = 0.5; variable 1: no variation
+    assert np.array_equal(d, [0.5, 0.5, 1.0, 1.0])
+    assert np.array_equal(Xhat[2:], np.zeros((2, 2)))
 
 
 def test_burgers_trajectory_invariant_under_scalar_scaling():
