@@ -200,3 +200,10 @@ def random_orthonormal(n: int, r: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     q, _ = np.linalg.qr(rng.standard_normal((n, r)))
     return q
+
+
+def probe_vectors(n: int, count: int = 4, seed: int = 77) -> np.ndarray:
+    """A seeded n x count Gaussian matrix. Stored trajectory records keep the
+    products W^T q~ with these vectors next to a subsample of q~, so that a
+    difference anywhere in a full-size state shows up in a few numbers."""
+    return np.random.default_rng(seed).standard_normal((n, count))

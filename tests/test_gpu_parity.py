@@ -301,36 +301,57 @@ def test_reduced_newton_nonconvergence_reported(g):
                                                    (False, 512, 2000)])
 def test_mixed_precision_against_fp64_oracle(g, hyper, n_cells, n_steps):
     """Mixed form (FP32 basis, FP32 projections with FP32 accumulation, FP64
-    core SVD and re-orthonormalisation) against the FP64 oracle run with the
-    same numerical-rank tolerance (1e-5, what FP32 projections resolve):
-    relative L2 of q~ within 1e-5 at every event."""
+    core SVD and re-orthonormalisation) against two FP64 oracles:
+
+    * parity: the oracle run with the mixed form's numerical-rank tolerance
+      (1e-5, what FP32 projections resolve), relative L2 of q~ within 1e-5 at
+      every event;
+    * error against the FP64 form: the oracle with the FP64 form's tolerance
+      (1e-10). The mixed form must lie within the distance that the rank
+      tolerance alone puts between the two oracles, plus 1e-5; that distance
+      (8.1e-4 at N = 512 over 2000 steps, 3.6e-5 and 4.4e-6 on the DEIM cases)
+      is above the 1e-5 target, so the mixed form does not reach the FP64
+      form's accuracy."""
     cfg = synth.config_burgers_hyper() if hyper else synth.config_burgers_small()
     cfg.n_cells = n_cells
     cfg.precision = 1
     q0 = synth.initial_state(cfg)
     saved = orom.RANK_TOL
-    orom.RANK_TOL = 1e-5
     try:
+        orom.RANK_TOL = 1e-5
         ref = orom.AdaptiveROM(cfg, q0)
+        orom.RANK_TOL = 1e-10
+        ref64 = orom.AdaptiveROM(cfg, q0)
         gpu = g.AdaptiveROM(cfg, q0)
         if hyper:
+            orom.RANK_TOL = 1e-5
             adopt_if_near_tie(ref, gpu, rtol=1e-6)
-        worst = 0.0
+        worst = worst64 = gap = 0.0
         for _ in range(n_steps // cfg.z):
+            orom.RANK_TOL = 1e-5
             for _ in range(cfg.z):
                 ref.step()
+            orom.RANK_TOL = 1e-10
+            for _ in range(cfg.z):
+                ref64.step()
             gpu.step(cfg.z)
+            orom.RANK_TOL = 1e-5
             if hyper:
                 adopt_if_near_tie(ref, gpu, rtol=1e-6)
-            worst = max(worst, rel(gpu.q_tilde(), ref.lifted()))
+            qg = gpu.q_tilde()
+            worst = max(worst, rel(qg, ref.lifted()))
+            worst64 = max(worst64, rel(qg, ref64.lifted()))
+            gap = max(gap, rel(ref.lifted(), ref64.lifted()))
     finally:
         orom.RANK_TOL = saved
     st = gpu.state()
     P = st["phi"][:, st["sigma"] > 0]
     assert np.max(np.abs(P.T @ P - np.eye(P.shape[1]))) <= 1e-6     # FP32 basis stays orthonormal
     assert gpu.info()["rank"] == orom.numerical_rank(ref.Phi)
-    print(f"mixed vs FP64 oracle: worst relative error {worst:.2e}")
+    print(f"mixed form N={n_cells}: vs oracle (tau 1e-5) {worst:.2e}; vs FP64 oracle (tau 1e-10) "
+          f"{worst64:.2e}; oracle tau gap {gap:.2e}")
     assert worst <= 1e-5, worst
+    assert worst64 <= gap + 1e-5, (worst64, gap)
     gpu.close()
 
 
