@@ -263,6 +263,46 @@ rom_status rom_isvd_update_dev(int64_t n, int32_t r, double lambda, double rank_
                                double* phi_dev, double* sigma_dev, const double* y_dev,
                                double* ubar_host, void* stream);
 
+/*
+ * Gradient of a terminal misfit of the adaptive ROM (the paper states no
+ * adjoint; this differentiates Algorithm 1 with the iSVD update of Algorithm
+ * 2 as this library computes it). For the plain-Galerkin Burgers ROM
+ * (problem ROM_BURGERS, precision ROM_FP64, n_s = 0, w_init <= 128):
+ *   J(nu, q0) = 1/2 || q~^{n_T} - target ||^2,
+ * q~^{n_T} the lifted state returned by the last of n_steps online steps
+ * (before that step's adaptation event, if it has one), and its gradient with
+ * respect to the viscosity nu and the initial state q0 (which also fixes
+ * q_ref = q0 and, through the training window, D and the POD basis). The call
+ * runs the offline stage and the forward pass itself, then the reverse sweep:
+ * transposed reduced Jacobian solves of every Galerkin step, the adjoint of
+ * every iSVD update (core SVD, rotation, projection, state transfer), the
+ * transposed periodic tridiagonal solve of every coarse and training FOM
+ * step, and the adjoint of the POD of the training matrix. Discrete
+ * decisions (Godunov branch, numerical rank, empty residual) are held fixed;
+ * Newton roots are differentiated at the computed root. All arithmetic is FP64.
+ *  cfg          configuration (as rom_init, restricted as above).
+ *  q0_host      N doubles, the initial state.
+ *  target_host  N doubles, the target of the misfit.
+ *  n_steps      online steps (>= 1).
+ *  ckpt_every   >= 1. The forward pass records every step of a segment of
+ *               ckpt_every steps (per event about 8 N (r + 4) bytes); with
+ *               ckpt_every < n_steps it keeps only the online state at the
+ *               start of each segment and the reverse sweep re-runs each
+ *               segment from it, so the memory is that of one segment plus
+ *               one state per segment. The gradient does not depend on it.
+ *  stream       cudaStream_t (NULL: the legacy default stream); the call
+ *               synchronises it before returning.
+ *  J, dJ_dnu    host scalars (out).
+ *  dJ_dq0       N doubles (out) or NULL.
+ *  q_final      N doubles (out): q~^{n_T}, or NULL.
+ * Errors: ROM_EINVAL (configuration or arguments outside the above),
+ * ROM_ENONFINITE (NaN/Inf in q0 or target, checked on the host), ROM_ENOMEM,
+ * and the errors of rom_init and rom_step.
+ */
+rom_status rom_adjoint(const rom_config* cfg, const double* q0_host, const double* target_host,
+                       int64_t n_steps, int32_t ckpt_every, void* stream, double* J,
+                       double* dJ_dnu, double* dJ_dq0, double* q_final);
+
 /* ------------------------------------------------------------------------
  * Batched execution of many independent ROMs.
  *

@@ -265,3 +265,55 @@ def debug_set_wait_limit(cycles: int):
     cycles (a test hook; <= 0 restores the default of about 2 s)."""
     lib = _lib.load()
     _lib.check(lib.rom_debug_set_wait_limit(int(cycles)), "rom_debug_set_wait_limit")
+
+
+def adjoint(cfg, q0, target, n_steps: int, ckpt_every: int = 50, stream: int | None = None,
+            want_q_final: bool = False):
+    """J = 1/2 |q~^{n_T} - target|^2 of the adaptive ROM and its gradient with
+    respect to nu and the initial state q0 (rom_adjoint). Returns
+    (J, dJ/dnu, dJ/dq0[, q~^{n_T}])."""
+    lib = _lib.load()
+    c = make_config(cfg)
+    n = int(cfg.n_cells) * int(cfg.n_var)
+    q0 = np.ascontiguousarray(q0, dtype=np.float64)
+    target = np.ascontiguousarray(target, dtype=np.float64)
+    if q0.shape != (n,) or target.shape != (n,):
+        raise ValueError(f"q0 and target must have {n} entries")
+    J, dnu = ctypes.c_double(), ctypes.c_double()
+    dq0 = np.empty(n)
+    qf = np.empty(n) if want_q_final else None
+    _lib.check(lib.rom_adjoint(ctypes.byref(c), _dptr(q0), _dptr(target), int(n_steps),
+                               int(ckpt_every), ctypes.c_void_p(stream or 0),
+                               ctypes.byref(J), ctypes.byref(dnu), _dptr(dq0),
+                               None if qf is None else _dptr(qf)), "rom_adjoint")
+    if want_q_final:
+        return J.value, dnu.value, dq0, qf
+    return J.value, dnu.value, dq0
+
+
+def misfit_function():
+    """A torch.autograd.Function over rom_adjoint: ``apply(nu, q0, cfg,
+    target, n_steps, ckpt_every)`` returns J as a 0-d float64 tensor and
+    backpropagates dJ/dnu and dJ/dq0 (device tensors on q0's device). The
+    forward and reverse passes both run in the library's kernels; torch only
+    carries the results."""
+    import torch
+
+    class _Misfit(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, nu, q0, cfg, target, n_steps, ckpt_every):
+            import copy
+            c = copy.copy(cfg)
+            c.nu = float(nu.detach().cpu())
+            J, dnu, dq0 = adjoint(c, q0.detach().cpu().double().numpy(),
+                                  target.detach().cpu().double().numpy(), n_steps, ckpt_every)
+            ctx.save_for_backward(torch.tensor(dnu, dtype=torch.float64, device=nu.device),
+                                  torch.from_numpy(dq0).to(q0.device))
+            return torch.tensor(J, dtype=torch.float64, device=q0.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            dnu, dq0 = ctx.saved_tensors
+            return gJ * dnu, gJ * dq0, None, None, None, None
+
+    return _Misfit

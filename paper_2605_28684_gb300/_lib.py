@@ -15,7 +15,7 @@ EXPORTED = [
     "rom_isvd_update_dev", "rom_profile", "rom_profile_read", "rom_fom_step_noalloc_dev",
     "rom_batch_init", "rom_batch_step", "rom_batch_state", "rom_batch_info", "rom_batch_layout",
     "rom_batch_profile", "rom_batch_profile_read", "rom_batch_destroy", "rom_batch_work",
-    "rom_debug_set_wait_limit",
+    "rom_debug_set_wait_limit", "rom_adjoint",
 ]
 
 
@@ -81,6 +81,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rom_isvd_update_dev.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
                                         ctypes.c_double, P, P, P, D, P]
     lib.rom_debug_set_wait_limit.argtypes = [ctypes.c_int64]
+    lib.rom_adjoint.argtypes = [ctypes.POINTER(RomConfigC), D, D, ctypes.c_int64, ctypes.c_int32, P,
+                                D, D, D, D]
     lib.rom_profile.argtypes = [P, ctypes.c_int32]
     lib.rom_profile_read.argtypes = [P, D, ctypes.POINTER(ctypes.c_int64)]
     I64P = ctypes.POINTER(ctypes.c_int64)
@@ -99,7 +101,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                  "rom_batch_layout", "rom_batch_profile", "rom_batch_profile_read", "rom_batch_work",
                  "rom_fom_step_noalloc_dev", "rom_profile", "rom_profile_read", "rom_init", "rom_step", "rom_update_basis", "rom_state", "rom_load_state",
                  "rom_samples", "rom_info", "rom_fom_rhs_dev", "rom_fom_step_dev",
-                 "rom_isvd_update_dev", "rom_debug_set_wait_limit"]:
+                 "rom_isvd_update_dev", "rom_debug_set_wait_limit", "rom_adjoint"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

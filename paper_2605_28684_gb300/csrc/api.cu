@@ -201,6 +201,7 @@ EventArgs event_args(rom_ctx* ctx, const double* y, int preprocess, double lambd
   A.partials = ctx->d.partials;
   A.core = ctx->d.core;
   A.ubar = ctx->d.ubar;
+  A.rec = nullptr;
   A.bar = ctx->d.bar;
   A.status = ctx->d.status;
   return A;
@@ -395,7 +396,14 @@ void rom_destroy(rom_ctx* ctx) {
   delete ctx;
 }
 
-rom_status rom_init(const rom_config* cfg_in, const double* q0_host, void* stream, rom_ctx** out) {
+}  // extern "C"
+
+namespace {
+
+// rom_init; keep_train keeps the training matrix (N x w_init) on the device
+// for the gradient pass.
+rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* stream, bool keep_train,
+                    rom_ctx** out) {
   if (!out) return ROM_EINVAL;
   *out = nullptr;
   rom_status vs = validate(cfg_in);
@@ -519,11 +527,21 @@ rom_status rom_init(const rom_config* cfg_in, const double* q0_host, void* strea
   }
   st = finish(ctx);
   if (st != ROM_OK) { rom_destroy(ctx); return st; }
-  cudaFree(ctx->q_train);
-  ctx->q_train = nullptr;
+  if (!keep_train) {
+    cudaFree(ctx->q_train);
+    ctx->q_train = nullptr;
+  }
   ctx->step = w;
   *out = ctx;
   return ROM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rom_status rom_init(const rom_config* cfg_in, const double* q0_host, void* stream, rom_ctx** out) {
+  return init_ctx(cfg_in, q0_host, stream, false, out);
 }
 
 rom_status rom_step(rom_ctx* ctx, int64_t n_steps) {
@@ -753,9 +771,10 @@ rom_status rom_fom_step_dev(int32_t problem, int64_t n_cells, double nu, double 
 
 rom_status rom_debug_set_wait_limit(int64_t cycles) {
   const long long c = cycles > 0 ? (long long)cycles : kSpinLimitCycles;
-  cudaError_t (*setters[])(long long) = {set_wait_limit_fom, set_wait_limit_euler,
-                                         set_wait_limit_isvd, set_wait_limit_reduced,
-                                         set_wait_limit_sampling, set_wait_limit_batch};
+  cudaError_t (*setters[])(long long) = {set_wait_limit_fom,      set_wait_limit_euler,
+                                         set_wait_limit_isvd,     set_wait_limit_reduced,
+                                         set_wait_limit_sampling, set_wait_limit_batch,
+                                         set_wait_limit_adjoint};
   for (auto f : setters)
     if (f(c) != cudaSuccess) return ROM_ECUDA;
   return ROM_OK;
@@ -792,7 +811,7 @@ rom_status rom_isvd_update_dev(int64_t n, int32_t r, double lambda, double rank_
   A.phi = phi_dev; A.phi32 = nullptr; A.gram = nullptr; A.sigma = sigma_dev; A.a = nullptr;
   A.transfer = 0; A.y = y_dev;
   A.q_ref = nullptr; A.drow = nullptr; A.preprocess = 0; A.yhat = nullptr; A.qres = qres;
-  A.partials = partials; A.core = core; A.ubar = ubar; A.bar = bar; A.status = ints;
+  A.partials = partials; A.core = core; A.ubar = ubar; A.rec = nullptr; A.bar = bar; A.status = ints;
   rom_status result = ROM_OK;
   cudaError_t e = cudaMemsetAsync(ints, 0, sizeof(int), s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ints + 1, &k, sizeof(int), cudaMemcpyHostToDevice, s);
@@ -815,3 +834,359 @@ rom_status rom_isvd_update_dev(int64_t n, int32_t r, double lambda, double rank_
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Gradient of a terminal misfit (rom_adjoint)
+// ---------------------------------------------------------------------------
+//
+// Forward: the offline stage (training matrix kept), then n_steps online
+// steps of Algorithm 1 launched one step at a time, recording each step's
+// root a^{n+1} and, at each event, the basis before the update with the
+// residual q (N x (r+1)), yhat, the new coarse state, the core's U, its
+// singular values, (rho, |yhat|, p), sigma and the ranks before and after.
+// With ckpt_every < n_steps the first pass keeps only the online state every
+// ckpt_every steps, and the reverse sweep re-runs each segment from its
+// checkpoint to record it. Reverse: the event and step adjoints from the last
+// step back to the first, then the offline adjoint (adjoint.cu).
+
+namespace {
+
+struct AdjSeg {          // records of one segment of the forward pass
+  int max_ev = 0;
+  double* a_hist = nullptr;    // steps x r
+  double* B = nullptr;         // max_ev x N x (r+1)
+  double* yhat = nullptr;      // max_ev x N
+  double* ynew = nullptr;      // max_ev x N
+  double* ubar = nullptr;      // max_ev x (r+1)^2
+  double* sbar = nullptr;      // max_ev x (r+1)
+  double* rec = nullptr;       // max_ev x (r+2)
+  double* sig = nullptr;       // max_ev x r
+  int* kold = nullptr;         // max_ev
+  int* knew = nullptr;         // max_ev
+  double* phi_end = nullptr;   // N x r
+};
+
+struct AdjBufs {
+  std::vector<void*> owned;
+  template <typename T>
+  cudaError_t alloc(T** p, size_t count) {
+    cudaError_t e = dalloc(p, count);
+    if (e == cudaSuccess) owned.push_back(*p);
+    return e;
+  }
+  ~AdjBufs() {
+    for (void* p : owned) cudaFree(p);
+  }
+};
+
+bool is_event_at(const rom_ctx* ctx, int64_t n) {
+  return ((n + 1 - ctx->cfg.w_init) % ctx->cfg.z) == 0;
+}
+
+// One online step (and its event) with recording into seg at local index m.
+cudaError_t record_step(rom_ctx* ctx, AdjSeg& sg, int m, int& ev, double* qT, double d) {
+  const int64_t N = ctx->N;
+  const int r = ctx->cfg.r;
+  cudaStream_t s = ctx->stream;
+  cudaError_t e = run_steps(ctx, 1);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(sg.a_hist + (size_t)m * r, ctx->d.a, sizeof(double) * r, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return e;
+  if (qT && (e = launch_adj_lift(N, r, ctx->d.phi, ctx->d.a, ctx->d.q_ref, d, qT, s)) != cudaSuccess) return e;
+  if (is_event_at(ctx, ctx->step)) {
+    const int x = ev++;
+    double* B = sg.B + (size_t)x * N * (r + 1);
+#define ACP(dst, src, bytes) \
+  if ((e = cudaMemcpyAsync((dst), (src), (bytes), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e
+    ACP(B, ctx->d.phi, sizeof(double) * N * r);
+    ACP(sg.kold + x, ctx->d.rank, sizeof(int));
+    ACP(sg.sig + (size_t)x * r, ctx->d.sigma, sizeof(double) * r);
+    if ((e = coarse_fom(ctx)) != cudaSuccess) return e;
+    EventArgs A = event_args(ctx, ctx->d.y_corr, 1, ctx->cfg.lambda, ctx->cfg.rank_tol, r, 1);
+    A.rec = sg.rec + (size_t)x * (r + 2);
+    if ((e = launch_event(A, km_of(ctx), ctx->grid, s)) != cudaSuccess) return e;
+    ACP(B + (size_t)r * N, ctx->d.qres, sizeof(double) * N);
+    ACP(sg.yhat + (size_t)x * N, ctx->d.yhat, sizeof(double) * N);
+    ACP(sg.ynew + (size_t)x * N, ctx->d.y_corr, sizeof(double) * N);
+    ACP(sg.ubar + (size_t)x * (r + 1) * (r + 1), ctx->d.ubar, sizeof(double) * (r + 1) * (r + 1));
+    ACP(sg.sbar + (size_t)x * (r + 1), ctx->d.core + core_sbar_offset(), sizeof(double) * (r + 1));
+    ACP(sg.knew + x, ctx->d.rank, sizeof(int));
+#undef ACP
+  }
+  ctx->step += 1;
+  return cudaSuccess;
+}
+
+// One online step without recording.
+cudaError_t plain_step(rom_ctx* ctx, double* qT, double d) {
+  cudaError_t e = run_steps(ctx, 1);
+  if (e != cudaSuccess) return e;
+  if (qT && (e = launch_adj_lift(ctx->N, ctx->cfg.r, ctx->d.phi, ctx->d.a, ctx->d.q_ref, d, qT,
+                                 ctx->stream)) != cudaSuccess)
+    return e;
+  if (is_event_at(ctx, ctx->step)) {
+    if ((e = coarse_fom(ctx)) != cudaSuccess) return e;
+    if ((e = run_event(ctx)) != cudaSuccess) return e;
+  }
+  ctx->step += 1;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" rom_status rom_adjoint(const rom_config* cfg, const double* q0_host, const double* target_host,
+                                  int64_t n_steps, int32_t ckpt_every, void* stream, double* J_out,
+                                  double* dJ_dnu, double* dJ_dq0, double* q_final) {
+  if (!cfg || !q0_host || !target_host || !J_out || !dJ_dnu || n_steps < 1 || ckpt_every < 1)
+    return ROM_EINVAL;
+  rom_status vs = validate(cfg);
+  if (vs != ROM_OK) return vs;
+  if (cfg->problem != ROM_BURGERS || cfg->precision != ROM_FP64 || cfg->n_s != 0 || cfg->w_init > 128)
+    return ROM_EINVAL;
+  const int64_t N = cfg->n_cells;
+  if (!all_finite(q0_host, N) || !all_finite(target_host, N)) return ROM_ENONFINITE;
+  rom_ctx* ctx = nullptr;
+  rom_status st = init_ctx(cfg, q0_host, stream, true, &ctx);
+  if (st != ROM_OK) return st;
+  struct Guard {
+    rom_ctx* c;
+    ~Guard() { rom_destroy(c); }
+  } guard{ctx};
+  cudaStream_t s = ctx->stream;
+  const int r = cfg->r, w = cfg->w_init, z = cfg->z;
+  const int G = ctx->grid;
+  const double dt = ctx->cfg.dt, nu = ctx->cfg.nu, lam = ctx->cfg.lambda;
+  const double hc = z * dt;
+  double d = 0.0;
+  RCK(cudaMemcpy(&d, ctx->d.dvals, sizeof(double), cudaMemcpyDeviceToHost));
+  int k0 = 0;
+  RCK(cudaMemcpy(&k0, ctx->d.rank, sizeof(int), cudaMemcpyDeviceToHost));
+  if (k0 < 1) return ROM_EINVAL;
+
+  AdjBufs ab;
+  cudaError_t e = cudaSuccess;
+#define AAL(p, n) \
+  if (e == cudaSuccess) e = ab.alloc(&(p), (size_t)(n))
+  // offline copies
+  double *phi0, *sig0, *a0, *ycorr0;
+  AAL(phi0, N * r); AAL(sig0, r); AAL(a0, r); AAL(ycorr0, N);
+  // checkpoints
+  const int64_t seg_len = ckpt_every < n_steps ? ckpt_every : n_steps;
+  const int64_t n_seg = (n_steps + seg_len - 1) / seg_len;
+  double *ck_phi = nullptr, *ck_sig = nullptr, *ck_a = nullptr, *ck_y = nullptr;
+  int* ck_rank = nullptr;
+  if (n_seg > 1) {
+    AAL(ck_phi, (size_t)n_seg * N * r); AAL(ck_sig, (size_t)n_seg * r); AAL(ck_a, (size_t)n_seg * r);
+    AAL(ck_y, (size_t)n_seg * N); AAL(ck_rank, n_seg);
+  }
+  AdjSeg sg;
+  sg.max_ev = (int)(seg_len / z + 2);
+  AAL(sg.a_hist, seg_len * r); AAL(sg.B, (size_t)sg.max_ev * N * (r + 1));
+  AAL(sg.yhat, (size_t)sg.max_ev * N); AAL(sg.ynew, (size_t)sg.max_ev * N);
+  AAL(sg.ubar, (size_t)sg.max_ev * (r + 1) * (r + 1)); AAL(sg.sbar, (size_t)sg.max_ev * (r + 1));
+  AAL(sg.rec, (size_t)sg.max_ev * (r + 2)); AAL(sg.sig, (size_t)sg.max_ev * r);
+  AAL(sg.kold, sg.max_ev); AAL(sg.knew, sg.max_ev); AAL(sg.phi_end, N * r);
+  // reverse state and work
+  double *phibar, *phibar2, *qtbar, *qrefbar, *ybar, *ybar2, *abar, *sigbar, *wv, *mpart, *vpart, *acc;
+  double *small, *part, *pnb, *bbar, *tchunk, *qT, *target, *Jd, *dtot, *mpartial;
+  GridBarrier* bar;
+  int* status;
+  AAL(phibar, N * r); AAL(phibar2, N * r); AAL(qtbar, N); AAL(qrefbar, N); AAL(ybar, N); AAL(ybar2, N);
+  AAL(abar, r); AAL(sigbar, r); AAL(wv, kMaxR); AAL(mpart, (size_t)G * kMaxR * kMaxR);
+  AAL(vpart, (size_t)G * kMaxR); AAL(acc, 2 * kAdjSlots); AAL(small, kAdjSmall);
+  AAL(part, (size_t)G * 16384); AAL(pnb, N * r); AAL(bbar, N * (r + 1)); AAL(tchunk, kMaxChunks * 16);
+  AAL(qT, N); AAL(target, N); AAL(Jd, 1); AAL(dtot, 1); AAL(mpartial, 256); AAL(bar, 1); AAL(status, 1);
+  // offline reverse
+  double *X, *R, *Xbar, *V0, *Am, *Ubar, *Uh, *H, *C2, *RtR, *RtH, *Y, *Cc, *Ma, *Mb, *Ys, *sinv2, *Gm;
+  double *qlastbar, *qb0, *qb1;
+  AAL(X, N * w); AAL(R, N * w); AAL(Xbar, N * w); AAL(V0, w * r); AAL(Am, r * r); AAL(Ubar, N * r);
+  AAL(Uh, r * r); AAL(H, N * r); AAL(C2, r * w); AAL(RtR, w * w); AAL(RtH, w * r); AAL(Y, w * r);
+  AAL(Cc, r * r); AAL(Ma, r * w); AAL(Mb, r * w); AAL(Ys, w * r); AAL(sinv2, r * r); AAL(Gm, N * r);
+  AAL(qlastbar, N); AAL(qb0, N); AAL(qb1, N);
+#undef AAL
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return ROM_ENOMEM;
+  }
+  RCK(cudaMemcpyAsync(phi0, ctx->d.phi, sizeof(double) * N * r, cudaMemcpyDeviceToDevice, s));
+  RCK(cudaMemcpyAsync(sig0, ctx->d.sigma, sizeof(double) * r, cudaMemcpyDeviceToDevice, s));
+  RCK(cudaMemcpyAsync(a0, ctx->d.a, sizeof(double) * r, cudaMemcpyDeviceToDevice, s));
+  RCK(cudaMemcpyAsync(ycorr0, ctx->d.y_corr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  RCK(cudaMemcpyAsync(target, target_host, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+  RCK(cudaMemsetAsync(acc, 0, sizeof(double) * 2 * kAdjSlots, s));
+  RCK(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s));
+  RCK(cudaMemsetAsync(status, 0, sizeof(int), s));
+  const int64_t step0 = ctx->step;
+
+  // ---- forward pass ----
+  int ev_first = 0;
+  for (int64_t m = 0; m < n_steps; ++m) {
+    double* qt = (m == n_steps - 1) ? qT : nullptr;
+    if (n_seg == 1) {
+      RCK(record_step(ctx, sg, (int)m, ev_first, qt, d));
+    } else {
+      if (m % seg_len == 0) {
+        const int64_t c = m / seg_len;
+        RCK(cudaMemcpyAsync(ck_phi + (size_t)c * N * r, ctx->d.phi, sizeof(double) * N * r, cudaMemcpyDeviceToDevice, s));
+        RCK(cudaMemcpyAsync(ck_sig + (size_t)c * r, ctx->d.sigma, sizeof(double) * r, cudaMemcpyDeviceToDevice, s));
+        RCK(cudaMemcpyAsync(ck_a + (size_t)c * r, ctx->d.a, sizeof(double) * r, cudaMemcpyDeviceToDevice, s));
+        RCK(cudaMemcpyAsync(ck_y + (size_t)c * N, ctx->d.y_corr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        RCK(cudaMemcpyAsync(ck_rank + c, ctx->d.rank, sizeof(int), cudaMemcpyDeviceToDevice, s));
+      }
+      RCK(plain_step(ctx, qt, d));
+    }
+  }
+  st = finish(ctx);
+  if (st != ROM_OK) return st;
+  if (n_seg == 1)
+    RCK(cudaMemcpyAsync(sg.phi_end, ctx->d.phi, sizeof(double) * N * r, cudaMemcpyDeviceToDevice, s));
+  RCK(launch_adj_misfit(N, qT, target, qtbar, mpartial, Jd, s));
+  RCK(cudaMemsetAsync(phibar, 0, sizeof(double) * N * r, s));
+  RCK(cudaMemsetAsync(qrefbar, 0, sizeof(double) * N, s));
+  RCK(cudaMemsetAsync(ybar, 0, sizeof(double) * N, s));
+  RCK(cudaMemsetAsync(abar, 0, sizeof(double) * r, s));
+  RCK(cudaMemsetAsync(sigbar, 0, sizeof(double) * r, s));
+
+  // ---- reverse sweep, segment by segment ----
+  for (int64_t c = n_seg - 1; c >= 0; --c) {
+    const int64_t m0 = c * seg_len, m1 = (m0 + seg_len < n_steps) ? m0 + seg_len : n_steps;
+    int n_ev = 0;
+    if (n_seg == 1) {
+      n_ev = ev_first;
+    } else {
+      RCK(cudaMemcpyAsync(ctx->d.phi, ck_phi + (size_t)c * N * r, sizeof(double) * N * r, cudaMemcpyDeviceToDevice, s));
+      RCK(cudaMemcpyAsync(ctx->d.sigma, ck_sig + (size_t)c * r, sizeof(double) * r, cudaMemcpyDeviceToDevice, s));
+      RCK(cudaMemcpyAsync(ctx->d.a, ck_a + (size_t)c * r, sizeof(double) * r, cudaMemcpyDeviceToDevice, s));
+      RCK(cudaMemcpyAsync(ctx->d.y_corr, ck_y + (size_t)c * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+      RCK(cudaMemcpyAsync(ctx->d.rank, ck_rank + c, sizeof(int), cudaMemcpyDeviceToDevice, s));
+      ctx->step = step0 + m0;
+      for (int64_t m = m0; m < m1; ++m) RCK(record_step(ctx, sg, (int)(m - m0), n_ev, nullptr, d));
+      RCK(cudaMemcpyAsync(sg.phi_end, ctx->d.phi, sizeof(double) * N * r, cudaMemcpyDeviceToDevice, s));
+      st = finish(ctx);
+      if (st != ROM_OK) return st;
+    }
+    // ranks of the segment's events and the rank at its end
+    std::vector<int> kold(n_ev + 1), knew(n_ev + 1);
+    if (n_ev > 0) {
+      RCK(cudaMemcpy(kold.data(), sg.kold, sizeof(int) * n_ev, cudaMemcpyDeviceToHost));
+      RCK(cudaMemcpy(knew.data(), sg.knew, sizeof(int) * n_ev, cudaMemcpyDeviceToHost));
+    }
+    int k_end = 0;
+    RCK(cudaMemcpy(&k_end, ctx->d.rank, sizeof(int), cudaMemcpyDeviceToHost));
+    // walk the segment backwards; ev = index of the next event at or after m
+    int ev = n_ev - 1;
+    // steps after the segment's last event use phi_end with rank k_end
+    for (int64_t m = m1 - 1; m >= m0; --m) {
+      const int64_t n_lvl = step0 + m;     // time level before the step
+      const bool has_ev = is_event_at(ctx, n_lvl);
+      const double* phi_step;
+      int k_step;
+      if (has_ev) {
+        const int x = ev;
+        const double* phinew = (x + 1 < n_ev) ? sg.B + (size_t)(x + 1) * N * (r + 1) : sg.phi_end;
+        AdjEventArgs E;
+        E.n = N; E.k = kold[x]; E.kn = knew[x]; E.r = r;
+        E.B = sg.B + (size_t)x * N * (r + 1); E.phinew = phinew;
+        E.a = sg.a_hist + (size_t)(m - m0) * r; E.q_ref = ctx->d.q_ref; E.d = d; E.lambda = lam;
+        E.abar = abar; E.phibar = phibar; E.pnb = pnb; E.bbar = bbar;
+        E.yhat = sg.yhat + (size_t)x * N; E.ynew = sg.ynew + (size_t)x * N;
+        E.ybar = ybar; E.ybar_new = ybar2; E.phibar_out = phibar2; E.qtbar = qtbar; E.qrefbar = qrefbar;
+        E.ubar = sg.ubar + (size_t)x * (r + 1) * (r + 1); E.sbar = sg.sbar + (size_t)x * (r + 1);
+        E.sigma_old = sg.sig + (size_t)x * r; E.rec = sg.rec + (size_t)x * (r + 2);
+        E.small = small; E.sigbar = sigbar; E.part = part; E.acc = acc;
+        if (E.k < 1) return ROM_ECUDA;
+        RCK(launch_adj_event(E, G, s));
+        std::swap(phibar, phibar2);
+        TbeArgs T;
+        T.y = E.ynew; T.rhs1 = ybar2; T.rhs2 = nullptr; T.x = ybar; T.n = N; T.nu = nu; T.h = hc;
+        T.chunk = tchunk; T.bar = bar; T.status = status; T.acc_nu = acc + kAdjSlots;
+        RCK(launch_adj_tbe(T, s));
+        RCK(cudaMemsetAsync(abar, 0, sizeof(double) * r, s));
+        phi_step = E.B;
+        k_step = E.k;
+        --ev;
+      } else if (ev + 1 < n_ev) {
+        phi_step = sg.B + (size_t)(ev + 1) * N * (r + 1);
+        k_step = kold[ev + 1];
+      } else {
+        phi_step = sg.phi_end;
+        k_step = k_end;
+      }
+      AdjStepArgs S;
+      S.n = N; S.k = k_step; S.phi = phi_step; S.q_ref = ctx->d.q_ref; S.d = d; S.nu = nu; S.dt = dt;
+      S.a = sg.a_hist + (size_t)(m - m0) * r; S.w = wv; S.abar = abar; S.qtbar = qtbar; S.phibar = phibar;
+      S.qrefbar = qrefbar; S.mpart = mpart; S.vpart = vpart; S.acc = acc;
+      if (S.k < 1) return ROM_ECUDA;
+      RCK(launch_adj_step(S, G, s));
+    }
+  }
+
+  // ---- offline adjoint ----
+  const double* Q = ctx->q_train;
+  const double* qlast = Q + (size_t)(w - 1) * N;
+  {
+    TbeArgs T;
+    T.y = ycorr0; T.rhs1 = ybar; T.rhs2 = nullptr; T.x = qlastbar; T.n = N; T.nu = nu; T.h = hc;
+    T.chunk = tchunk; T.bar = bar; T.status = status; T.acc_nu = acc + kAdjSlots;
+    RCK(launch_adj_tbe(T, s));
+    AdjA0Args A0{N, k0, phi0, qlast, ctx->d.q_ref, d, abar, phibar, qlastbar, qrefbar, acc};
+    RCK(launch_adj_a0(A0, G, s));
+  }
+  const int k = k0;
+  RCK(launch_adj_xhat(N, w, Q, ctx->d.q_ref, d, X, s));
+  // V0 = X^T U (w x k)
+  RCK(launch_tn(TnArgs{N, w, k, X, N, phi0, N, 1.0, part, V0}, G, s));
+  // Ubar = Phi-bar - U sym(U^T Phi-bar); -sym goes to Uh's buffer, reused below
+  RCK(launch_tn(TnArgs{N, k, k, phi0, N, phibar, N, 1.0, part, Am}, G, s));
+  RCK(launch_adj_neg_sym(Am, Uh, k, s));
+  RCK(launch_nn(NnArgs{N, k, k, phi0, N, Uh, k, 1, 1.0, 1.0, phibar, N, Ubar, N}, s));
+  // Uh = U^T Ubar; H = Ubar - U Uh
+  RCK(launch_tn(TnArgs{N, k, k, phi0, N, Ubar, N, 1.0, part, Uh}, G, s));
+  RCK(launch_nn(NnArgs{N, k, k, phi0, N, Uh, k, 1, -1.0, 1.0, Ubar, N, H, N}, s));
+  // R = (I - U U^T) X by two passes: R1 = X - U V0^T, R = R1 - U (U^T R1)
+  RCK(launch_nn(NnArgs{N, k, w, phi0, N, V0, 1, k, -1.0, 1.0, X, N, R, N}, s));
+  RCK(launch_tn(TnArgs{N, k, w, phi0, N, R, N, 1.0, part, C2}, G, s));
+  RCK(launch_nn(NnArgs{N, k, w, phi0, N, C2, w, 1, -1.0, 1.0, R, N, R, N}, s));
+  RCK(launch_tn(TnArgs{N, w, w, R, N, R, N, 1.0, part, RtR}, G, s));
+  RCK(launch_tn(TnArgs{N, w, k, R, N, H, N, 1.0, part, RtH}, G, s));
+  {
+    AdjPodArgs P{N, w, k, sig0, sigbar, V0, Uh, RtR, RtH, Y, Cc, Ma, Mb, Ys, sinv2};
+    RCK(launch_adj_pod_small(P, s));
+  }
+  // G = U C + H diag(1/s^2) + R Y diag(1/s^2)
+  RCK(launch_nn(NnArgs{N, k, k, phi0, N, Cc, k, 1, 1.0, 0.0, Gm, N, Gm, N}, s));
+  RCK(launch_nn(NnArgs{N, k, k, H, N, sinv2, k, 1, 1.0, 1.0, Gm, N, Gm, N}, s));
+  RCK(launch_nn(NnArgs{N, w, k, R, N, Ys, k, 1, 1.0, 1.0, Gm, N, Gm, N}, s));
+  // Xbar = U Ma + G Mb
+  RCK(launch_nn(NnArgs{N, k, w, phi0, N, Ma, w, 1, 1.0, 0.0, Xbar, N, Xbar, N}, s));
+  RCK(launch_nn(NnArgs{N, k, w, Gm, N, Mb, w, 1, 1.0, 1.0, Xbar, N, Xbar, N}, s));
+  // Qbar (into R's buffer) and q_ref-bar
+  double* Qbar = R;
+  {
+    AdjXcArgs XA{N, w, Q, ctx->d.q_ref, d, Xbar, Qbar, qlastbar, qrefbar, acc, dtot};
+    RCK(launch_adj_xc(XA, G, s));
+  }
+  // reversed training trajectory
+  RCK(cudaMemsetAsync(qb0, 0, sizeof(double) * N, s));
+  double* qcur = qb0;
+  double* qnext = qb1;
+  for (int j = w - 1; j >= 0; --j) {
+    TbeArgs T;
+    T.y = Q + (size_t)j * N; T.rhs1 = qcur; T.rhs2 = Qbar + (size_t)j * N; T.x = qnext; T.n = N;
+    T.nu = nu; T.h = dt; T.chunk = tchunk; T.bar = bar; T.status = status; T.acc_nu = acc + kAdjSlots;
+    RCK(launch_adj_tbe(T, s));
+    std::swap(qcur, qnext);
+  }
+  RCK(launch_adj_add(N, qcur, qrefbar, qnext, s));       // q0-bar
+  double* nubar_d = dtot;
+  RCK(launch_adj_sum_slots(acc + kAdjSlots, nubar_d, 0, s));
+  RCK(cudaStreamSynchronize(s));
+  int dst = 0;
+  RCK(cudaMemcpy(&dst, status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (dst != 0) return status_to_rom(dst);
+  RCK(cudaMemcpy(J_out, Jd, sizeof(double), cudaMemcpyDeviceToHost));
+  RCK(cudaMemcpy(dJ_dnu, nubar_d, sizeof(double), cudaMemcpyDeviceToHost));
+  if (dJ_dq0) RCK(cudaMemcpy(dJ_dq0, qnext, sizeof(double) * N, cudaMemcpyDeviceToHost));
+  if (q_final) RCK(cudaMemcpy(q_final, qT, sizeof(double) * N, cudaMemcpyDeviceToHost));
+  return ROM_OK;
+}

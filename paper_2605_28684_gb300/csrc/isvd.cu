@@ -21,6 +21,7 @@ ROM_ISVD_DECLARE_BOTH(65)
 
 size_t event_smem_bytes() { return sizeof(EventSmem); }
 size_t core_ws_doubles() { return kWsSize; }
+size_t core_sbar_offset() { return kWsSbar; }
 
 cudaError_t launch_event(const EventArgs& A, int km, int grid, cudaStream_t s) {
   switch (km) {

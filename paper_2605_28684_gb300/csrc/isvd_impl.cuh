@@ -230,6 +230,11 @@ __global__ void __launch_bounds__(kBlock) isvd_event_kernel(EventArgs A) {
     }
     sm.d_desc[k] = 0.0;
     sm.z[k] = rho;
+    if (A.rec && b == 0) {
+      A.rec[0] = rho;
+      A.rec[1] = ynorm;
+      for (int j = 0; j < k; ++j) A.rec[2 + j] = sm.z[j];
+    }
     secular_setup(sm.S, n, sm.d_desc, sm.z);
   }
   __syncthreads();

@@ -46,6 +46,7 @@ cudaError_t set_wait_limit_isvd(long long cycles);
 cudaError_t set_wait_limit_reduced(long long cycles);
 cudaError_t set_wait_limit_sampling(long long cycles);
 cudaError_t set_wait_limit_batch(long long cycles);
+cudaError_t set_wait_limit_adjoint(long long cycles);
 
 // ---------------------------------------------------------------- barrier --
 

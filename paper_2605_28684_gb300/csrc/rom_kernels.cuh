@@ -26,6 +26,8 @@ struct EventArgs {
   double* partials;     // >= 3 * grid * (KM + 2)
   double* core;         // core_ws_doubles()
   double* ubar;         // (r+1)^2
+  double* rec;          // null, or receives (rho, ||yhat||, p_0 .. p_{k-1}) of the core
+                        // (rho = 0 for an empty residual), for the gradient pass
   GridBarrier* bar;
   int* status;
 };
@@ -143,5 +145,182 @@ template <>
 __device__ __forceinline__ const double* basis<double>(const SampleArgs& A) { return A.phi; }
 template <>
 __device__ __forceinline__ const float* basis<float>(const SampleArgs& A) { return A.phi32; }
+
+}  // namespace rom
+
+// ---------------------------------------------------------------------------
+// Gradient pass (adjoint.cu): reverse sweep of the plain-Galerkin Burgers ROM
+// in FP64. All matrices are column-major with the leading dimension given;
+// small results of reductions are row-major m x nc.
+// ---------------------------------------------------------------------------
+namespace rom {
+
+constexpr int kAdjSlots = 256;   // per-CTA accumulator slots of the scalar adjoints
+
+// Adjoint of one reduced backward-Euler step with no event (three launches:
+// Jacobian partials, one-CTA transposed solve, row pass).
+struct AdjStepArgs {
+  int64_t n;
+  int k;                  // live rank of the basis in effect
+  const double* phi;      // N x k, leading dimension n
+  const double* q_ref;
+  double d, nu, dt;
+  const double* a;        // k: the step's root a^{n+1}
+  double* w;              // k: adjoint of the step's residual (written)
+  double* abar;           // k: adjoint of a; in: after the step, out: before it
+  double* qtbar;          // N: adjoint at the step's lifted state (read, then zeroed)
+  double* phibar;         // N x k, accumulated
+  double* qrefbar;        // N, accumulated
+  double* mpart;          // grid x kMaxR^2 partial sums
+  double* vpart;          // grid x kMaxR partial sums
+  double* acc;            // [0, kAdjSlots): d-bar slots; [kAdjSlots, 2 kAdjSlots): nu-bar slots
+};
+cudaError_t launch_adj_step(const AdjStepArgs& A, int grid, cudaStream_t s);
+
+// x = (I - h J_f(y))^{-T} (rhs1 + rhs2) for periodic Burgers (FP64, chunked
+// PCR); acc_nu[cta] += h x . f_nu(y).
+struct TbeArgs {
+  const double* y;
+  const double* rhs1;
+  const double* rhs2;     // may be null
+  double* x;
+  int64_t n;
+  double nu, h;
+  double* chunk;          // kMaxChunks * 16 doubles
+  GridBarrier* bar;
+  int* status;
+  double* acc_nu;         // kAdjSlots slots
+};
+cudaError_t launch_adj_tbe(const TbeArgs& A, cudaStream_t s);
+
+// out (m x nc, row-major) = alpha A^T B over N rows (m, nc <= 128, m*nc <= 16384);
+// part holds grid * m * nc doubles.
+struct TnArgs {
+  int64_t n;
+  int m, nc;
+  const double* A;
+  int64_t lda;
+  const double* B;
+  int64_t ldb;
+  double alpha;
+  double* part;
+  double* out;
+};
+cudaError_t launch_tn(const TnArgs& A, int grid, cudaStream_t s);
+
+// C = beta Cin + alpha A M over N rows; A is N x m, M(j, l) = M[j * msj + l * msl]
+// (device, m x nc with m, nc <= 128, m * nc <= 16384); C may alias Cin.
+struct NnArgs {
+  int64_t n;
+  int m, nc;
+  const double* A;
+  int64_t lda;
+  const double* M;
+  int64_t msj, msl;
+  double alpha, beta;
+  const double* Cin;
+  int64_t ldcin;
+  double* C;
+  int64_t ldc;
+};
+cudaError_t launch_nn(const NnArgs& A, cudaStream_t s);
+
+// Event pieces (rows of the iSVD adjoint and of the state transfer).
+struct AdjEventArgs {
+  int64_t n;
+  int k, kn, r;           // rank before and after the event; capacity
+  double* B;              // N x (k+1): Phi_old, then qhat in column k (finalised from column r)
+  const double* phinew;   // N x kn
+  const double* a;        // k: the step's root in the old basis
+  const double* q_ref;
+  double d, lambda;
+  const double* abar;     // kn
+  const double* phibar;   // N x kn
+  double* pnb;            // N x kn work
+  double* bbar;           // N x (k+1) work
+  const double* yhat;
+  const double* ynew;
+  const double* ybar;     // N in
+  double* ybar_new;       // N out
+  double* phibar_out;     // N x k out
+  double* qtbar;
+  double* qrefbar;
+  const double* ubar;     // (k+1)^2 column-major
+  const double* sbar;     // k+1
+  const double* sigma_old;
+  const double* rec;      // rho, ||yhat||, p (k)
+  double* small;          // device work for the small matrices (kAdjSmall doubles)
+  double* sigbar;         // r: in sigma_new-bar (kn), out sigma_old-bar (k)
+  double* part;           // partials for launch_tn
+  double* acc;
+};
+constexpr int kAdjSmall = 12 * kMaxCore * kMaxCore;
+cudaError_t launch_adj_event(const AdjEventArgs& A, int grid, cudaStream_t s);
+
+// Offline stage: the a0 transfer rows, the POD adjoint and the reversed
+// training trajectory are driven from api.cu through these pieces.
+struct AdjA0Args {
+  int64_t n;
+  int k;
+  const double* phi;      // N x k (POD basis)
+  const double* qlast;
+  const double* q_ref;
+  double d;
+  const double* abar;     // k
+  double* phibar;         // N x k (accumulated)
+  double* qlastbar;       // N (accumulated)
+  double* qrefbar;
+  double* acc;
+};
+cudaError_t launch_adj_a0(const AdjA0Args& A, int grid, cudaStream_t s);
+// X = d (Q - q_ref 1^T), N x w
+cudaError_t launch_adj_xhat(int64_t n, int w, const double* Q, const double* q_ref, double d,
+                            double* X, cudaStream_t s);
+// small dense pieces of the POD adjoint (see adjoint.cu)
+struct AdjPodArgs {
+  int64_t n;
+  int w, k;
+  const double* s;        // k kept singular values
+  const double* sbar;     // k
+  const double* V0;       // w x k row-major: X^T U
+  const double* Uh;       // k x k row-major: U^T Ubar
+  const double* RtR;      // w x w row-major
+  const double* RtH;      // w x k row-major
+  double* Y;              // w x k row-major out
+  double* C;              // k x k row-major out (coefficients of U in g)
+  double* Ma;             // k x w row-major out
+  double* Mb;             // k x w row-major out
+  double* Ys;             // w x k row-major out: Y / s^2
+  double* sinv2;          // k x k row-major out: diag(1 / s^2)
+};
+cudaError_t launch_adj_pod_small(const AdjPodArgs& A, cudaStream_t s);
+// Qbar from Xbar (two passes around the reduction of d-bar), see adjoint.cu
+struct AdjXcArgs {
+  int64_t n;
+  int w;
+  const double* Q;
+  const double* q_ref;
+  double d;
+  const double* Xbar;     // N x w
+  double* Qbar;           // N x w out
+  const double* qlastbar;
+  double* qrefbar;
+  double* acc;            // d-bar slots (pass 1 adds sum Xbar o Xc)
+  double* dtot;           // device scalar: total d-bar (written between the passes)
+};
+cudaError_t launch_adj_xc(const AdjXcArgs& A, int grid, cudaStream_t s);
+// sum of the kAdjSlots slots at acc (fixed order) into *out (+ *out if add)
+cudaError_t launch_adj_sum_slots(const double* acc, double* out, int add, cudaStream_t s);
+// M = -(A + A^T) / 2 for a k x k row-major A (one CTA)
+cudaError_t launch_adj_neg_sym(const double* Am, double* M, int k, cudaStream_t s);
+// y = a + b (N)
+cudaError_t launch_adj_add(int64_t n, const double* a, const double* b, double* y, cudaStream_t s);
+// lift q = q_ref + Phi a / d (N)
+cudaError_t launch_adj_lift(int64_t n, int k, const double* phi, const double* a, const double* q_ref,
+                            double d, double* q, cudaStream_t s);
+// J = 1/2 |q - target|^2 and qtbar = q - target
+cudaError_t launch_adj_misfit(int64_t n, const double* q, const double* target, double* qtbar,
+                              double* part, double* J, cudaStream_t s);
+size_t core_sbar_offset();
 
 }  // namespace rom
