@@ -14,6 +14,9 @@ passage of the paper:
                      exact reduced Jacobian I - dt Phi^T D J_f D^-1 Phi.
 * ``hyper_step``     Eq. deim_galerkin_rom (DEIM with U = Phi) discretised the
                      same way: a - a^n - dt (P^T Phi)^+ P^T D f(q~(a)) = 0.
+* ``lspg_step``      Eq. lspg_minimization with the test basis of Eq.
+                     lspg_test_basis_be, by Gauss-Newton.
+* ``hyper_lspg_step`` Eq. hyperreduced_lspg / hyperreduced_lspg_stationarity.
 * ``qdeim``          Eq. qdeim_qr: first pivots of a column-pivoted QR of Phi^T.
 * ``fgs_extend``     Eq. fgs_selection with the feature map Theta(y) = y: the
                      cells with the largest squared forward difference of the
@@ -177,6 +180,63 @@ def hyper_step(a_prev, Phi, q_ref, d, P, M, cfg):
 
 
 # ----------------------------------------------------------------------------
+# least-squares Petrov-Galerkin steps (Sec. 3.1, Sec. 3.2)
+# ----------------------------------------------------------------------------
+
+def lspg_residual(a, a_prev, Phi, q_ref, d, cfg):
+    """D r(q~(a)) with the backward-Euler residual r(q) = q - q^{n-1} - dt f(q)
+    (Eq. be_residual_rom_section); the previous state is the lifted reduced
+    state q~(a_prev) in the current basis."""
+    qt = lift(a, Phi, q_ref, d)
+    qp = lift(a_prev, Phi, q_ref, d)
+    return d * (qt - qp - cfg.dt * fv.fom_f(qt, cfg.problem, cfg.nu, cfg.gamma))
+
+
+def lspg_test_basis(a, Phi, q_ref, d, cfg):
+    """Psi = (I - dt D J_f(q~) D^-1) Phi (Eq. lspg_test_basis_be)."""
+    qt = lift(a, Phi, q_ref, d)
+    Jf = fv.fom_jac(qt, cfg.problem, cfg.nu, cfg.gamma)
+    return Phi - cfg.dt * (d[:, None] * (Jf @ (Phi / d[:, None])))
+
+
+def _gauss_newton(a_prev, resid, jac, tol, max_iter):
+    """Gauss-Newton for min |resid(a)|^2 from a_prev: each step is the least
+    squares solution of jac(a) delta = -resid(a) (minimum norm, so null basis
+    columns keep a zero step); stop once max|delta| <= tol (1 + max|a|)."""
+    a = a_prev.copy()
+    for it in range(1, max_iter + 1):
+        delta = np.linalg.lstsq(jac(a), -resid(a), rcond=None)[0]
+        a = a + delta
+        if np.max(np.abs(delta)) <= tol * (1.0 + np.max(np.abs(a))):
+            return a, it
+    raise NewtonNoConvergence(f"Gauss-Newton did not converge in {max_iter} iterations")
+
+
+def lspg_step(a_prev, Phi, q_ref, d, cfg):
+    """One LSPG step: Eq. lspg_minimization, a = argmin |D r(q~(a))|, by
+    Gauss-Newton with the Jacobian d(D r)/da = Psi; its fixed point satisfies
+    Eq. lspg_stationarity, Psi^T D r = 0."""
+    return _gauss_newton(a_prev,
+                         lambda a: lspg_residual(a, a_prev, Phi, q_ref, d, cfg),
+                         lambda a: lspg_test_basis(a, Phi, q_ref, d, cfg),
+                         cfg.newton_tol, cfg.newton_max)
+
+
+def hyper_lspg_step(a_prev, Phi, q_ref, d, P, M, cfg):
+    """One hyper-reduced LSPG step (Eq. hyperreduced_lspg): minimise
+    |Phi M P^T D r| = |M P^T D r| (Phi orthonormal, M = (P^T Phi)^+) by
+    Gauss-Newton with the Jacobian M P^T Psi; the fixed point satisfies Eq.
+    hyperreduced_lspg_stationarity."""
+    def resid(a):
+        return M @ lspg_residual(a, a_prev, Phi, q_ref, d, cfg)[P]
+
+    def jac(a):
+        return M @ lspg_test_basis(a, Phi, q_ref, d, cfg)[P, :]
+
+    return _gauss_newton(a_prev, resid, jac, cfg.newton_tol, cfg.newton_max)
+
+
+# ----------------------------------------------------------------------------
 # sampling
 # ----------------------------------------------------------------------------
 
@@ -320,6 +380,10 @@ class AdaptiveROM:
 
     def rom_step(self, a_prev):
         c = self.cfg
+        if getattr(c, "projection", 0) == 1:        # LSPG
+            if c.n_s > 0:
+                return hyper_lspg_step(a_prev, self.Phi, self.q_ref, self.d, self.P, self.M, c)
+            return lspg_step(a_prev, self.Phi, self.q_ref, self.d, c)
         if c.n_s > 0:
             return hyper_step(a_prev, self.Phi, self.q_ref, self.d, self.P, self.M, c)
         return galerkin_step(a_prev, self.Phi, self.q_ref, self.d, c)

@@ -22,7 +22,7 @@ Workloads (the paper's problem families, Sec. 5.1 and 5.2 / App. B):
 from __future__ import annotations
 
 import math
-from dataclasses import dataclass, field, asdict
+from dataclasses import dataclass, field, fields, asdict
 
 import numpy as np
 
@@ -117,6 +117,7 @@ class RomConfig:
     newton_max: int = 20
     n_online: int = 2000      # online steps after the training window
     precision: int = 0        # 0: FP64, 1: mixed FP32
+    projection: int = 0       # 0: Galerkin, 1: least-squares Petrov-Galerkin
     seed: int = 0
     amplitude: float = 0.5
 
@@ -126,6 +127,15 @@ class RomConfig:
 
     def to_dict(self):
         return asdict(self)
+
+    def matches(self, stored: dict) -> bool:
+        """True if a configuration stored with a record describes this one:
+        every stored field is equal, and fields the record predates hold
+        their defaults."""
+        cur = self.to_dict()
+        defaults = {f.name: f.default for f in fields(self)}
+        return (all(cur.get(k) == v for k, v in stored.items())
+                and all(cur[k] == defaults[k] for k in cur.keys() - stored.keys()))
 
 
 LAMBDA_BY_Z = {5: 0.5, 10: 0.1, 20: 1e-7}

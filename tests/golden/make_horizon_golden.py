@@ -5,7 +5,9 @@ Cases (Algorithm 1, online loop from n = w_init):
 
 * ``c1``  Burgers DEIM-Galerkin, N = 16384, r = 32, n_s = 96, z = 5,
           lambda = 0.5, all 20 000 online steps;
-* ``c2``  Sod shock tube, 8192 cells, r = 40, z = 10, lambda = 0.01, to t = 0.2;
+* ``c2``  Sod shock tube, 8192 cells, r = 40, z = 10, lambda = 0.01, to t = 0.2
+          or to the step whose reduced Newton solve has no root (stored as
+          ``fail_step``, the time level of that step; -1 if none);
 * ``c3``  twelve instances of the 256-instance Burgers batch (the smallest
           and largest N, the highest r, and nine more spread over N), 2000
           online steps each.
@@ -54,9 +56,23 @@ def run_case(cfg, n_steps, tau, stride=STRIDE, fingerprints=False):
     W = synth.probe_vectors(cfg.n)
     steps, qs, norms, probes, ranks = [], [], [], [], []
     fp_sum, fp_sq, fp_step = [], [], []
+    fail_step = -1
     for k in range(n_steps):
         event = m.is_event(m.n)
-        m.step()
+        try:
+            m.step()
+        except orom.NewtonNoConvergence:
+            # the reduced Newton solve has no root any more (the state left the
+            # physical range); the records end at the last completed step
+            fail_step = m.n
+            if not steps or steps[-1] != m.n:     # the last completed step
+                q = m.lifted()
+                steps.append(m.n)
+                qs.append(q[sub])
+                norms.append(float(np.linalg.norm(q)))
+                probes.append(W.T @ q)
+                ranks.append(orom.numerical_rank(m.Phi))
+            break
         if fingerprints and event:
             P = np.asarray(m.P, dtype=np.int64)
             fp_sum.append(int(P.sum()))
@@ -70,7 +86,8 @@ def run_case(cfg, n_steps, tau, stride=STRIDE, fingerprints=False):
             probes.append(W.T @ q)
             ranks.append(orom.numerical_rank(m.Phi))
     out = dict(steps=np.array(steps), sub=sub, q_sub=np.array(qs), norm=np.array(norms),
-               probe=np.array(probes), rank=np.array(ranks), min_gap=np.array(m.min_gap))
+               probe=np.array(probes), rank=np.array(ranks), min_gap=np.array(m.min_gap),
+               fail_step=np.array(fail_step))
     if fingerprints:
         out.update(fp_step=np.array(fp_step), fp_sum=np.array(fp_sum), fp_sumsq=np.array(fp_sq))
     return out

@@ -377,3 +377,102 @@ def test_basis_path_equals_batch_svd_of_weighted_snapshots(lam):
     # measured: 4e-16 s_1 and 1e-8 (the last compared direction is 4x above the next)
     assert np.allclose(m.sigma[:n_live], s[:n_live], rtol=0, atol=1e-12 * s[0])
     assert principal_angle_sin(m.Phi[:, :n_live], U[:, :n_live]) < 1e-6
+
+
+# ------------------------------------------------------------------- LSPG ---
+
+def test_lspg_with_a_full_basis_is_the_fom_step():
+    """r = N: the trial manifold is the whole space, the minimum of |D r| is
+    zero and the LSPG step (Eq. lspg_minimization) is the backward-Euler FOM
+    step (Eq. be_residual_rom_section), solved here by the FOM's own Newton
+    with a sparse LU."""
+    n = 48
+    cfg = synth.config_burgers_small()
+    cfg.n_cells, cfg.r, cfg.dt, cfg.nu = n, n, 1e-3, 0.01
+    q_prev = synth.burgers_ic(n, 5)
+    q_ref = synth.burgers_ic(n, 6)
+    d = np.full(n, 2.5)
+    Phi = synth.random_orthonormal(n, n, 3)
+    a_prev = Phi.T @ (d * (q_prev - q_ref))
+    a, _ = rom.lspg_step(a_prev, Phi, q_ref, d, cfg)
+    q_fom = fv.be_step(q_prev, cfg.dt, 0, cfg.nu)
+    assert np.max(np.abs(rom.lift(a, Phi, q_ref, d) - q_fom)) <= 1e-12 * np.max(np.abs(q_fom))
+
+
+def test_lspg_step_of_a_nearly_linear_operator_is_the_least_squares_solution():
+    """Near u = 0 the Burgers operator is the viscous term nu L (the flux is
+    quadratic in u, here 1e-3 of the diffusion), so the LSPG step is the
+    linear least-squares problem min |(I - dt nu L) Phi a - Phi a_prev|:
+    Gauss-Newton must reach the solution the normal equations give directly
+    (to the size of the neglected flux), which differs from the Galerkin
+    solution Phi^T (I - dt nu L) Phi a = a_prev."""
+    n, r = 64, 6
+    cfg = synth.config_burgers_small()
+    cfg.n_cells, cfg.r, cfg.dt, cfg.nu = n, r, 5e-4, 0.02
+    Phi = synth.random_orthonormal(n, r, 8)
+    q_ref = np.zeros(n)
+    d = np.ones(n)
+    a_prev = np.random.default_rng(2).standard_normal(r) * 1e-3
+    L = (np.roll(np.eye(n), 1, axis=0) - 2 * np.eye(n) + np.roll(np.eye(n), -1, axis=0)) * n * n
+    A = np.eye(n) - cfg.dt * cfg.nu * L
+    a_ls = np.linalg.solve((A @ Phi).T @ (A @ Phi), (A @ Phi).T @ (Phi @ a_prev))
+    a, _ = rom.lspg_step(a_prev, Phi, q_ref, d, cfg)
+    assert np.max(np.abs(a - a_ls)) <= 1e-4 * np.max(np.abs(a_ls))
+    a_g = np.linalg.solve(Phi.T @ A @ Phi, a_prev)
+    assert np.max(np.abs(a_g - a_ls)) > 1e-3 * np.max(np.abs(a_ls))
+
+
+def test_hyper_reduced_lspg_equals_deim_galerkin():
+    """With the DEIM basis equal to the trial basis and P^T Phi of full column
+    rank, (P^T Phi)^+ P^T Phi = I, so the hyper-reduced LSPG objective
+    |(P^T Phi)^+ P^T D r| (Eq. hyperreduced_lspg) is the norm of the
+    DEIM-Galerkin residual (Eq. deim_galerkin_rom) and its Gauss-Newton
+    matrix is that residual's square Jacobian: the minimiser is the
+    DEIM-Galerkin root."""
+    cfg = synth.config_burgers_hyper()
+    cfg.n_cells, cfg.r, cfg.n_s = 512, 8, 24
+    q0 = synth.initial_state(cfg)
+    m = rom.AdaptiveROM(cfg, q0)
+    for _ in range(7):
+        m.step()
+    a_g, _ = rom.hyper_step(m.a, m.Phi, m.q_ref, m.d, m.P, m.M, cfg)
+    a_l, _ = rom.hyper_lspg_step(m.a, m.Phi, m.q_ref, m.d, m.P, m.M, cfg)
+    assert np.max(np.abs(a_l - a_g)) <= 1e-11 * np.max(np.abs(a_g))
+
+
+def test_lspg_and_galerkin_agree_as_dt_vanishes():
+    """LSPG tests the residual with Psi = Phi - dt D J_f D^-1 Phi, Galerkin
+    with Phi; the two steps from the same state differ at least at second
+    order in dt (more here, where f is nearly in span(Phi) right after
+    training): halving dt divides the difference by at least three."""
+    cfg = synth.config_burgers_small()
+    q0 = synth.initial_state(cfg)
+    m = rom.AdaptiveROM(cfg, q0)
+    diffs = []
+    for dt in (4e-4, 2e-4, 1e-4):
+        c = copy.copy(cfg)
+        c.dt = dt
+        a_g, _ = rom.galerkin_step(m.a, m.Phi, m.q_ref, m.d, c)
+        a_l, _ = rom.lspg_step(m.a, m.Phi, m.q_ref, m.d, c)
+        diffs.append(np.linalg.norm(a_g - a_l))
+    assert diffs[0] / diffs[1] > 3.0 and diffs[1] / diffs[2] > 3.0, diffs
+    assert diffs[2] > 0.0
+
+
+def test_lspg_adaptive_rom_runs_and_tracks_the_fom():
+    """Algorithm 1 with the LSPG step (plain projection): the ROM error
+    against the fine FOM stays of the size the Galerkin ROM reaches."""
+    cfg = synth.config_burgers_small()
+    cfg.n_cells, cfg.n_online = 256, 300
+    q0 = synth.initial_state(cfg)
+    res = {}
+    for proj in (0, 1):
+        c = copy.copy(cfg)
+        c.projection = proj
+        m = rom.AdaptiveROM(c, q0)
+        q = m.Q_train[:, -1]
+        for _ in range(cfg.n_online):
+            qt = m.step()
+            q = fv.be_step(q, c.dt, 0, c.nu)
+        res[proj] = rom.relative_error(qt, q)
+    assert res[1] < 5 * res[0] + 1e-6, res
