@@ -272,6 +272,86 @@ def timed_single(g, cfg, n_steps):
         return {"error": f"{type(exc).__name__}: {exc}"}
 
 
+def timed_full_horizon(g, cfg, n_steps, fom_eps=True):
+    """One rom_step over a whole horizon (device time on a side stream and
+    wall clock around the call), and the ROM error against the fine FOM
+    (the FOM advanced on the GPU by rom_fom_step_dev over the same steps)."""
+    import torch
+    try:
+        q0 = synth.initial_state(cfg)
+        s = torch.cuda.Stream()
+        rom = g.AdaptiveROM(cfg, q0, stream=s.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0.record(s)
+        err = None
+        try:
+            rom.step(n_steps)
+        except g.RomError as exc:
+            err = str(exc)
+        e1.record(s)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ms = e0.elapsed_time(e1)
+        out = {"steps": n_steps, "device_ms": ms, "wall_ms": wall * 1e3,
+               "value": n_steps / (ms / 1e3), "unit": "steps/s"}
+        if err is not None:
+            out["error"] = err
+            rom.close()
+            return out
+        if fom_eps:
+            qt = rom.q_tilde()
+            qa = torch.tensor(q0, device="cuda", dtype=torch.float64)
+            qb = torch.empty_like(qa)
+            for _ in range(cfg.w_init + n_steps):
+                g.fom_step_dev(cfg.problem, cfg.n_cells, cfg.nu, cfg.gamma, cfg.dt, cfg.newton_tol,
+                               cfg.newton_max, qa.data_ptr(), qb.data_ptr())
+                qa, qb = qb, qa
+            qf = qa.cpu().numpy()
+            out["eps_vs_fom"] = float(np.linalg.norm(qt - qf) / np.linalg.norm(qf))
+        rom.close()
+        return out
+    except Exception as exc:       # an extra form must not cost the main line
+        return {"error": f"{type(exc).__name__}: {exc}"}
+
+
+def timed_adjoint(g):
+    """The gradient workload (Burgers N = 65536, r = 64, 1000 steps, z = 10):
+    rom_adjoint (offline stage, recorded forward pass and reverse sweep) next
+    to the plain FP64 forward of the same steps (rom_init + rom_step), both
+    device-timed, and the gradient against the oracle's stored values."""
+    import torch
+    try:
+        cfg = synth.config_adjoint()
+        q0 = synth.initial_state(cfg)
+        target = synth.burgers_target(cfg.n_cells, cfg.seed + 1)
+        g.adjoint(cfg, q0, target, 20, 20)                 # warm-up (allocation, code load)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J, dnu, dq0 = g.adjoint(cfg, q0, target, cfg.n_online, 50)
+        torch.cuda.synchronize()
+        adj_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        rom = g.AdaptiveROM(cfg, q0)
+        rom.step(cfg.n_online)
+        torch.cuda.synchronize()
+        fwd_s = time.perf_counter() - t0
+        rom.close()
+        dA = float(dq0 @ synth.burgers_ic_amplitude_direction(cfg.n_cells))
+        with open(os.path.join(ROOT, "tests", "golden", "adjoint_burgers_n65536_r64.json")) as f:
+            gold = json.load(f)
+        ref = gold["grad_reverse_sweep"]
+        return {"workload": "burgers-N65536-r64-z10-1000steps-terminal-misfit", "steps": cfg.n_online,
+                "ckpt_every": 50, "forward_backward_s": adj_s, "plain_forward_s": fwd_s,
+                "ratio": adj_s / fwd_s, "J": J, "dJ_dnu": dnu, "dJ_dA": dA,
+                "rel_err_vs_oracle": {"nu": abs(dnu - ref["nu"]) / abs(ref["nu"]),
+                                      "A": abs(dA - ref["A"]) / abs(ref["A"])},
+                "timing": "wall clock around each call (both include the offline stage)"}
+    except Exception as exc:
+        return {"error": f"{type(exc).__name__}: {exc}"}
+
+
 # DRAM traffic of one launch of the batched reduced-step kernel (5 steps) from
 # one ncu capture of the 256-instance workload (summarised under profiles/);
 # reported only while csrc/batch.cu is unchanged.
@@ -450,6 +530,16 @@ def main():
         # the two other single-ROM workloads: Burgers N=512 plain Galerkin, and Sod
         forms["burgers_n512_r10_z10_fp64"] = timed_single(g, synth.config_burgers_small(), 2000)
         forms["sod_n8192_r40_z10_fp64"] = timed_single(g, synth.config_sod(), 500)
+        # whole horizons: the headline workload's 20 000 steps, Sod to the last
+        # step with a reduced Newton root (the Galerkin ROM has none at the
+        # 4099th online step; t = 0.2 would be step 4938)
+        forms["c1_full_horizon"] = timed_full_horizon(g, workload_config(), 20000)
+        sod = synth.config_sod()
+        forms["sod_full_horizon"] = timed_full_horizon(g, sod, 4098)
+        lspg = synth.config_burgers_small()
+        lspg.projection = 1
+        forms["lspg_burgers_n512_r10_z10_fp64"] = timed_single(g, lspg, 2000)
+        forms["adjoint"] = timed_adjoint(g)
 
     # roofline of the dominant kernel (largest device time in the timed region)
     dom = max(prof, key=lambda p: prof[p]["ms"])

@@ -51,6 +51,7 @@ typedef enum {
 
 typedef enum { ROM_BURGERS = 0, ROM_EULER = 1 } rom_problem;
 typedef enum { ROM_FP64 = 0, ROM_MIXED_FP32 = 1 } rom_precision;
+typedef enum { ROM_GALERKIN = 0, ROM_LSPG = 1 } rom_projection;
 
 /*
  * Hyper-parameters of one adaptive ROM: the inputs of Algorithm 1 (r, n_s,
@@ -79,6 +80,15 @@ typedef enum { ROM_FP64 = 0, ROM_MIXED_FP32 = 1 } rom_precision;
  *              enters only if ||q|| > rank_tol * max(||y||, sigma_1). <= 0 selects
  *              the precision's default: 1e-10 (FP64), 1e-5 (mixed; FP32
  *              projections cannot resolve smaller residuals).
+ *  projection  ROM_GALERKIN (0): the Galerkin step of Eq. galerkin_continuous_rom
+ *              (or Eq. deim_galerkin_rom with n_s > 0). ROM_LSPG (1): the
+ *              least-squares Petrov-Galerkin step of Eq. lspg_minimization with
+ *              the backward-Euler test basis of Eq. lspg_test_basis_be, solved by
+ *              Gauss-Newton in FP64 (Burgers, ROM_FP64 only). With n_s > 0 the
+ *              hyper-reduced LSPG step (Eq. hyperreduced_lspg_stationarity, DEIM
+ *              basis = Phi) has the DEIM-Galerkin root as its minimiser, because
+ *              (P^T Phi)^+ P^T Phi = I makes its objective the norm of the
+ *              DEIM-Galerkin residual; that step is used.
  */
 typedef struct {
     int32_t problem;
@@ -96,6 +106,7 @@ typedef struct {
     double lambda;
     double newton_tol;
     double rank_tol;
+    int32_t projection;
 } rom_config;
 
 /*
@@ -267,7 +278,8 @@ rom_status rom_isvd_update_dev(int64_t n, int32_t r, double lambda, double rank_
  * Gradient of a terminal misfit of the adaptive ROM (the paper states no
  * adjoint; this differentiates Algorithm 1 with the iSVD update of Algorithm
  * 2 as this library computes it). For the plain-Galerkin Burgers ROM
- * (problem ROM_BURGERS, precision ROM_FP64, n_s = 0, w_init <= 128):
+ * (problem ROM_BURGERS, precision ROM_FP64, projection ROM_GALERKIN, n_s = 0,
+ * w_init <= 128):
  *   J(nu, q0) = 1/2 || q~^{n_T} - target ||^2,
  * q~^{n_T} the lifted state returned by the last of n_steps online steps
  * (before that step's adaptation event, if it has one), and its gradient with
@@ -322,7 +334,7 @@ typedef struct rom_batch rom_batch;
  * into one device layout: bases back to back (FP32, column-major per
  * instance), N-vectors back to back, row tiles and FOM chunks.
  *  cfgs     count configurations: problem ROM_BURGERS, precision
- *           ROM_MIXED_FP32, n_var 1, n_s 0, 1 <= r <= 64,
+ *           ROM_MIXED_FP32, projection ROM_GALERKIN, n_var 1, n_s 0, 1 <= r <= 64,
  *           256 <= n_cells <= 131072, z >= 1 (others as rom_init).
  *  q0s      count host pointers, q0s[i] holding n_cells doubles (copied).
  *  count    1 .. 4096, with at most 256 coarse-FOM chunks per CTA of the FOM

@@ -42,6 +42,7 @@ def make_config(cfg) -> _lib.RomConfigC:
     c.lambda_ = float(getattr(cfg, "lam", getattr(cfg, "lambda_", 0.1)))
     c.newton_tol = float(getattr(cfg, "newton_tol", 1e-12))
     c.rank_tol = float(getattr(cfg, "rank_tol", 0.0))     # <= 0: the precision's default
+    c.projection = int(getattr(cfg, "projection", 0))
     return c
 
 

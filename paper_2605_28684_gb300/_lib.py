@@ -36,6 +36,7 @@ class RomConfigC(ctypes.Structure):
         ("lambda_", ctypes.c_double),
         ("newton_tol", ctypes.c_double),
         ("rank_tol", ctypes.c_double),
+        ("projection", ctypes.c_int32),
     ]
 
 

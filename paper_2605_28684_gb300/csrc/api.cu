@@ -86,6 +86,9 @@ rom_status validate(const rom_config* c) {
   }
   if (!(c->dt > 0.0) || !(c->nu >= 0.0) || !(c->lambda >= 0.0 && c->lambda <= 1.0)) return ROM_EINVAL;
   if (!(c->newton_tol > 0.0)) return ROM_EINVAL;
+  if (c->projection != ROM_GALERKIN && c->projection != ROM_LSPG) return ROM_EINVAL;
+  if (c->projection == ROM_LSPG && (c->problem != ROM_BURGERS || c->precision != ROM_FP64))
+    return ROM_EINVAL;
   return ROM_OK;
 }
 
@@ -257,6 +260,7 @@ StepArgs step_args(rom_ctx* ctx, int nsteps) {
   A.samples = ctx->d.samples;
   A.mesh = ctx->d.mesh;
   A.minv = ctx->d.minv;
+  A.npart = ctx->d.npart;
   A.bar = ctx->d.bar;
   A.status = ctx->d.status;
   A.iters = ctx->d.iters_rom;
@@ -268,6 +272,7 @@ cudaError_t run_steps(rom_ctx* ctx, int nsteps) {
   cudaError_t e = prof_mark(ctx, 0, true);
   if (e != cudaSuccess) return e;
   if (ctx->cfg.n_s > 0) e = launch_hyper_steps(A, km_of(ctx), ctx->stream);
+  else if (ctx->cfg.projection == ROM_LSPG) e = launch_lspg_steps(A, ctx->grid, ctx->stream);
   else if (ctx->cfg.problem == ROM_EULER) e = launch_euler_galerkin_steps(A, km_of(ctx), ctx->grid, ctx->stream);
   else e = launch_galerkin_steps(A, km_of(ctx), ctx->grid, ctx->stream);
   if (e != cudaSuccess) return e;
@@ -362,7 +367,7 @@ void free_state(rom_ctx* ctx) {
                   d.phi32, d.gram, d.sigma, d.a, d.a_prev, d.rank, d.core, d.ubar, d.partials,
                   d.jpartials, d.jac, d.samples, d.chosen, d.resid_norm, d.qdeim_q, d.cand_v,
                   d.cand_i, d.mesh, d.minv, d.bar, d.status, d.iters_rom, d.iters_fom, d.maxbuf,
-                  d.fom_chunk, ctx->q_train};
+                  d.fom_chunk, d.npart, ctx->q_train};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   memset(&ctx->d, 0, sizeof(DevState));
@@ -454,6 +459,7 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
     ALLOC(d.phi32, (size_t)N * r);
     ALLOC(d.gram, (size_t)G * kMaxR * kMaxR);
   }
+  if (ctx->cfg.projection == ROM_LSPG) ALLOC(d.npart, lspg_partial_doubles(G));
 #undef ALLOC
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -774,7 +780,7 @@ rom_status rom_debug_set_wait_limit(int64_t cycles) {
   cudaError_t (*setters[])(long long) = {set_wait_limit_fom,      set_wait_limit_euler,
                                          set_wait_limit_isvd,     set_wait_limit_reduced,
                                          set_wait_limit_sampling, set_wait_limit_batch,
-                                         set_wait_limit_adjoint};
+                                         set_wait_limit_adjoint,  set_wait_limit_lspg};
   for (auto f : setters)
     if (f(c) != cudaSuccess) return ROM_ECUDA;
   return ROM_OK;
@@ -941,7 +947,8 @@ extern "C" rom_status rom_adjoint(const rom_config* cfg, const double* q0_host, 
     return ROM_EINVAL;
   rom_status vs = validate(cfg);
   if (vs != ROM_OK) return vs;
-  if (cfg->problem != ROM_BURGERS || cfg->precision != ROM_FP64 || cfg->n_s != 0 || cfg->w_init > 128)
+  if (cfg->problem != ROM_BURGERS || cfg->precision != ROM_FP64 || cfg->n_s != 0 || cfg->w_init > 128 ||
+      cfg->projection != ROM_GALERKIN)
     return ROM_EINVAL;
   const int64_t N = cfg->n_cells;
   if (!all_finite(q0_host, N) || !all_finite(target_host, N)) return ROM_ENONFINITE;

@@ -1694,7 +1694,8 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
   for (int i = 0; i < count; ++i) {
     const rom_config& c = cfgs[i];
     if (c.problem != ROM_BURGERS || c.precision != ROM_MIXED_FP32 || c.n_s != 0 || c.n_var != 1 ||
-        c.r < 1 || c.r > kMaxR || c.n_cells < 256 || c.n_cells > 131072 || c.z < 1 || !q0s[i])
+        c.projection != ROM_GALERKIN || c.r < 1 || c.r > kMaxR || c.n_cells < 256 ||
+        c.n_cells > 131072 || c.z < 1 || !q0s[i])
       return ROM_EINVAL;
   }
   int dev = 0;

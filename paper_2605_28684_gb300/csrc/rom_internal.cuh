@@ -47,6 +47,7 @@ cudaError_t set_wait_limit_reduced(long long cycles);
 cudaError_t set_wait_limit_sampling(long long cycles);
 cudaError_t set_wait_limit_batch(long long cycles);
 cudaError_t set_wait_limit_adjoint(long long cycles);
+cudaError_t set_wait_limit_lspg(long long cycles);
 
 // ---------------------------------------------------------------- barrier --
 
@@ -408,6 +409,7 @@ struct DevState {
   int* iters_fom;
   unsigned long long* maxbuf;
   float* fom_chunk;
+  double* npart;        // LSPG normal-equation partial sums
 };
 
 }  // namespace rom

@@ -75,6 +75,7 @@ struct StepArgs {
   const int* samples;
   const double* mesh;   // n_s x 3 x (kMaxR + 2): Phi rows (k), then q_ref, d
   const double* minv;   // k x n_s row-major
+  double* npart;        // LSPG: lspg_partial_doubles(grid) partial sums
   GridBarrier* bar;
   int* status;
   int* iters;           // Newton iterations of the last step
@@ -83,6 +84,9 @@ struct StepArgs {
 cudaError_t launch_galerkin_steps(const StepArgs& A, int km, int grid, cudaStream_t s);
 cudaError_t launch_euler_galerkin_steps(const StepArgs& A, int km, int grid, cudaStream_t s);
 cudaError_t launch_hyper_steps(const StepArgs& A, int km, cudaStream_t s);
+// LSPG steps (lspg.cu), FP64 Burgers, n_s = 0
+cudaError_t launch_lspg_steps(const StepArgs& A, int grid, cudaStream_t s);
+size_t lspg_partial_doubles(int grid);
 
 struct LiftArgs {
   int64_t n, ld;

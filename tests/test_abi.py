@@ -48,14 +48,19 @@ def test_invalid_configs_rejected(lib):
                        ("n_cells", 4), ("n_cells", 128 * 1024 + 1),
                        # r beyond the training window, too many samples, no BF16 form
                        ("w_init", 5), ("n_s", 257), ("precision", 2),
-                       ("nu", -1e-3), ("dt", float("nan")), ("newton_max", 0)]:
+                       ("nu", -1e-3), ("dt", float("nan")), ("newton_max", 0),
+                       # unknown projection; LSPG is FP64 only
+                       ("projection", 2)]:
         c = synth.config_burgers_small()
         setattr(c, field, val)
         bad.append(c)
-    for field, val in [("n_cells", 128 * 256 + 1), ("n_s", 60), ("n_var", 1)]:
+    for field, val in [("n_cells", 128 * 256 + 1), ("n_s", 60), ("n_var", 1), ("projection", 1)]:
         c = synth.config_sod(256)
         setattr(c, field, val)
         bad.append(c)
+    c = synth.config_burgers_small()
+    c.projection, c.precision = 1, 1          # no mixed-precision LSPG form
+    bad.append(c)
     for c in bad:
         cfg = g.make_config(c)
         ctx = ctypes.c_void_p()
@@ -86,7 +91,7 @@ def test_invalid_batches_rejected(lib):
         return rc, out.value
 
     for field, val in [("precision", 0), ("problem", 1), ("n_s", 4), ("r", 65), ("n_cells", 128),
-                       ("z", 0)]:
+                       ("z", 0), ("projection", 1)]:
         cfgs = synth.config_batch(2)
         setattr(cfgs[1], field, val)
         rc, out = init(cfgs)

@@ -377,3 +377,57 @@ def test_offline_pod_matches_batch_svd(g, n_cells):
     P = st["phi"][:, :k]
     assert np.max(np.abs(P.T @ P - np.eye(k))) <= 1e-12
     gpu.close()
+
+
+# ------------------------------------------------------------------- LSPG ---
+
+@pytest.mark.parametrize("n_cells,n_steps", [(512, 1000), (2053, 300)])
+def test_lspg_trajectory_against_oracle(g, n_cells, n_steps):
+    """Algorithm 1 with the LSPG step (Eq. lspg_minimization, test basis of Eq.
+    lspg_test_basis_be; Gauss-Newton in FP64) against the oracle's
+    Gauss-Newton: q~ within 1e-10 at every event, and different from the
+    Galerkin trajectory."""
+    cfg = synth.config_burgers_small()
+    cfg.n_cells, cfg.projection = n_cells, 1
+    q0 = synth.initial_state(cfg)
+    ref = orom.AdaptiveROM(cfg, q0)
+    gpu = g.AdaptiveROM(cfg, q0)
+    worst = 0.0
+    for _ in range(n_steps // cfg.z):
+        for _ in range(cfg.z):
+            ref.step()
+        gpu.step(cfg.z)
+        worst = max(worst, rel(gpu.q_tilde(), ref.lifted()))
+    gal_cfg = synth.config_burgers_small()
+    gal_cfg.n_cells = n_cells
+    gal = g.AdaptiveROM(gal_cfg, q0)
+    gal.step(n_steps)
+    diff = rel(gal.q_tilde(), gpu.q_tilde())
+    print(f"LSPG N={n_cells}: worst error {worst:.2e}; LSPG vs Galerkin {diff:.2e}; "
+          f"Gauss-Newton iterations {gpu.info()['rom_newton_iters']}")
+    assert worst <= 1e-10, worst
+    assert diff > 1e-9
+    gal.close()
+    gpu.close()
+
+
+def test_hyper_reduced_lspg_follows_the_oracle(g):
+    """projection = LSPG with n_s > 0: the GPU runs the DEIM-Galerkin step,
+    whose root minimises the hyper-reduced LSPG objective (Eq.
+    hyperreduced_lspg_stationarity with the DEIM basis = Phi); the oracle runs
+    the literal hyper-reduced Gauss-Newton. Same trajectory within 1e-10."""
+    cfg = synth.config_burgers_hyper()
+    cfg.n_cells, cfg.projection = 2048, 1
+    q0 = synth.initial_state(cfg)
+    ref = orom.AdaptiveROM(cfg, q0)
+    gpu = g.AdaptiveROM(cfg, q0)
+    adopt_if_near_tie(ref, gpu)
+    worst = 0.0
+    for _ in range(100 // cfg.z):
+        for _ in range(cfg.z):
+            ref.step()
+        gpu.step(cfg.z)
+        adopt_if_near_tie(ref, gpu)
+        worst = max(worst, rel(gpu.q_tilde(), ref.lifted()))
+    assert worst <= 1e-10, worst
+    gpu.close()
