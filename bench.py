@@ -352,6 +352,62 @@ def timed_adjoint(g):
         return {"error": f"{type(exc).__name__}: {exc}"}
 
 
+def timed_paper_sweep(g):
+    """The paper's Burgers setting (Gaussian pulse, N = 1000, dt = 1e-3,
+    r = w_init = 4) for z in {5, 10, 25, 50} x lambda in {1e-7 ... 1}: 24 ROMs in
+    one batch. Device time of the 496 online steps (one call on a capturable
+    stream), then, in a second untimed pass, the mean ROM error against the
+    fine FOM over the horizon and, per instance, the error of the correction
+    signal (the coarse FOM state of the last event) next to the ROM error at
+    that time (the paper's study of the correction signal)."""
+    import torch
+    try:
+        cfgs = synth.config_paper_burgers_sweep()
+        q0 = synth.initial_state(cfgs[0])
+        n_on, w = cfgs[0].n_online, cfgs[0].w_init
+        fom = [q0]
+        qa = torch.tensor(q0, device="cuda", dtype=torch.float64)
+        qb = torch.empty_like(qa)
+        for _ in range(w + n_on):
+            g.fom_step_dev(0, 1000, 0.01, 1.4, 1e-3, 1e-12, 20, qa.data_ptr(), qb.data_ptr())
+            qa, qb = qb, qa
+            fom.append(qa.cpu().numpy())
+        s = torch.cuda.Stream()
+        b = g.Batch(cfgs, [q0] * len(cfgs), stream=s.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        b.step(n_on)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        b.close()
+        b = g.Batch(cfgs, [q0] * len(cfgs))
+        mean = np.zeros(len(cfgs))
+        stride = 16
+        for j in range(n_on // stride):
+            b.step(stride)
+            qf = fom[w + (j + 1) * stride]
+            for i in range(len(cfgs)):
+                mean[i] += np.linalg.norm(b.q_tilde(i) - qf) / np.linalg.norm(qf) / (n_on // stride)
+        table, signal = {}, {}
+        for i, c in enumerate(cfgs):
+            st = b.state(i, y_corr=True)
+            n_ev = w + (n_on // c.z) * c.z            # time level of the last correction snapshot
+            qe = fom[n_ev]
+            table.setdefault(str(c.z), {})[f"{c.lam:g}"] = mean[i]
+            signal.setdefault(str(c.z), {})[f"{c.lam:g}"] = {
+                "signal_error": float(np.linalg.norm(st["y_corr"] - qe) / np.linalg.norm(qe))}
+        b.close()
+        best = {z: min(row, key=row.get) for z, row in table.items()}
+        return {"instances": len(cfgs), "steps": n_on, "device_ms": ms,
+                "value": len(cfgs) * n_on / (ms / 1e3), "unit": "ROM-steps/s",
+                "mean_rom_error": table, "best_lambda_by_z": best, "correction_signal": signal,
+                "note": "mixed form (FP32 basis), plain Galerkin; the paper's ROM is LSPG-QDEIM"}
+    except Exception as exc:
+        return {"error": f"{type(exc).__name__}: {exc}"}
+
+
 # DRAM traffic of one launch of the batched reduced-step kernel (5 steps) from
 # one ncu capture of the 256-instance workload (summarised under profiles/);
 # reported only while csrc/batch.cu is unchanged.
@@ -540,6 +596,7 @@ def main():
         lspg.projection = 1
         forms["lspg_burgers_n512_r10_z10_fp64"] = timed_single(g, lspg, 2000)
         forms["adjoint"] = timed_adjoint(g)
+        forms["paper_burgers_sweep"] = timed_paper_sweep(g)
 
     # roofline of the dominant kernel (largest device time in the timed region)
     dom = max(prof, key=lambda p: prof[p]["ms"])

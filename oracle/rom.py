@@ -22,6 +22,9 @@ passage of the paper:
                      cells with the largest squared forward difference of the
                      correction snapshot, skipping cells already chosen.
 * ``isvd_update``    Algorithm 2 / Eqs. isvd_residual ... isvd_truncation.
+* ``windowed_svd_update``, ``direct_update``  the comparison rules of App. A
+                     (Eqs. wsvd_window_matrix, wsvd_update; direct_optimization,
+                     direct_update) on the window of correction snapshots.
 * ``AdaptiveROM``    Algorithm 1.
 
 Readings where the paper is silent: see the module-level constants and the
@@ -336,6 +339,45 @@ def isvd_update(Phi, sigma, yhat, lam, r, return_core=False):
 
 
 # ----------------------------------------------------------------------------
+# comparison update rules (App. A): windowed SVD and the Direct method
+# ----------------------------------------------------------------------------
+
+def windowed_svd_update(Y, r):
+    """Eqs. wsvd_window_matrix and wsvd_update: the leading r left singular
+    vectors (and values) of the window of preprocessed correction snapshots
+    Y (N x w), by the thin SVD, with the same numerical-rank truncation and
+    sign convention as the POD."""
+    U, s, _ = np.linalg.svd(Y, full_matrices=False)
+    keep = min(r, U.shape[1])
+    Phi = np.zeros((Y.shape[0], r))
+    sig = np.zeros(r)
+    P, sk = drop_null_directions(sign_normalise(U[:, :keep]), s[:keep])
+    Phi[:, :keep], sig[:keep] = P, sk
+    return Phi, sig
+
+
+def direct_update(Phi, Y, r):
+    """Eqs. direct_optimization and direct_update: Phi_new = Y (Phi^+ Y)^+ for
+    the window Y (N x w), the pseudo-inverses cut at the numerical-rank
+    tolerance. Reading: the update fixes a subspace, and the ROM's projections
+    assume an orthonormal basis, so the returned basis is an orthonormal basis
+    of span(Y (Phi^+ Y)^+) (its dominant left singular vectors, sign convention
+    as the POD's); its 'singular values' are those of Phi^+ Y, which set its
+    rank."""
+    C = np.linalg.pinv(Phi, rcond=RANK_TOL) @ Y
+    sC = np.linalg.svd(C, compute_uv=False)
+    rank = int(np.count_nonzero(sC > RANK_TOL * sC[0])) if sC.size and sC[0] > 0 else 0
+    X = Y @ np.linalg.pinv(C, rcond=RANK_TOL)
+    U, _, _ = np.linalg.svd(X, full_matrices=False)
+    k = min(rank, r)
+    Phi_new = np.zeros((Y.shape[0], r))
+    Phi_new[:, :k] = sign_normalise(U[:, :k])
+    sig = np.zeros(r)
+    sig[:k] = sC[:k]
+    return Phi_new, sig
+
+
+# ----------------------------------------------------------------------------
 # Algorithm 1
 # ----------------------------------------------------------------------------
 
@@ -368,6 +410,15 @@ class AdaptiveROM:
         self.events = 0
         self.newton_iters = []
         self.min_gap = np.inf
+        # the correction-snapshot window of the comparison update rules,
+        # initialised with the last w training snapshots (App. A)
+        self.rule = getattr(cfg, "update_rule", 0)
+        self.window = None
+        if self.rule in (1, 2):
+            w = cfg.window
+            cols = [self.d * (Q_train[:, j] - self.q_ref) for j in range(Q_train.shape[1] - w,
+                                                                         Q_train.shape[1])]
+            self.window = np.stack(cols, axis=1)
 
     # -- pieces --------------------------------------------------------------
     def coarse_step(self, y):
@@ -399,10 +450,18 @@ class AdaptiveROM:
         c = self.cfg
         self.y_corr = self.coarse_step(self.y_corr)
         yhat = self.d * (self.y_corr - self.q_ref)
-        Phi_new, sigma_new, _, _, s_all = isvd_update(self.Phi, self.sigma, yhat, c.lam, c.r,
-                                                      return_core=True)
-        if s_all.shape[0] > c.r and s_all[0] > 0:
-            self.min_gap = min(self.min_gap, (s_all[c.r - 1] - s_all[c.r]) / s_all[0])
+        if self.rule in (1, 2):
+            # drop the oldest snapshot, append the new one
+            self.window = np.concatenate([self.window[:, 1:], yhat[:, None]], axis=1)
+            if self.rule == 1:
+                Phi_new, sigma_new = windowed_svd_update(self.window, c.r)
+            else:
+                Phi_new, sigma_new = direct_update(self.Phi, self.window, c.r)
+        else:
+            Phi_new, sigma_new, _, _, s_all = isvd_update(self.Phi, self.sigma, yhat, c.lam, c.r,
+                                                          return_core=True)
+            if s_all.shape[0] > c.r and s_all[0] > 0:
+                self.min_gap = min(self.min_gap, (s_all[c.r - 1] - s_all[c.r]) / s_all[0])
         self.Phi, self.sigma = Phi_new, sigma_new
         if c.n_s > 0:
             self._refresh_sampling()

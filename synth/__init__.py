@@ -61,6 +61,13 @@ def burgers_ic(n_cells: int, seed: int, amplitude: float = 0.5) -> np.ndarray:
     return 1.0 + amplitude * np.sin(TWO_PI * x) + 0.1 * mode_sum(n_cells, seed)
 
 
+def gaussian_ic(n_cells: int, width: float = 0.1) -> np.ndarray:
+    """u0 = exp(-((x - 1/2) / width)^2 / 2): the Gaussian pulse of the paper's
+    Burgers experiments (Sec. 5.1, L = 1, width 0.1), at the cell centres."""
+    x = cell_centres(n_cells)
+    return np.exp(-0.5 * ((x - 0.5) / width) ** 2)
+
+
 def burgers_ic_amplitude_direction(n_cells: int) -> np.ndarray:
     """d u0 / d A = sin(2 pi x): the direction of the amplitude parameter."""
     return np.sin(TWO_PI * cell_centres(n_cells))
@@ -118,6 +125,9 @@ class RomConfig:
     n_online: int = 2000      # online steps after the training window
     precision: int = 0        # 0: FP64, 1: mixed FP32
     projection: int = 0       # 0: Galerkin, 1: least-squares Petrov-Galerkin
+    ic: str = "fourier"       # "fourier": the seeded family; "gaussian": the paper's pulse
+    update_rule: int = 0      # 0: iSVD (Algorithm 2); 1: windowed SVD; 2: Direct (App. A)
+    window: int = 0           # snapshots in the window of rules 1 and 2
     seed: int = 0
     amplitude: float = 0.5
 
@@ -191,6 +201,21 @@ def config_batch(count: int = 256, seed0: int = 1000, n_online: int = 2000):
     return out
 
 
+PAPER_SWEEP_Z = (5, 10, 25, 50)
+PAPER_SWEEP_LAMBDA = (1e-7, 0.1, 0.25, 0.5, 0.75, 1.0)
+
+
+def config_paper_burgers_sweep(precision: int = 1):
+    """The paper's Burgers setting (Sec. 5.1): Gaussian pulse, N = 1000 cells,
+    nu = 0.01, dt = 1e-3, 500 steps in all (w_init = 4 training steps, 496
+    online), r = w_init = 4, for every adaptation interval z in {5, 10, 25, 50}
+    and forgetting factor lambda in {1e-7, 0.1, 0.25, 0.5, 0.75, 1} (the
+    batched engine runs the mixed form, plain Galerkin)."""
+    return [RomConfig(problem=BURGERS, n_cells=1000, r=4, n_s=0, w_init=4, z=z, dt=1e-3, nu=0.01,
+                      lam=lam, n_online=496, ic="gaussian", precision=precision)
+            for z in PAPER_SWEEP_Z for lam in PAPER_SWEEP_LAMBDA]
+
+
 def config_adjoint() -> RomConfig:
     """Burgers N=65536, r=64, nu=5e-3, z=10, lambda=0.1, 1000 steps (terminal misfit)."""
     return RomConfig(problem=BURGERS, n_cells=65536, r=64, n_s=0, w_init=100, z=10,
@@ -199,6 +224,8 @@ def config_adjoint() -> RomConfig:
 
 def initial_state(cfg: RomConfig) -> np.ndarray:
     """The seeded initial state q0 of a configuration."""
+    if cfg.problem == BURGERS and cfg.ic == "gaussian":
+        return gaussian_ic(cfg.n_cells)
     if cfg.problem == BURGERS:
         return burgers_ic(cfg.n_cells, cfg.seed, cfg.amplitude)
     return sod_conserved_ic(cfg.n_cells, cfg.seed, cfg.gamma)

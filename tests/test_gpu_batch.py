@@ -219,3 +219,42 @@ def test_batch_graph_replay_matches_direct_launches(g):
         assert bg.state(i)["step"] == bd.state(i)["step"] == 143
     bg.close()
     bd.close()
+
+
+def test_paper_burgers_sweep_as_one_batch(g):
+    """The paper's Burgers setting (Gaussian pulse, N = 1000, dt = 1e-3,
+    r = w_init = 4) for all 24 pairs of z in {5, 10, 25, 50} and lambda in
+    {1e-7 ... 1} as one batch, 496 online steps. Three instances against their
+    oracles (1e-5), and the paper's finding on the forgetting factor at z = 10
+    (Sec. 5.1: lambda = 0.1 and 0.25 best, 0.75 and 1 distinctly worse), with
+    the ROM error measured against the fine FOM (advanced on the GPU)."""
+    cfgs = synth.config_paper_burgers_sweep()
+    q0 = synth.initial_state(cfgs[0])
+    b = g.Batch(cfgs, [q0] * len(cfgs))
+    qa = torch.tensor(q0, device="cuda", dtype=torch.float64)
+    qb = torch.empty_like(qa)
+    for _ in range(cfgs[0].w_init):
+        g.fom_step_dev(0, 1000, 0.01, 1.4, 1e-3, 1e-12, 20, qa.data_ptr(), qb.data_ptr())
+        qa, qb = qb, qa
+    eps = np.zeros(len(cfgs))
+    for _ in range(cfgs[0].n_online):
+        b.step(1)
+        g.fom_step_dev(0, 1000, 0.01, 1.4, 1e-3, 1e-12, 20, qa.data_ptr(), qb.data_ptr())
+        qa, qb = qb, qa
+        qf = qa.cpu().numpy()
+        for i in range(len(cfgs)):
+            eps[i] += rel(b.q_tilde(i), qf) / cfgs[0].n_online
+    table = {(c.z, c.lam): e for c, e in zip(cfgs, eps)}
+    for z in synth.PAPER_SWEEP_Z:
+        print(f"z={z}: " + "  ".join(f"lam={lam:g}: {table[(z, lam)]:.2e}" for lam in synth.PAPER_SWEEP_LAMBDA))
+    picks = [1, 8, 19]
+    refs, worst = run_oracles([cfgs[i] for i in picks], [q0] * 3, 100, 100)
+    b2 = g.Batch([cfgs[i] for i in picks], [q0] * 3)
+    b2.step(100)
+    for j, ref in enumerate(refs):
+        assert rel(b2.q_tilde(j), ref.lifted()) <= 1e-5, j
+    b2.close()
+    b.close()
+    best = min(table[(10, 0.1)], table[(10, 0.25)])
+    assert best < table[(10, 0.75)] < table[(10, 1.0)]
+    assert table[(50, 0.1)] > table[(10, 0.1)]

@@ -476,3 +476,78 @@ def test_lspg_adaptive_rom_runs_and_tracks_the_fom():
             q = fv.be_step(q, c.dt, 0, c.nu)
         res[proj] = rom.relative_error(qt, q)
     assert res[1] < 5 * res[0] + 1e-6, res
+
+
+# ------------------------------------------------- comparison update rules ---
+
+def test_windowed_svd_equals_the_rank_growing_isvd_of_the_window():
+    """Eq. wsvd_update by LAPACK against the same window fed column by column
+    through the iSVD with lambda = 1 and no truncation (Algorithm 2 in its
+    rank-growing mode reproduces the thin SVD of the concatenated columns):
+    same singular values and subspace."""
+    rng = np.random.default_rng(12)
+    n, w, r = 80, 12, 5
+    Y = low_rank_stream(n, 9, w, seed=13) + 1e-3 * rng.standard_normal((n, w))
+    Phi_w, s_w = rom.windowed_svd_update(Y, r)
+    Phi, s = rom.pod(Y[:, :1], 1)
+    for j in range(1, w):
+        Phi, s = rom.isvd_update(Phi, s, Y[:, j], 1.0, w)
+    assert np.allclose(s_w, s[:r], rtol=1e-10)
+    assert principal_angle_sin(Phi_w, Phi[:, :r]) < 1e-8
+
+
+def test_direct_update_minimises_its_objective_and_keeps_a_fitted_span():
+    """Eq. direct_optimization: X = Y (Phi^+ Y)^+ minimises |X Phi^+ Y - Y|_F,
+    so random perturbations of X never lower it; and a window inside
+    span(Phi) of full rank r leaves that span unchanged."""
+    rng = np.random.default_rng(21)
+    n, w, r = 60, 8, 4
+    Phi = synth.random_orthonormal(n, r, 22)
+    Y = rng.standard_normal((n, w))
+    C = Phi.T @ Y
+    X = Y @ np.linalg.pinv(C)
+    f0 = np.linalg.norm(X @ C - Y)
+    for _ in range(20):
+        Xp = X + 1e-3 * rng.standard_normal(X.shape)
+        assert np.linalg.norm(Xp @ C - Y) >= f0
+    Yin = Phi @ rng.standard_normal((r, w))
+    Phi_new, s = rom.direct_update(Phi, Yin, r)
+    assert np.count_nonzero(s) == r
+    assert principal_angle_sin(Phi_new, Phi) < 1e-12
+    assert np.max(np.abs(Phi_new.T @ Phi_new - np.eye(r))) < 1e-13
+
+
+def test_window_of_the_comparison_rules_holds_the_last_snapshots():
+    """App. A: the window starts as the last w training snapshots and at every
+    event drops the oldest and appends the new preprocessed correction
+    snapshot."""
+    cfg = synth.config_burgers_small()
+    cfg.n_cells, cfg.w_init, cfg.r, cfg.z = 128, 20, 4, 5
+    cfg.update_rule, cfg.window = 2, 6
+    q0 = synth.initial_state(cfg)
+    m = rom.AdaptiveROM(cfg, q0)
+    expect = [m.d * (m.Q_train[:, j] - m.q_ref) for j in range(14, 20)]
+    assert np.array_equal(m.window, np.stack(expect, axis=1))
+    snaps = []
+    for _ in range(3 * cfg.z):
+        m.step()
+        if m.is_event(m.n - 1):
+            snaps.append(m.d * (m.y_corr - m.q_ref))
+    expect = expect[3:] + snaps
+    assert np.array_equal(m.window, np.stack(expect, axis=1))
+
+
+@pytest.mark.parametrize("rule", [1, 2])
+def test_comparison_rules_track_the_fom(rule):
+    """Algorithm 1 with the windowed-SVD and Direct updates stays close to the
+    fine FOM over 300 steps (history-aware rules, App. A)."""
+    cfg = synth.config_burgers_small()
+    cfg.n_cells, cfg.n_online, cfg.r = 256, 300, 6
+    cfg.update_rule, cfg.window = rule, 16
+    q0 = synth.initial_state(cfg)
+    m = rom.AdaptiveROM(cfg, q0)
+    q = m.Q_train[:, -1]
+    for _ in range(cfg.n_online):
+        qt = m.step()
+        q = fv.be_step(q, cfg.dt, 0, cfg.nu)
+    assert rom.relative_error(qt, q) < 1e-2
