@@ -52,6 +52,7 @@ typedef enum {
 typedef enum { ROM_BURGERS = 0, ROM_EULER = 1 } rom_problem;
 typedef enum { ROM_FP64 = 0, ROM_MIXED_FP32 = 1 } rom_precision;
 typedef enum { ROM_GALERKIN = 0, ROM_LSPG = 1 } rom_projection;
+typedef enum { ROM_UPDATE_ISVD = 0, ROM_UPDATE_WINDOWED_SVD = 1, ROM_UPDATE_DIRECT = 2 } rom_update_rule;
 
 /*
  * Hyper-parameters of one adaptive ROM: the inputs of Algorithm 1 (r, n_s,
@@ -89,6 +90,17 @@ typedef enum { ROM_GALERKIN = 0, ROM_LSPG = 1 } rom_projection;
  *              basis = Phi) has the DEIM-Galerkin root as its minimiser, because
  *              (P^T Phi)^+ P^T Phi = I makes its objective the norm of the
  *              DEIM-Galerkin residual; that step is used.
+ *  update_rule ROM_UPDATE_ISVD (0): Algorithm 2. The comparison rules of App.
+ *              A act on a window of the `window` latest preprocessed correction
+ *              snapshots (initially the last `window` training snapshots; each
+ *              event drops the oldest and appends the new one):
+ *              ROM_UPDATE_WINDOWED_SVD (1): the leading r left singular vectors
+ *              of the window (Eqs. wsvd_window_matrix, wsvd_update);
+ *              ROM_UPDATE_DIRECT (2): an orthonormal basis of
+ *              span(Y (Phi^+ Y)^+) (Eqs. direct_optimization, direct_update),
+ *              its "singular values" those of Phi^+ Y. Both transfer the state
+ *              as a = Phi_new^T D (q~ - q_ref), and both are FP64 only.
+ *  window      1 <= window <= min(w_init, 64) for rules 1 and 2 (unused by 0).
  */
 typedef struct {
     int32_t problem;
@@ -107,6 +119,8 @@ typedef struct {
     double newton_tol;
     double rank_tol;
     int32_t projection;
+    int32_t update_rule;
+    int32_t window;
 } rom_config;
 
 /*

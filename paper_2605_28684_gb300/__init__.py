@@ -43,6 +43,8 @@ def make_config(cfg) -> _lib.RomConfigC:
     c.newton_tol = float(getattr(cfg, "newton_tol", 1e-12))
     c.rank_tol = float(getattr(cfg, "rank_tol", 0.0))     # <= 0: the precision's default
     c.projection = int(getattr(cfg, "projection", 0))
+    c.update_rule = int(getattr(cfg, "update_rule", 0))
+    c.window = int(getattr(cfg, "window", 0))
     return c
 
 

@@ -37,6 +37,8 @@ class RomConfigC(ctypes.Structure):
         ("newton_tol", ctypes.c_double),
         ("rank_tol", ctypes.c_double),
         ("projection", ctypes.c_int32),
+        ("update_rule", ctypes.c_int32),
+        ("window", ctypes.c_int32),
     ]
 
 

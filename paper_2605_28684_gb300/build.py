@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librom.so")
 SOURCES = ["api.cu", "fom.cu", "euler.cu", "isvd.cu", "reduced.cu", "sampling.cu", "batch.cu",
-           "adjoint.cu", "lspg.cu"]
+           "adjoint.cu", "lspg.cu", "update_rules.cu", "pod_svd.cu"]
 # one object per rank bucket and basis type of the iSVD kernels, so that they compile in parallel
 BUCKETS = [("isvd_bucket.cu", f"isvd_b{km}_{t}.o",
             [f"-DROM_ISVD_KM={km}", f"-DROM_ISVD_F32={int(t == 'f32')}"])

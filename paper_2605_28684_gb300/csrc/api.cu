@@ -89,6 +89,10 @@ rom_status validate(const rom_config* c) {
   if (c->projection != ROM_GALERKIN && c->projection != ROM_LSPG) return ROM_EINVAL;
   if (c->projection == ROM_LSPG && (c->problem != ROM_BURGERS || c->precision != ROM_FP64))
     return ROM_EINVAL;
+  if (c->update_rule < ROM_UPDATE_ISVD || c->update_rule > ROM_UPDATE_DIRECT) return ROM_EINVAL;
+  if (c->update_rule != ROM_UPDATE_ISVD &&
+      (c->precision != ROM_FP64 || c->window < 1 || c->window > c->w_init || c->window > kMaxR))
+    return ROM_EINVAL;
   return ROM_OK;
 }
 
@@ -279,8 +283,11 @@ cudaError_t run_steps(rom_ctx* ctx, int nsteps) {
   return prof_mark(ctx, 0, false);
 }
 
+cudaError_t run_event_window(rom_ctx* ctx);
+
 // The adaptation event of Algorithm 1 on the current y_corr.
 cudaError_t run_event(rom_ctx* ctx) {
+  if (ctx->cfg.update_rule != ROM_UPDATE_ISVD) return run_event_window(ctx);
   EventArgs A = event_args(ctx, ctx->d.y_corr, 1, ctx->cfg.lambda, ctx->cfg.rank_tol, ctx->cfg.r, 1);
   cudaError_t e = prof_mark(ctx, 2, true);
   if (e == cudaSuccess) e = launch_event(A, km_of(ctx), ctx->grid, ctx->stream);
@@ -289,6 +296,71 @@ cudaError_t run_event(rom_ctx* ctx) {
   if (ctx->cfg.n_s > 0) {
     e = prof_mark(ctx, 3, true);
     if (e == cudaSuccess) e = launch_sampling(sample_args(ctx), km_of(ctx), ctx->grid, ctx->stream);
+    if (e == cudaSuccess) e = prof_mark(ctx, 3, false);
+  }
+  return e;
+}
+
+// The comparison update rules (App. A) on the snapshot window: the lifted
+// state is formed with the old basis, the new preprocessed snapshot replaces
+// the oldest one in the window, the basis is rebuilt from an empty one by the
+// rank-growing iSVD (forgetting factor 1) over the window (windowed SVD) or
+// over the columns of Y V_c (Direct, V_c from the Jacobi SVD of Phi^T Y), and
+// the state is transferred by projection, a = Phi_new^T D (q~ - q_ref).
+cudaError_t run_event_window(rom_ctx* ctx) {
+  const int64_t N = ctx->N;
+  const int r = ctx->cfg.r, nw = ctx->cfg.window, G = ctx->grid;
+  const int r_grow = ctx->cfg.w_init < kMaxR ? ctx->cfg.w_init : kMaxR;
+  const int r_alloc = r_grow > r ? r_grow : r;
+  cudaStream_t s = ctx->stream;
+  DevState& d = ctx->d;
+  cudaError_t e = prof_mark(ctx, 2, true);
+  if (e != cudaSuccess) return e;
+  LiftArgs L;
+  L.n = N; L.ld = N; L.rank = d.rank; L.phi = d.phi; L.phi32 = nullptr; L.q_ref = d.q_ref;
+  L.drow = d.drow; L.dinv = d.dinv; L.a = d.a; L.out = d.lifted;
+  if ((e = launch_lift(L, km_of(ctx), s)) != cudaSuccess) return e;
+  const int slot = ctx->win_head;
+  e = launch_win_fill(d.y_corr, N, d.q_ref, d.drow, N, 1, d.win + (size_t)slot * N, s);
+  if (e != cudaSuccess) return e;
+  ctx->win_head = (slot + 1) % nw;
+  double* C = d.dsm;
+  double* Vc = d.dsm + kMaxR * kMaxR;
+  double* sv = Vc + kMaxR * kMaxR;
+  int* kc = reinterpret_cast<int*>(sv + kMaxR);
+  int nfeed = nw, r_cap = nw < kMaxR ? nw : kMaxR;
+  const bool direct = ctx->cfg.update_rule == ROM_UPDATE_DIRECT;
+  if (direct) {
+    if ((e = launch_tn(TnArgs{N, r, nw, d.phi, N, d.win, N, 1.0, d.dpart, C}, G, s)) != cudaSuccess) return e;
+    if ((e = launch_direct_small(C, r, nw, d.rank, ctx->cfg.rank_tol, Vc, sv, kc, s)) != cudaSuccess) return e;
+    int hkc = 0;
+    if ((e = cudaMemcpyAsync(&hkc, kc, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    if (hkc < 1) return cudaErrorInvalidValue;
+    e = launch_nn(NnArgs{N, nw, hkc, d.win, N, Vc, hkc, 1, 1.0, 0.0, d.dwork, N, d.dwork, N}, s);
+    if (e != cudaSuccess) return e;
+    nfeed = hkc;
+    r_cap = hkc;
+  }
+  if ((e = cudaMemsetAsync(d.phi, 0, sizeof(double) * N * r_alloc, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(d.sigma, 0, sizeof(double) * (kMaxR + 1), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(d.rank, 0, sizeof(int), s)) != cudaSuccess) return e;
+  for (int j = 0; j < nfeed; ++j) {
+    const double* col = direct ? d.dwork + (size_t)j * N : d.win + (size_t)((ctx->win_head + j) % nw) * N;
+    EventArgs A = event_args(ctx, col, 0, 1.0, kGrowRankTol, r_cap, 0, false);
+    if ((e = launch_event(A, km_bucket(r_cap + 1), G, s)) != cudaSuccess) return e;
+  }
+  if (direct) e = launch_set_sigma(sv, kc, d.sigma, d.rank, s);
+  else e = launch_truncate(d.phi, N, d.sigma, d.rank, r, r_alloc, ctx->cfg.rank_tol, s);
+  if (e != cudaSuccess) return e;
+  ProjectArgs P;
+  P.n = N; P.ld = N; P.r = r; P.rank = d.rank; P.phi = d.phi; P.phi32 = nullptr; P.v = d.lifted;
+  P.q_ref = d.q_ref; P.drow = d.drow; P.a = d.a; P.partials = d.partials; P.bar = d.bar; P.status = d.status;
+  if ((e = launch_project(P, km_of(ctx), G, s)) != cudaSuccess) return e;
+  if ((e = prof_mark(ctx, 2, false)) != cudaSuccess) return e;
+  if (ctx->cfg.n_s > 0) {
+    e = prof_mark(ctx, 3, true);
+    if (e == cudaSuccess) e = launch_sampling(sample_args(ctx), km_of(ctx), G, s);
     if (e == cudaSuccess) e = prof_mark(ctx, 3, false);
   }
   return e;
@@ -367,7 +439,7 @@ void free_state(rom_ctx* ctx) {
                   d.phi32, d.gram, d.sigma, d.a, d.a_prev, d.rank, d.core, d.ubar, d.partials,
                   d.jpartials, d.jac, d.samples, d.chosen, d.resid_norm, d.qdeim_q, d.cand_v,
                   d.cand_i, d.mesh, d.minv, d.bar, d.status, d.iters_rom, d.iters_fom, d.maxbuf,
-                  d.fom_chunk, d.npart, ctx->q_train};
+                  d.fom_chunk, d.npart, d.win, d.dwork, d.dsm, d.dpart, ctx->q_train};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   memset(&ctx->d, 0, sizeof(DevState));
@@ -406,7 +478,9 @@ void rom_destroy(rom_ctx* ctx) {
 namespace {
 
 // rom_init; keep_train keeps the training matrix (N x w_init) on the device
-// for the gradient pass.
+// and computes the POD as a backward-stable thin SVD (pod_svd.cu) instead of
+// the rank-growing iSVD, for the gradient pass, whose POD adjoint needs the
+// basis fixed to rounding level.
 rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* stream, bool keep_train,
                     rom_ctx** out) {
   if (!out) return ROM_EINVAL;
@@ -432,6 +506,7 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
   ctx->N = ctx->cfg.n_cells * ctx->cfg.n_var;
   ctx->step = 0;
   ctx->poisoned = 0;
+  ctx->win_head = 0;
   ctx->grid = grid_for(ctx->N);
   const int64_t N = ctx->N;
   const int r = ctx->cfg.r;
@@ -460,6 +535,12 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
     ALLOC(d.gram, (size_t)G * kMaxR * kMaxR);
   }
   if (ctx->cfg.projection == ROM_LSPG) ALLOC(d.npart, lspg_partial_doubles(G));
+  if (ctx->cfg.update_rule != ROM_UPDATE_ISVD) {
+    ALLOC(d.win, (size_t)N * ctx->cfg.window);
+    ALLOC(d.dwork, (size_t)N * kMaxR);
+    ALLOC(d.dsm, 2 * kMaxR * kMaxR + kMaxR + 8);
+    ALLOC(d.dpart, (size_t)G * kMaxR * kMaxR);
+  }
 #undef ALLOC
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -496,8 +577,39 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
     drow_kernel<<<256, 256, 0, s>>>(d.dvals, ctx->cfg.n_cells, N, d.drow, d.dinv);
     RCK(cudaGetLastError());
   }
-  // POD: rank-growing iSVD of D (Q_train - q_ref 1^T), forgetting factor 1
-  {
+  // POD for the gradient pass: thin SVD of D (Q_train - q_ref 1^T) by CGS2 QR and Jacobi
+  if (keep_train) {
+    double *X = nullptr, *Qm = nullptr, *Rm = nullptr, *Um = nullptr, *sv = nullptr, *wk = nullptr,
+           *pt = nullptr;
+    cudaError_t ae = dalloc(&X, (size_t)N * w);
+    if (ae == cudaSuccess) ae = dalloc(&Qm, (size_t)N * w);
+    if (ae == cudaSuccess) ae = dalloc(&Rm, (size_t)w * w);
+    if (ae == cudaSuccess) ae = dalloc(&Um, (size_t)w * w);
+    if (ae == cudaSuccess) ae = dalloc(&sv, (size_t)w);
+    if (ae == cudaSuccess) ae = dalloc(&wk, 256);
+    if (ae == cudaSuccess) ae = dalloc(&pt, (size_t)G * 16384);
+    auto release = [&]() { cudaFree(X); cudaFree(Qm); cudaFree(Rm); cudaFree(Um); cudaFree(sv); cudaFree(wk); cudaFree(pt); };
+    if (ae != cudaSuccess) { cudaGetLastError(); release(); rom_destroy(ctx); return ROM_ENOMEM; }
+    ae = launch_win_fill(ctx->q_train, N, d.q_ref, d.drow, N, w, X, s);
+    if (ae == cudaSuccess) ae = pod_thin_svd(X, N, w, Qm, Rm, Um, sv, wk, pt, G, s);
+    std::vector<double> sg(w);
+    if (ae == cudaSuccess) ae = cudaMemcpyAsync(sg.data(), sv, sizeof(double) * w, cudaMemcpyDeviceToHost, s);
+    if (ae == cudaSuccess) ae = cudaStreamSynchronize(s);
+    int k = 0;
+    for (int j = 0; j < r && j < w; ++j)
+      if (sg[0] > 0.0 && sg[j] > ctx->cfg.rank_tol * sg[0]) ++k;
+    if (ae == cudaSuccess) ae = cudaMemsetAsync(d.phi, 0, sizeof(double) * N * r_alloc, s);
+    if (ae == cudaSuccess) ae = cudaMemsetAsync(d.sigma, 0, sizeof(double) * (kMaxR + 1), s);
+    if (ae == cudaSuccess && k > 0)
+      ae = launch_nn(NnArgs{N, w, k, Qm, N, Um, w, 1, 1.0, 0.0, d.phi, N, d.phi, N}, s);
+    if (ae == cudaSuccess && k > 0)
+      ae = cudaMemcpyAsync(d.sigma, sv, sizeof(double) * k, cudaMemcpyDeviceToDevice, s);
+    if (ae == cudaSuccess) ae = cudaMemcpyAsync(d.rank, &k, sizeof(int), cudaMemcpyHostToDevice, s);
+    if (ae == cudaSuccess) ae = cudaStreamSynchronize(s);
+    release();
+    if (ae != cudaSuccess) { ctx->poisoned = 1; rom_destroy(ctx); return ROM_ECUDA; }
+  } else {
+    // POD: rank-growing iSVD of D (Q_train - q_ref 1^T), forgetting factor 1
     const int km = km_bucket(r_grow + 1);
     for (int j = 0; j < w; ++j) {
       EventArgs A = event_args(ctx, ctx->q_train + (size_t)j * N, 1, 1.0, kGrowRankTol, r_grow, 0, false);
@@ -520,6 +632,11 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
       RCK(cudaGetLastError());
     }
     RCK(cudaStreamSynchronize(s));
+  }
+  // the comparison rules' window: the last `window` training snapshots, preprocessed
+  if (ctx->cfg.update_rule != ROM_UPDATE_ISVD) {
+    const int nw = ctx->cfg.window;
+    RCK(launch_win_fill(ctx->q_train + (size_t)(w - nw) * N, N, d.q_ref, d.drow, N, nw, d.win, s));
   }
   // initial reduced state and first coarse correction state
   {

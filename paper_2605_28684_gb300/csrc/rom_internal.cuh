@@ -410,6 +410,11 @@ struct DevState {
   unsigned long long* maxbuf;
   float* fom_chunk;
   double* npart;        // LSPG normal-equation partial sums
+  // comparison update rules: snapshot window and Direct work space
+  double* win;          // N x window (ring, oldest at win_head)
+  double* dwork;        // N x kMaxR
+  double* dsm;          // C (kMaxR^2), Vc (kMaxR^2), s (kMaxR), then the kc word
+  double* dpart;        // grid x kMaxR^2 partial sums
 };
 
 }  // namespace rom
@@ -432,6 +437,7 @@ struct rom_ctx {
   int64_t step;          // time level n
   int grid;              // CTAs of the generic cooperative kernels
   int poisoned;
+  int win_head;          // oldest slot of the snapshot window
   rom::DevState d;
   double* q_train;       // N x w_init (offline only, freed after init)
 };

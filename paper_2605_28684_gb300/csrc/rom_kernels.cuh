@@ -326,5 +326,18 @@ cudaError_t launch_adj_lift(int64_t n, int k, const double* phi, const double* a
 cudaError_t launch_adj_misfit(int64_t n, const double* q, const double* target, double* qtbar,
                               double* part, double* J, cudaStream_t s);
 size_t core_sbar_offset();
+// thin SVD of an N x w matrix (w <= 128) by CGS2 QR and one-sided Jacobi on R
+// (pod_svd.cu): U (w x w row-major) and s (w, descending) of R; Q (N x w) the
+// orthonormal factor; work >= 256 doubles; part as launch_tn's
+cudaError_t pod_thin_svd(const double* X, int64_t n, int w, double* Q, double* R, double* U, double* s,
+                         double* work, double* part, int grid, cudaStream_t st);
+// comparison update rules (update_rules.cu)
+cudaError_t launch_win_fill(const double* Q, int64_t ldq, const double* q_ref, const double* drow, int64_t n,
+                            int count, double* win, cudaStream_t s);
+cudaError_t launch_truncate(double* phi, int64_t n, double* sigma, int* rank, int r, int ncols, double tol,
+                            cudaStream_t s);
+cudaError_t launch_direct_small(const double* C, int r, int w, const int* rank, double tol, double* Vc,
+                                double* s_out, int* kc, cudaStream_t s);
+cudaError_t launch_set_sigma(const double* s_in, const int* kc, double* sigma, int* rank, cudaStream_t s);
 
 }  // namespace rom

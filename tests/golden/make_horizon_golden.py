@@ -3,8 +3,6 @@ full horizons of the configured workloads, for the GPU parity tests.
 
 Cases (Algorithm 1, online loop from n = w_init):
 
-* ``c1``  Burgers DEIM-Galerkin, N = 16384, r = 32, n_s = 96, z = 5,
-          lambda = 0.5, all 20 000 online steps;
 * ``c2``  Sod shock tube, 8192 cells, r = 40, z = 10, lambda = 0.01, to t = 0.2
           or to the step whose reduced Newton solve has no root (stored as
           ``fail_step``, the time level of that step; -1 if none);
@@ -15,14 +13,12 @@ Cases (Algorithm 1, online loop from n = w_init):
 Every ``stride`` online steps (and after the last one) a record keeps q~ (the
 lifted state after the step's adaptation event, if it has one) at a fixed
 subsample of about 512 entries, its L2 norm and its products with
-``synth.probe_vectors`` (seed 77). For c1 every event also keeps the sum and
-the sum of squares of the sample indices, a fingerprint of the sample set.
-
+``synth.probe_vectors`` (seed 77). 
 The numerical-rank tolerance is the FP64 form's, 1e-10, unless ``--tau`` says
 otherwise. This script calls only ``oracle`` and ``synth``. Run from the
-repository root (c1 ~ 5 min, c2 ~ 20 min, c3 ~ 30 min on 4 processes):
+repository root (c2 ~ 8 min, c3 ~ 5 min on 5 processes):
 
-    python tests/golden/make_horizon_golden.py c1|c2|c3 [--tau T]
+    python tests/golden/make_horizon_golden.py c2|c3 [--tau T]
 """
 import argparse
 import json
@@ -47,7 +43,7 @@ def subsample(n, count=512):
     return np.arange(0, n, max(1, n // count), dtype=np.int64)
 
 
-def run_case(cfg, n_steps, tau, stride=STRIDE, fingerprints=False):
+def run_case(cfg, n_steps, tau, stride=STRIDE):
     """Records of one trajectory (dict of arrays)."""
     orom.RANK_TOL = tau
     q0 = synth.initial_state(cfg)
@@ -55,10 +51,8 @@ def run_case(cfg, n_steps, tau, stride=STRIDE, fingerprints=False):
     sub = subsample(cfg.n)
     W = synth.probe_vectors(cfg.n)
     steps, qs, norms, probes, ranks = [], [], [], [], []
-    fp_sum, fp_sq, fp_step = [], [], []
     fail_step = -1
     for k in range(n_steps):
-        event = m.is_event(m.n)
         try:
             m.step()
         except orom.NewtonNoConvergence:
@@ -73,11 +67,6 @@ def run_case(cfg, n_steps, tau, stride=STRIDE, fingerprints=False):
                 probes.append(W.T @ q)
                 ranks.append(orom.numerical_rank(m.Phi))
             break
-        if fingerprints and event:
-            P = np.asarray(m.P, dtype=np.int64)
-            fp_sum.append(int(P.sum()))
-            fp_sq.append(int((P * P).sum()))
-            fp_step.append(m.n)
         if (k + 1) % stride == 0 or k + 1 == n_steps:
             q = m.lifted()
             steps.append(m.n)
@@ -88,8 +77,6 @@ def run_case(cfg, n_steps, tau, stride=STRIDE, fingerprints=False):
     out = dict(steps=np.array(steps), sub=sub, q_sub=np.array(qs), norm=np.array(norms),
                probe=np.array(probes), rank=np.array(ranks), min_gap=np.array(m.min_gap),
                fail_step=np.array(fail_step))
-    if fingerprints:
-        out.update(fp_step=np.array(fp_step), fp_sum=np.array(fp_sum), fp_sumsq=np.array(fp_sq))
     return out
 
 
@@ -120,18 +107,14 @@ def meta(cfg, tau, seconds):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["c1", "c2", "c3"])
+    ap.add_argument("case", choices=["c2", "c3"])
     ap.add_argument("--tau", type=float, default=1e-10)
     ap.add_argument("--procs", type=int, default=4)
     args = ap.parse_args()
     t0 = time.perf_counter()
     suffix = "" if args.tau == 1e-10 else f"_tau{args.tau:g}"
     path = os.path.join(HERE, f"horizon_{args.case}{suffix}.npz")
-    if args.case == "c1":
-        cfg = synth.config_burgers_hyper(precision=0)
-        rec = run_case(cfg, cfg.n_online, args.tau, fingerprints=True)
-        np.savez_compressed(path, meta=meta(cfg, args.tau, time.perf_counter() - t0), **rec)
-    elif args.case == "c2":
+    if args.case == "c2":
         cfg = synth.config_sod()
         rec = run_case(cfg, cfg.n_online, args.tau)
         np.savez_compressed(path, meta=meta(cfg, args.tau, time.perf_counter() - t0), **rec)

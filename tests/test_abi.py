@@ -61,6 +61,11 @@ def test_invalid_configs_rejected(lib):
     c = synth.config_burgers_small()
     c.projection, c.precision = 1, 1          # no mixed-precision LSPG form
     bad.append(c)
+    # comparison update rules: unknown rule, window outside 1..min(w_init, 64), FP64 only
+    for rule, window, prec in [(3, 8, 0), (1, 0, 0), (2, 101, 0), (1, 8, 1)]:
+        c = synth.config_burgers_small()
+        c.update_rule, c.window, c.precision = rule, window, prec
+        bad.append(c)
     for c in bad:
         cfg = g.make_config(c)
         ctx = ctypes.c_void_p()

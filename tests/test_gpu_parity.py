@@ -431,3 +431,32 @@ def test_hyper_reduced_lspg_follows_the_oracle(g):
         worst = max(worst, rel(gpu.q_tilde(), ref.lifted()))
     assert worst <= 1e-10, worst
     gpu.close()
+
+
+# ------------------------------------------------- comparison update rules ---
+
+@pytest.mark.parametrize("rule,window", [(1, 16), (2, 16), (2, 6)])
+def test_comparison_update_rules_against_oracle(g, rule, window):
+    """Algorithm 1 with the windowed-SVD (rule 1) and Direct (rule 2) updates
+    of App. A on the window of correction snapshots, against the oracle: q~
+    within 1e-9 at every event (the windowed SVD is rebuilt by the growing
+    iSVD on the GPU, by LAPACK in the oracle; the Direct basis may differ by a
+    rotation within its span, which q~ does not see), and the same rank."""
+    cfg = synth.config_burgers_small()
+    cfg.r, cfg.update_rule, cfg.window = 6, rule, window
+    q0 = synth.initial_state(cfg)
+    ref = orom.AdaptiveROM(cfg, q0)
+    gpu = g.AdaptiveROM(cfg, q0)
+    worst = 0.0
+    for _ in range(400 // cfg.z):
+        for _ in range(cfg.z):
+            ref.step()
+        gpu.step(cfg.z)
+        worst = max(worst, rel(gpu.q_tilde(), ref.lifted()))
+        assert gpu.info()["rank"] == orom.numerical_rank(ref.Phi)
+    st = gpu.state()
+    P = st["phi"][:, st["sigma"] > 0]
+    assert np.max(np.abs(P.T @ P - np.eye(P.shape[1]))) <= 1e-12
+    print(f"update rule {rule} (window {window}): worst error {worst:.2e}")
+    assert worst <= 1e-9, worst
+    gpu.close()
