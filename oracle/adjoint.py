@@ -263,8 +263,8 @@ def _online_step(cfg, st, q_ref, d):
 
 
 def _check_cfg(cfg):
-    if cfg.problem != 0 or cfg.n_var != 1 or cfg.n_s != 0:
-        raise ValueError("the gradient oracle covers plain-Galerkin Burgers ROMs only")
+    if cfg.problem != 0 or cfg.n_var != 1 or cfg.n_s != 0 or getattr(cfg, "time_scheme", 0) != 0:
+        raise ValueError("the gradient oracle covers plain backward-Euler Galerkin Burgers ROMs only")
 
 
 def misfit(cfg, n_steps, target):

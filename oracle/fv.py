@@ -17,6 +17,11 @@ Test infrastructure only; see the package docstring.
 * Backward Euler (Eq. be_residual_rom_section / Eq. coarse_fom_backward_euler):
   ``q - q_prev - h f(q) = 0`` solved by Newton from ``q_prev`` with
   ``(I - h J_f) delta = -r``; stop once ``max|delta| <= tol (1 + max|q|)``.
+* Explicit steps (App. D, the RDE solver): the four-stage, third-order
+  strong-stability-preserving Runge-Kutta scheme. The paper names the scheme
+  without its coefficients; this is the one with SSP coefficient 2 (Spiteri
+  and Ruuth, SIAM J. Numer. Anal. 40, 2002): three half steps of forward
+  Euler, an average with the start value, and a last half step.
 """
 from __future__ import annotations
 
@@ -232,3 +237,19 @@ def be_step(q_prev, h, problem, nu=0.0, gamma=1.4, tol=1e-12, max_iter=20,
         if np.max(np.abs(delta)) <= tol * (1.0 + np.max(np.abs(q))):
             return (q, it) if return_iters else q
     raise NewtonNoConvergence(f"BE Newton did not converge in {max_iter} iterations")
+
+
+def ssprk43_step(q, h, rhs):
+    """One step of the four-stage, third-order SSP Runge-Kutta scheme for
+    dq/dt = rhs(q): q1 = q + h/2 rhs(q), q2 = q1 + h/2 rhs(q1),
+    q3 = 2/3 q + 1/3 (q2 + h/2 rhs(q2)), q_new = q3 + h/2 rhs(q3).
+    On dq/dt = lam q it multiplies q by 1 + z + z^2/2 + z^3/6 + z^4/48, z = h lam."""
+    q1 = q + 0.5 * h * rhs(q)
+    q2 = q1 + 0.5 * h * rhs(q1)
+    q3 = (2.0 / 3.0) * q + (1.0 / 3.0) * (q2 + 0.5 * h * rhs(q2))
+    return q3 + 0.5 * h * rhs(q3)
+
+
+def explicit_step(q_prev, h, problem, nu=0.0, gamma=1.4):
+    """One SSPRK(4,3) step of the FOM dq/dt = f(q)."""
+    return ssprk43_step(q_prev, h, lambda u: fom_f(u, problem, nu, gamma))

@@ -50,14 +50,21 @@ class NewtonNoConvergence(RuntimeError):
 # offline pieces
 # ----------------------------------------------------------------------------
 
+def fine_fom_step(q, cfg):
+    """One fine FOM step: backward Euler (Eq. fom_lmm with the BE
+    coefficients, Eq. fom_discrete_solve), or SSPRK(4,3) for the explicit
+    form (time_scheme 1, the RDE solver of App. D)."""
+    if getattr(cfg, "time_scheme", 0) == 1:
+        return fv.explicit_step(q, cfg.dt, cfg.problem, cfg.nu, cfg.gamma)
+    return fv.be_step(q, cfg.dt, cfg.problem, cfg.nu, cfg.gamma, cfg.newton_tol, cfg.newton_max)
+
+
 def fom_trajectory(q0, n_steps, cfg):
-    """Fine backward-Euler FOM states q^1..q^n_steps as columns (Eq. fom_lmm
-    with the BE coefficients, Eq. fom_discrete_solve)."""
+    """Fine FOM states q^1..q^n_steps as columns."""
     out = np.empty((q0.shape[0], n_steps))
     q = q0
     for k in range(n_steps):
-        q = fv.be_step(q, cfg.dt, cfg.problem, cfg.nu, cfg.gamma,
-                       cfg.newton_tol, cfg.newton_max)
+        q = fine_fom_step(q, cfg)
         out[:, k] = q
     return out
 
@@ -164,6 +171,28 @@ def _newton(a_prev, resid, jac, tol, max_iter):
         if np.max(np.abs(delta)) <= tol * (1.0 + np.max(np.abs(a))):
             return a, it
     raise NewtonNoConvergence(f"reduced Newton did not converge in {max_iter} iterations")
+
+
+def galerkin_rhs(a, Phi, q_ref, d, cfg):
+    """da/dt = Phi^T D f(q~(a)) (Eq. galerkin_continuous_rom)."""
+    return Phi.T @ (d * fv.fom_f(lift(a, Phi, q_ref, d), cfg.problem, cfg.nu, cfg.gamma))
+
+
+def hyper_rhs(a, Phi, q_ref, d, P, M, cfg):
+    """da/dt = (P^T Phi)^+ P^T D f(q~(a)) (Eq. deim_galerkin_rom, continuous in
+    time); f on the full lifted state, then sampled."""
+    f = fv.fom_f(lift(a, Phi, q_ref, d), cfg.problem, cfg.nu, cfg.gamma)
+    return M @ (d * f)[P]
+
+
+def explicit_galerkin_step(a_prev, Phi, q_ref, d, cfg, P=None, M=None):
+    """One SSPRK(4,3) step of the Galerkin ROM (hyper-reduced when P is given);
+    returns (a_new, 0): no iterations."""
+    if P is None:
+        rhs = lambda a: galerkin_rhs(a, Phi, q_ref, d, cfg)      # noqa: E731
+    else:
+        rhs = lambda a: hyper_rhs(a, Phi, q_ref, d, P, M, cfg)   # noqa: E731
+    return fv.ssprk43_step(a_prev, cfg.dt, rhs), 0
 
 
 def galerkin_step(a_prev, Phi, q_ref, d, cfg):
@@ -338,6 +367,31 @@ def isvd_update(Phi, sigma, yhat, lam, r, return_core=False):
     return Phi_new, s_new
 
 
+def rank_decision_margin(Phi, sigma, yhat, lam, r):
+    """Diagnostic, not part of the method: how close the two rank decisions of
+    one ``isvd_update`` come to the tolerance, as min |log(x / RANK_TOL)| over
+    x = ||q|| / max(||yhat||, sigma_1) (is the new direction empty?) and
+    x = s_j / s_1 of the kept core singular values (is direction j null?).
+    A small margin means that a rounding-level change can flip the rank."""
+    k = Phi.shape[1]
+    p, q = project_cgs2(Phi, yhat)
+    rho = float(np.linalg.norm(q))
+    scale = max(float(np.linalg.norm(yhat)), float(sigma[0]) if k else 0.0)
+    out = np.inf
+    if scale > 0 and rho > 0:
+        out = abs(np.log(rho / (RANK_TOL * scale)))
+    K = np.zeros((k + 1, k + 1))
+    K[:k, :k] = lam * np.diag(sigma)
+    K[:k, k] = p
+    K[k, k] = rho if rho > RANK_TOL * scale else 0.0
+    sb = np.linalg.svd(K, compute_uv=False)[:min(r, k + 1)]
+    if sb.shape[0] and sb[0] > 0:
+        pos = sb[sb > 0]
+        if pos.shape[0]:
+            out = min(out, float(np.min(np.abs(np.log(pos / (RANK_TOL * sb[0]))))))
+    return out
+
+
 # ----------------------------------------------------------------------------
 # comparison update rules (App. A): windowed SVD and the Direct method
 # ----------------------------------------------------------------------------
@@ -410,6 +464,12 @@ class AdaptiveROM:
         self.events = 0
         self.newton_iters = []
         self.min_gap = np.inf
+        # diagnostic: the closest call of the rank decisions (the POD's and
+        # those of every event)
+        s_pod = np.linalg.svd(Xhat, compute_uv=False)[:cfg.r]
+        pos = s_pod[s_pod > 0]
+        self.min_rank_margin = (float(np.min(np.abs(np.log(pos / (RANK_TOL * s_pod[0])))))
+                                if pos.shape[0] else np.inf)
         # the correction-snapshot window of the comparison update rules,
         # initialised with the last w training snapshots (App. A)
         self.rule = getattr(cfg, "update_rule", 0)
@@ -431,6 +491,10 @@ class AdaptiveROM:
 
     def rom_step(self, a_prev):
         c = self.cfg
+        if getattr(c, "time_scheme", 0) == 1:       # explicit Galerkin (App. D form)
+            if c.n_s > 0:
+                return explicit_galerkin_step(a_prev, self.Phi, self.q_ref, self.d, c, self.P, self.M)
+            return explicit_galerkin_step(a_prev, self.Phi, self.q_ref, self.d, c)
         if getattr(c, "projection", 0) == 1:        # LSPG
             if c.n_s > 0:
                 return hyper_lspg_step(a_prev, self.Phi, self.q_ref, self.d, self.P, self.M, c)
@@ -458,6 +522,8 @@ class AdaptiveROM:
             else:
                 Phi_new, sigma_new = direct_update(self.Phi, self.window, c.r)
         else:
+            self.min_rank_margin = min(self.min_rank_margin,
+                                       rank_decision_margin(self.Phi, self.sigma, yhat, c.lam, c.r))
             Phi_new, sigma_new, _, _, s_all = isvd_update(self.Phi, self.sigma, yhat, c.lam, c.r,
                                                           return_core=True)
             if s_all.shape[0] > c.r and s_all[0] > 0:

@@ -128,6 +128,7 @@ class RomConfig:
     ic: str = "fourier"       # "fourier": the seeded family; "gaussian": the paper's pulse
     update_rule: int = 0      # 0: iSVD (Algorithm 2); 1: windowed SVD; 2: Direct (App. A)
     window: int = 0           # snapshots in the window of rules 1 and 2
+    time_scheme: int = 0      # 0: backward Euler; 1: SSPRK(4,3), explicit (Galerkin only)
     seed: int = 0
     amplitude: float = 0.5
 

@@ -13,7 +13,10 @@ Cases (Algorithm 1, online loop from n = w_init):
 Every ``stride`` online steps (and after the last one) a record keeps q~ (the
 lifted state after the step's adaptation event, if it has one) at a fixed
 subsample of about 512 entries, its L2 norm and its products with
-``synth.probe_vectors`` (seed 77). 
+``synth.probe_vectors`` (seed 77). Each case also keeps ``rank_margin``, the
+closest call of the oracle's rank decisions over the run (the minimum of
+|log(x / tau)| over the quantities x that the rank tolerance tau is compared
+with), which says whether a rounding-level change could flip a rank.
 The numerical-rank tolerance is the FP64 form's, 1e-10, unless ``--tau`` says
 otherwise. This script calls only ``oracle`` and ``synth``. Run from the
 repository root (c2 ~ 8 min, c3 ~ 5 min on 5 processes):
@@ -76,7 +79,7 @@ def run_case(cfg, n_steps, tau, stride=STRIDE):
             ranks.append(orom.numerical_rank(m.Phi))
     out = dict(steps=np.array(steps), sub=sub, q_sub=np.array(qs), norm=np.array(norms),
                probe=np.array(probes), rank=np.array(ranks), min_gap=np.array(m.min_gap),
-               fail_step=np.array(fail_step))
+               rank_margin=np.array(m.min_rank_margin), fail_step=np.array(fail_step))
     return out
 
 
