@@ -272,10 +272,13 @@ def timed_single(g, cfg, n_steps):
         return {"error": f"{type(exc).__name__}: {exc}"}
 
 
-def timed_full_horizon(g, cfg, n_steps, fom_eps=True):
+def timed_full_horizon(g, cfg, n_steps, fom_eps=True, chunk=None):
     """One rom_step over a whole horizon (device time on a side stream and
     wall clock around the call), and the ROM error against the fine FOM
-    (the FOM advanced on the GPU by rom_fom_step_dev over the same steps)."""
+    (the FOM advanced on the GPU by rom_fom_step_dev over the same steps).
+    With ``chunk``, rom_step runs in calls of that many steps and the horizon
+    ends at the first call that fails (a ROM that leaves the physical range):
+    the steps completed before it are timed and reported."""
     import torch
     try:
         q0 = synth.initial_state(cfg)
@@ -286,18 +289,38 @@ def timed_full_horizon(g, cfg, n_steps, fom_eps=True):
         t0 = time.perf_counter()
         e0.record(s)
         err = None
-        try:
-            rom.step(n_steps)
-        except g.RomError as exc:
-            err = str(exc)
-        e1.record(s)
+        done = 0
+        if chunk is None:
+            try:
+                rom.step(n_steps)
+                done = n_steps
+            except g.RomError as exc:
+                err = str(exc)
+        else:
+            while done < n_steps:
+                m = min(chunk, n_steps - done)
+                try:
+                    rom.step(m)
+                except g.RomError as exc:
+                    err = str(exc)
+                    break
+                done += m
+                e1.record(s)
+        if chunk is None or err is None or done == 0:
+            e1.record(s)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         ms = e0.elapsed_time(e1)
-        out = {"steps": n_steps, "device_ms": ms, "wall_ms": wall * 1e3,
-               "value": n_steps / (ms / 1e3), "unit": "steps/s"}
+        out = {"steps": done, "device_ms": ms, "wall_ms": wall * 1e3,
+               "value": done / (ms / 1e3) if done else 0.0, "unit": "steps/s"}
         if err is not None:
-            out["error"] = err
+            out["stopped"] = f"after {done} of {n_steps} steps (t = {(cfg.w_init + done) * cfg.dt:.4f}): {err}"
+            if chunk is None or done == 0:
+                out["error"] = err
+                rom.close()
+                return out
+            fom_eps = False
+        if not fom_eps:
             rom.close()
             return out
         if fom_eps:
@@ -442,6 +465,7 @@ def timed_batch(g, args, stream, dist, world):
     torch.cuda.synchronize()
     prof = b.profile_read()
     work = b.work()
+    fwork = b.fom_work()
     lay = b.layout()
     b.profile(False)
     b.close()
@@ -450,6 +474,17 @@ def timed_batch(g, args, stream, dist, world):
     step_s = prof["reduced_steps"]["ms"] / 1e3
     gbs = work["sweep_bytes"] / step_s / 1e9
     launches = max(1, prof["reduced_steps"]["launches"])
+    # the coarse FOM kernel: 24 bytes per row and Newton iteration (read the
+    # iterate and the previous state, write the update)
+    fom_s = prof["coarse_fom"]["ms"] / 1e3
+    fom_launches = max(1, prof["coarse_fom"]["launches"])
+    fom_gbs = fwork["fom_bytes"] / fom_s / 1e9 if fom_s > 0 else 0.0
+    fom_roof = {"bound": "hbm", "kernel": "batch_fom_kernel", "achieved": fom_gbs,
+                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": fom_gbs / pk["hbm_gbs"],
+                "peak_source": pk["source"], "algorithmic_bytes": fwork["fom_bytes"] / fom_launches,
+                "row_iterations_per_launch": fwork["row_iterations"] / fom_launches,
+                "avg_launch_us": fom_s / fom_launches * 1e6, "traffic": None,
+                "per": "launch (the coarse step of the instances that adapt at that step)"}
     traffic = None
     if TRAFFIC_BATCH["bytes"] is not None and TRAFFIC_BATCH["sha1"] == src_sha1(TRAFFIC_BATCH["src"]) \
             and len(cfgs) == 256:
@@ -470,7 +505,8 @@ def timed_batch(g, args, stream, dist, world):
                          "peak_source": pk["source"],
                          "algorithmic_bytes": work["sweep_bytes"] / launches,
                          "avg_launch_us": step_s / launches * 1e6, "traffic": traffic,
-                         "per": "launch (5 steps of every instance)"}}
+                         "per": "launch (5 steps of every instance)"},
+            "fom_roofline": fom_roof}
 
 
 # ------------------------------------------------------------------- main ---
@@ -586,12 +622,13 @@ def main():
         # the two other single-ROM workloads: Burgers N=512 plain Galerkin, and Sod
         forms["burgers_n512_r10_z10_fp64"] = timed_single(g, synth.config_burgers_small(), 2000)
         forms["sod_n8192_r40_z10_fp64"] = timed_single(g, synth.config_sod(), 500)
-        # whole horizons: the headline workload's 20 000 steps, Sod to the last
-        # step with a reduced Newton root (the Galerkin ROM has none at the
-        # 4099th online step; t = 0.2 would be step 4938)
+        # whole horizons: the headline workload's 20 000 steps; Sod towards
+        # t = 0.2 (4938 online steps) in calls of 100 steps, ending at the
+        # first call that fails (the Galerkin ROM leaves the physical range
+        # near the 4099th online step)
         forms["c1_full_horizon"] = timed_full_horizon(g, workload_config(), 20000)
         sod = synth.config_sod()
-        forms["sod_full_horizon"] = timed_full_horizon(g, sod, 4098)
+        forms["sod_full_horizon"] = timed_full_horizon(g, sod, sod.n_online, chunk=100)
         lspg = synth.config_burgers_small()
         lspg.projection = 1
         forms["lspg_burgers_n512_r10_z10_fp64"] = timed_single(g, lspg, 2000)

@@ -53,6 +53,7 @@ typedef enum { ROM_BURGERS = 0, ROM_EULER = 1 } rom_problem;
 typedef enum { ROM_FP64 = 0, ROM_MIXED_FP32 = 1 } rom_precision;
 typedef enum { ROM_GALERKIN = 0, ROM_LSPG = 1 } rom_projection;
 typedef enum { ROM_UPDATE_ISVD = 0, ROM_UPDATE_WINDOWED_SVD = 1, ROM_UPDATE_DIRECT = 2 } rom_update_rule;
+typedef enum { ROM_BACKWARD_EULER = 0, ROM_SSPRK43 = 1 } rom_time_scheme;
 
 /*
  * Hyper-parameters of one adaptive ROM: the inputs of Algorithm 1 (r, n_s,
@@ -101,6 +102,17 @@ typedef enum { ROM_UPDATE_ISVD = 0, ROM_UPDATE_WINDOWED_SVD = 1, ROM_UPDATE_DIRE
  *              its "singular values" those of Phi^+ Y. Both transfer the state
  *              as a = Phi_new^T D (q~ - q_ref), and both are FP64 only.
  *  window      1 <= window <= min(w_init, 64) for rules 1 and 2 (unused by 0).
+ *  time_scheme ROM_BACKWARD_EULER (0): fine FOM steps and reduced steps by
+ *              backward Euler (Newton). ROM_SSPRK43 (1): the explicit form of
+ *              the paper's RDE solver (App. D): the fine FOM steps of the
+ *              training window and the Galerkin (or DEIM-Galerkin) reduced
+ *              steps da/dt = Phi^T D f (or (P^T Phi)^+ P^T D f) advance by the
+ *              four-stage, third-order SSP Runge-Kutta scheme (SSP coefficient
+ *              2: three half steps of forward Euler, an average with the start
+ *              value after the third, a last half step); the coarse correction
+ *              step stays backward Euler over z*dt (Eq.
+ *              coarse_fom_backward_euler). Galerkin, ROM_FP64 and
+ *              ROM_UPDATE_ISVD only.
  */
 typedef struct {
     int32_t problem;
@@ -121,6 +133,7 @@ typedef struct {
     int32_t projection;
     int32_t update_rule;
     int32_t window;
+    int32_t time_scheme;
 } rom_config;
 
 /*
@@ -410,6 +423,13 @@ rom_status rom_batch_profile_read(rom_batch* b, double* ms_total, int64_t* launc
  * basis and three FP32 words of reference-state data per row: 4 n_cells k +
  * 12 n_cells bytes, k the rank at that step). Either output may be NULL. */
 rom_status rom_batch_work(rom_batch* b, int64_t* newton_iters, double* sweep_bytes);
+
+/* Work of the coarse FOM steps (Eq. coarse_fom_backward_euler) since the last
+ * rom_batch_profile call (or init): Newton iterations times n_cells, summed
+ * over the instances and their events, and the algorithmic bytes of those
+ * iterations (each reads the iterate and the previous state and writes the
+ * update: 24 bytes a row). Either output may be NULL. */
+rom_status rom_batch_fom_work(rom_batch* b, int64_t* row_iterations, double* fom_bytes);
 
 /* Releases the batch and all its device memory (NULL is ignored). */
 void rom_batch_destroy(rom_batch* b);

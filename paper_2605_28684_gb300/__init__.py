@@ -45,6 +45,7 @@ def make_config(cfg) -> _lib.RomConfigC:
     c.projection = int(getattr(cfg, "projection", 0))
     c.update_rule = int(getattr(cfg, "update_rule", 0))
     c.window = int(getattr(cfg, "window", 0))
+    c.time_scheme = int(getattr(cfg, "time_scheme", 0))
     return c
 
 
@@ -223,6 +224,14 @@ class Batch:
         _lib.check(self._lib.rom_batch_work(self._b, ctypes.byref(it), ctypes.byref(by)),
                    "rom_batch_work")
         return dict(newton_iters=it.value, sweep_bytes=by.value)
+
+    def fom_work(self):
+        """Coarse FOM work since the last profile call: Newton iterations times
+        n_cells over all instances and events, and their algorithmic bytes."""
+        it, by = ctypes.c_int64(), ctypes.c_double()
+        _lib.check(self._lib.rom_batch_fom_work(self._b, ctypes.byref(it), ctypes.byref(by)),
+                   "rom_batch_fom_work")
+        return dict(row_iterations=it.value, fom_bytes=by.value)
 
     def close(self):
         if getattr(self, "_b", None) is not None and self._b.value:

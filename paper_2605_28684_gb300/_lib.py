@@ -15,7 +15,7 @@ EXPORTED = [
     "rom_isvd_update_dev", "rom_profile", "rom_profile_read", "rom_fom_step_noalloc_dev",
     "rom_batch_init", "rom_batch_step", "rom_batch_state", "rom_batch_info", "rom_batch_layout",
     "rom_batch_profile", "rom_batch_profile_read", "rom_batch_destroy", "rom_batch_work",
-    "rom_debug_set_wait_limit", "rom_adjoint",
+    "rom_debug_set_wait_limit", "rom_adjoint", "rom_batch_fom_work",
 ]
 
 
@@ -39,6 +39,7 @@ class RomConfigC(ctypes.Structure):
         ("projection", ctypes.c_int32),
         ("update_rule", ctypes.c_int32),
         ("window", ctypes.c_int32),
+        ("time_scheme", ctypes.c_int32),
     ]
 
 
@@ -98,11 +99,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rom_batch_profile.argtypes = [P, ctypes.c_int32]
     lib.rom_batch_profile_read.argtypes = [P, D, I64P]
     lib.rom_batch_work.argtypes = [P, I64P, D]
+    lib.rom_batch_fom_work.argtypes = [P, I64P, D]
     lib.rom_batch_destroy.argtypes = [P]
     lib.rom_batch_destroy.restype = None
     for name in ["rom_batch_init", "rom_batch_step", "rom_batch_state", "rom_batch_info",
                  "rom_batch_layout", "rom_batch_profile", "rom_batch_profile_read", "rom_batch_work",
-                 "rom_fom_step_noalloc_dev", "rom_profile", "rom_profile_read", "rom_init", "rom_step", "rom_update_basis", "rom_state", "rom_load_state",
+                 "rom_batch_fom_work", "rom_fom_step_noalloc_dev", "rom_profile", "rom_profile_read", "rom_init", "rom_step", "rom_update_basis", "rom_state", "rom_load_state",
                  "rom_samples", "rom_info", "rom_fom_rhs_dev", "rom_fom_step_dev",
                  "rom_isvd_update_dev", "rom_debug_set_wait_limit", "rom_adjoint"]:
         getattr(lib, name).restype = ctypes.c_int

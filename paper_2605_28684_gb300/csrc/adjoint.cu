@@ -19,10 +19,11 @@
 //    [Phi, q/|q|] U and of the projection p = Phi^T yhat, q = yhat - Phi p,
 //    with every basis adjoint projected onto the tangent space of orthonormal
 //    bases (adj_event_*).
-//  * POD of the training matrix X: the kept triplets (u_c, s_c, v_c) only,
-//    with the complement of span(U) handled through R = (I - U U^T) X and the
-//    push-through identity (s^2 I - R R^T)^-1 h = (h + R (s^2 I - R^T R)^-1 R^T h) / s^2
-//    (adj_pod_small_kernel and the generic tall-skinny products).
+//  * POD of the training matrix X: the thin-SVD adjoint over all w singular
+//    triplets of X (the backward-stable SVD of pod_svd.cu with V accumulated
+//    from its rotations), so the gaps s_c^2 - s_i^2 come from the singular
+//    values themselves (adj_pod_full_kernel and the generic tall-skinny
+//    products).
 // Scalar adjoints (d-bar, nu-bar) are summed per CTA into fixed slots and
 // reduced in a fixed order, so the result does not depend on scheduling.
 #include <cfloat>
@@ -695,100 +696,50 @@ __global__ void __launch_bounds__(kT) adj_a0_kernel(AdjA0Args A) {
   if (t == 0) A.acc[b] += sd;
 }
 
-__global__ void adj_xhat_kernel(int64_t n, int w, const double* Q, const double* q_ref, double d,
-                                double* X) {
-  const int64_t tot = n * (int64_t)w;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % n;
-    X[e] = d * (Q[e] - q_ref[i]);
-  }
-}
-
-// One CTA per kept column c for the solves, then CTA 0 assembles the small
-// matrices (launched twice: phase 0 the solves, phase 1 the assembly).
-//  phase 0: y_c = (s_c^2 I - R^T R)^-1 (R^T h_c) by Cholesky (w x w, FP64).
-//  phase 1: C_ic = (U^T Ubar)_ic / (s_c^2 - s_i^2) (i != c),
-//           X^T g_c = (V0 C)_c + (R^T h_c + R^T R y_c) / s_c^2,
-//           Ma = diag(sbar) V^T + (X^T G)^T, Mb = diag(s) V^T = V0^T,
-//           Ys = Y diag(1/s^2), sinv2 = diag(1/s^2).
-__global__ void __launch_bounds__(kT) adj_pod_small_kernel(AdjPodArgs A, int phase) {
+// The POD adjoint over every singular triplet of the thin SVD X = U S V^T
+// (N x w, U = [u_1 ... u_w], descending s). Kept columns c < k carry
+// Ubar_c and sbar_c; with A = U^T Ubar (w x k) and F_ic = 1 / (s_c^2 - s_i^2)
+// (zero for i = c and for equal values):
+//   Pbar_ic += F_ic A_ic s_c,  Pbar_ci += F_ic A_ic s_i,  Pbar_cc += sbar_c,
+//   Xbar = U Pbar V^T + (Ubar - U A) S_k^-1 V_k^T
+//        = U B1 + Ubar B2,  B1 = Pbar V^T - A S_k^-1 V_k^T,  B2 = S_k^-1 V_k^T.
+// The gaps come from the singular values themselves, never from a Gram
+// matrix of X, so singular values far below the rounding of X^T X (kept
+// directions near the rank tolerance) keep their relative accuracy.
+// One CTA: B1 (w x w row-major) and B2 (k x w row-major).
+__global__ void __launch_bounds__(kT) adj_pod_full_kernel(AdjPodArgs A) {
   extern __shared__ __align__(16) double smem[];
   const int w = A.w, k = A.k, t = threadIdx.x;
-  if (phase == 0) {
-    const int c = blockIdx.x;
-    double* M = smem;            // w x w
-    double* y = M + w * w;       // w
-    const double s2 = A.s[c] * A.s[c];
-    for (int e = t; e < w * w; e += kT) {
-      const int i = e / w, j = e % w;
-      M[e] = (i == j ? s2 : 0.0) - A.RtR[e];
-    }
-    for (int i = t; i < w; i += kT) y[i] = A.RtH[i * k + c];
-    __syncthreads();
-    // Cholesky M = L L^T (lower, in place), column by column
-    for (int j = 0; j < w; ++j) {
-      if (t == 0) M[j * w + j] = sqrt(fmax(M[j * w + j], DBL_MIN));
-      __syncthreads();
-      const double djj = M[j * w + j];
-      for (int i = j + 1 + t; i < w; i += kT) M[i * w + j] /= djj;
-      __syncthreads();
-      const int rem = w - j - 1;
-      for (int e = t; e < rem * rem; e += kT) {
-        const int i = j + 1 + e / rem, l = j + 1 + e % rem;
-        if (l <= i) M[i * w + l] -= M[i * w + j] * M[l * w + j];
-      }
-      __syncthreads();
-    }
-    // L z = y, then L^T x = z (warp 0)
-    if (t < 32) {
-      for (int i = 0; i < w; ++i) {
-        double s = 0.0;
-        for (int l = t; l < i; l += 32) s += M[i * w + l] * y[l];
-        s = warp_sum(s);
-        if (t == 0) y[i] = (y[i] - s) / M[i * w + i];
-        __syncwarp();
-      }
-      for (int i = w - 1; i >= 0; --i) {
-        double s = 0.0;
-        for (int l = i + 1 + t; l < w; l += 32) s += M[l * w + i] * y[l];
-        s = warp_sum(s);
-        if (t == 0) y[i] = (y[i] - s) / M[i * w + i];
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    for (int i = t; i < w; i += kT) A.Y[i * k + c] = y[i];
-    return;
-  }
-  // phase 1 (one CTA)
-  double* Cm = smem;                 // k x k
-  double* XtG = Cm + k * k;          // w x k
-  for (int e = t; e < k * k; e += kT) {
-    const int i = e / k, c = e % k;
-    const double diff = A.s[c] * A.s[c] - A.s[i] * A.s[i];
-    const double v = (i != c && diff != 0.0) ? A.Uh[i * k + c] / diff : 0.0;
-    Cm[e] = v;
-    A.C[e] = v;
-    A.sinv2[e] = (i == c) ? 1.0 / (A.s[c] * A.s[c]) : 0.0;
-  }
+  double* P = smem;                  // w x w: Pbar
+  for (int e = t; e < w * w; e += kT) P[e] = 0.0;
   __syncthreads();
-  for (int e = t; e < w * k; e += kT) {
-    const int i = e / k, c = e % k;
+  // each entry of Pbar is written by exactly one thread: the (i, c) term goes
+  // to P[i][c] (c < k) and its mirror to P[c][i]; both are summed per entry
+  for (int e = t; e < w * w; e += kT) {
+    const int i = e / w, j = e % w;
     double v = 0.0;
-    for (int m = 0; m < k; ++m) v = fma(A.V0[i * k + m], Cm[m * k + c], v);
-    double r = A.RtH[i * k + c];
-    for (int m = 0; m < w; ++m) r = fma(A.RtR[i * w + m], A.Y[m * k + c], r);
-    const double is2 = 1.0 / (A.s[c] * A.s[c]);
-    XtG[e] = v + r * is2;
-    A.Ys[e] = A.Y[e] * is2;
+    if (j < k && i != j) {           // F_ij A_ij s_j
+      const double diff = A.s[j] * A.s[j] - A.s[i] * A.s[i];
+      if (diff != 0.0) v += A.A[i * k + j] / diff * A.s[j];
+    }
+    if (i < k && i != j) {           // F_ji A_ji s_j (mirror of the (j, i) term)
+      const double diff = A.s[i] * A.s[i] - A.s[j] * A.s[j];
+      if (diff != 0.0) v += A.A[j * k + i] / diff * A.s[j];
+    }
+    if (i == j && i < k) v += A.sbar[i];
+    P[e] = v;
   }
   __syncthreads();
+  for (int e = t; e < w * w; e += kT) {
+    const int i = e / w, j = e % w;
+    double v = 0.0;
+    for (int l = 0; l < w; ++l) v = fma(P[i * w + l], A.V[j * w + l], v);
+    for (int c = 0; c < k; ++c) v -= A.A[i * k + c] / A.s[c] * A.V[j * w + c];
+    A.B1[e] = v;
+  }
   for (int e = t; e < k * w; e += kT) {
-    const int c = e / w, i = e % w;
-    const double v0 = A.V0[i * k + c];            // s_c v_c[i]
-    A.Ma[e] = A.sbar[c] * v0 / A.s[c] + XtG[i * k + c];
-    A.Mb[e] = v0;
+    const int c = e / w, j = e % w;
+    A.B2[e] = A.V[j * w + c] / A.s[c];
   }
 }
 
@@ -981,22 +932,12 @@ cudaError_t launch_adj_a0(const AdjA0Args& A, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_adj_xhat(int64_t n, int w, const double* Q, const double* q_ref, double d,
-                            double* X, cudaStream_t s) {
-  adj_xhat_kernel<<<1024, kT, 0, s>>>(n, w, Q, q_ref, d, X);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_adj_pod_small(const AdjPodArgs& A, cudaStream_t s) {
-  if (A.w < 1 || A.w > 128 || A.k < 1 || A.k > kMaxR) return cudaErrorInvalidValue;
-  const size_t smem0 = sizeof(double) * (A.w * A.w + A.w);
-  const size_t smem1 = sizeof(double) * (A.k * A.k + A.w * A.k);
-  const size_t smax = smem0 > smem1 ? smem0 : smem1;
-  cudaError_t e = cudaFuncSetAttribute(adj_pod_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smax);
+cudaError_t launch_adj_pod_full(const AdjPodArgs& A, cudaStream_t s) {
+  if (A.w < 1 || A.w > 128 || A.k < 1 || A.k > A.w || A.k > kMaxR) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(double) * A.w * A.w;
+  cudaError_t e = cudaFuncSetAttribute(adj_pod_full_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  adj_pod_small_kernel<<<A.k, kT, smem0, s>>>(A, 0);
-  adj_pod_small_kernel<<<1, kT, smem1, s>>>(A, 1);
+  adj_pod_full_kernel<<<1, kT, smem, s>>>(A);
   return cudaGetLastError();
 }
 

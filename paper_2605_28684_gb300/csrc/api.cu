@@ -93,6 +93,10 @@ rom_status validate(const rom_config* c) {
   if (c->update_rule != ROM_UPDATE_ISVD &&
       (c->precision != ROM_FP64 || c->window < 1 || c->window > c->w_init || c->window > kMaxR))
     return ROM_EINVAL;
+  if (c->time_scheme != ROM_BACKWARD_EULER && c->time_scheme != ROM_SSPRK43) return ROM_EINVAL;
+  if (c->time_scheme == ROM_SSPRK43 &&
+      (c->projection != ROM_GALERKIN || c->precision != ROM_FP64 || c->update_rule != ROM_UPDATE_ISVD))
+    return ROM_EINVAL;
   return ROM_OK;
 }
 
@@ -257,6 +261,7 @@ StepArgs step_args(rom_ctx* ctx, int nsteps) {
   A.tol = ctx->cfg.newton_tol;
   A.max_iter = ctx->cfg.newton_max;
   A.nsteps = nsteps;
+  A.explicit_rk = ctx->cfg.time_scheme == ROM_SSPRK43 ? 1 : 0;
   A.partials = ctx->d.partials;
   A.jpartials = ctx->d.jpartials;
   A.jac = ctx->d.jac;
@@ -557,11 +562,16 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
   RCK(cudaMemsetAsync(d.rank, 0, sizeof(int), s));
   RCK(cudaMemcpyAsync(d.y_tmp, q0_host, sizeof(double) * N, cudaMemcpyHostToDevice, s));
   RCK(cudaMemcpyAsync(d.q_ref, d.y_tmp, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
-  // training window: w_init fine BE steps
+  // training window: w_init fine FOM steps (backward Euler, or SSPRK(4,3) in
+  // the explicit form with yhat, qres and lifted as its stage scratch)
   const double* prev = d.y_tmp;
   for (int j = 0; j < w; ++j) {
     double* cur = ctx->q_train + (size_t)j * N;
-    RCK(fom_step(ctx, prev, cur, ctx->cfg.dt));
+    if (ctx->cfg.time_scheme == ROM_SSPRK43)
+      RCK(launch_fom_explicit_step(fom_params(ctx, ctx->cfg.dt), ctx->cfg.n_var, prev, cur, d.yhat, d.qres,
+                                   d.lifted, s));
+    else
+      RCK(fom_step(ctx, prev, cur, ctx->cfg.dt));
     prev = cur;
   }
   rom_status st = finish(ctx);
@@ -1065,7 +1075,7 @@ extern "C" rom_status rom_adjoint(const rom_config* cfg, const double* q0_host, 
   rom_status vs = validate(cfg);
   if (vs != ROM_OK) return vs;
   if (cfg->problem != ROM_BURGERS || cfg->precision != ROM_FP64 || cfg->n_s != 0 || cfg->w_init > 128 ||
-      cfg->projection != ROM_GALERKIN)
+      cfg->projection != ROM_GALERKIN || cfg->time_scheme != ROM_BACKWARD_EULER)
     return ROM_EINVAL;
   const int64_t N = cfg->n_cells;
   if (!all_finite(q0_host, N) || !all_finite(target_host, N)) return ROM_ENONFINITE;
@@ -1121,11 +1131,11 @@ extern "C" rom_status rom_adjoint(const rom_config* cfg, const double* q0_host, 
   AAL(part, (size_t)G * 16384); AAL(pnb, N * r); AAL(bbar, N * (r + 1)); AAL(tchunk, kMaxChunks * 16);
   AAL(qT, N); AAL(target, N); AAL(Jd, 1); AAL(dtot, 1); AAL(mpartial, 256); AAL(bar, 1); AAL(status, 1);
   // offline reverse
-  double *X, *R, *Xbar, *V0, *Am, *Ubar, *Uh, *H, *C2, *RtR, *RtH, *Y, *Cc, *Ma, *Mb, *Ys, *sinv2, *Gm;
+  double *X, *Qf, *Uf, *Xbar, *Rw, *Uw, *sw, *Vw, *Vtmp, *wk, *Aw, *B1, *B2, *Am, *Ubar, *Uh;
   double *qlastbar, *qb0, *qb1;
-  AAL(X, N * w); AAL(R, N * w); AAL(Xbar, N * w); AAL(V0, w * r); AAL(Am, r * r); AAL(Ubar, N * r);
-  AAL(Uh, r * r); AAL(H, N * r); AAL(C2, r * w); AAL(RtR, w * w); AAL(RtH, w * r); AAL(Y, w * r);
-  AAL(Cc, r * r); AAL(Ma, r * w); AAL(Mb, r * w); AAL(Ys, w * r); AAL(sinv2, r * r); AAL(Gm, N * r);
+  AAL(X, N * w); AAL(Qf, N * w); AAL(Uf, N * w); AAL(Xbar, N * w); AAL(Rw, w * w); AAL(Uw, w * w);
+  AAL(sw, w); AAL(Vw, w * w); AAL(Vtmp, w * w); AAL(wk, 256); AAL(Aw, w * r); AAL(B1, w * w);
+  AAL(B2, r * w); AAL(Am, r * r); AAL(Ubar, N * r); AAL(Uh, r * r);
   AAL(qlastbar, N); AAL(qb0, N); AAL(qb1, N);
 #undef AAL
   if (e != cudaSuccess) {
@@ -1257,35 +1267,25 @@ extern "C" rom_status rom_adjoint(const rom_config* cfg, const double* q0_host, 
     RCK(launch_adj_a0(A0, G, s));
   }
   const int k = k0;
-  RCK(launch_adj_xhat(N, w, Q, ctx->d.q_ref, d, X, s));
-  // V0 = X^T U (w x k)
-  RCK(launch_tn(TnArgs{N, w, k, X, N, phi0, N, 1.0, part, V0}, G, s));
-  // Ubar = Phi-bar - U sym(U^T Phi-bar); -sym goes to Uh's buffer, reused below
+  // X = D (Q - q_ref 1^T) and its thin SVD with every triplet: the same
+  // calls as the forward POD, so U[:, :k] and s[:k] are the forward's bits
+  RCK(launch_win_fill(Q, N, ctx->d.q_ref, ctx->d.drow, N, w, X, s));
+  RCK(pod_thin_svd(X, N, w, Qf, Rw, Uw, sw, wk, part, G, s, Vw, Vtmp));
+  RCK(launch_nn(NnArgs{N, w, w, Qf, N, Uw, w, 1, 1.0, 0.0, Uf, N, Uf, N}, s));
+  // Ubar = Phi-bar - U sym(U^T Phi-bar) (tangent part at the POD basis)
   RCK(launch_tn(TnArgs{N, k, k, phi0, N, phibar, N, 1.0, part, Am}, G, s));
   RCK(launch_adj_neg_sym(Am, Uh, k, s));
   RCK(launch_nn(NnArgs{N, k, k, phi0, N, Uh, k, 1, 1.0, 1.0, phibar, N, Ubar, N}, s));
-  // Uh = U^T Ubar; H = Ubar - U Uh
-  RCK(launch_tn(TnArgs{N, k, k, phi0, N, Ubar, N, 1.0, part, Uh}, G, s));
-  RCK(launch_nn(NnArgs{N, k, k, phi0, N, Uh, k, 1, -1.0, 1.0, Ubar, N, H, N}, s));
-  // R = (I - U U^T) X by two passes: R1 = X - U V0^T, R = R1 - U (U^T R1)
-  RCK(launch_nn(NnArgs{N, k, w, phi0, N, V0, 1, k, -1.0, 1.0, X, N, R, N}, s));
-  RCK(launch_tn(TnArgs{N, k, w, phi0, N, R, N, 1.0, part, C2}, G, s));
-  RCK(launch_nn(NnArgs{N, k, w, phi0, N, C2, w, 1, -1.0, 1.0, R, N, R, N}, s));
-  RCK(launch_tn(TnArgs{N, w, w, R, N, R, N, 1.0, part, RtR}, G, s));
-  RCK(launch_tn(TnArgs{N, w, k, R, N, H, N, 1.0, part, RtH}, G, s));
+  // A = U^T Ubar over all w columns of U; Xbar = U B1 + Ubar B2
+  RCK(launch_tn(TnArgs{N, w, k, Uf, N, Ubar, N, 1.0, part, Aw}, G, s));
   {
-    AdjPodArgs P{N, w, k, sig0, sigbar, V0, Uh, RtR, RtH, Y, Cc, Ma, Mb, Ys, sinv2};
-    RCK(launch_adj_pod_small(P, s));
+    AdjPodArgs P{N, w, k, sw, sigbar, Aw, Vw, B1, B2};
+    RCK(launch_adj_pod_full(P, s));
   }
-  // G = U C + H diag(1/s^2) + R Y diag(1/s^2)
-  RCK(launch_nn(NnArgs{N, k, k, phi0, N, Cc, k, 1, 1.0, 0.0, Gm, N, Gm, N}, s));
-  RCK(launch_nn(NnArgs{N, k, k, H, N, sinv2, k, 1, 1.0, 1.0, Gm, N, Gm, N}, s));
-  RCK(launch_nn(NnArgs{N, w, k, R, N, Ys, k, 1, 1.0, 1.0, Gm, N, Gm, N}, s));
-  // Xbar = U Ma + G Mb
-  RCK(launch_nn(NnArgs{N, k, w, phi0, N, Ma, w, 1, 1.0, 0.0, Xbar, N, Xbar, N}, s));
-  RCK(launch_nn(NnArgs{N, k, w, Gm, N, Mb, w, 1, 1.0, 1.0, Xbar, N, Xbar, N}, s));
-  // Qbar (into R's buffer) and q_ref-bar
-  double* Qbar = R;
+  RCK(launch_nn(NnArgs{N, w, w, Uf, N, B1, w, 1, 1.0, 0.0, Xbar, N, Xbar, N}, s));
+  RCK(launch_nn(NnArgs{N, k, w, Ubar, N, B2, w, 1, 1.0, 1.0, Xbar, N, Xbar, N}, s));
+  // Qbar (into Qf's buffer) and q_ref-bar
+  double* Qbar = Qf;
   {
     AdjXcArgs XA{N, w, Q, ctx->d.q_ref, d, Xbar, Qbar, qlastbar, qrefbar, acc, dtot};
     RCK(launch_adj_xc(XA, G, s));

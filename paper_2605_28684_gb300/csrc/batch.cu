@@ -4,20 +4,20 @@
 // re-orthonormalisation). Every instance runs the online loop of Algorithm 1
 // with the plain Galerkin step and the iSVD of Algorithm 2.
 //
-// All instances advance in lockstep, one time step at a time, so that one
-// pass over the bases serves every instance: a Newton iteration streams the
-// live columns of the FP32 bases of the whole batch once, and the batch is
-// limited by memory traffic and latency instead of running hundreds of small
+// One launch serves every instance, so that the whole batch streams its FP32
+// bases through the GPU together instead of running hundreds of small
 // latency-bound solves one after another. Work is cut into row tiles
-// (instance, first row, last row); CTAs take tiles from a queue ordered by
-// decreasing cost, and per-tile partial sums are combined per instance in tile
-// order, so results do not depend on which CTA took which tile. Three
-// persistent cooperative kernels:
-//   batch_steps_kernel  BE Galerkin steps: per iteration a sweep over the
-//                       tiles (FP32 lift, FP32 difference-form residual, FP32
-//                       projection, FP32 reduced Jacobian when due) and an
-//                       instance phase (Newton update with the inverse of the
-//                       reduced Jacobian).
+// (instance, first row, last row), and per-tile partial sums are combined per
+// instance in tile order, so results do not depend on which CTA took which
+// tile. Three persistent cooperative kernels:
+//   batch_steps_kernel  BE Galerkin steps as dataflow: CTAs take the tiles of
+//                       every instance's current Newton iteration from a work
+//                       array (FP32 lift, FP32 difference-form residual, FP32
+//                       projection, FP32 reduced Jacobian when due); the CTA
+//                       that completes an instance's last tile runs its Newton
+//                       update (inverse of the reduced Jacobian) and appends
+//                       its next iteration, so instances advance
+//                       independently, without a grid barrier per iteration.
 //   batch_fom_kernel    the coarse FOM step (Eq. coarse_fom_backward_euler)
 //                       of the instances that adapt now: Newton with FP64
 //                       residuals and a chunked PCR solver over (instance,
@@ -90,9 +90,9 @@ struct BArgs {
   double* sigma;           // count x kMaxR
   int* rank;
   int* need_jac;
-  int* active;
   int* iters_rom;
   int* iters_fom;
+  long long* fom_its;      // count: coarse FOM Newton iterations since reset
   long long* sweeps;       // count: Newton iterations (sweeps over the basis) since reset
   long long* sweep_cols;   // count: basis columns streamed by those sweeps (rank each time)
   float* jlu;              // count x kMaxR x kMaxR: inverse of the reduced Jacobian (FP32)
@@ -112,7 +112,14 @@ struct BArgs {
   float* ev_u;             // count x kMaxCore x kMaxR: rotation U(:, 0:k') (FP32)
   double* ev_anew;         // count x kMaxR: transferred state before a <- R a
   float* ev_r;             // count x kMaxR x kMaxR: Cholesky factor R (FP32 copy)
-  unsigned int* ctl;       // [0..3] tile queues, [4..5] active counts (host-zeroed)
+  unsigned int* ctl;       // [0..3] tile queues of the sweeps; steps kernel: [0] claimed
+                           // entries, [1] appended entries, [2] instances done (host-zeroed)
+  unsigned long long* wq;  // steps kernel work entries: epoch << 32 | tile
+  long long wq_cap;        // entries of wq
+  int* tcount;             // count: tiles of the current iteration counted in
+  int* inst_it;            // count: Newton iteration of the current step
+  int* inst_step;          // count: step of the launch
+  unsigned int* epoch;     // launches of the steps kernel so far
   long long* M;            // online steps done by every instance
   GridBarrier* bar;
   int* status;
@@ -353,7 +360,8 @@ struct StepSmem {
   float x[kMaxR];
   int piv[kMaxR];
   double sc[4];
-  int q;
+  long long base;
+  int q, act, cnt;
 };
 
 struct CoreSmem {
@@ -563,12 +571,16 @@ __device__ void step_tile(const BArgs& A, StepSmem& sm, int tile, int i, bool ja
   }
 }
 
-// Newton update of instance i after a sweep (one CTA).
-__device__ void step_instance(const BArgs& A, StepSmem& sm, int i, int it, unsigned int* nact) {
+// Newton update of instance i once every tile of its current iteration has
+// reported (run by the CTA that completed the last one), then the instance's
+// next work: the tiles of its next iteration, of its next step, or nothing
+// when the last step of the launch has converged.
+__device__ __noinline__ void update_instance(const BArgs& A, StepSmem& sm, int i, unsigned int epoch) {
   const Inst I = A.inst[i];
   const int t = threadIdx.x;
   const int k = A.rank[i];
-  const int jac = A.need_jac[i];
+  const int it = __ldcg(&A.inst_it[i]);
+  const int jac = __ldcg(&A.need_jac[i]);
   sum_tiles(A.gpart, I.tile0, I.tile1, k, 0, sm.g);
   __syncthreads();
   float* J = sm.J;
@@ -591,15 +603,16 @@ __device__ void step_instance(const BArgs& A, StepSmem& sm, int i, int it, unsig
   }
   double* a = A.a + (size_t)i * kMaxR;
   const double* an = A.an + (size_t)i * kMaxR;
-  for (int j = t; j < k; j += blockDim.x) sm.x[j] = (float)(-(a[j] - an[j] - I.dt * sm.g[j]));
+  for (int j = t; j < k; j += blockDim.x) sm.x[j] = (float)(-(__ldcg(&a[j]) - __ldcg(&an[j]) - I.dt * sm.g[j]));
   __syncthreads();
   inv_apply(sm.Ji, sm.x, k);
+  // act: 0 stop (error recorded), 1 next iteration, 2 next step, 3 launch done
   if (t < 32) {
     unsigned int kd = 0u, ka = 0u;
     bool bad = false;
     for (int j = t; j < k; j += 32) {
       const float dlt = sm.x[j];
-      const double v = a[j] + (double)dlt;
+      const double v = __ldcg(&a[j]) + (double)dlt;
       a[j] = v;
       kd = max(kd, __float_as_uint(fabsf(dlt)));
       ka = max(ka, __float_as_uint(fabsf((float)v)));
@@ -612,27 +625,92 @@ __device__ void step_instance(const BArgs& A, StepSmem& sm, int i, int it, unsig
     const double tol = fmax(I.tol, 1e-7);
     if (t == 0) {
       const bool conv = (double)__uint_as_float(kd) <= tol * (1.0 + (double)__uint_as_float(ka));
+      int act = 0;
       if (bad) {
         record_status(A.status, kStNonFinite);
       } else if (conv) {
-        A.active[i] = 0;
+        // per-instance state written by whichever CTA ran the last update:
+        // read through L2
         A.iters_rom[i] = it;
-        A.sweeps[i] += it;
-        A.sweep_cols[i] += (long long)it * k;
+        A.sweeps[i] = __ldcg(&A.sweeps[i]) + it;
+        A.sweep_cols[i] = __ldcg(&A.sweep_cols[i]) + (long long)it * k;
+        const int stp = __ldcg(&A.inst_step[i]) + 1;
+        if (stp >= A.nsteps) {
+          act = 3;
+        } else {
+          A.inst_step[i] = stp;
+          A.inst_it[i] = 1;
+          act = 2;
+        }
       } else if (it >= I.maxit) {
         record_status(A.status, kStNoConv);
       } else {
-        A.active[i] = 1;
+        A.inst_it[i] = it + 1;
         if (it % 8 == 0) A.need_jac[i] = 1;    // stale Jacobian: refresh at this iterate
-        atomicAdd(nact, 1u);
+        act = 1;
       }
-      sm.sc[0] = conv ? 1.0 : 0.0;
+      sm.act = act;
     }
   }
   __syncthreads();
-  if (sm.sc[0] > 0.0)
-    for (int j = t; j < k; j += blockDim.x) A.an[(size_t)i * kMaxR + j] = a[j];
+  const int act = sm.act;
+  if (act >= 2)
+    for (int j = t; j < k; j += blockDim.x) A.an[(size_t)i * kMaxR + j] = __ldcg(&a[j]);
+  if (act == 0) return;
+  if (t == 0) A.tcount[i] = 0;
+  __threadfence();
   __syncthreads();
+  if (act == 3) {
+    if (t == 0) atomicAdd(&A.ctl[2], 1u);
+    return;
+  }
+  // publish the next iteration's tiles: the state writes above are fenced
+  // before the entries that let other CTAs read them
+  const int n = I.tile1 - I.tile0;
+  if (t == 0) sm.base = (long long)atomicAdd(&A.ctl[1], (unsigned int)n) + A.ntiles;
+  __syncthreads();
+  const long long base = sm.base;
+  if (base + n > A.wq_cap) {       // cannot happen within the iteration limits
+    if (t == 0) record_status(A.status, kStNoConv);
+    return;
+  }
+  volatile unsigned long long* wq = A.wq;
+  for (int e = t; e < n; e += blockDim.x)
+    wq[base + e] = ((unsigned long long)epoch << 32) | (unsigned int)(I.tile0 + e);
+}
+
+// Tile of work entry h, or -1 once every instance is done, an error status is
+// set, or the wait runs out (a timeout is recorded). Thread 0 waits; the
+// result goes to every thread.
+__device__ int wait_entry(const BArgs& A, long long h, unsigned int epoch, StepSmem& sm) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tile = -1;
+    const volatile unsigned long long* wq = A.wq;
+    const volatile unsigned int* done = &A.ctl[2];
+    const volatile int* st = A.status;
+    const long long limit = c_wait_limit;
+    const long long t0 = clock64();
+    for (;;) {
+      if (h < A.wq_cap) {
+        const unsigned long long v = wq[h];
+        if ((unsigned int)(v >> 32) == epoch) {
+          tile = (int)(unsigned int)(v & 0xffffffffull);
+          break;
+        }
+      }
+      if (*done >= (unsigned int)A.count || *st != 0) break;
+      if (clock64() - t0 > limit) {
+        record_status(A.status, kStTimeout);
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    sm.q = tile;
+  }
+  __syncthreads();
+  return sm.q;
 }
 
 // Largest current rank over the batch (every CTA computes the same value).
@@ -665,6 +743,20 @@ constexpr int kLowRank = 16;   // rank limit of the two-CTAs-per-SM instantiatio
 // Two instantiations are launched back to back for every segment of steps:
 // MAXKB = kLowRank (two CTAs per SM; fewer registers) runs when every rank
 // is at most kLowRank, MAXKB = kMaxR otherwise; the other one returns at once.
+//
+// Dataflow over a work array (wq): an entry names a row tile of one
+// instance's current Newton iteration; the first iteration of the first step
+// of every instance is filled in at the start. A CTA claims entries in order
+// (the claim of the next one goes out before it works on the current one),
+// computes the tile's partials, and counts the tile in; the CTA that counts
+// an instance's last tile runs that instance's update at once and appends its
+// next iteration's tiles. Instances therefore advance independently, and the
+// small per-instance work overlaps the other instances' streaming; there is
+// no grid-wide barrier per iteration. Entries carry the launch's epoch, so
+// entries of an earlier launch are never taken for this one's. No CTA that
+// appends waits for anything, and a CTA waits only for an entry that was
+// claimed by it, so every wait ends: the entry is written, or every instance
+// is done, or an error is recorded, or the bounded wait runs out.
 template <int MAXKB>
 __global__ void __launch_bounds__(kBT, MAXKB <= kLowRank ? 2 : 1) batch_steps_kernel(BArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -674,34 +766,40 @@ __global__ void __launch_bounds__(kBT, MAXKB <= kLowRank ? 2 : 1) batch_steps_ke
     const int mr = batch_max_rank(A);
     if (MAXKB < kMaxR ? (mr > MAXKB) : (mr <= kLowRank)) return;
   }
-  for (int i = b; i < A.count; i += G)
+  const unsigned int epoch = __ldcg(A.epoch) + 1u;
+  for (int i = b; i < A.count; i += G) {
     for (int j = t; j < kMaxR; j += blockDim.x) A.an[(size_t)i * kMaxR + j] = A.a[(size_t)i * kMaxR + j];
-  int gi = 0;   // iteration counter over the whole launch (queue parity)
-  for (int step = 0; step < A.nsteps; ++step) {
-    for (int it = 1;; ++it, ++gi) {
-      const int par = gi & 1;
-      for_each_tile(&A.ctl[par], A.ntiles, &sm.q, [&](int q) {
-        const int4 dsc = __ldg(&A.qdesc[q]);
-        const int tile = dsc.x, i = dsc.y;
-        if (it > 1 && !__ldcg(&A.active[i])) return;
-        const bool jac = __ldcg(&A.need_jac[i]) != 0;
-        with_bucket_upto<MAXKB>(A.rank[i], [&](auto kb) { step_tile<decltype(kb)::value>(A, sm, tile, i, jac); });
-      });
-      if (!grid_sync(A.bar, A.status)) return;
-      if (b == 0 && t == 0) {
-        A.ctl[par ^ 1] = 0u;
-        A.ctl[4 + (par ^ 1)] = 0u;
-      }
-      for (int i = b; i < A.count; i += G) {
-        if (it > 1 && !__ldcg(&A.active[i])) continue;
-        step_instance(A, sm, i, it, &A.ctl[4 + par]);
-      }
-      if (!grid_sync(A.bar, A.status)) return;
-      if (__ldcg(A.status) != 0) return;
-      if (__ldcg(&A.ctl[4 + par]) == 0u) { ++gi; break; }
+    if (t == 0) {
+      A.tcount[i] = 0;
+      A.inst_it[i] = 1;
+      A.inst_step[i] = 0;
     }
   }
-  if (b == 0 && t == 0) *A.M += A.nsteps;
+  for (long long q = (long long)b * blockDim.x + t; q < A.ntiles; q += (long long)G * blockDim.x)
+    A.wq[q] = ((unsigned long long)epoch << 32) | (unsigned int)__ldg(&A.qdesc[q]).x;
+  if (!grid_sync(A.bar, A.status)) return;
+  if (b == 0 && t == 0) *A.epoch = epoch;
+  long long h = 0;     // the claimed entry (thread 0)
+  if (t == 0) h = (long long)atomicAdd(&A.ctl[0], 1u);
+  for (;;) {
+    const int tile = wait_entry(A, h, epoch, sm);
+    if (tile < 0) break;
+    if (t == 0) h = (long long)atomicAdd(&A.ctl[0], 1u);
+    const int i = __ldg(&A.tile_inst[tile]);
+    const bool jac = __ldcg(&A.need_jac[i]) != 0;
+    with_bucket_upto<MAXKB>(A.rank[i], [&](auto kb) { step_tile<decltype(kb)::value>(A, sm, tile, i, jac); });
+    __threadfence();
+    __syncthreads();
+    if (t == 0) sm.cnt = atomicAdd(&A.tcount[i], 1);
+    __syncthreads();
+    const int ntile_i = A.inst[i].tile1 - A.inst[i].tile0;
+    if (sm.cnt == ntile_i - 1) {
+      __threadfence();
+      update_instance(A, sm, i, epoch);
+    }
+  }
+  if (b == 0 && t == 0 && __ldcg(&A.ctl[2]) >= (unsigned int)A.count && __ldcg(A.status) == 0)
+    *A.M += A.nsteps;
 }
 
 // One residual sweep over the tiles into the per-tile partials (scratch),
@@ -935,7 +1033,10 @@ __global__ void __launch_bounds__(kFomT, 2) batch_fom_kernel(BArgs A) {
         fail = 1;
       } else if ((double)__uint_as_float(kd) <= I.tol * (1.0 + (double)__uint_as_float(ku))) {
         s_done[i] = 1;
-        if (b == 0) A.iters_fom[i] = it;
+        if (b == 0) {
+          A.iters_fom[i] = it;
+          A.fom_its[i] += it;
+        }
       } else if (it >= I.maxit) {
         if (b == 0) record_status(A.status, kStNoConv);
         fail = 1;
@@ -1460,6 +1561,7 @@ struct rom_batch {
   int grid_sweep, grid_fom, grid_lo;
   long long M;                 // online steps done by every instance
   int ntiles, nchunks, fom_maxit;
+  int steps_per_launch;        // steps of one launch of the steps kernel
   int poisoned;
   std::vector<Inst> hinst;
   std::vector<rom_config> cfg;
@@ -1566,16 +1668,23 @@ cudaError_t launch_coop(const void* fn, int grid, int block, size_t smem, BArgs&
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, s);
 }
 
+// nsteps steps of every instance, in launches of at most steps_per_launch
+// steps (the bound that sizes the work array of the steps kernel).
 cudaError_t run_steps(rom_batch* B, int nsteps) {
-  cudaError_t e = cudaMemsetAsync(B->A.ctl, 0, 8 * sizeof(unsigned int), B->stream);
-  if (e != cudaSuccess) return e;
-  B->A.nsteps = nsteps;
-  if ((e = prof_mark(B, 0)) != cudaSuccess) return e;
-  e = launch_coop((const void*)batch_steps_kernel<kLowRank>, B->grid_lo, kBT, sizeof(StepSmem), B->A, B->stream);
-  if (e != cudaSuccess) return e;
-  e = launch_coop((const void*)batch_steps_kernel<kMaxR>, B->grid_sweep, kBT, sizeof(StepSmem), B->A, B->stream);
-  if (e != cudaSuccess) return e;
-  return prof_mark(B, 0);
+  for (int done = 0; done < nsteps;) {
+    const int n = std::min(nsteps - done, B->steps_per_launch);
+    cudaError_t e = cudaMemsetAsync(B->A.ctl, 0, 8 * sizeof(unsigned int), B->stream);
+    if (e != cudaSuccess) return e;
+    B->A.nsteps = n;
+    if ((e = prof_mark(B, 0)) != cudaSuccess) return e;
+    e = launch_coop((const void*)batch_steps_kernel<kLowRank>, B->grid_lo, kBT, sizeof(StepSmem), B->A, B->stream);
+    if (e != cudaSuccess) return e;
+    e = launch_coop((const void*)batch_steps_kernel<kMaxR>, B->grid_sweep, kBT, sizeof(StepSmem), B->A, B->stream);
+    if (e != cudaSuccess) return e;
+    if ((e = prof_mark(B, 0)) != cudaSuccess) return e;
+    done += n;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t run_event(rom_batch* B) {
@@ -1694,7 +1803,7 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
   for (int i = 0; i < count; ++i) {
     const rom_config& c = cfgs[i];
     if (c.problem != ROM_BURGERS || c.precision != ROM_MIXED_FP32 || c.n_s != 0 || c.n_var != 1 ||
-        c.projection != ROM_GALERKIN || c.r < 1 || c.r > kMaxR || c.n_cells < 256 ||
+        c.projection != ROM_GALERKIN || c.time_scheme != ROM_BACKWARD_EULER || c.r < 1 || c.r > kMaxR || c.n_cells < 256 ||
         c.n_cells > 131072 || c.z < 1 || !q0s[i])
       return ROM_EINVAL;
   }
@@ -1752,6 +1861,16 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
   B->ntiles = ntiles_max;
   B->nchunks = (int)cinst.size();
   B->fom_maxit = fom_maxit;
+  // work array of the steps kernel: the first iteration's tiles plus one
+  // append of every tile per Newton iteration of every step of a launch
+  // (fom_maxit is the largest Newton limit of the batch); at most 16 steps
+  // a launch, fewer where the array would pass 4M entries
+  {
+    const long long budget = 4LL << 20;
+    long long spl = (budget / std::max(1, ntiles_max) - 1) / std::max(1, fom_maxit);
+    B->steps_per_launch = (int)std::max(1LL, std::min(16LL, spl));
+  }
+  const long long wq_cap = (long long)ntiles_max * (1 + (long long)B->steps_per_launch * fom_maxit);
   BArgs& A = B->A;
   A.count = count;
   A.ntiles = B->ntiles;
@@ -1767,7 +1886,7 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
   BA(d_ci, B->nchunks); BA(d_cc, B->nchunks); BA(d_qdesc, B->ntiles);
   BA(A.phi, phi_tot); BA(A.q_ref, vec_tot); BA(A.y_corr, vec_tot); BA(A.y_new, vec_tot); BA(A.dy, vec_tot);
   BA(A.a, (size_t)count * kMaxR); BA(A.an, (size_t)count * kMaxR); BA(A.sigma, (size_t)count * kMaxR);
-  BA(A.sweeps, count); BA(A.sweep_cols, count); BA(A.rank, count); BA(A.need_jac, count); BA(A.active, count); BA(A.iters_rom, count); BA(A.iters_fom, count);
+  BA(A.sweeps, count); BA(A.sweep_cols, count); BA(A.rank, count); BA(A.need_jac, count); BA(A.iters_rom, count); BA(A.iters_fom, count); BA(A.fom_its, count);
   BA(A.jlu, (size_t)count * kMaxR * kMaxR);
   BA(A.gpart, (size_t)B->ntiles * kPS); BA(A.gpart2, (size_t)B->ntiles * kPS);
   BA(A.mpart, (size_t)B->ntiles * kMaxR * kMaxR); BA(A.gram_part, (size_t)B->ntiles * kMaxR * kMaxR);
@@ -1777,6 +1896,8 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
   BA(A.qres, vec_tot); BA(A.yhat32, vec_tot); BA(A.qr32, vec_tot); BA(A.dq32, vec_tot); BA(A.lq32, vec_tot);
   BA(A.ev_u, (size_t)count * kMaxCore * kMaxR); BA(A.ev_anew, (size_t)count * kMaxR);
   BA(A.ev_r, (size_t)count * kMaxR * kMaxR); BA(A.ctl, 8); BA(A.M, 1); BA(A.bar, 1); BA(A.status, 1);
+  BA(A.wq, wq_cap); BA(A.tcount, count); BA(A.inst_it, count); BA(A.inst_step, count); BA(A.epoch, 1);
+  A.wq_cap = wq_cap;
   BA(B->lift, nmax);
 #undef BA
   if (e != cudaSuccess) {
@@ -1804,9 +1925,12 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
       cudaMemsetAsync(A.need_jac, 0, sizeof(int) * count, s) != cudaSuccess ||
       cudaMemsetAsync(A.iters_rom, 0, sizeof(int) * count, s) != cudaSuccess ||
       cudaMemsetAsync(A.iters_fom, 0, sizeof(int) * count, s) != cudaSuccess ||
+      cudaMemsetAsync(A.fom_its, 0, sizeof(long long) * count, s) != cudaSuccess ||
       cudaMemsetAsync(A.sweeps, 0, sizeof(long long) * count, s) != cudaSuccess ||
       cudaMemsetAsync(A.sweep_cols, 0, sizeof(long long) * count, s) != cudaSuccess ||
       cudaMemsetAsync(A.M, 0, sizeof(long long), s) != cudaSuccess ||
+      cudaMemsetAsync(A.epoch, 0, sizeof(unsigned int), s) != cudaSuccess ||
+      cudaMemsetAsync(A.wq, 0, sizeof(unsigned long long) * wq_cap, s) != cudaSuccess ||
       cudaMemsetAsync(A.bar, 0, sizeof(GridBarrier), s) != cudaSuccess ||
       cudaMemsetAsync(A.status, 0, sizeof(int), s) != cudaSuccess)
     return fail(ROM_ECUDA);
@@ -2027,7 +2151,24 @@ rom_status rom_batch_profile(rom_batch* B, int32_t enable) {
   for (int p = 0; p < 3; ++p) { B->prof_ms[p] = 0.0; B->prof_cnt[p] = 0; }
   BCK(cudaMemsetAsync(B->A.sweeps, 0, sizeof(long long) * B->count, B->stream));
   BCK(cudaMemsetAsync(B->A.sweep_cols, 0, sizeof(long long) * B->count, B->stream));
+  BCK(cudaMemsetAsync(B->A.fom_its, 0, sizeof(long long) * B->count, B->stream));
   BCK(cudaStreamSynchronize(B->stream));
+  return ROM_OK;
+}
+
+rom_status rom_batch_fom_work(rom_batch* B, int64_t* row_iterations, double* fom_bytes) {
+  if (!B) return ROM_EINVAL;
+  if (B->poisoned) return ROM_ESTATE;
+  std::vector<long long> it(B->count);
+  BCK(cudaMemcpyAsync(it.data(), B->A.fom_its, sizeof(long long) * B->count, cudaMemcpyDeviceToHost,
+                      B->stream));
+  BCK(cudaStreamSynchronize(B->stream));
+  long long rows = 0;
+  for (int i = 0; i < B->count; ++i) rows += (long long)B->hinst[i].n * it[i];
+  if (row_iterations) *row_iterations = rows;
+  // a Newton iteration of backward Euler reads the iterate and the previous
+  // state and writes the update: three FP64 words per row
+  if (fom_bytes) *fom_bytes = 24.0 * (double)rows;
   return ROM_OK;
 }
 

@@ -508,9 +508,10 @@ __global__ void __launch_bounds__(kBlock) euler_galerkin_kernel(StepArgs A) {
     __syncthreads();
     bool conv = false;
     int it;
-    for (it = 1; it <= A.max_iter; ++it) {
+    const int nit = A.explicit_rk ? 4 : A.max_iter;   // SSPRK(4,3): four stages (App. D)
+    for (it = 1; it <= nit; ++it) {
       const int par = it & 1;
-      const bool jac_it = (it == 1);
+      const bool jac_it = !A.explicit_rk && (it == 1);
       // lift the three variables on cells c0-1 .. c1 (ends clamped: ghost cells)
       for (int e = t; e < 3 * W2; e += blockDim.x) {
         int v = e / W2, cc = e % W2;
@@ -649,6 +650,22 @@ __global__ void __launch_bounds__(kBlock) euler_galerkin_kernel(StepArgs A) {
         lu_factor(s_J, s_piv, k);
       }
       grid_reduce_cols(part, G, stride, k, s_g);
+      if (A.explicit_rk) {
+        // stage: x <- x + dt/2 Phi^T D f(x); after the third, x <- 2/3 a^n + 1/3 x
+        int bad = 0;
+        for (int j = t; j < k; j += blockDim.x) {
+          double v = s_a[j] + 0.5 * A.dt * s_g[j];
+          if (it == 3) v = (2.0 / 3.0) * s_ap[j] + (1.0 / 3.0) * v;
+          s_a[j] = v;
+          bad |= !isfinite(v);
+        }
+        if (__syncthreads_or(bad)) {
+          if (b == 0 && t == 0) record_status(A.status, kStNonFinite);
+          return;
+        }
+        if (it == 4) conv = true;
+        continue;
+      }
       for (int j = t; j < k; j += blockDim.x) {
         double gg = s_a[j] - s_ap[j] - A.dt * s_g[j];
         s_x[j] = (float)(-gg);
@@ -681,7 +698,7 @@ __global__ void __launch_bounds__(kBlock) euler_galerkin_kernel(StepArgs A) {
       }
       if (s_sc[0] > 0.0) { conv = true; break; }
     }
-    it_total = conv ? it : A.max_iter;
+    it_total = A.explicit_rk ? 0 : (conv ? it : A.max_iter);
     if (!conv) {
       if (b == 0 && t == 0) record_status(A.status, kStNoConv);
       return;

@@ -287,6 +287,41 @@ cudaError_t launch_fom_step(const FomParams& p, const double* q_prev, double* q,
                                      dim3(threads), args, 0, s);
 }
 
+namespace {
+
+// One stage of the four-stage, third-order SSP Runge-Kutta scheme (App. D)
+// given f = f(x): out = x + h/2 f, or out = 2/3 u0 + 1/3 (x + h/2 f) in the
+// third stage. Works on the whole state vector (n entries, any layout).
+__global__ void rk_stage_kernel(const double* __restrict__ x, const double* __restrict__ f,
+                                const double* __restrict__ u0, double* __restrict__ out, int64_t n,
+                                double h2, int third) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v = x[i] + h2 * f[i];
+    if (third) v = (2.0 / 3.0) * u0[i] + (1.0 / 3.0) * v;
+    out[i] = v;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_fom_explicit_step(const FomParams& p, int n_var, const double* q_prev, double* q,
+                                     double* w1, double* w2, double* f, cudaStream_t s) {
+  const int64_t n = p.n_cells * n_var;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  const double h2 = 0.5 * p.h;
+  const double* x[4] = {q_prev, w1, w2, w1};
+  double* o[4] = {w1, w2, w1, q};
+  for (int st = 0; st < 4; ++st) {
+    cudaError_t e = launch_fom_rhs(p, x[st], f, s);
+    if (e != cudaSuccess) return e;
+    rk_stage_kernel<<<blocks, 256, 0, s>>>(x[st], f, q_prev, o[st], n, h2, st == 2 ? 1 : 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // Wait bound of this translation unit's kernels (see rom_internal.cuh).
 cudaError_t set_wait_limit_fom(long long cycles) { return set_wait_limit_here(cycles); }
 

@@ -12,7 +12,8 @@
 //  2. R = U_R S V_R^T by one-sided Jacobi on the columns of R (one CTA, FP64,
 //     round-robin order of disjoint pairs, one warp per pair), which resolves
 //     the small singular values to high relative accuracy.
-//  3. U = Q U_R (the leading columns only, on the caller's side).
+//  3. U = Q U_R (on the caller's side); V = the accumulated rotations when
+//     asked for (the gradient pass needs every triplet).
 #include <cfloat>
 #include <cmath>
 
@@ -52,8 +53,11 @@ constexpr int kJT = 1024;
 // of R are rotated pairwise until orthogonal; their norms are the singular
 // values and the normalised columns the left singular vectors. Output:
 // U (w x w row-major, column c = c-th singular direction by descending
-// singular value) and s (w).
-__global__ void __launch_bounds__(kJT) jacobi_svd_kernel(const double* R, int w, double* U, double* s_out) {
+// singular value) and s (w). With Vw non-null the rotations are also applied
+// to the columns of J = I (Vw, column-major, global memory): R J = U S, so
+// V = J, written row-major to V_out in the same column order as U.
+__global__ void __launch_bounds__(kJT) jacobi_svd_kernel(const double* R, int w, double* U, double* s_out,
+                                                         double* Vw, double* V_out) {
   extern __shared__ __align__(16) double sm[];
   double* X = sm;                 // column-major: X[col * w + row]
   double* nrm = X + w * w;        // w
@@ -63,6 +67,7 @@ __global__ void __launch_bounds__(kJT) jacobi_svd_kernel(const double* R, int w,
   for (int e = t; e < w * w; e += kJT) {
     const int row = e / w, col = e % w;
     X[col * w + row] = R[e];
+    if (Vw) Vw[col * w + row] = (row == col) ? 1.0 : 0.0;
   }
   __syncthreads();
   const int m = (w % 2) ? w + 1 : w;       // players; an odd w has one idle player
@@ -97,6 +102,12 @@ __global__ void __launch_bounds__(kJT) jacobi_svd_kernel(const double* R, int w,
             X[p * w + c] = cs * xp - sn * xq;
             X[q * w + c] = sn * xp + cs * xq;
           }
+          if (Vw)
+            for (int c = lane; c < w; c += 32) {
+              const double vp = Vw[p * w + c], vq = Vw[q * w + c];
+              Vw[p * w + c] = cs * vp - sn * vq;
+              Vw[q * w + c] = sn * vp + cs * vq;
+            }
           if (lane == 0) s_rot = 1;
         }
       }
@@ -127,14 +138,15 @@ __global__ void __launch_bounds__(kJT) jacobi_svd_kernel(const double* R, int w,
     const int src = order[c];
     const double nn = nrm[src];
     U[e] = nn > 0.0 ? X[src * w + row] / nn : 0.0;
+    if (Vw) V_out[e] = Vw[src * w + row];
   }
 }
 
 }  // namespace
 
 cudaError_t pod_thin_svd(const double* X, int64_t n, int w, double* Q, double* R, double* U, double* s,
-                         double* work, double* part, int grid, cudaStream_t st) {
-  if (w < 1 || w > 128) return cudaErrorInvalidValue;
+                         double* work, double* part, int grid, cudaStream_t st, double* V, double* Vwork) {
+  if (w < 1 || w > 128 || (V == nullptr) != (Vwork == nullptr)) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(R, 0, sizeof(double) * w * w, st);
   if (e != cudaSuccess) return e;
   double* c = work;                 // w
@@ -162,7 +174,7 @@ cudaError_t pod_thin_svd(const double* X, int64_t n, int w, double* Q, double* R
   if ((e = cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
       cudaSuccess)
     return e;
-  jacobi_svd_kernel<<<1, kJT, smem, st>>>(R, w, U, s);
+  jacobi_svd_kernel<<<1, kJT, smem, st>>>(R, w, U, s, Vwork, V);
   return cudaGetLastError();
 }
 

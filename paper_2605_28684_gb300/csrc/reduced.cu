@@ -10,6 +10,11 @@
 // formed in FP32 once per step at a^n and factorised by LU with partial
 // pivoting in FP32 (a chord iteration). Stopping rule as the oracle:
 // max|delta| <= tol (1 + max|a|).
+// The explicit form (App. D, the RDE solver's scheme) advances the same
+// right-hand sides da/dt = Phi^T D f (or (P^T Phi)^+ P^T D f) by the
+// four-stage, third-order SSP Runge-Kutta scheme: each of the four stages is
+// one pass of the Newton loop's residual evaluation, x <- x + dt/2 rhs(x),
+// with x <- 2/3 a^n + 1/3 x after the third; no Jacobian, no iteration.
 #include <cfloat>
 #include <cmath>
 #include <type_traits>
@@ -93,9 +98,10 @@ __global__ void __launch_bounds__(kBlock) galerkin_steps_kernel(StepArgs A) {
     __syncthreads();
     bool conv = false;
     int it;
-    for (it = 1; it <= A.max_iter; ++it) {
+    const int nit = A.explicit_rk ? 4 : A.max_iter;
+    for (it = 1; it <= nit; ++it) {
       const int par = it & 1;
-      const bool jac_it = (it == 1);
+      const bool jac_it = !A.explicit_rk && (it == 1);
       // lift q~ on rows beg-1 .. end (with the periodic halo)
       for (int e = t; e < rows + 2; e += blockDim.x) {
         int64_t i = (beg - 1 + e + N) % N;
@@ -207,6 +213,21 @@ __global__ void __launch_bounds__(kBlock) galerkin_steps_kernel(StepArgs A) {
       }
       // residual g (every CTA, fixed-order sum) and Newton update
       grid_reduce_cols(part, G, stride, k, s_g);
+      if (A.explicit_rk) {
+        int bad = 0;
+        for (int j = t; j < k; j += blockDim.x) {
+          double v = s_a[j] + 0.5 * A.dt * s_g[j];
+          if (it == 3) v = (2.0 / 3.0) * s_ap[j] + (1.0 / 3.0) * v;
+          s_a[j] = v;
+          bad |= !isfinite(v);
+        }
+        if (__syncthreads_or(bad)) {
+          if (b == 0 && t == 0) record_status(A.status, kStNonFinite);
+          return;
+        }
+        if (it == 4) conv = true;
+        continue;
+      }
       for (int j = t; j < k; j += blockDim.x) {
         double g = s_a[j] - s_ap[j] - A.dt * s_g[j];
         s_x[j] = (float)(-g);
@@ -240,7 +261,7 @@ __global__ void __launch_bounds__(kBlock) galerkin_steps_kernel(StepArgs A) {
       }
       if (s_sc[0] > 0.0) { conv = true; break; }
     }
-    it_total = conv ? it : A.max_iter;
+    it_total = A.explicit_rk ? 0 : (conv ? it : A.max_iter);
     if (!conv) {
       if (b == 0 && t == 0) record_status(A.status, kStNoConv);
       return;
@@ -310,7 +331,8 @@ __global__ void __launch_bounds__(kBlock) hyper_steps_kernel(StepArgs A) {
     __syncthreads();
     bool conv = false;
     int it;
-    for (it = 1; it <= A.max_iter; ++it) {
+    const int nit = A.explicit_rk ? 4 : A.max_iter;
+    for (it = 1; it <= nit; ++it) {
       // lift at the 3 stencil rows of every sample
       for (int e = t; e < nm; e += blockDim.x) {
         const double* row = s_mesh + (size_t)e * k;
@@ -325,7 +347,7 @@ __global__ void __launch_bounds__(kBlock) hyper_steps_kernel(StepArgs A) {
         s_jr3[3 * q] = rf.dl; s_jr3[3 * q + 1] = rf.dc; s_jr3[3 * q + 2] = rf.dr;
       }
       __syncthreads();
-      if (it == 1) {
+      if (it == 1 && !A.explicit_rk) {
         // sampled rows of D J_f D^-1 Phi (FP32), then J = I - dt M A (FP32)
         for (int e = t; e < ns * k; e += blockDim.x) {
           int q = e / k, l = e % k;
@@ -344,6 +366,28 @@ __global__ void __launch_bounds__(kBlock) hyper_steps_kernel(StepArgs A) {
         __syncthreads();
         lu_factor(s_J, s_piv, k);
         lu_inverse(s_J, s_piv, s_Ji, k);
+      }
+      if (A.explicit_rk) {
+        // stage: a_j <- a_j + dt/2 sum_q M_jq (d f)_q (one warp per j; the
+        // lift above read the old a, and a_j is written by its own warp only)
+        int bad = 0;
+        for (int j = wid; j < k; j += nw) {
+          double s = 0.0;
+          for (int q = lane; q < ns; q += 32) s = fma(A.minv[(size_t)j * ns + q], s_f[q], s);
+          s = warp_sum(s);
+          if (lane == 0) {
+            double v = s_a[j] + 0.5 * A.dt * s;
+            if (it == 3) v = (2.0 / 3.0) * s_ap[j] + (1.0 / 3.0) * v;
+            s_a[j] = v;
+            bad |= !isfinite(v);
+          }
+        }
+        if (__syncthreads_or(bad)) {
+          if (t == 0) record_status(A.status, kStNonFinite);
+          return;
+        }
+        if (it == 4) conv = true;
+        continue;
       }
       // residual g_j = a_j - a^n_j - dt sum_q M_jq (d f)_q: one warp per j
       for (int j = wid; j < k; j += nw) {
@@ -381,7 +425,7 @@ __global__ void __launch_bounds__(kBlock) hyper_steps_kernel(StepArgs A) {
       }
       if (s_sc[0] > 0.0) { conv = true; break; }
     }
-    it_total = conv ? it : A.max_iter;
+    it_total = A.explicit_rk ? 0 : (conv ? it : A.max_iter);
     if (!conv) {
       if (t == 0) record_status(A.status, kStNoConv);
       return;

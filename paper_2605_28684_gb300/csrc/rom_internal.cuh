@@ -355,6 +355,10 @@ struct FomScratch {
 
 // Host launchers (fom.cu). q_dev receives the new state; q_prev_dev is read only.
 cudaError_t launch_fom_rhs(const FomParams& p, const double* q, double* f, cudaStream_t s);
+// One SSPRK(4,3) step of the FOM (App. D) over n_cells * n_var entries; w1,
+// w2 and f are caller-owned scratch vectors of that length (fom.cu).
+cudaError_t launch_fom_explicit_step(const FomParams& p, int n_var, const double* q_prev, double* q,
+                                     double* w1, double* w2, double* f, cudaStream_t s);
 cudaError_t launch_fom_step(const FomParams& p, const double* q_prev, double* q,
                             const FomScratch& sc, cudaStream_t s);
 size_t fom_chunk_floats();

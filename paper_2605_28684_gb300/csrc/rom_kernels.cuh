@@ -67,6 +67,7 @@ struct StepArgs {
   double nu, gamma, dt, tol;
   int max_iter;
   int nsteps;
+  int explicit_rk;      // 1: SSPRK(4,3) stages instead of backward-Euler Newton (App. D)
   double* partials;     // 2 * grid * (KM + 2)
   float* jpartials;     // grid * kMaxR * kMaxR
   float* jac;           // kMaxR * kMaxR
@@ -277,27 +278,18 @@ struct AdjA0Args {
   double* acc;
 };
 cudaError_t launch_adj_a0(const AdjA0Args& A, int grid, cudaStream_t s);
-// X = d (Q - q_ref 1^T), N x w
-cudaError_t launch_adj_xhat(int64_t n, int w, const double* Q, const double* q_ref, double d,
-                            double* X, cudaStream_t s);
-// small dense pieces of the POD adjoint (see adjoint.cu)
+// small dense pieces of the POD adjoint over all w triplets (see adjoint.cu)
 struct AdjPodArgs {
   int64_t n;
   int w, k;
-  const double* s;        // k kept singular values
+  const double* s;        // w singular values, descending
   const double* sbar;     // k
-  const double* V0;       // w x k row-major: X^T U
-  const double* Uh;       // k x k row-major: U^T Ubar
-  const double* RtR;      // w x w row-major
-  const double* RtH;      // w x k row-major
-  double* Y;              // w x k row-major out
-  double* C;              // k x k row-major out (coefficients of U in g)
-  double* Ma;             // k x w row-major out
-  double* Mb;             // k x w row-major out
-  double* Ys;             // w x k row-major out: Y / s^2
-  double* sinv2;          // k x k row-major out: diag(1 / s^2)
+  const double* A;        // w x k row-major: U^T Ubar
+  const double* V;        // w x w row-major: right singular vectors (columns)
+  double* B1;             // w x w row-major out
+  double* B2;             // k x w row-major out
 };
-cudaError_t launch_adj_pod_small(const AdjPodArgs& A, cudaStream_t s);
+cudaError_t launch_adj_pod_full(const AdjPodArgs& A, cudaStream_t s);
 // Qbar from Xbar (two passes around the reduction of d-bar), see adjoint.cu
 struct AdjXcArgs {
   int64_t n;
@@ -328,9 +320,12 @@ cudaError_t launch_adj_misfit(int64_t n, const double* q, const double* target, 
 size_t core_sbar_offset();
 // thin SVD of an N x w matrix (w <= 128) by CGS2 QR and one-sided Jacobi on R
 // (pod_svd.cu): U (w x w row-major) and s (w, descending) of R; Q (N x w) the
-// orthonormal factor; work >= 256 doubles; part as launch_tn's
+// orthonormal factor; work >= 256 doubles; part as launch_tn's. With V and
+// Vwork (w x w each) non-null, V (row-major) gets the right singular vectors
+// from the accumulated rotations; U and s do not depend on it.
 cudaError_t pod_thin_svd(const double* X, int64_t n, int w, double* Q, double* R, double* U, double* s,
-                         double* work, double* part, int grid, cudaStream_t st);
+                         double* work, double* part, int grid, cudaStream_t st, double* V = nullptr,
+                         double* Vwork = nullptr);
 // comparison update rules (update_rules.cu)
 cudaError_t launch_win_fill(const double* Q, int64_t ldq, const double* q_ref, const double* drow, int64_t n,
                             int count, double* win, cudaStream_t s);

@@ -38,12 +38,14 @@ struct SampleSmem {
   double X[256 * kMaxR];     // (P^T Phi)^+ columns being solved (n_s <= 256)
 };
 
-// Bitonic sort (descending value, ascending index) of 512 (value, index) pairs.
-__device__ void block_sort512(double* v, int* idx) {
-  for (int size = 2; size <= 512; size <<= 1) {
+// Bitonic sort (descending value, ascending index) of SIZE (value, index)
+// pairs in shared memory, SIZE a power of two <= 2 * blockDim.x.
+template <int SIZE>
+__device__ void block_sort(double* v, int* idx) {
+  for (int size = 2; size <= SIZE; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       __syncthreads();
-      for (int t = threadIdx.x; t < 256; t += blockDim.x) {
+      for (int t = threadIdx.x; t < SIZE / 2; t += blockDim.x) {
         int i = 2 * t - (t & (stride - 1));
         int j = i + stride;
         bool up = ((i & size) == 0);
@@ -77,6 +79,12 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
   // Each thread owns at most kRowsPerThread rows of this CTA's range and keeps
   // their remaining norms and chosen flags in registers across the pivots.
   constexpr int kRowsPerThread = 4;
+  // the first row of every thread is kept in registers across the pivots
+  // (bucket size 9; larger buckets reload it)
+  constexpr int KC = KM <= 9 ? KM : 1;
+  double x0[KC];
+#pragma unroll
+  for (int j = 0; j < KC; ++j) x0[j] = 0.0;
   double res[kRowsPerThread];
   bool taken[kRowsPerThread];
   ArgMax best{-1.0, 0x7fffffff};
@@ -87,7 +95,16 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
     taken[r] = false;
     if (i < end) {
       double s = 0.0;
-      for (int j = 0; j < k; ++j) { double x = (double)phi[j * ld + i]; s = fma(x, x, s); }
+      if (KM <= 9 && r == 0) {
+#pragma unroll
+        for (int j = 0; j < KC; ++j)
+          if (j < k) x0[j] = (double)phi[j * ld + i];
+#pragma unroll
+        for (int j = 0; j < KC; ++j)
+          if (j < k) s = fma(x0[j], x0[j], s);
+      } else {
+        for (int j = 0; j < k; ++j) { double x = (double)phi[j * ld + i]; s = fma(x, x, s); }
+      }
       res[r] = s;
       if (argmax_better(s, (int)i, best.v, best.i)) { best.v = s; best.i = (int)i; }
     }
@@ -98,7 +115,6 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
 
   // Candidate slots are double-buffered by step parity, so one grid barrier
   // per pivot suffices: step s reads slot s&1 and writes slot (s+1)&1.
-  const int wid = t >> 5, nwarp = blockDim.x >> 5;
   for (int step = 0; step < kq; ++step) {
     const size_t rd = (size_t)(step & 1), wr = (size_t)((step + 1) & 1);
     // global pivot (every CTA, same fixed-order reduction)
@@ -112,25 +128,26 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
     const int p = g.i;
     if (t == 0) sm.piv[step] = p;
     // residual direction of row p against the previous directions: classical
-    // Gram-Schmidt twice, the dot products of one pass computed by all warps
-    for (int j = t; j < k; j += blockDim.x) sm.v[j] = (double)phi[j * ld + p];
-    __syncthreads();
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int l = wid; l < step; l += nwarp) {
-        double s = 0.0;
-        for (int j = lane; j < k; j += 32) s = fma(sm.v[j], sm.q[l * kMaxR + j], s);
-        s = warp_sum(s);
-        if (lane == 0) sm.w[l] = s;
-      }
-      __syncthreads();
-      for (int j = t; j < k; j += blockDim.x) {
-        double x = sm.v[j];
-        for (int l = 0; l < step; ++l) x = fma(-sm.w[l], sm.q[l * kMaxR + j], x);
-        sm.v[j] = x;
-      }
-      __syncthreads();
-    }
+    // Gram-Schmidt twice, by warp 0 alone (lanes over the k entries; no block
+    // barriers between the dot products and the updates)
     if (t < 32) {
+      for (int j = lane; j < k; j += 32) sm.v[j] = (double)phi[j * ld + p];
+      __syncwarp();
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int l = 0; l < step; ++l) {
+          double s = 0.0;
+          for (int j = lane; j < k; j += 32) s = fma(sm.v[j], sm.q[l * kMaxR + j], s);
+          s = warp_sum(s);
+          if (lane == 0) sm.w[l] = s;
+        }
+        __syncwarp();
+        for (int j = lane; j < k; j += 32) {
+          double x = sm.v[j];
+          for (int l = 0; l < step; ++l) x = fma(-sm.w[l], sm.q[l * kMaxR + j], x);
+          sm.v[j] = x;
+        }
+        __syncwarp();
+      }
       double s = 0.0;
       for (int j = lane; j < k; j += 32) s = fma(sm.v[j], sm.v[j], s);
       s = warp_sum(s);
@@ -146,7 +163,13 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
       const int64_t i = beg + t + (int64_t)r * blockDim.x;
       if (i < end) {
         double c = 0.0;
-        for (int j = 0; j < k; ++j) c = fma((double)phi[j * ld + i], sm.q[step * kMaxR + j], c);
+        if (KM <= 9 && r == 0) {
+#pragma unroll
+          for (int j = 0; j < KC; ++j)
+            if (j < k) c = fma(x0[j], sm.q[step * kMaxR + j], c);
+        } else {
+          for (int j = 0; j < k; ++j) c = fma((double)phi[j * ld + i], sm.q[step * kMaxR + j], c);
+        }
         res[r] = fma(-c, c, res[r]);
         if (i == p) taken[r] = true;
         if (!taken[r] && argmax_better(res[r], (int)i, best.v, best.i)) { best.v = res[r]; best.i = (int)i; }
@@ -158,12 +181,18 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
   }
 
   // ---- feature-guided points: local top-m by (y_{i+1} - y_i)^2 ----
+  // Every CTA sorts its candidates (passes of 256 merged into a running top
+  // 256) and publishes its first min(m, 256) entries, their count and its
+  // m-th value (-1 if it has fewer than m). CTA 0 then gathers the entries at
+  // or above the largest published m-th value, lb: some list holds m
+  // entries >= lb, so the global top m are among them.
   const int m = A.n_s - kq;
   if (kq > 0 && !grid_sync(A.bar, A.status)) return;   // all CTAs have read the last slot
+  const int mm = m < 256 ? m : 256;
   if (m > 0) {
     for (int e = t; e < 512; e += blockDim.x) { sm.cv[e] = -1.0; sm.ci[e] = 0x7fffffff; }
     __syncthreads();
-    // rows of this CTA in passes of 256 candidates merged with the current top
+    const bool one_pass = (end - beg) <= 256;
     for (int64_t base = beg; base < end; base += 256) {
       int64_t i = base + t;
       double sc = -1.0;
@@ -177,66 +206,76 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
           ii = (int)i;
         }
       }
-      sm.cv[256 + t] = sc;
-      sm.ci[256 + t] = ii;
-      block_sort512(sm.cv, sm.ci);      // top 256 end up in [0, 256)
+      if (one_pass) {
+        sm.cv[t] = sc;
+        sm.ci[t] = ii;
+        block_sort<256>(sm.cv, sm.ci);
+      } else {
+        sm.cv[256 + t] = sc;
+        sm.ci[256 + t] = ii;
+        block_sort<512>(sm.cv, sm.ci);      // top 256 end up in [0, 256)
+      }
     }
-    const int mm = m < 256 ? m : 256;
+    int cnt = 0;                            // valid (non-negative) entries among the first mm
     for (int e = t; e < mm; e += blockDim.x) {
       A.cand_v[(size_t)b * kMaxNs + e] = sm.cv[e];
       A.cand_i[(size_t)b * kMaxNs + e] = sm.ci[e];
+      cnt += (sm.cv[e] >= 0.0) ? 1 : 0;
+    }
+    cnt = (int)block_sum((double)cnt, sm.red);
+    if (t == 0) {
+      A.chosen[b] = cnt;
+      A.resid[b] = (cnt >= m) ? sm.cv[m - 1] : -1.0;
     }
   }
   if (!grid_sync(A.bar, A.status)) return;
   if (b != 0) return;
 
   // ---- CTA 0: top-m of the G sorted candidate lists ----
-  // lb = max over lists of their m-th entry: some list holds m entries >= lb,
-  // so nothing below lb can be in the top m. The entries >= lb are gathered
-  // and sorted in shared memory; if there are more than 512 of them the lists
-  // are merged one pick at a time instead.
   if (m > 0) {
-    __shared__ int s_len[1024];
-    __shared__ int s_cnt[1024];
-    __shared__ int s_off[1025];
-    const int mm = m < 256 ? m : 256;
+    __shared__ int s_tot;
     double lb = -1.0;
-    for (int bb = t; bb < G; bb += blockDim.x) {
-      const double* lv = A.cand_v + (size_t)bb * kMaxNs;
-      int lo = 0, hi = mm;                       // valid entries have value >= 0
-      while (lo < hi) { int mid = (lo + hi) >> 1; if (__ldcg(lv + mid) >= 0.0) lo = mid + 1; else hi = mid; }
-      s_len[bb] = lo;
-      if (lo >= m) lb = fmax(lb, __ldcg(lv + m - 1));
-    }
+    for (int bb = t; bb < G; bb += blockDim.x) lb = fmax(lb, __ldcg(&A.resid[bb]));
     lb = block_max(lb, sm.red);
+    if (t == 0) s_tot = 0;
+    for (int e = t; e < 512; e += blockDim.x) { sm.cv[e] = -1.0; sm.ci[e] = 0x7fffffff; }
+    __syncthreads();
+    // each thread walks one list in batches of 8 independent loads and appends
+    // the entries >= lb (the order of appending does not matter: they are sorted)
+    bool overflow = false;
     for (int bb = t; bb < G; bb += blockDim.x) {
+      const int len = __ldcg(&A.chosen[bb]);
       const double* lv = A.cand_v + (size_t)bb * kMaxNs;
-      int lo = 0, hi = s_len[bb];
-      while (lo < hi) { int mid = (lo + hi) >> 1; if (__ldcg(lv + mid) >= lb) lo = mid + 1; else hi = mid; }
-      s_cnt[bb] = lo;
-    }
-    __syncthreads();
-    if (t == 0) {
-      int o = 0;
-      for (int bb = 0; bb < G; ++bb) { s_off[bb] = o; o += s_cnt[bb]; }
-      s_off[G] = o;
-    }
-    __syncthreads();
-    const int total = s_off[G];
-    if (total <= 512) {
-      for (int e = t; e < 512; e += blockDim.x) { sm.cv[e] = -1.0; sm.ci[e] = 0x7fffffff; }
-      __syncthreads();
-      for (int bb = t; bb < G; bb += blockDim.x) {
-        const int o = s_off[bb], c = s_cnt[bb];
-#pragma unroll 4
-        for (int e = 0; e < c; ++e) {
-          sm.cv[o + e] = __ldcg(A.cand_v + (size_t)bb * kMaxNs + e);
-          sm.ci[o + e] = __ldcg(A.cand_i + (size_t)bb * kMaxNs + e);
+      const int* li = A.cand_i + (size_t)bb * kMaxNs;
+      bool more = true;
+      for (int e0 = 0; e0 < len && more; e0 += 8) {
+        double v8[8];
+        int i8[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          v8[u] = (e0 + u < len) ? __ldcg(lv + e0 + u) : -1.0;
+          i8[u] = (e0 + u < len) ? __ldcg(li + e0 + u) : 0x7fffffff;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (v8[u] >= lb && v8[u] >= 0.0) {
+            const int o = atomicAdd(&s_tot, 1);
+            if (o < 512) { sm.cv[o] = v8[u]; sm.ci[o] = i8[u]; } else { overflow = true; }
+          } else {
+            more = false;
+          }
         }
       }
-      block_sort512(sm.cv, sm.ci);
+    }
+    __syncthreads();
+    const int total = s_tot;
+    if (!overflow && total <= 512) {
+      if (total <= 128) block_sort<128>(sm.cv, sm.ci);
+      else if (total <= 256) block_sort<256>(sm.cv, sm.ci);
+      else block_sort<512>(sm.cv, sm.ci);
       for (int e = t; e < m; e += blockDim.x) sm.piv[kq + e] = sm.ci[e];
     } else {
+      // more than 512 entries at or above lb: merge the lists one pick at a time
       __shared__ int head[1024];
       for (int bb = t; bb < G; bb += blockDim.x) head[bb] = 0;
       __syncthreads();
@@ -245,7 +284,7 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
         int gb = -1;
         for (int bb = t; bb < G; bb += blockDim.x) {
           int h = head[bb];
-          if (h < s_len[bb]) {
+          if (h < __ldcg(&A.chosen[bb])) {
             double v = A.cand_v[(size_t)bb * kMaxNs + h];
             int i = A.cand_i[(size_t)bb * kMaxNs + h];
             if (argmax_better(v, i, g.v, g.i)) { g.v = v; g.i = i; }
@@ -254,7 +293,7 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
         g = block_argmax(g, sm.red, sm.redi);
         for (int bb = t; bb < G; bb += blockDim.x) {
           int h = head[bb];
-          if (h < s_len[bb] && A.cand_i[(size_t)bb * kMaxNs + h] == g.i) gb = bb;
+          if (h < __ldcg(&A.chosen[bb]) && A.cand_i[(size_t)bb * kMaxNs + h] == g.i) gb = bb;
         }
         __syncthreads();
         if (gb >= 0) head[gb] += 1;
@@ -268,13 +307,26 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
   for (int s = t; s < ns; s += blockDim.x) A.samples[s] = sm.piv[s];
 
   // ---- stencil mesh: Phi, q_ref, D on rows i-1, i, i+1 of every sample ----
-  for (int e = t; e < ns * 3; e += blockDim.x) {
-    int s = e / 3, o = e % 3;
-    int64_t i = ((int64_t)sm.piv[s] + (o - 1) + N) % N;
-    double* row = A.mesh + (size_t)e * kMeshStride;
-    for (int j = 0; j < kMaxR; ++j) row[j] = (j < k) ? (double)phi[j * ld + i] : 0.0;
-    row[kMaxR] = A.q_ref[i];
-    row[kMaxR + 1] = A.drow[i];
+  // one warp per mesh row, lanes over its kMaxR + 2 entries; the basis rows of
+  // the samples themselves (o = 1) are also staged in shared memory (X) for
+  // the Gram matrix
+  double* Ps = sm.X;                       // ns x k (row-major), rows of P^T Phi
+  {
+    const int wid = t >> 5, nw = blockDim.x >> 5;
+    for (int e = wid; e < ns * 3; e += nw) {
+      const int s = e / 3, o = e % 3;
+      const int64_t i = ((int64_t)sm.piv[s] + (o - 1) + N) % N;
+      double* row = A.mesh + (size_t)e * kMeshStride;
+      for (int j = lane; j < kMaxR; j += 32) {
+        const double v = (j < k) ? (double)phi[j * ld + i] : 0.0;
+        row[j] = v;
+        if (o == 1 && j < k) Ps[s * k + j] = v;
+      }
+      if (lane == 0) {
+        row[kMaxR] = A.q_ref[i];
+        row[kMaxR + 1] = A.drow[i];
+      }
+    }
   }
   __syncthreads();
   // ---- G = A^T A with A = P^T Phi (k x k), FP64: one warp per entry ----
@@ -283,48 +335,48 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
     for (int e = wid; e < k * k; e += nw) {
       int r = e / k, c = e % k;
       double s = 0.0;
-      for (int q = lane; q < ns; q += 32)
-        s = fma(A.mesh[(size_t)(3 * q + 1) * kMeshStride + r], A.mesh[(size_t)(3 * q + 1) * kMeshStride + c], s);
+      for (int q = lane; q < ns; q += 32) s = fma(Ps[q * k + r], Ps[q * k + c], s);
       s = warp_sum(s);
       if (lane == 0) sm.G[r * kMaxR + c] = s;
     }
   }
   __syncthreads();
-  // Cholesky (lower), one column at a time
-  for (int j = 0; j < k; ++j) {
-    if (t < 32) {
+  // Cholesky (lower) by warp 0, one column at a time
+  if (t < 32) {
+    for (int j = 0; j < k; ++j) {
       double s = 0.0;
       for (int l = lane; l < j; l += 32) s += sm.G[j * kMaxR + l] * sm.G[j * kMaxR + l];
       s = warp_sum(s);
       if (lane == 0) sm.G[j * kMaxR + j] = sqrt(fmax(sm.G[j * kMaxR + j] - s, DBL_MIN));
+      __syncwarp();
+      for (int i = j + 1 + lane; i < k; i += 32) {
+        double v = sm.G[i * kMaxR + j];
+        for (int l = 0; l < j; ++l) v -= sm.G[i * kMaxR + l] * sm.G[j * kMaxR + l];
+        sm.G[i * kMaxR + j] = v / sm.G[j * kMaxR + j];
+      }
+      __syncwarp();
     }
-    __syncthreads();
-    for (int i = j + 1 + t; i < k; i += blockDim.x) {
-      double s = sm.G[i * kMaxR + j];
-      for (int l = 0; l < j; ++l) s -= sm.G[i * kMaxR + l] * sm.G[j * kMaxR + l];
-      sm.G[i * kMaxR + j] = s / sm.G[j * kMaxR + j];
-    }
-    __syncthreads();
   }
-  // M = G^{-1} A^T: each sample column q solves L L^T x = A(q, :)^T, with x in
-  // shared memory (X[q * k + i])
-  double* X = sm.X;
+  __syncthreads();
+  // M = G^{-1} A^T: each sample column q solves L L^T x = A(q, :)^T; the
+  // solution overwrites the staged row q in shared memory
   for (int q = t; q < ns; q += blockDim.x) {
+    double* x = Ps + q * k;
     for (int i = 0; i < k; ++i) {
-      double s = A.mesh[(size_t)(3 * q + 1) * kMeshStride + i];
-      for (int l = 0; l < i; ++l) s -= sm.G[i * kMaxR + l] * X[q * k + l];
-      X[q * k + i] = s / sm.G[i * kMaxR + i];
+      double s = x[i];
+      for (int l = 0; l < i; ++l) s -= sm.G[i * kMaxR + l] * x[l];
+      x[i] = s / sm.G[i * kMaxR + i];
     }
     for (int i = k - 1; i >= 0; --i) {
-      double s = X[q * k + i];
-      for (int l = i + 1; l < k; ++l) s -= sm.G[l * kMaxR + i] * X[q * k + l];
-      X[q * k + i] = s / sm.G[i * kMaxR + i];
+      double s = x[i];
+      for (int l = i + 1; l < k; ++l) s -= sm.G[l * kMaxR + i] * x[l];
+      x[i] = s / sm.G[i * kMaxR + i];
     }
   }
   __syncthreads();
   for (int e = t; e < A.r * ns; e += blockDim.x) {
     int i = e / ns, q = e % ns;
-    A.minv[e] = (i < k) ? X[q * k + i] : 0.0;
+    A.minv[e] = (i < k) ? Ps[q * k + i] : 0.0;
   }
 }
 

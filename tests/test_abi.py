@@ -66,6 +66,12 @@ def test_invalid_configs_rejected(lib):
         c = synth.config_burgers_small()
         c.update_rule, c.window, c.precision = rule, window, prec
         bad.append(c)
+    # time schemes: unknown; the explicit form is Galerkin, FP64 and iSVD only
+    for field, val in [("time_scheme", 2), ("projection", 1), ("precision", 1), ("update_rule", 1)]:
+        c = synth.config_burgers_small()
+        c.time_scheme, c.window = 1, 8
+        setattr(c, field, val)
+        bad.append(c)
     for c in bad:
         cfg = g.make_config(c)
         ctx = ctypes.c_void_p()
@@ -96,7 +102,7 @@ def test_invalid_batches_rejected(lib):
         return rc, out.value
 
     for field, val in [("precision", 0), ("problem", 1), ("n_s", 4), ("r", 65), ("n_cells", 128),
-                       ("z", 0), ("projection", 1)]:
+                       ("z", 0), ("projection", 1), ("time_scheme", 1)]:
         cfgs = synth.config_batch(2)
         setattr(cfgs[1], field, val)
         rc, out = init(cfgs)
@@ -159,6 +165,7 @@ def test_context_calls_reject_a_null_context(lib):
     assert lib.rom_batch_layout(None, None, None, None, None, None, None) == EINVAL
     assert lib.rom_batch_profile(None, 1) == EINVAL
     assert lib.rom_batch_work(None, None, None) == EINVAL
+    assert lib.rom_batch_fom_work(None, None, None) == EINVAL
     assert lib.rom_batch_profile_read(None, dp, i64) == EINVAL
     for code in range(8):
         assert lib.rom_status_string(code)
