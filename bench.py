@@ -632,6 +632,15 @@ def main():
         lspg = synth.config_burgers_small()
         lspg.projection = 1
         forms["lspg_burgers_n512_r10_z10_fp64"] = timed_single(g, lspg, 2000)
+        # the explicit form (SSPRK(4,3) fine and reduced steps, coarse BE
+        # correction): Sod Galerkin at the configured size, and Burgers
+        # DEIM-Galerkin with r QDEIM + r feature-guided points
+        sod_x = synth.config_sod()
+        sod_x.time_scheme = 1
+        forms["sod_explicit_galerkin_n8192_r40_z10_fp64"] = timed_single(g, sod_x, 500)
+        bx = synth.config_burgers_small()
+        bx.time_scheme, bx.n_s = 1, 20
+        forms["burgers_explicit_deim_n512_r10_ns20_fp64"] = timed_single(g, bx, 2000)
         forms["adjoint"] = timed_adjoint(g)
         forms["paper_burgers_sweep"] = timed_paper_sweep(g)
 

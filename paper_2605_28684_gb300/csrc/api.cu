@@ -235,6 +235,9 @@ SampleArgs sample_args(rom_ctx* ctx) {
   S.resid = ctx->d.resid_norm;
   S.cand_v = ctx->d.cand_v;
   S.cand_i = ctx->d.cand_i;
+  S.merge_v = ctx->d.merge_v;
+  S.merge_i = ctx->d.merge_i;
+  S.merge_ctr = ctx->d.merge_ctr;
   S.qdir = ctx->d.qdeim_q;
   S.mesh = ctx->d.mesh;
   S.minv = ctx->d.minv;
@@ -443,7 +446,7 @@ void free_state(rom_ctx* ctx) {
   void* ptrs[] = {d.q_ref, d.y_corr, d.y_tmp, d.yhat, d.qres, d.lifted, d.dvals, d.drow, d.dinv, d.phi,
                   d.phi32, d.gram, d.sigma, d.a, d.a_prev, d.rank, d.core, d.ubar, d.partials,
                   d.jpartials, d.jac, d.samples, d.chosen, d.resid_norm, d.qdeim_q, d.cand_v,
-                  d.cand_i, d.mesh, d.minv, d.bar, d.status, d.iters_rom, d.iters_fom, d.maxbuf,
+                  d.cand_i, d.merge_v, d.merge_i, d.merge_ctr, d.mesh, d.minv, d.bar, d.status, d.iters_rom, d.iters_fom, d.maxbuf,
                   d.fom_chunk, d.npart, d.win, d.dwork, d.dsm, d.dpart, ctx->q_train};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -531,7 +534,8 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
   ALLOC(d.partials, (size_t)3 * G * (kMaxCore + 2)); ALLOC(d.jpartials, (size_t)G * kMaxR * kMaxR);
   ALLOC(d.jac, kMaxR * kMaxR); ALLOC(d.samples, ns); ALLOC(d.chosen, N); ALLOC(d.resid_norm, N);
   ALLOC(d.qdeim_q, kMaxR * kMaxR); ALLOC(d.cand_v, (size_t)G * kMaxNs);
-  ALLOC(d.cand_i, (size_t)G * kMaxNs); ALLOC(d.mesh, (size_t)ns * 3 * kMeshStride);
+  ALLOC(d.cand_i, (size_t)G * kMaxNs); ALLOC(d.merge_v, (size_t)G * kMaxNs);
+  ALLOC(d.merge_i, (size_t)G * kMaxNs); ALLOC(d.merge_ctr, 2); ALLOC(d.mesh, (size_t)ns * 3 * kMeshStride);
   ALLOC(d.minv, (size_t)kMaxR * ns); ALLOC(d.bar, 1); ALLOC(d.status, 1); ALLOC(d.iters_rom, 1);
   ALLOC(d.iters_fom, 1); ALLOC(d.maxbuf, 4); ALLOC(d.fom_chunk, fom_chunk_floats());
   ALLOC(ctx->q_train, (size_t)N * w);

@@ -404,6 +404,9 @@ struct DevState {
   double* qdeim_q;      // kMaxR * kMaxR (orthonormal pivot directions)
   double* cand_v;       // grid * kMaxNs candidate values
   int* cand_i;          // grid * kMaxNs candidate indices
+  double* merge_v;      // grid * kMaxNs merged candidates (values)
+  int* merge_i;         // grid * kMaxNs merged candidates (indices)
+  unsigned int* merge_ctr;  // 2 merge counters
   double* mesh;         // n_s * 3 * (kMaxR + 2): Phi rows, q_ref, d of the stencil
   double* minv;         // r x n_s  ((P^T Phi)^+, row-major r x n_s)
   // control

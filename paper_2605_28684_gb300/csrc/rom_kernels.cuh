@@ -117,6 +117,9 @@ struct SampleArgs {
   double* resid;        // n
   double* cand_v;       // grid * kMaxNs
   int* cand_i;          // grid * kMaxNs
+  double* merge_v;      // grid * kMaxNs: entries at or above the merge threshold
+  int* merge_i;         // grid * kMaxNs
+  unsigned int* merge_ctr;  // 2: entries appended, CTAs done
   double* qdir;         // kMaxR * kMaxR
   double* mesh;         // n_s x 3 x (kMaxR + 2)
   double* minv;         // r x n_s

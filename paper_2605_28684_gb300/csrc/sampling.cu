@@ -32,7 +32,9 @@ struct SampleSmem {
   double red[64];
   int redi[32];
   double G[kMaxR * kMaxR];   // A^T A and its Cholesky factor
+  double gdinv[kMaxR];       // 1 / L_jj
   int piv[kMaxNs];
+  long long off;
   double cv[512];
   int ci[512];
   double X[256 * kMaxR];     // (P^T Phi)^+ columns being solved (n_s <= 256)
@@ -75,6 +77,9 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
   const int kq = k < A.n_s ? k : A.n_s;
   const int lane = t & 31;
 
+  // the merge counters (entries appended, CTAs done) are reset here, ahead of
+  // the grid barriers that separate this from their first use
+  if (b == 0 && t == 0) { A.merge_ctr[0] = 0u; A.merge_ctr[1] = 0u; }
   // ---- initial residual norms and first local argmax ----
   // Each thread owns at most kRowsPerThread rows of this CTA's range and keeps
   // their remaining norms and chosen flags in registers across the pivots.
@@ -229,50 +234,61 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
     }
   }
   if (!grid_sync(A.bar, A.status)) return;
-  if (b != 0) return;
 
-  // ---- CTA 0: top-m of the G sorted candidate lists ----
+  // ---- top-m of the G sorted candidate lists ----
+  // Every CTA finds lb (the largest published m-th value) and appends its own
+  // entries >= lb to one compact array (some list holds m such entries, so
+  // the global top m are among them; the order of appending does not matter:
+  // CTA 0 sorts them by value, then index). CTA 0 waits for the G appends
+  // (a bounded wait), sorts and keeps the first m.
   if (m > 0) {
-    __shared__ int s_tot;
     double lb = -1.0;
     for (int bb = t; bb < G; bb += blockDim.x) lb = fmax(lb, __ldcg(&A.resid[bb]));
     lb = block_max(lb, sm.red);
-    if (t == 0) s_tot = 0;
-    for (int e = t; e < 512; e += blockDim.x) { sm.cv[e] = -1.0; sm.ci[e] = 0x7fffffff; }
+    int c = 0;                               // this CTA's entries >= lb (a prefix: sorted)
+    for (int e = t; e < mm; e += blockDim.x) c += (sm.cv[e] >= lb && sm.cv[e] >= 0.0) ? 1 : 0;
+    c = (int)block_sum((double)c, sm.red);
+    if (t == 0) sm.off = (c > 0) ? (long long)atomicAdd(&A.merge_ctr[0], (unsigned int)c) : 0;
     __syncthreads();
-    // each thread walks one list in batches of 8 independent loads and appends
-    // the entries >= lb (the order of appending does not matter: they are sorted)
-    bool overflow = false;
-    for (int bb = t; bb < G; bb += blockDim.x) {
-      const int len = __ldcg(&A.chosen[bb]);
-      const double* lv = A.cand_v + (size_t)bb * kMaxNs;
-      const int* li = A.cand_i + (size_t)bb * kMaxNs;
-      bool more = true;
-      for (int e0 = 0; e0 < len && more; e0 += 8) {
-        double v8[8];
-        int i8[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          v8[u] = (e0 + u < len) ? __ldcg(lv + e0 + u) : -1.0;
-          i8[u] = (e0 + u < len) ? __ldcg(li + e0 + u) : 0x7fffffff;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          if (v8[u] >= lb && v8[u] >= 0.0) {
-            const int o = atomicAdd(&s_tot, 1);
-            if (o < 512) { sm.cv[o] = v8[u]; sm.ci[o] = i8[u]; } else { overflow = true; }
-          } else {
-            more = false;
-          }
+    const long long off = sm.off;
+    for (int e = t; e < c; e += blockDim.x) {
+      A.merge_v[off + e] = sm.cv[e];
+      A.merge_i[off + e] = sm.ci[e];
+    }
+    __threadfence();
+    __syncthreads();
+    if (t == 0) atomicAdd(&A.merge_ctr[1], 1u);
+  }
+  if (b != 0) return;
+  if (m > 0) {
+    __shared__ int s_ok;
+    if (t == 0) {
+      const volatile unsigned int* done = &A.merge_ctr[1];
+      const long long limit = c_wait_limit;
+      const long long t0 = clock64();
+      int ok = 1;
+      while (*done < (unsigned int)G) {
+        if (clock64() - t0 > limit) {
+          record_status(A.status, kStTimeout);
+          ok = 0;
+          break;
         }
       }
+      __threadfence();
+      s_ok = ok;
     }
     __syncthreads();
-    const int total = s_tot;
-    if (!overflow && total <= 512) {
+    if (!s_ok) return;
+    const int total = (int)__ldcg(&A.merge_ctr[0]);
+    if (total <= 512) {
+      for (int e = t; e < 512; e += blockDim.x) {
+        sm.cv[e] = (e < total) ? __ldcg(&A.merge_v[e]) : -1.0;
+        sm.ci[e] = (e < total) ? __ldcg(&A.merge_i[e]) : 0x7fffffff;
+      }
       if (total <= 128) block_sort<128>(sm.cv, sm.ci);
       else if (total <= 256) block_sort<256>(sm.cv, sm.ci);
       else block_sort<512>(sm.cv, sm.ci);
+      __syncthreads();
       for (int e = t; e < m; e += blockDim.x) sm.piv[kq + e] = sm.ci[e];
     } else {
       // more than 512 entries at or above lb: merge the lists one pick at a time
@@ -307,24 +323,53 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
   for (int s = t; s < ns; s += blockDim.x) A.samples[s] = sm.piv[s];
 
   // ---- stencil mesh: Phi, q_ref, D on rows i-1, i, i+1 of every sample ----
-  // one warp per mesh row, lanes over its kMaxR + 2 entries; the basis rows of
-  // the samples themselves (o = 1) are also staged in shared memory (X) for
-  // the Gram matrix
+  // a warp takes kSpw samples per pass and issues all their loads (lanes over
+  // the kMaxR basis entries of the three rows; lanes 0..2 q_ref and D) before
+  // any store; the basis rows of the samples themselves (o = 1) are also
+  // staged in shared memory (X) for the Gram matrix
   double* Ps = sm.X;                       // ns x k (row-major), rows of P^T Phi
   {
+    constexpr int kSpw = 2;
     const int wid = t >> 5, nw = blockDim.x >> 5;
-    for (int e = wid; e < ns * 3; e += nw) {
-      const int s = e / 3, o = e % 3;
-      const int64_t i = ((int64_t)sm.piv[s] + (o - 1) + N) % N;
-      double* row = A.mesh + (size_t)e * kMeshStride;
-      for (int j = lane; j < kMaxR; j += 32) {
-        const double v = (j < k) ? (double)phi[j * ld + i] : 0.0;
-        row[j] = v;
-        if (o == 1 && j < k) Ps[s * k + j] = v;
+    for (int s0 = wid * kSpw; s0 < ns; s0 += nw * kSpw) {
+      double v[kSpw][2][3], qv[kSpw], dv[kSpw];
+#pragma unroll
+      for (int u = 0; u < kSpw; ++u) {
+        const int sidx = s0 + u;
+        const bool ok = sidx < ns;
+        const int64_t ic = ok ? (int64_t)sm.piv[sidx] : 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = lane + 32 * h;
+#pragma unroll
+          for (int o = 0; o < 3; ++o) {
+            const int64_t i = (ic + (o - 1) + N) % N;
+            v[u][h][o] = (ok && j < k) ? (double)phi[j * ld + i] : 0.0;
+          }
+        }
+        const int64_t il = (ic + ((lane < 3 ? lane : 1) - 1) + N) % N;
+        qv[u] = (ok && lane < 3) ? A.q_ref[il] : 0.0;
+        dv[u] = (ok && lane < 3) ? A.drow[il] : 0.0;
       }
-      if (lane == 0) {
-        row[kMaxR] = A.q_ref[i];
-        row[kMaxR + 1] = A.drow[i];
+#pragma unroll
+      for (int u = 0; u < kSpw; ++u) {
+        const int sidx = s0 + u;
+        if (sidx >= ns) continue;
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+          double* row = A.mesh + (size_t)(3 * sidx + o) * kMeshStride;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int j = lane + 32 * h;
+            if (j < kMaxR) row[j] = v[u][h][o];
+            if (o == 1 && j < k) Ps[sidx * k + j] = v[u][h][o];
+          }
+        }
+        if (lane < 3) {
+          double* row = A.mesh + (size_t)(3 * sidx + lane) * kMeshStride;
+          row[kMaxR] = qv[u];
+          row[kMaxR + 1] = dv[u];
+        }
       }
     }
   }
@@ -347,12 +392,17 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
       double s = 0.0;
       for (int l = lane; l < j; l += 32) s += sm.G[j * kMaxR + l] * sm.G[j * kMaxR + l];
       s = warp_sum(s);
-      if (lane == 0) sm.G[j * kMaxR + j] = sqrt(fmax(sm.G[j * kMaxR + j] - s, DBL_MIN));
+      if (lane == 0) {
+        const double djj = sqrt(fmax(sm.G[j * kMaxR + j] - s, DBL_MIN));
+        sm.G[j * kMaxR + j] = djj;
+        sm.gdinv[j] = 1.0 / djj;       // one FP64 division per column
+      }
       __syncwarp();
+      const double rj = sm.gdinv[j];
       for (int i = j + 1 + lane; i < k; i += 32) {
         double v = sm.G[i * kMaxR + j];
         for (int l = 0; l < j; ++l) v -= sm.G[i * kMaxR + l] * sm.G[j * kMaxR + l];
-        sm.G[i * kMaxR + j] = v / sm.G[j * kMaxR + j];
+        sm.G[i * kMaxR + j] = v * rj;
       }
       __syncwarp();
     }
@@ -365,12 +415,12 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
     for (int i = 0; i < k; ++i) {
       double s = x[i];
       for (int l = 0; l < i; ++l) s -= sm.G[i * kMaxR + l] * x[l];
-      x[i] = s / sm.G[i * kMaxR + i];
+      x[i] = s * sm.gdinv[i];
     }
     for (int i = k - 1; i >= 0; --i) {
       double s = x[i];
       for (int l = i + 1; l < k; ++l) s -= sm.G[l * kMaxR + i] * x[l];
-      x[i] = s / sm.G[i * kMaxR + i];
+      x[i] = s * sm.gdinv[i];
     }
   }
   __syncthreads();
