@@ -560,12 +560,20 @@ __global__ void __launch_bounds__(kT) adj_core_kernel(AdjEventArgs A) {
   }
   for (int j = t; j < n; j += kT) s[j] = A.sbar[j];
   __syncthreads();
-  // W = K^T U: row r < k: lam sigma_r U[r][:]; row k: p^T U[:k][:] + rho U[k][:]
+  // W = K^T U: row r < k: lam sigma_r U[r][:]; row k: z^T U with z = [p; rho]
+  // the core's last column. Row k of K K^T is rho z^T, so for a left singular
+  // vector u_c, z^T u_c = s_c^2 u_c[k] / rho exactly; that form keeps the
+  // relative accuracy of the small singular directions, where the dot
+  // product p^T u + rho u[k] cancels terms of size |p| down to about s_c
+  // (with lambda << 1 every direction but one is small). An empty new
+  // direction (rho = 0) keeps the dot product.
   for (int e = t; e < n * n; e += kT) {
     const int row = e / n, col = e % n;
     double v;
     if (row < k) {
       v = lam * A.sigma_old[row] * U[row * n + col];
+    } else if (rho > 0.0) {
+      v = s[col] * s[col] * U[k * n + col] / rho;
     } else {
       v = rho * U[k * n + col];
       for (int m = 0; m < k; ++m) v = fma(A.rec[2 + m], U[m * n + col], v);

@@ -523,13 +523,70 @@ __device__ __forceinline__ void compute_chunk(const TileCtx& T, int c0, const Ch
   __syncthreads();
 }
 
+// Segments per warp pass of the barrier-free sweep: keeps about 32 basis
+// loads in flight per lane.
 template <int KB>
-__device__ void step_tile(const BArgs& A, StepSmem& sm, int tile, int i, bool jac) {
-  constexpr int RPT = Rpt<KB>::v;
-  constexpr int CR = kBT * RPT;
+struct Useg {
+  static constexpr int v = KB <= 8 ? 4 : KB <= 16 ? 2 : 1;
+};
+
+// Lift, FP32 operator and projection of the tile rows [r0, r1) without a
+// block barrier: a warp takes 32 consecutive rows at a time (a segment);
+// lanes 1..30 own one row each, and lanes 0 and 31 load the rows on either
+// side, so the stencil's neighbours come from the adjacent lanes by warp
+// shuffles (the tile's outer rows are read from the neighbouring rows,
+// periodically at the instance's ends). Each row is evaluated by one lane,
+// as in the staged form; only the partial sums' grouping differs.
+template <int KB>
+__device__ __forceinline__ void stream_tile(const TileCtx& T, int r0, int r1, const float* af,
+                                            float (&acc)[KB]) {
+  constexpr int U = Useg<KB>::v;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int rows = r1 - r0;
+  const int nseg = (rows + 29) / 30;
+  float a[KB];
+#pragma unroll
+  for (int j = 0; j < KB; ++j) a[j] = af[j];
+  for (int s0 = wid * U; s0 < nseg; s0 += nw * U) {
+    float x[U][KB], q[U], dq[U], lq[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int rl = (s0 + u) * 30 + lane - 1;     // row in the tile, -1 .. rows
+      const bool live = (s0 + u) < nseg && rl <= rows;
+      int row = r0 + rl;
+      if (row < 0) row += T.N;
+      else if (row >= T.N) row -= T.N;
+      if (!live) row = r0;                          // in bounds; nothing is read there
+#pragma unroll
+      for (int j = 0; j < KB; ++j) x[u][j] = (live && j < T.k) ? __ldg(&T.phi[(size_t)j * T.N + row]) : 0.f;
+      q[u] = live ? __ldg(&T.qr[row]) : 0.f;
+      dq[u] = live ? __ldg(&T.dq[row]) : 0.f;
+      lq[u] = live ? __ldg(&T.lq[row]) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int rl = (s0 + u) * 30 + lane - 1;
+      float sd = 0.f;
+#pragma unroll
+      for (int j = 0; j < KB; ++j) sd = fmaf(x[u][j], a[j], sd);
+      const float d = T.dinv_f * sd;
+      const float dm = __shfl_up_sync(full, d, 1), dp = __shfl_down_sync(full, d, 1);
+      const float qm = __shfl_up_sync(full, q[u], 1), qp = __shfl_down_sync(full, q[u], 1);
+      const float em = __shfl_up_sync(full, dq[u], 1);
+      if (lane >= 1 && lane <= 30 && (s0 + u) < nseg && rl < rows) {
+        const float f = burgers_f32(qm, q[u], qp, dm, d, dp, em, dq[u], lq[u], T.inv_dx, T.c2);
+        const float w = f * T.d_f;
+#pragma unroll
+        for (int j = 0; j < KB; ++j) acc[j] = fmaf(x[u][j], w, acc[j]);
+      }
+    }
+  }
+}
+
+// The tile context of instance i's tile `tile`.
+__device__ __forceinline__ TileCtx tile_ctx(const BArgs& A, int tile, int i, int k) {
   const Inst I = A.inst[i];
-  const int t = threadIdx.x;
-  const int k = A.rank[i];
   TileCtx T;
   T.phi = A.phi + I.phi_off;
   T.qr = A.qr32 + I.vec_off;
@@ -542,6 +599,20 @@ __device__ void step_tile(const BArgs& A, StepSmem& sm, int tile, int i, bool ja
   T.c2 = (float)I.nu * T.inv_dx * T.inv_dx;
   T.d_f = (float)I.d;
   T.dinv_f = (float)I.dinv;
+  return T;
+}
+
+// A tile whose iteration also forms the reduced Jacobian (the first after a
+// basis change, and every eighth without convergence): rows staged in shared
+// memory by chunks. Kept out of line so that its registers do not weigh on
+// the barrier-free sweep of all other tiles.
+template <int KB>
+__device__ __noinline__ void step_tile_jac(const BArgs& A, StepSmem& sm, int tile, int i) {
+  constexpr int RPT = Rpt<KB>::v;
+  constexpr int CR = kBT * RPT;
+  const int t = threadIdx.x;
+  const int k = A.rank[i];
+  const TileCtx T = tile_ctx(A, tile, i, k);
   const int r0 = A.tile_r0[tile], r1 = T.r1;
   for (int j = t; j < KB; j += kBT) sm.af[j] = (j < k) ? (float)__ldcg(&A.a[(size_t)i * kMaxR + j]) : 0.f;
   float acc[KB];
@@ -550,25 +621,40 @@ __device__ void step_tile(const BArgs& A, StepSmem& sm, int tile, int i, bool ja
   float m[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) m[q] = 0.f;
-  // (two chunks in flight, with double-buffered registers, measured slower)
   ChunkRegs<KB> ra;
   load_chunk<KB>(T, r0, ra);
   __syncthreads();
   for (int c0 = r0; c0 < r1; c0 += CR) {
     if (c0 > r0) load_chunk<KB>(T, c0, ra);
-    compute_chunk<KB>(T, c0, ra, sm, jac, acc, m);
+    compute_chunk<KB>(T, c0, ra, sm, true, acc, m);
   }
-  double* gp = A.gpart + (size_t)tile * kPS;
-  tile_reduce<KB>(acc, k, sm.red, gp);
+  tile_reduce<KB>(acc, k, sm.red, A.gpart + (size_t)tile * kPS);
+  __syncthreads();
+  for (int e = t; e < k * k; e += kBT) sm.W[e] = 0.f;
+  __syncthreads();
+  blk_flush<KB>(m, k, sm.W);
+  __syncthreads();
+  float* mp = A.mpart + (size_t)tile * kMaxR * kMaxR;
+  for (int e = t; e < k * k; e += kBT) mp[e] = sm.W[e];
+}
+
+template <int KB>
+__device__ void step_tile(const BArgs& A, StepSmem& sm, int tile, int i, bool jac) {
   if (jac) {
-    __syncthreads();
-    for (int e = t; e < k * k; e += kBT) sm.W[e] = 0.f;
-    __syncthreads();
-    blk_flush<KB>(m, k, sm.W);
-    __syncthreads();
-    float* mp = A.mpart + (size_t)tile * kMaxR * kMaxR;
-    for (int e = t; e < k * k; e += kBT) mp[e] = sm.W[e];
+    step_tile_jac<KB>(A, sm, tile, i);
+    return;
   }
+  const int t = threadIdx.x;
+  const int k = A.rank[i];
+  const TileCtx T = tile_ctx(A, tile, i, k);
+  const int r0 = A.tile_r0[tile], r1 = T.r1;
+  for (int j = t; j < KB; j += kBT) sm.af[j] = (j < k) ? (float)__ldcg(&A.a[(size_t)i * kMaxR + j]) : 0.f;
+  float acc[KB];
+#pragma unroll
+  for (int j = 0; j < KB; ++j) acc[j] = 0.f;
+  __syncthreads();                        // sm.af written above
+  stream_tile<KB>(T, r0, r1, sm.af, acc);
+  tile_reduce<KB>(acc, k, sm.red, A.gpart + (size_t)tile * kPS);
 }
 
 // Newton update of instance i once every tile of its current iteration has
