@@ -112,8 +112,9 @@ struct BArgs {
   float* ev_u;             // count x kMaxCore x kMaxR: rotation U(:, 0:k') (FP32)
   double* ev_anew;         // count x kMaxR: transferred state before a <- R a
   float* ev_r;             // count x kMaxR x kMaxR: Cholesky factor R (FP32 copy)
-  unsigned int* ctl;       // [0..3] tile queues of the sweeps; steps kernel: [0] claimed
-                           // entries, [1] appended entries, [2] instances done (host-zeroed)
+  unsigned int* ctl;       // [0..3] tile queues of the sweeps; steps kernel: [0] first
+                           // iterations claimed, [1] entries appended, [2] instances
+                           // done, [3] appended entries claimed (host-zeroed)
   unsigned long long* wq;  // steps kernel work entries: epoch << 32 | tile
   long long wq_cap;        // entries of wq
   int* tcount;             // count: tiles of the current iteration counted in
@@ -740,8 +741,18 @@ __device__ __noinline__ void update_instance(const BArgs& A, StepSmem& sm, int i
   }
   __syncthreads();
   const int act = sm.act;
-  if (act >= 2)
-    for (int j = t; j < k; j += blockDim.x) A.an[(size_t)i * kMaxR + j] = __ldcg(&a[j]);
+  if (act >= 2) {
+    // converged: the root becomes the next step's start value; within a launch
+    // the basis is fixed, so the next step's Newton iteration starts from the
+    // linear extrapolation 2 a^{n+1} - a^n (its error, O(dt^2), is below the
+    // stopping level of the FP32 projections; the root is the same)
+    for (int j = t; j < k; j += blockDim.x) {
+      const double root = __ldcg(&a[j]);
+      const double start = __ldcg(&an[j]);
+      A.an[(size_t)i * kMaxR + j] = root;
+      if (act == 2) a[j] = 2.0 * root - start;
+    }
+  }
   if (act == 0) return;
   if (t == 0) A.tcount[i] = 0;
   __threadfence();
@@ -765,32 +776,57 @@ __device__ __noinline__ void update_instance(const BArgs& A, StepSmem& sm, int i
     wq[base + e] = ((unsigned long long)epoch << 32) | (unsigned int)(I.tile0 + e);
 }
 
-// Tile of work entry h, or -1 once every instance is done, an error status is
-// set, or the wait runs out (a timeout is recorded). Thread 0 waits; the
-// result goes to every thread.
-__device__ int wait_entry(const BArgs& A, long long h, unsigned int epoch, StepSmem& sm) {
+// Next tile for this CTA, or -1 once every instance is done, an error status
+// is set, or the wait runs out (a timeout is recorded). Appended iterations
+// (entries ntiles + [0, ctl[1])) go first, so that an instance moves on to
+// its next iteration before instances that have not started take CTAs; the
+// first iterations (entries [0, ntiles), in the order of decreasing cost)
+// come next. An entry is claimed only once it exists (appended entries by a
+// compare-and-swap on their head below the tail), so a claim never waits for
+// future work: the claimed entry is written, or about to be, by the CTA that
+// reserved it. Thread 0 claims; the result goes to every thread.
+__device__ int claim_tile(const BArgs& A, unsigned int epoch, StepSmem& sm) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int tile = -1;
+    volatile unsigned int* ctl = A.ctl;
     const volatile unsigned long long* wq = A.wq;
-    const volatile unsigned int* done = &A.ctl[2];
     const volatile int* st = A.status;
     const long long limit = c_wait_limit;
     const long long t0 = clock64();
+    long long idx = -1;
     for (;;) {
-      if (h < A.wq_cap) {
-        const unsigned long long v = wq[h];
-        if ((unsigned int)(v >> 32) == epoch) {
-          tile = (int)(unsigned int)(v & 0xffffffffull);
-          break;
-        }
+      unsigned int hh = ctl[3];
+      while (hh < ctl[1]) {
+        const unsigned int old = atomicCAS(&A.ctl[3], hh, hh + 1u);
+        if (old == hh) { idx = (long long)A.ntiles + hh; break; }
+        hh = old;
       }
-      if (*done >= (unsigned int)A.count || *st != 0) break;
+      if (idx < 0 && ctl[0] < (unsigned int)A.ntiles) {
+        const unsigned int c = atomicAdd(&A.ctl[0], 1u);
+        if (c < (unsigned int)A.ntiles) idx = c;
+      }
+      if (idx >= 0) break;
+      if (ctl[2] >= (unsigned int)A.count || *st != 0) break;
       if (clock64() - t0 > limit) {
         record_status(A.status, kStTimeout);
         break;
       }
       __nanosleep(64);
+    }
+    if (idx >= 0 && idx < A.wq_cap) {
+      for (;;) {       // the entry is reserved: wait for its write
+        const unsigned long long v = wq[idx];
+        if ((unsigned int)(v >> 32) == epoch) {
+          tile = (int)(unsigned int)(v & 0xffffffffull);
+          break;
+        }
+        if (*st != 0) break;
+        if (clock64() - t0 > limit) {
+          record_status(A.status, kStTimeout);
+          break;
+        }
+      }
     }
     __threadfence();
     sm.q = tile;
@@ -832,17 +868,17 @@ constexpr int kLowRank = 16;   // rank limit of the two-CTAs-per-SM instantiatio
 //
 // Dataflow over a work array (wq): an entry names a row tile of one
 // instance's current Newton iteration; the first iteration of the first step
-// of every instance is filled in at the start. A CTA claims entries in order
-// (the claim of the next one goes out before it works on the current one),
-// computes the tile's partials, and counts the tile in; the CTA that counts
-// an instance's last tile runs that instance's update at once and appends its
-// next iteration's tiles. Instances therefore advance independently, and the
-// small per-instance work overlaps the other instances' streaming; there is
-// no grid-wide barrier per iteration. Entries carry the launch's epoch, so
-// entries of an earlier launch are never taken for this one's. No CTA that
-// appends waits for anything, and a CTA waits only for an entry that was
-// claimed by it, so every wait ends: the entry is written, or every instance
-// is done, or an error is recorded, or the bounded wait runs out.
+// of every instance is filled in at the start. A CTA claims an entry
+// (appended iterations first, see claim_tile), computes the tile's partials,
+// and counts the tile in; the CTA that counts an instance's last tile runs
+// that instance's update at once and appends its next iteration's tiles.
+// Instances therefore advance independently, and the small per-instance work
+// overlaps the other instances' streaming; there is no grid-wide barrier per
+// iteration. Entries carry the launch's epoch, so entries of an earlier
+// launch are never taken for this one's. No CTA that appends waits for
+// anything, and a CTA claims only entries that exist, so every wait ends:
+// the entry is written, or every instance is done, or an error is recorded,
+// or the bounded wait runs out.
 template <int MAXKB>
 __global__ void __launch_bounds__(kBT, MAXKB <= kLowRank ? 2 : 1) batch_steps_kernel(BArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -865,12 +901,9 @@ __global__ void __launch_bounds__(kBT, MAXKB <= kLowRank ? 2 : 1) batch_steps_ke
     A.wq[q] = ((unsigned long long)epoch << 32) | (unsigned int)__ldg(&A.qdesc[q]).x;
   if (!grid_sync(A.bar, A.status)) return;
   if (b == 0 && t == 0) *A.epoch = epoch;
-  long long h = 0;     // the claimed entry (thread 0)
-  if (t == 0) h = (long long)atomicAdd(&A.ctl[0], 1u);
   for (;;) {
-    const int tile = wait_entry(A, h, epoch, sm);
+    const int tile = claim_tile(A, epoch, sm);
     if (tile < 0) break;
-    if (t == 0) h = (long long)atomicAdd(&A.ctl[0], 1u);
     const int i = __ldg(&A.tile_inst[tile]);
     const bool jac = __ldcg(&A.need_jac[i]) != 0;
     with_bucket_upto<MAXKB>(A.rank[i], [&](auto kb) { step_tile<decltype(kb)::value>(A, sm, tile, i, jac); });
