@@ -20,8 +20,10 @@
 //                       independently, without a grid barrier per iteration.
 //   batch_fom_kernel    the coarse FOM step (Eq. coarse_fom_backward_euler)
 //                       of the instances that adapt now: Newton with FP64
-//                       residuals and a chunked PCR solver over (instance,
-//                       chunk) work items.
+//                       residuals over (instance, chunk) work items; the
+//                       linear solve eliminates each thread's block of rows
+//                       (Thomas), solves the block separators of a chunk by
+//                       PCR and the chunk separators of an instance by PCR.
 //   batch_event_kernel  Algorithm 2 for those instances: projections, one CTA
 //                       per instance for the core SVD, rotation with a fused
 //                       Gram matrix, FP64 Cholesky, basis <- basis R^-1.
@@ -47,7 +49,9 @@ namespace rom {
 namespace {
 
 constexpr int kBT = 256;          // threads of the sweep kernels
-constexpr int kFomT = 512;        // threads of the FOM kernel (one row each; two CTAs per SM)
+constexpr int kFomT = 512;        // threads of the FOM kernel (two CTAs per SM)
+constexpr int kFomR = 4;          // rows per thread of a FOM chunk
+constexpr int kFomRows = kFomR * kFomT;   // rows per FOM chunk
 constexpr int kFomMaxChunks = 256; // FOM chunks per instance (power of two)
 constexpr int kFomItems = 256;     // FOM work items (chunks) per CTA
 constexpr int kPS = kMaxR + 4;    // stride of the per-tile partial vectors
@@ -112,9 +116,8 @@ struct BArgs {
   float* ev_u;             // count x kMaxCore x kMaxR: rotation U(:, 0:k') (FP32)
   double* ev_anew;         // count x kMaxR: transferred state before a <- R a
   float* ev_r;             // count x kMaxR x kMaxR: Cholesky factor R (FP32 copy)
-  unsigned int* ctl;       // [0..3] tile queues of the sweeps; steps kernel: [0] first
-                           // iterations claimed, [1] entries appended, [2] instances
-                           // done, [3] appended entries claimed (host-zeroed)
+  unsigned int* ctl;       // [0..3] tile queues of the sweeps; steps kernel: [0] claimed
+                           // entries, [1] appended entries, [2] instances done (host-zeroed)
   unsigned long long* wq;  // steps kernel work entries: epoch << 32 | tile
   long long wq_cap;        // entries of wq
   int* tcount;             // count: tiles of the current iteration counted in
@@ -776,57 +779,32 @@ __device__ __noinline__ void update_instance(const BArgs& A, StepSmem& sm, int i
     wq[base + e] = ((unsigned long long)epoch << 32) | (unsigned int)(I.tile0 + e);
 }
 
-// Next tile for this CTA, or -1 once every instance is done, an error status
-// is set, or the wait runs out (a timeout is recorded). Appended iterations
-// (entries ntiles + [0, ctl[1])) go first, so that an instance moves on to
-// its next iteration before instances that have not started take CTAs; the
-// first iterations (entries [0, ntiles), in the order of decreasing cost)
-// come next. An entry is claimed only once it exists (appended entries by a
-// compare-and-swap on their head below the tail), so a claim never waits for
-// future work: the claimed entry is written, or about to be, by the CTA that
-// reserved it. Thread 0 claims; the result goes to every thread.
-__device__ int claim_tile(const BArgs& A, unsigned int epoch, StepSmem& sm) {
+// Tile of work entry h, or -1 once every instance is done, an error status is
+// set, or the wait runs out (a timeout is recorded). Thread 0 waits; the
+// result goes to every thread.
+__device__ int wait_entry(const BArgs& A, long long h, unsigned int epoch, StepSmem& sm) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int tile = -1;
-    volatile unsigned int* ctl = A.ctl;
     const volatile unsigned long long* wq = A.wq;
+    const volatile unsigned int* done = &A.ctl[2];
     const volatile int* st = A.status;
     const long long limit = c_wait_limit;
     const long long t0 = clock64();
-    long long idx = -1;
     for (;;) {
-      unsigned int hh = ctl[3];
-      while (hh < ctl[1]) {
-        const unsigned int old = atomicCAS(&A.ctl[3], hh, hh + 1u);
-        if (old == hh) { idx = (long long)A.ntiles + hh; break; }
-        hh = old;
+      if (h < A.wq_cap) {
+        const unsigned long long v = wq[h];
+        if ((unsigned int)(v >> 32) == epoch) {
+          tile = (int)(unsigned int)(v & 0xffffffffull);
+          break;
+        }
       }
-      if (idx < 0 && ctl[0] < (unsigned int)A.ntiles) {
-        const unsigned int c = atomicAdd(&A.ctl[0], 1u);
-        if (c < (unsigned int)A.ntiles) idx = c;
-      }
-      if (idx >= 0) break;
-      if (ctl[2] >= (unsigned int)A.count || *st != 0) break;
+      if (*done >= (unsigned int)A.count || *st != 0) break;
       if (clock64() - t0 > limit) {
         record_status(A.status, kStTimeout);
         break;
       }
       __nanosleep(64);
-    }
-    if (idx >= 0 && idx < A.wq_cap) {
-      for (;;) {       // the entry is reserved: wait for its write
-        const unsigned long long v = wq[idx];
-        if ((unsigned int)(v >> 32) == epoch) {
-          tile = (int)(unsigned int)(v & 0xffffffffull);
-          break;
-        }
-        if (*st != 0) break;
-        if (clock64() - t0 > limit) {
-          record_status(A.status, kStTimeout);
-          break;
-        }
-      }
     }
     __threadfence();
     sm.q = tile;
@@ -868,17 +846,17 @@ constexpr int kLowRank = 16;   // rank limit of the two-CTAs-per-SM instantiatio
 //
 // Dataflow over a work array (wq): an entry names a row tile of one
 // instance's current Newton iteration; the first iteration of the first step
-// of every instance is filled in at the start. A CTA claims an entry
-// (appended iterations first, see claim_tile), computes the tile's partials,
-// and counts the tile in; the CTA that counts an instance's last tile runs
-// that instance's update at once and appends its next iteration's tiles.
-// Instances therefore advance independently, and the small per-instance work
-// overlaps the other instances' streaming; there is no grid-wide barrier per
-// iteration. Entries carry the launch's epoch, so entries of an earlier
-// launch are never taken for this one's. No CTA that appends waits for
-// anything, and a CTA claims only entries that exist, so every wait ends:
-// the entry is written, or every instance is done, or an error is recorded,
-// or the bounded wait runs out.
+// of every instance is filled in at the start. A CTA claims entries in order
+// (the claim of the next one goes out before it works on the current one),
+// computes the tile's partials, and counts the tile in; the CTA that counts
+// an instance's last tile runs that instance's update at once and appends its
+// next iteration's tiles. Instances therefore advance independently, and the
+// small per-instance work overlaps the other instances' streaming; there is
+// no grid-wide barrier per iteration. Entries carry the launch's epoch, so
+// entries of an earlier launch are never taken for this one's. No CTA that
+// appends waits for anything, and a CTA waits only for an entry that was
+// claimed by it, so every wait ends: the entry is written, or every instance
+// is done, or an error is recorded, or the bounded wait runs out.
 template <int MAXKB>
 __global__ void __launch_bounds__(kBT, MAXKB <= kLowRank ? 2 : 1) batch_steps_kernel(BArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -901,9 +879,12 @@ __global__ void __launch_bounds__(kBT, MAXKB <= kLowRank ? 2 : 1) batch_steps_ke
     A.wq[q] = ((unsigned long long)epoch << 32) | (unsigned int)__ldg(&A.qdesc[q]).x;
   if (!grid_sync(A.bar, A.status)) return;
   if (b == 0 && t == 0) *A.epoch = epoch;
+  long long h = 0;     // the claimed entry (thread 0)
+  if (t == 0) h = (long long)atomicAdd(&A.ctl[0], 1u);
   for (;;) {
-    const int tile = claim_tile(A, epoch, sm);
+    const int tile = wait_entry(A, h, epoch, sm);
     if (tile < 0) break;
+    if (t == 0) h = (long long)atomicAdd(&A.ctl[0], 1u);
     const int i = __ldg(&A.tile_inst[tile]);
     const bool jac = __ldcg(&A.need_jac[i]) != 0;
     with_bucket_upto<MAXKB>(A.rank[i], [&](auto kb) { step_tile<decltype(kb)::value>(A, sm, tile, i, jac); });
@@ -946,7 +927,7 @@ __device__ __forceinline__ int64_t fchunk_begin(int c, int C, int64_t n) { retur
 __global__ void __launch_bounds__(kFomT, 2) batch_fom_kernel(BArgs A) {
   __shared__ float sa[kFomT], sc[kFomT], sd0[kFomT], sd1[kFomT], sd2[kFomT], sib[kFomT];
   __shared__ float ra[kFomMaxChunks], rb[kFomMaxChunks], rc[kFomMaxChunks], rd[kFomMaxChunks];
-  __shared__ double su[kFomT];
+  __shared__ double su[kFomRows + 2];
   __shared__ unsigned int redu[32];
   __shared__ unsigned char s_done[kMaxBatch];
   // this CTA's work items (chunks q = b + G j), read once per launch
@@ -974,7 +955,18 @@ __global__ void __launch_bounds__(kFomT, 2) batch_fom_kernel(BArgs A) {
   __syncthreads();
   for (int it = 1; it <= A.fom_maxit; ++it) {
     const int par = it & 1;
-    // ---- A: residual (FP64), Jacobian rows (FP32), interior PCR per chunk ----
+    // ---- A: residual (FP64), Jacobian rows (FP32), two-level solve per chunk ----
+    // Thread p owns rows [kFomR p, kFomR p + rt) of the chunk; the last of
+    // them is its separator. Level 1: a Thomas sweep (three right-hand
+    // sides) writes each of its other rows as x = y + v x_L + w x_s, x_L the
+    // separator on its left (the previous thread's, or the previous chunk's
+    // separator s_left for p = 0) and x_s its own. Level 2: the separators of
+    // threads 0 .. nt-2 form a tridiagonal system between s_left and the
+    // chunk's separator s_self (the last thread's), solved by PCR into
+    // x_s = Y + V s_left + W s_self. The chunk separator's own row, and the
+    // chunk's first and last-but-one rows in terms of (s_left, s_self), go to
+    // the separator system across chunks (B). FP32: the solve only steers the
+    // Newton iteration; the FP64 residual fixes the root.
     for (int j = 0; j < nitems; ++j) {
       const int i = it_inst[j];
       if (s_done[i]) continue;
@@ -982,7 +974,10 @@ __global__ void __launch_bounds__(kFomT, 2) batch_fom_kernel(BArgs A) {
       const int64_t n = it_n[j];
       const int64_t beg = it_beg[j];
       const int m = it_m[j];
-      const int mi = m - 1;
+      const int nt = (m + kFomR - 1) / kFomR;       // active threads
+      const int r0 = kFomR * t;
+      const int rt = max(0, min(kFomR, m - r0));    // rows of this thread
+      const int ni = rt - 1;                        // its interior rows
       // iterate it-1: the previous snapshot extrapolated by the previous
       // increment (it == 1), else y_new
       const double* ucur = (it == 1 ? A.y_corr : A.y_new) + it_vec[j];
@@ -993,74 +988,149 @@ __global__ void __launch_bounds__(kFomT, 2) batch_fom_kernel(BArgs A) {
       const double inv_dx = (double)n;
       const float nu_f = (float)nu, inv_dx_f = (float)n, h_f = (float)h;
       __syncthreads();
-      const bool act = t < m;
-      // the chunk's rows and its two halo rows (loaded together)
-      double u = act ? __ldcg(&ucur[beg + t]) : 0.0;
-      const double un = act ? uprev[beg + t] : 0.0;
-      double hl = 0.0, hr = 0.0;
-      const int64_t il = (beg - 1 + n) % n, ir = (beg + m) % n;
-      if (t == 0) hl = __ldcg(&ucur[il]);
-      if (t == m - 1) hr = __ldcg(&ucur[ir]);
-      if (it == 1) {
-        if (act) u += dy[beg + t];
-        if (t == 0) hl += dy[il];
-        if (t == m - 1) hr += dy[ir];
+      double un[kFomR];
+#pragma unroll
+      for (int r = 0; r < kFomR; ++r) {
+        un[r] = 0.0;
+        if (r < rt) {
+          double u = __ldcg(&ucur[beg + r0 + r]);
+          if (it == 1) u += dy[beg + r0 + r];
+          su[1 + r0 + r] = u;
+          un[r] = uprev[beg + r0 + r];
+        }
       }
-      su[t] = u;
+      if (t == 0) {
+        const int64_t il = (beg - 1 + n) % n, ir = (beg + m) % n;
+        double hl = __ldcg(&ucur[il]), hr = __ldcg(&ucur[ir]);
+        if (it == 1) { hl += dy[il]; hr += dy[ir]; }
+        su[0] = hl;
+        su[m + 1] = hr;
+      }
       __syncthreads();
-      float a_t = 0.f, b_t = 1.f, c_t = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
-      if (act) {
-        const double ul = (t > 0) ? su[t - 1] : hl;
-        const double ur = (t < m - 1) ? su[t + 1] : hr;
-        const double f = burgers_f(ul, u, ur, nu, inv_dx);
-        const double res = u - un - h * f;
-        float dl, dc, dr;
-        burgers_band(ul, u, ur, nu_f, inv_dx_f, dl, dc, dr);
-        a_t = -h_f * dl;
-        b_t = 1.f - h_f * dc;
-        c_t = -h_f * dr;
-        d0 = (float)(-res);
+      float a_[kFomR], b_[kFomR], c_[kFomR], d_[kFomR];
+#pragma unroll
+      for (int r = 0; r < kFomR; ++r) {
+        a_[r] = 0.f; b_[r] = 1.f; c_[r] = 0.f; d_[r] = 0.f;
+        if (r < rt) {
+          const int e = r0 + r;
+          const double ul = su[e], u = su[e + 1], ur = su[e + 2];
+          const double f = burgers_f(ul, u, ur, nu, inv_dx);
+          const double res = u - un[r] - h * f;
+          float dl, dc, dr;
+          burgers_band(ul, u, ur, nu_f, inv_dx_f, dl, dc, dr);
+          a_[r] = -h_f * dl;
+          b_[r] = 1.f - h_f * dc;
+          c_[r] = -h_f * dr;
+          d_[r] = (float)(-res);
+        }
       }
       float* ch = A.fom_chunk + (size_t)q * kFomChunkStride;
-      if (t == m - 1) { ch[0] = a_t; ch[1] = b_t; ch[2] = c_t; ch[3] = d0; }
-      if (t < mi) {
-        if (t == 0) { d1 = -a_t; a_t = 0.f; }
-        if (t == mi - 1) { d2 = -c_t; c_t = 0.f; }
-      } else {
-        a_t = 0.f; b_t = 1.f; c_t = 0.f; d0 = d1 = d2 = 0.f;
+      float* rows3 = A.fom_row + 3 * (size_t)(it_vec[j] + beg);
+      // level 1: Thomas over rows 0 .. ni-1 with x_{-1} = x_L, x_{ni} = x_s
+      float Y[kFomR], V[kFomR], W[kFomR], g[kFomR];
+#pragma unroll
+      for (int r = 0; r < kFomR; ++r) { Y[r] = 0.f; V[r] = 0.f; W[r] = 0.f; g[r] = 0.f; }
+#pragma unroll
+      for (int r = 0; r < kFomR - 1; ++r) {
+        if (r < ni) {
+          const float am = (r > 0) ? a_[r] : 0.f;
+          const float beta = b_[r] - ((r > 0) ? am * g[r - 1] : 0.f);
+          const float ib = __frcp_rn(beta);
+          g[r] = (r + 1 < ni) ? c_[r] * ib : 0.f;
+          Y[r] = (d_[r] - ((r > 0) ? am * Y[r - 1] : 0.f)) * ib;
+          V[r] = ((r == 0 ? -a_[0] : 0.f) - ((r > 0) ? am * V[r - 1] : 0.f)) * ib;
+          W[r] = ((r + 1 == ni ? -c_[r] : 0.f) - ((r > 0) ? am * W[r - 1] : 0.f)) * ib;
+        }
       }
-      // PCR (FP32: the solve only steers the iteration); each row publishes
-      // the reciprocal of its diagonal once per level
-      sa[t] = a_t; sc[t] = c_t; sd0[t] = d0; sd1[t] = d1; sd2[t] = d2; sib[t] = __frcp_rn(b_t);
+#pragma unroll
+      for (int r = kFomR - 3; r >= 0; --r) {
+        if (r + 1 < ni) {
+          Y[r] -= g[r] * Y[r + 1];
+          V[r] -= g[r] * V[r + 1];
+          W[r] -= g[r] * W[r + 1];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kFomR - 1; ++r)
+        if (r < ni) {
+          float* rw = rows3 + 3 * (size_t)(r0 + r);
+          rw[0] = Y[r]; rw[1] = V[r]; rw[2] = W[r];
+        }
+      // this thread's separator row and its interior ends
+      float as_ = 0.f, bs_ = 1.f, cs_ = 0.f, ds_ = 0.f;
+      float yF = 0.f, vF = 0.f, wF = 0.f, yL = 0.f, vL = 0.f, wL = 0.f;
+#pragma unroll
+      for (int r = 0; r < kFomR; ++r)
+        if (r == rt - 1) { as_ = a_[r]; bs_ = b_[r]; cs_ = c_[r]; ds_ = d_[r]; }
+#pragma unroll
+      for (int r = 0; r < kFomR - 1; ++r)
+        if (r == ni - 1) { yL = Y[r]; vL = V[r]; wL = W[r]; }
+      if (ni >= 1) { yF = Y[0]; vF = V[0]; wF = W[0]; }
+      if (t == nt - 1) { ch[0] = as_; ch[1] = bs_; ch[2] = cs_; ch[3] = ds_; }
+      // publish the first interior row (coefficients of (x_L, x_s)) for the
+      // thread on the left
+      sd0[t] = yF; sd1[t] = vF; sd2[t] = wF; sib[t] = (ni >= 1) ? 1.f : 0.f;
+      __syncthreads();
+      // level 2: the reduced row of separator p in (x_{p-1}, x_p, x_{p+1})
+      const int mi = nt - 1;
+      float a2 = 0.f, b2 = 1.f, c2 = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f;
+      if (t < mi) {
+        if (ni >= 1) { a2 = as_ * vL; b2 = bs_ + as_ * wL; e0 = ds_ - as_ * yL; }
+        else { a2 = as_; b2 = bs_; e0 = ds_; }
+        if (sib[t + 1] > 0.f) { b2 += cs_ * sd1[t + 1]; c2 = cs_ * sd2[t + 1]; e0 -= cs_ * sd0[t + 1]; }
+        else { c2 = cs_; }
+        if (t == 0) { e1 = -a2; a2 = 0.f; }
+        if (t == mi - 1) { e2 = -c2; c2 = 0.f; }
+      }
+      __syncthreads();
+      sa[t] = a2; sc[t] = c2; sd0[t] = e0; sd1[t] = e1; sd2[t] = e2; sib[t] = __frcp_rn(b2);
       __syncthreads();
       for (int s = 1; s < mi; s <<= 1) {
-        float na = a_t, nb = b_t, nc = c_t, n0 = d0, n1 = d1, n2 = d2;
+        float na = a2, nb = b2, nc = c2, n0 = e0, n1 = e1, n2 = e2;
         if (t < mi) {
           const int tm = t - s, tp = t + s;
           float am = 0.f, ibm = 1.f, cm = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f;
           float ap = 0.f, ibp = 1.f, cp = 0.f, p0 = 0.f, p1 = 0.f, p2 = 0.f;
           if (tm >= 0) { am = sa[tm]; ibm = sib[tm]; cm = sc[tm]; m0 = sd0[tm]; m1 = sd1[tm]; m2 = sd2[tm]; }
           if (tp < mi) { ap = sa[tp]; ibp = sib[tp]; cp = sc[tp]; p0 = sd0[tp]; p1 = sd1[tp]; p2 = sd2[tp]; }
-          const float al = -a_t * ibm, ga = -c_t * ibp;
+          const float al = -a2 * ibm, ga = -c2 * ibp;
           na = al * am;
           nc = ga * cp;
-          nb = b_t + al * cm + ga * ap;
-          n0 = d0 + al * m0 + ga * p0;
-          n1 = d1 + al * m1 + ga * p1;
-          n2 = d2 + al * m2 + ga * p2;
+          nb = b2 + al * cm + ga * ap;
+          n0 = e0 + al * m0 + ga * p0;
+          n1 = e1 + al * m1 + ga * p1;
+          n2 = e2 + al * m2 + ga * p2;
         }
         __syncthreads();
-        a_t = na; b_t = nb; c_t = nc; d0 = n0; d1 = n1; d2 = n2;
-        sa[t] = a_t; sc[t] = c_t; sd0[t] = d0; sd1[t] = d1; sd2[t] = d2; sib[t] = __frcp_rn(b_t);
+        a2 = na; b2 = nb; c2 = nc; e0 = n0; e1 = n1; e2 = n2;
+        sa[t] = a2; sc[t] = c2; sd0[t] = e0; sd1[t] = e1; sd2[t] = e2; sib[t] = __frcp_rn(b2);
         __syncthreads();
       }
+      // separator solutions x_p = Ys + Vs s_left + Ws s_self (threads < mi)
+      float Ys = 0.f, Vs = 0.f, Ws = 0.f;
       if (t < mi) {
         const float ib = sib[t];
-        const float yv = d0 * ib, vv = d1 * ib, wv = d2 * ib;
-        float* row = A.fom_row + 3 * (size_t)(it_vec[j] + beg + t);
-        row[0] = yv; row[1] = vv; row[2] = wv;
-        if (t == 0) { ch[4] = yv; ch[5] = vv; ch[6] = wv; }
-        if (t == mi - 1) { ch[7] = yv; ch[8] = vv; ch[9] = wv; }
+        Ys = e0 * ib; Vs = e1 * ib; Ws = e2 * ib;
+        float* rw = rows3 + 3 * (size_t)(r0 + rt - 1);
+        rw[0] = Ys; rw[1] = Vs; rw[2] = Ws;
+      }
+      __syncthreads();
+      sd0[t] = Ys; sd1[t] = Vs; sd2[t] = Ws;
+      __syncthreads();
+      // the chunk's first row and its last-but-one row in (s_left, s_self)
+      if (t == 0) {
+        if (nt == 1) { ch[4] = yF; ch[5] = vF; ch[6] = wF; }          // x_s = s_self
+        else if (ni >= 1) { ch[4] = yF + wF * Ys; ch[5] = vF + wF * Vs; ch[6] = wF * Ws; }
+        else { ch[4] = Ys; ch[5] = Vs; ch[6] = Ws; }
+      }
+      if (t == nt - 1) {
+        if (nt == 1) { ch[7] = yL; ch[8] = vL; ch[9] = wL; }          // x_L = s_left
+        else if (ni >= 1) {
+          const float yp = sd0[t - 1], vp = sd1[t - 1], wp = sd2[t - 1];
+          ch[7] = yL + vL * yp; ch[8] = vL * vp; ch[9] = vL * wp + wL;
+        } else {
+          ch[7] = sd0[t - 1]; ch[8] = sd1[t - 1]; ch[9] = sd2[t - 1];
+        }
       }
     }
     if (!grid_sync(A.bar, A.status)) return;
@@ -1111,26 +1181,45 @@ __global__ void __launch_bounds__(kFomT, 2) batch_fom_kernel(BArgs A) {
       const int C = it_C[j], c = it_c[j];
       const int64_t beg = it_beg[j];
       const int m = it_m[j];
-      const int mi = m - 1;
+      const int nt = (m + kFomR - 1) / kFomR;
+      const int r0 = kFomR * t;
+      const int rt = max(0, min(kFomR, m - r0));
+      const int ni = rt - 1;
       const long long vec_off = it_vec[j];
       const float s_left = __ldcg(&A.fom_sep[it_chunk0[j] + (c - 1 + C) % C]);
       const float s_self = __ldcg(&A.fom_sep[it_chunk0[j] + c]);
+      const float* rows3 = A.fom_row + 3 * (size_t)(vec_off + beg);
       unsigned int kd = 0u, ku = 0u;
-      if (t < m) {
-        float dl;
-        if (t < mi) {
-          const float* row = A.fom_row + 3 * (size_t)(vec_off + beg + t);
-          dl = __ldcg(row) + __ldcg(row + 1) * s_left + __ldcg(row + 2) * s_self;
-        } else {
-          dl = s_self;
+      if (rt > 0) {
+        // this thread's separator and the one on its left (the previous
+        // thread's, whose block has kFomR rows, or s_left)
+        float xs = s_self, xl = s_left;
+        if (t < nt - 1) {
+          const float* rw = rows3 + 3 * (size_t)(r0 + rt - 1);
+          xs = __ldcg(rw) + __ldcg(rw + 1) * s_left + __ldcg(rw + 2) * s_self;
+        }
+        if (t > 0) {
+          const float* rw = rows3 + 3 * (size_t)(r0 - 1);
+          xl = __ldcg(rw) + __ldcg(rw + 1) * s_left + __ldcg(rw + 2) * s_self;
         }
         const double* ucur = (it == 1 ? A.y_corr : A.y_new) + vec_off;
-        double u = __ldcg(&ucur[beg + t]) + (double)dl;
-        if (it == 1) u += A.dy[vec_off + beg + t];
-        A.y_new[vec_off + beg + t] = u;
-        kd = __float_as_uint(fabsf(dl));
-        ku = isfinite(u) ? __float_as_uint(fabsf((float)u)) : 0x7fc00000u;
-        if (!isfinite(dl)) kd = 0x7fc00000u;
+#pragma unroll
+        for (int r = 0; r < kFomR; ++r) {
+          if (r < rt) {
+            float dl;
+            if (r < ni) {
+              const float* rw = rows3 + 3 * (size_t)(r0 + r);
+              dl = __ldcg(rw) + __ldcg(rw + 1) * xl + __ldcg(rw + 2) * xs;
+            } else {
+              dl = xs;
+            }
+            double u = __ldcg(&ucur[beg + r0 + r]) + (double)dl;
+            if (it == 1) u += A.dy[vec_off + beg + r0 + r];
+            A.y_new[vec_off + beg + r0 + r] = u;
+            kd = max(kd, isfinite(dl) ? __float_as_uint(fabsf(dl)) : 0x7fc00000u);
+            ku = max(ku, isfinite(u) ? __float_as_uint(fabsf((float)u)) : 0x7fc00000u);
+          }
+        }
       }
       kd = block_max_u32(kd, redu);
       ku = block_max_u32(ku, redu);
@@ -1970,8 +2059,8 @@ rom_status rom_batch_init(const rom_config* cfgs, const double* const* q0s, int3
     vec_tot += ((long long)I.n + 31) / 32 * 32;
     ntiles_max += (I.n + kTileRowsMin - 1) / kTileRowsMin;
     int C = 4;
-    while ((I.n + C - 1) / C > kFomT && C < kFomMaxChunks) C *= 2;
-    if ((I.n + C - 1) / C > kFomT) { delete B; return ROM_EINVAL; }
+    while ((I.n + C - 1) / C > kFomRows && C < kFomMaxChunks) C *= 2;
+    if ((I.n + C - 1) / C > kFomRows) { delete B; return ROM_EINVAL; }
     I.chunk0 = (int)cinst.size();
     I.nchunk = C;
     for (int q = 0; q < C; ++q) { cinst.push_back(i); cc.push_back(q); }
