@@ -113,6 +113,7 @@ rom_status status_to_rom(int st) {
 // Synchronise, read and clear the device status word.
 rom_status finish(rom_ctx* ctx) {
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess && ctx->fom_overlap) e = cudaStreamSynchronize(ctx->fom_stream);
   if (e != cudaSuccess) { ctx->poisoned = 1; return ROM_ECUDA; }
   int st = 0;
   e = cudaMemcpy(&st, ctx->d.status, sizeof(int), cudaMemcpyDeviceToHost);
@@ -120,6 +121,7 @@ rom_status finish(rom_ctx* ctx) {
   if (st != 0) {
     cudaMemset(ctx->d.status, 0, sizeof(int));
     cudaMemset(ctx->d.bar, 0, sizeof(GridBarrier));
+    cudaMemset(ctx->d.fom_bar, 0, sizeof(GridBarrier));
     if (st == kStTimeout) ctx->poisoned = 1;
   }
   return status_to_rom(st);
@@ -147,7 +149,7 @@ cudaError_t prof_flush(rom_ctx* ctx) {
 }
 
 // Record an event before (begin) / after (end) a phase launch when enabled.
-cudaError_t prof_mark(rom_ctx* ctx, int phase, bool begin) {
+cudaError_t prof_mark(rom_ctx* ctx, int phase, bool begin, cudaStream_t on = nullptr) {
   if (!ctx->prof_on) return cudaSuccess;
   if (begin && ctx->prof_n >= kMaxProfEvents) {
     cudaError_t e = prof_flush(ctx);
@@ -155,7 +157,7 @@ cudaError_t prof_mark(rom_ctx* ctx, int phase, bool begin) {
   }
   int i = ctx->prof_n;
   if (begin) ctx->prof_phase[i] = phase;
-  cudaError_t e = cudaEventRecord(ctx->prof_ev[2 * i + (begin ? 0 : 1)], ctx->stream);
+  cudaError_t e = cudaEventRecord(ctx->prof_ev[2 * i + (begin ? 0 : 1)], on ? on : ctx->stream);
   if (!begin) ctx->prof_n += 1;
   return e;
 }
@@ -176,7 +178,7 @@ FomScratch fom_scratch(const rom_ctx* ctx) {
   FomScratch s;
   s.chunk = ctx->d.fom_chunk;
   s.maxbuf = ctx->d.maxbuf;
-  s.bar = ctx->d.bar;
+  s.bar = ctx->d.fom_bar;
   s.status = ctx->d.status;
   s.iters = ctx->d.iters_fom;
   return s;
@@ -374,6 +376,34 @@ cudaError_t run_event_window(rom_ctx* ctx) {
   return e;
 }
 
+// The coarse FOM step of a cycle on fom_stream, after everything queued on
+// the context's stream so far; coarse_fom_join makes the stream wait for it
+// and takes the new snapshot. The reduced steps queued in between run beside
+// it: they read neither y_corr nor y_tmp, and the FOM kernel has its own
+// grid barrier and scratch.
+cudaError_t coarse_fom_fork(rom_ctx* ctx) {
+  cudaStream_t fs = ctx->fom_stream;
+  cudaError_t e = cudaEventRecord(ctx->ev_fork, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(fs, ctx->ev_fork, 0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d.maxbuf, 0, 4 * sizeof(unsigned long long), fs);
+  if (e == cudaSuccess) e = prof_mark(ctx, 1, true, fs);
+  if (e == cudaSuccess)
+    e = launch_fom_step(fom_params(ctx, ctx->cfg.z * ctx->cfg.dt), ctx->d.y_corr, ctx->d.y_tmp,
+                        fom_scratch(ctx), fs);
+  if (e == cudaSuccess) e = prof_mark(ctx, 1, false, fs);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, fs);
+  return e;
+}
+
+cudaError_t coarse_fom_join(rom_ctx* ctx) {
+  cudaError_t e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
+  if (e != cudaSuccess) return e;
+  double* t = ctx->d.y_corr;
+  ctx->d.y_corr = ctx->d.y_tmp;
+  ctx->d.y_tmp = t;
+  return cudaSuccess;
+}
+
 cudaError_t coarse_fom(rom_ctx* ctx) {
   cudaError_t e = cudaMemsetAsync(ctx->d.maxbuf, 0, 4 * sizeof(unsigned long long), ctx->stream);
   if (e == cudaSuccess) e = prof_mark(ctx, 1, true);
@@ -446,7 +476,7 @@ void free_state(rom_ctx* ctx) {
   void* ptrs[] = {d.q_ref, d.y_corr, d.y_tmp, d.yhat, d.qres, d.lifted, d.dvals, d.drow, d.dinv, d.phi,
                   d.phi32, d.gram, d.sigma, d.a, d.a_prev, d.rank, d.core, d.ubar, d.partials,
                   d.jpartials, d.jac, d.samples, d.chosen, d.resid_norm, d.qdeim_q, d.cand_v,
-                  d.cand_i, d.merge_v, d.merge_i, d.merge_ctr, d.mesh, d.minv, d.bar, d.status, d.iters_rom, d.iters_fom, d.maxbuf,
+                  d.cand_i, d.merge_v, d.merge_i, d.merge_ctr, d.mesh, d.minv, d.bar, d.fom_bar, d.status, d.iters_rom, d.iters_fom, d.maxbuf,
                   d.fom_chunk, d.npart, d.win, d.dwork, d.dsm, d.dpart, ctx->q_train};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -475,6 +505,13 @@ const char* rom_status_string(rom_status s) {
 void rom_destroy(rom_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->fom_overlap) {
+    cudaStreamSynchronize(ctx->fom_stream);
+    cudaStreamDestroy(ctx->fom_stream);
+    cudaEventDestroy(ctx->ev_fork);
+    cudaEventDestroy(ctx->ev_join);
+    ctx->fom_overlap = 0;
+  }
   if (ctx->prof_ev_made)
     for (int i = 0; i < 2 * kMaxProfEvents; ++i) cudaEventDestroy(ctx->prof_ev[i]);
   free_state(ctx);
@@ -500,6 +537,7 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
   if (!device_ok()) return ROM_ECUDA;
   rom_ctx* ctx = new rom_ctx;
   memset(&ctx->d, 0, sizeof(DevState));
+  ctx->fom_overlap = 0;
   ctx->q_train = nullptr;
   ctx->prof_on = 0;
   ctx->prof_n = 0;
@@ -516,6 +554,29 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
   ctx->poisoned = 0;
   ctx->win_head = 0;
   ctx->grid = grid_for(ctx->N);
+  if (ctx->cfg.n_s > 0) {
+    // the DEIM steps are one CTA without a grid barrier, so the coarse FOM
+    // step can run beside them on its own stream
+    if (cudaStreamCreateWithFlags(&ctx->fom_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete ctx;
+      return ROM_ECUDA;
+    }
+    if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      cudaStreamDestroy(ctx->fom_stream);
+      delete ctx;
+      return ROM_ECUDA;
+    }
+    if (cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      cudaEventDestroy(ctx->ev_fork);
+      cudaStreamDestroy(ctx->fom_stream);
+      delete ctx;
+      return ROM_ECUDA;
+    }
+    ctx->fom_overlap = 1;
+  }
   const int64_t N = ctx->N;
   const int r = ctx->cfg.r;
   const int w = ctx->cfg.w_init;
@@ -536,7 +597,7 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
   ALLOC(d.qdeim_q, kMaxR * kMaxR); ALLOC(d.cand_v, (size_t)G * kMaxNs);
   ALLOC(d.cand_i, (size_t)G * kMaxNs); ALLOC(d.merge_v, (size_t)G * kMaxNs);
   ALLOC(d.merge_i, (size_t)G * kMaxNs); ALLOC(d.merge_ctr, 2); ALLOC(d.mesh, (size_t)ns * 3 * kMeshStride);
-  ALLOC(d.minv, (size_t)kMaxR * ns); ALLOC(d.bar, 1); ALLOC(d.status, 1); ALLOC(d.iters_rom, 1);
+  ALLOC(d.minv, (size_t)kMaxR * ns); ALLOC(d.bar, 1); ALLOC(d.fom_bar, 1); ALLOC(d.status, 1); ALLOC(d.iters_rom, 1);
   ALLOC(d.iters_fom, 1); ALLOC(d.maxbuf, 4); ALLOC(d.fom_chunk, fom_chunk_floats());
   ALLOC(ctx->q_train, (size_t)N * w);
   if (ctx->cfg.precision == ROM_MIXED_FP32) {
@@ -559,6 +620,7 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
   }
   cudaStream_t s = ctx->stream;
   RCK(cudaMemsetAsync(d.bar, 0, sizeof(GridBarrier), s));
+  RCK(cudaMemsetAsync(d.fom_bar, 0, sizeof(GridBarrier), s));
   RCK(cudaMemsetAsync(d.status, 0, sizeof(int), s));
   RCK(cudaMemsetAsync(d.phi, 0, sizeof(double) * N * r_alloc, s));
   RCK(cudaMemsetAsync(d.sigma, 0, sizeof(double) * (kMaxR + 1), s));
@@ -690,13 +752,20 @@ rom_status rom_step(rom_ctx* ctx, int64_t n_steps) {
     if (m < 0) m += z;
     int64_t to_event = z - m;
     int64_t seg = n_steps < to_event ? n_steps : to_event;
-    RCK(run_steps(ctx, (int)seg));
+    const bool event = seg == to_event;
+    if (event && ctx->fom_overlap) {
+      // the coarse FOM step depends only on the previous snapshot: it runs
+      // beside the reduced steps of the interval
+      RCK(coarse_fom_fork(ctx));
+      RCK(run_steps(ctx, (int)seg));
+      RCK(coarse_fom_join(ctx));
+    } else {
+      RCK(run_steps(ctx, (int)seg));
+      if (event) RCK(coarse_fom(ctx));
+    }
     ctx->step += seg;
     n_steps -= seg;
-    if (seg == to_event) {
-      RCK(coarse_fom(ctx));
-      RCK(run_event(ctx));
-    }
+    if (event) RCK(run_event(ctx));
   }
   return finish(ctx);
 }

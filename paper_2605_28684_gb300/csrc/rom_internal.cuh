@@ -411,6 +411,7 @@ struct DevState {
   double* minv;         // r x n_s  ((P^T Phi)^+, row-major r x n_s)
   // control
   GridBarrier* bar;
+  GridBarrier* fom_bar;  // the coarse FOM step's own barrier (it may run beside a step kernel)
   int* status;
   int* iters_rom;
   int* iters_fom;
@@ -440,6 +441,11 @@ struct rom_ctx {
   double prof_ms[kPhases];
   long long prof_cnt[kPhases];
   cudaStream_t stream;
+  // the coarse FOM step of an adaptation cycle runs on fom_stream beside the
+  // reduced steps when those are the single-CTA DEIM kernel (fom_overlap)
+  cudaStream_t fom_stream;
+  cudaEvent_t ev_fork, ev_join;
+  int fom_overlap;
   int64_t N;
   int64_t step;          // time level n
   int grid;              // CTAs of the generic cooperative kernels

@@ -63,49 +63,10 @@ __device__ void block_sort(double* v, int* idx) {
   __syncthreads();
 }
 
-// Sorts the first SIZE (value, index) pairs of v/idx in place in the order of
-// argmax_better (larger value, then lower index; equal pairs, which only the
-// empty sentinels can be, by position), by ranking: every entry counts the
-// entries ahead of it and moves to that position. SIZE^2 / threads
-// comparisons on broadcast shared-memory reads and two barriers, against the
-// log^2 SIZE barrier stages of a bitonic network. tv/ti: SIZE scratch entries.
-template <int SIZE>
-__device__ void rank_sort(double* v, int* idx, double* tv, int* ti) {
-  __syncthreads();
-  for (int e = threadIdx.x; e < SIZE; e += blockDim.x) { tv[e] = v[e]; ti[e] = idx[e]; }
-  __syncthreads();
-  for (int e = threadIdx.x; e < SIZE; e += blockDim.x) {
-    const long long ke = argmax_key(tv[e]);
-    const int ie = ti[e];
-    int r = 0;
-    for (int j = 0; j < SIZE; ++j) {
-      const long long kj = argmax_key(tv[j]);
-      const int ij = ti[j];
-      r += (kj > ke || (kj == ke && (ij < ie || (ij == ie && j < e)))) ? 1 : 0;
-    }
-    v[r] = tv[e];
-    idx[r] = ie;
-  }
-  __syncthreads();
-}
-
-// 1 / sqrt(x) in FP64 for a normal x: an FP32 estimate (about 22 correct
-// bits) refined by two Newton steps for 1/y^2 = x, y <- y (3 - x y^2) / 2,
-// each of which doubles the correct bits. Outside the FP32 range the FP64
-// division and square root are used. A dependent FP64 division or square
-// root costs hundreds of cycles on this part; this costs a few FMAs.
-__device__ __forceinline__ double rsqrt_nr(double x) {
-  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
-  double y = (double)rsqrtf((float)x);
-  y = y * fma(-0.5 * x, y * y, 1.5);
-  y = y * fma(-0.5 * x, y * y, 1.5);
-  return y;
-}
-
 }  // namespace
 
 template <int KM, typename TPhi>
-__global__ void __launch_bounds__(kBlock, 1) sampling_kernel(SampleArgs A) {
+__global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
   const TPhi* phi = basis<TPhi>(A);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SampleSmem& sm = *reinterpret_cast<SampleSmem*>(smem_raw);
@@ -178,23 +139,11 @@ __global__ void __launch_bounds__(kBlock, 1) sampling_kernel(SampleArgs A) {
       for (int j = lane; j < k; j += 32) sm.v[j] = (double)phi[j * ld + p];
       __syncwarp();
       for (int pass = 0; pass < 2; ++pass) {
-        // the step dot products in groups of eight independent reductions
-        for (int l0 = 0; l0 < step; l0 += 8) {
-          double d8[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            d8[u] = 0.0;
-            if (l0 + u < step)
-              for (int j = lane; j < k; j += 32) d8[u] = fma(sm.v[j], sm.q[(l0 + u) * kMaxR + j], d8[u]);
-          }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int u = 0; u < 8; ++u) d8[u] += __shfl_xor_sync(0xffffffffu, d8[u], o);
-          if (lane == 0)
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-              if (l0 + u < step) sm.w[l0 + u] = d8[u];
+        for (int l = 0; l < step; ++l) {
+          double s = 0.0;
+          for (int j = lane; j < k; j += 32) s = fma(sm.v[j], sm.q[l * kMaxR + j], s);
+          s = warp_sum(s);
+          if (lane == 0) sm.w[l] = s;
         }
         __syncwarp();
         for (int j = lane; j < k; j += 32) {
@@ -207,7 +156,7 @@ __global__ void __launch_bounds__(kBlock, 1) sampling_kernel(SampleArgs A) {
       double s = 0.0;
       for (int j = lane; j < k; j += 32) s = fma(sm.v[j], sm.v[j], s);
       s = warp_sum(s);
-      double inv = s > 0.0 ? rsqrt_nr(s) : 0.0;
+      double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
       for (int j = lane; j < k; j += 32) sm.q[step * kMaxR + j] = sm.v[j] * inv;
     }
     __syncthreads();
@@ -265,7 +214,7 @@ __global__ void __launch_bounds__(kBlock, 1) sampling_kernel(SampleArgs A) {
       if (one_pass) {
         sm.cv[t] = sc;
         sm.ci[t] = ii;
-        rank_sort<256>(sm.cv, sm.ci, sm.X, reinterpret_cast<int*>(sm.X + 512));
+        block_sort<256>(sm.cv, sm.ci);
       } else {
         sm.cv[256 + t] = sc;
         sm.ci[256 + t] = ii;
@@ -336,11 +285,9 @@ __global__ void __launch_bounds__(kBlock, 1) sampling_kernel(SampleArgs A) {
         sm.cv[e] = (e < total) ? __ldcg(&A.merge_v[e]) : -1.0;
         sm.ci[e] = (e < total) ? __ldcg(&A.merge_i[e]) : 0x7fffffff;
       }
-      double* tv = sm.X;                                 // scratch (the mesh rows come later)
-      int* ti = reinterpret_cast<int*>(sm.X + 512);
-      if (total <= 128) rank_sort<128>(sm.cv, sm.ci, tv, ti);
-      else if (total <= 256) rank_sort<256>(sm.cv, sm.ci, tv, ti);
-      else rank_sort<512>(sm.cv, sm.ci, tv, ti);
+      if (total <= 128) block_sort<128>(sm.cv, sm.ci);
+      else if (total <= 256) block_sort<256>(sm.cv, sm.ci);
+      else block_sort<512>(sm.cv, sm.ci);
       __syncthreads();
       for (int e = t; e < m; e += blockDim.x) sm.piv[kq + e] = sm.ci[e];
     } else {
@@ -446,10 +393,9 @@ __global__ void __launch_bounds__(kBlock, 1) sampling_kernel(SampleArgs A) {
       for (int l = lane; l < j; l += 32) s += sm.G[j * kMaxR + l] * sm.G[j * kMaxR + l];
       s = warp_sum(s);
       if (lane == 0) {
-        const double x = fmax(sm.G[j * kMaxR + j] - s, DBL_MIN);
-        const double rj = rsqrt_nr(x);
-        sm.G[j * kMaxR + j] = x * rj;    // sqrt(x)
-        sm.gdinv[j] = rj;
+        const double djj = sqrt(fmax(sm.G[j * kMaxR + j] - s, DBL_MIN));
+        sm.G[j * kMaxR + j] = djj;
+        sm.gdinv[j] = 1.0 / djj;       // one FP64 division per column
       }
       __syncwarp();
       const double rj = sm.gdinv[j];
