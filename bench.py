@@ -233,8 +233,14 @@ def algorithmic_work(phase: str, cfg, rank: int, launches: dict, fom_iters: floa
         # per Newton iteration: read q (with halo) and q_prev, write q
         return 24 * N * fom_iters, 30 * N * fom_iters
     if phase == "sampling":
-        # k QDEIM passes over Phi, the feature pass over y
-        return 8 * N * k * (k + 1) + 8 * N, 2 * N * k * (k + 1) + 3 * N
+        # QDEIM: the initial norms read Phi (k columns); each of the k - 1
+        # updates reads Phi and the s earlier coordinates of every row and
+        # writes one coordinate
+        return (8 * N * k * k + 8 * N * (k - 1) * k // 2,
+                2 * N * k * k + N * (k - 1) * k + 2 * N * (k - 1))
+    if phase == "feature_select":
+        # read y, write the keys, read them in the selection
+        return 24 * N, 2 * N
     # reduced steps: per Newton iteration the stencil mesh (Phi rows, q_ref,
     # d) and (P^T Phi)^+ are read once
     per_it = 8 * (3 * ns * (k + 2) + k * ns)
@@ -668,7 +674,8 @@ def main():
                  "hbm_frac": f_hbm, "fp64_frac": f_alu})
     phases = {p: {"ms_total": prof[p]["ms"], "launches": prof[p]["launches"],
                   "avg_us": prof[p]["ms"] * 1e3 / max(1, prof[p]["launches"])} for p in prof}
-    gpu_launches = sum(prof[p]["launches"] for p in prof)
+    # kernels: one per phase launch, two for the feature-guided selection
+    gpu_launches = sum(prof[p]["launches"] for p in prof) + prof.get("feature_select", {}).get("launches", 0)
 
     # end to end through the public API from pinned host buffers
     q0_pin = torch.from_numpy(q0.copy()).pin_memory()

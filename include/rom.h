@@ -211,12 +211,16 @@ rom_status rom_info(rom_ctx* ctx, int32_t* rank, int32_t* rom_newton_iters,
                     int32_t* fom_newton_iters);
 
 /*
- * Per-phase device timing (CUDA events recorded on the context's stream around
- * every launch of a phase while enabled). Phases: 0 reduced steps, 1 coarse
- * FOM step, 2 iSVD update, 3 sampling refresh. rom_profile(ctx, 1) clears the
- * totals and starts recording; rom_profile(ctx, 0) stops. rom_profile_read
- * synchronises and returns, per phase, the summed milliseconds and the number
- * of launches (arrays of 4). Errors: ROM_EINVAL, ROM_ECUDA, ROM_ESTATE.
+ * Per-phase device timing (CUDA events recorded around every launch of a
+ * phase, on the stream it runs on, while enabled). Phases: 0 reduced steps,
+ * 1 coarse FOM step, 2 iSVD update, 3 sampling refresh (QDEIM points, the
+ * sampled operator and stencil mesh), 4 feature-guided candidate selection on
+ * a new correction snapshot (hyper-reduced models; in an adaptation cycle it
+ * runs after the coarse FOM step, beside the reduced steps).
+ * rom_profile(ctx, 1) clears the totals and starts recording;
+ * rom_profile(ctx, 0) stops. rom_profile_read synchronises and returns, per
+ * phase, the summed milliseconds and the number of launches (arrays of 5).
+ * Errors: ROM_EINVAL, ROM_ECUDA, ROM_ESTATE.
  */
 rom_status rom_profile(rom_ctx* ctx, int32_t enable);
 rom_status rom_profile_read(rom_ctx* ctx, double* ms_total, int64_t* launches);

@@ -126,14 +126,14 @@ class AdaptiveROM:
         _lib.check(self._lib.rom_info(self._ctx, *[ctypes.byref(x) for x in v]), "rom_info")
         return dict(rank=v[0].value, rom_newton_iters=v[1].value, fom_newton_iters=v[2].value)
 
-    PHASES = ("reduced_steps", "coarse_fom", "isvd_update", "sampling")
+    PHASES = ("reduced_steps", "coarse_fom", "isvd_update", "sampling", "feature_select")
 
     def profile(self, enable: bool):
         _lib.check(self._lib.rom_profile(self._ctx, 1 if enable else 0), "rom_profile")
 
     def profile_read(self):
-        ms = (ctypes.c_double * 4)()
-        cnt = (ctypes.c_int64 * 4)()
+        ms = (ctypes.c_double * len(self.PHASES))()
+        cnt = (ctypes.c_int64 * len(self.PHASES))()
         _lib.check(self._lib.rom_profile_read(self._ctx, ms, cnt), "rom_profile_read")
         return {p: dict(ms=ms[i], launches=cnt[i]) for i, p in enumerate(self.PHASES)}
 

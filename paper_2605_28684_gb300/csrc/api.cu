@@ -136,6 +136,7 @@ float* basis32(const rom_ctx* ctx) { return mixed(ctx) ? ctx->d.phi32 : nullptr;
 cudaError_t prof_flush(rom_ctx* ctx) {
   if (ctx->prof_n == 0) return cudaSuccess;
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess && ctx->fom_overlap) e = cudaStreamSynchronize(ctx->fom_stream);
   if (e != cudaSuccess) return e;
   for (int i = 0; i < ctx->prof_n; ++i) {
     float ms = 0.f;
@@ -190,6 +191,18 @@ cudaError_t fom_step(rom_ctx* ctx, const double* q_prev, double* q, double h) {
   return launch_fom_step(fom_params(ctx, h), q_prev, q, fom_scratch(ctx), ctx->stream);
 }
 
+// The feature-guided candidates of a new correction snapshot y (hyper-reduced
+// models only), on stream s (the stream that produced y).
+cudaError_t select_features(rom_ctx* ctx, const double* y, cudaStream_t s) {
+  if (ctx->cfg.n_s <= 0) return cudaSuccess;
+  cudaError_t e = prof_mark(ctx, 4, true, s);
+  if (e == cudaSuccess)
+    e = launch_fgs(y, ctx->N, fgs_list_length(ctx->N, ctx->cfg.r, ctx->cfg.n_s), ctx->d.fgs_key, ctx->d.fgs_v,
+                   ctx->d.fgs_i, s);
+  if (e == cudaSuccess) e = prof_mark(ctx, 4, false, s);
+  return e;
+}
+
 EventArgs event_args(rom_ctx* ctx, const double* y, int preprocess, double lambda, double rank_tol,
                      int r_cap, int transfer, bool online = true) {
   EventArgs A;
@@ -229,18 +242,14 @@ SampleArgs sample_args(rom_ctx* ctx) {
   S.rank = ctx->d.rank;
   S.phi = ctx->d.phi;
   S.phi32 = basis32(ctx);
-  S.y = ctx->d.y_corr;
   S.q_ref = ctx->d.q_ref;
   S.drow = ctx->d.drow;
+  S.fgs_i = ctx->d.fgs_i;
+  S.fgs_t = fgs_list_length(ctx->N, ctx->cfg.r, ctx->cfg.n_s);
   S.samples = ctx->d.samples;
-  S.chosen = ctx->d.chosen;
-  S.resid = ctx->d.resid_norm;
   S.cand_v = ctx->d.cand_v;
   S.cand_i = ctx->d.cand_i;
-  S.merge_v = ctx->d.merge_v;
-  S.merge_i = ctx->d.merge_i;
-  S.merge_ctr = ctx->d.merge_ctr;
-  S.qdir = ctx->d.qdeim_q;
+  S.qd_u = ctx->d.qd_u;
   S.mesh = ctx->d.mesh;
   S.minv = ctx->d.minv;
   S.bar = ctx->d.bar;
@@ -391,6 +400,7 @@ cudaError_t coarse_fom_fork(rom_ctx* ctx) {
     e = launch_fom_step(fom_params(ctx, ctx->cfg.z * ctx->cfg.dt), ctx->d.y_corr, ctx->d.y_tmp,
                         fom_scratch(ctx), fs);
   if (e == cudaSuccess) e = prof_mark(ctx, 1, false, fs);
+  if (e == cudaSuccess) e = select_features(ctx, ctx->d.y_tmp, fs);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, fs);
   return e;
 }
@@ -411,6 +421,7 @@ cudaError_t coarse_fom(rom_ctx* ctx) {
     e = launch_fom_step(fom_params(ctx, ctx->cfg.z * ctx->cfg.dt), ctx->d.y_corr, ctx->d.y_tmp,
                         fom_scratch(ctx), ctx->stream);
   if (e == cudaSuccess) e = prof_mark(ctx, 1, false);
+  if (e == cudaSuccess) e = select_features(ctx, ctx->d.y_tmp, ctx->stream);
   if (e != cudaSuccess) return e;
   double* t = ctx->d.y_corr;
   ctx->d.y_corr = ctx->d.y_tmp;
@@ -475,8 +486,8 @@ void free_state(rom_ctx* ctx) {
   DevState& d = ctx->d;
   void* ptrs[] = {d.q_ref, d.y_corr, d.y_tmp, d.yhat, d.qres, d.lifted, d.dvals, d.drow, d.dinv, d.phi,
                   d.phi32, d.gram, d.sigma, d.a, d.a_prev, d.rank, d.core, d.ubar, d.partials,
-                  d.jpartials, d.jac, d.samples, d.chosen, d.resid_norm, d.qdeim_q, d.cand_v,
-                  d.cand_i, d.merge_v, d.merge_i, d.merge_ctr, d.mesh, d.minv, d.bar, d.fom_bar, d.status, d.iters_rom, d.iters_fom, d.maxbuf,
+                  d.jpartials, d.jac, d.samples, d.qd_u, d.cand_v,
+                  d.cand_i, d.fgs_key, d.fgs_v, d.fgs_i, d.mesh, d.minv, d.bar, d.fom_bar, d.status, d.iters_rom, d.iters_fom, d.maxbuf,
                   d.fom_chunk, d.npart, d.win, d.dwork, d.dsm, d.dpart, ctx->q_train};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -593,10 +604,12 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
   ALLOC(d.sigma, kMaxR + 1); ALLOC(d.a, kMaxR + 1); ALLOC(d.a_prev, kMaxR + 1); ALLOC(d.rank, 1);
   ALLOC(d.core, core_ws_doubles()); ALLOC(d.ubar, kMaxCore * kMaxCore);
   ALLOC(d.partials, (size_t)3 * G * (kMaxCore + 2)); ALLOC(d.jpartials, (size_t)G * kMaxR * kMaxR);
-  ALLOC(d.jac, kMaxR * kMaxR); ALLOC(d.samples, ns); ALLOC(d.chosen, N); ALLOC(d.resid_norm, N);
-  ALLOC(d.qdeim_q, kMaxR * kMaxR); ALLOC(d.cand_v, (size_t)G * kMaxNs);
-  ALLOC(d.cand_i, (size_t)G * kMaxNs); ALLOC(d.merge_v, (size_t)G * kMaxNs);
-  ALLOC(d.merge_i, (size_t)G * kMaxNs); ALLOC(d.merge_ctr, 2); ALLOC(d.mesh, (size_t)ns * 3 * kMeshStride);
+  ALLOC(d.jac, kMaxR * kMaxR); ALLOC(d.samples, ns); ALLOC(d.cand_v, (size_t)G * kMaxNs);
+  ALLOC(d.cand_i, (size_t)G * kMaxNs); ALLOC(d.mesh, (size_t)ns * 3 * kMeshStride);
+  if (ctx->cfg.n_s > 0) {
+    ALLOC(d.qd_u, (size_t)N * r); ALLOC(d.fgs_key, N);
+    ALLOC(d.fgs_v, 2 * kMaxNs); ALLOC(d.fgs_i, 2 * kMaxNs);
+  }
   ALLOC(d.minv, (size_t)kMaxR * ns); ALLOC(d.bar, 1); ALLOC(d.fom_bar, 1); ALLOC(d.status, 1); ALLOC(d.iters_rom, 1);
   ALLOC(d.iters_fom, 1); ALLOC(d.maxbuf, 4); ALLOC(d.fom_chunk, fom_chunk_floats());
   ALLOC(ctx->q_train, (size_t)N * w);
@@ -722,6 +735,7 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
     P.drow = d.drow; P.a = d.a; P.partials = d.partials; P.bar = d.bar; P.status = d.status;
     RCK(launch_project(P, km_of(ctx), G, s));
     RCK(fom_step(ctx, qlast, d.y_corr, ctx->cfg.z * ctx->cfg.dt));
+    RCK(select_features(ctx, d.y_corr, s));
     if (ctx->cfg.n_s > 0) RCK(launch_sampling(sample_args(ctx), km_of(ctx), G, s));
   }
   st = finish(ctx);
@@ -777,6 +791,7 @@ rom_status rom_update_basis(rom_ctx* ctx, const double* y_host) {
   if (y_host) {
     RCK(cudaMemcpyAsync(ctx->d.y_corr, y_host, sizeof(double) * ctx->N, cudaMemcpyHostToDevice,
                         ctx->stream));
+    RCK(select_features(ctx, ctx->d.y_corr, ctx->stream));
   } else {
     RCK(coarse_fom(ctx));
   }
@@ -859,6 +874,7 @@ rom_status rom_load_state(rom_ctx* ctx, const double* phi, const double* sigma, 
   RCK(cudaMemcpyAsync(ctx->d.a, a, sizeof(double) * r, cudaMemcpyHostToDevice, s));
   RCK(cudaMemcpyAsync(ctx->d.y_corr, y_corr, sizeof(double) * N, cudaMemcpyHostToDevice, s));
   RCK(cudaMemcpyAsync(ctx->d.rank, &k, sizeof(int), cudaMemcpyHostToDevice, s));
+  RCK(select_features(ctx, ctx->d.y_corr, s));
   if (ctx->cfg.n_s > 0) RCK(launch_sampling(sample_args(ctx), km_of(ctx), ctx->grid, s));
   rom_status st = finish(ctx);   // (also waits for the staged host copies above)
   if (st == ROM_OK) ctx->step = step;

@@ -7,8 +7,9 @@
 //   g(a) = a - a^n - dt (P^T Phi)^+ P^T D f(q~(a)) = 0.
 // Both are solved by Newton from a^n. The residual g is FP64 and fixes the
 // root; the Jacobian  I - dt Phi^T D J_f D^-1 Phi  (or its sampled form) is
-// formed in FP32 once per step at a^n and factorised by LU with partial
-// pivoting in FP32 (a chord iteration). Stopping rule as the oracle:
+// formed in FP32 once per step at a^n (the sampled form: once per launch, and
+// again whenever a step needs more than three iterations) and factorised by
+// LU with partial pivoting in FP32 (a chord iteration). Stopping rule as the oracle:
 // max|delta| <= tol (1 + max|a|).
 // The explicit form (App. D, the RDE solver's scheme) advances the same
 // right-hand sides da/dt = Phi^T D f (or (P^T Phi)^+ P^T D f) by the
@@ -326,6 +327,12 @@ __global__ void __launch_bounds__(kBlock) hyper_steps_kernel(StepArgs A) {
   for (int j = t; j < KM; j += blockDim.x) s_a[j] = (j < k) ? A.a[j] : 0.0;
   __syncthreads();
   int it_total = 0;
+  // The sampled Jacobian (its FP32 inverse) is formed at the first iteration
+  // of the launch and kept over its steps (the basis and samples are fixed
+  // within a launch, and z dt is short); it is formed again at the next
+  // iteration whenever a step has not converged after kChordIters.
+  constexpr int kChordIters = 3;
+  bool need_jac = true;
   for (int step = 0; step < A.nsteps; ++step) {
     for (int j = t; j < k; j += blockDim.x) s_ap[j] = s_a[j];
     __syncthreads();
@@ -347,7 +354,8 @@ __global__ void __launch_bounds__(kBlock) hyper_steps_kernel(StepArgs A) {
         s_jr3[3 * q] = rf.dl; s_jr3[3 * q + 1] = rf.dc; s_jr3[3 * q + 2] = rf.dr;
       }
       __syncthreads();
-      if (it == 1 && !A.explicit_rk) {
+      if (need_jac && !A.explicit_rk) {
+        need_jac = false;
         // sampled rows of D J_f D^-1 Phi (FP32), then J = I - dt M A (FP32)
         for (int e = t; e < ns * k; e += blockDim.x) {
           int q = e / k, l = e % k;
@@ -424,6 +432,7 @@ __global__ void __launch_bounds__(kBlock) hyper_steps_kernel(StepArgs A) {
         return;
       }
       if (s_sc[0] > 0.0) { conv = true; break; }
+      if (it >= kChordIters) need_jac = true;
     }
     it_total = A.explicit_rk ? 0 : (conv ? it : A.max_iter);
     if (!conv) {

@@ -399,14 +399,12 @@ struct DevState {
   float* jac;           // kMaxR * kMaxR
   // sampling (hyper-reduction)
   int* samples;         // n_s
-  int* chosen;          // N flags (QDEIM picks)
-  double* resid_norm;   // N (QDEIM residual norms)
-  double* qdeim_q;      // kMaxR * kMaxR (orthonormal pivot directions)
+  double* qd_u;         // N x r: row coordinates along the QDEIM residual directions
   double* cand_v;       // grid * kMaxNs candidate values
   int* cand_i;          // grid * kMaxNs candidate indices
-  double* merge_v;      // grid * kMaxNs merged candidates (values)
-  int* merge_i;         // grid * kMaxNs merged candidates (indices)
-  unsigned int* merge_ctr;  // 2 merge counters
+  unsigned long long* fgs_key;  // N: feature keys of the correction snapshot
+  double* fgs_v;        // feature-guided candidates (values), best first
+  int* fgs_i;           // their cell indices
   double* mesh;         // n_s * 3 * (kMaxR + 2): Phi rows, q_ref, d of the stencil
   double* minv;         // r x n_s  ((P^T Phi)^+, row-major r x n_s)
   // control
@@ -427,7 +425,7 @@ struct DevState {
 
 }  // namespace rom
 
-constexpr int kPhases = 4;
+constexpr int kPhases = 5;
 constexpr int kMaxProfEvents = 4096;
 
 struct rom_ctx {

@@ -109,24 +109,27 @@ struct SampleArgs {
   const int* rank;
   const double* phi;
   const float* phi32;
-  const double* y;      // correction snapshot (feature-guided points)
   const double* q_ref;
   const double* drow;
+  const int* fgs_i;     // feature-guided candidates, best first (launch_fgs)
+  int fgs_t;            // their number (>= fgs_list_length(n, r, n_s))
   int* samples;
-  int* chosen;          // n flags
-  double* resid;        // n
   double* cand_v;       // grid * kMaxNs
   int* cand_i;          // grid * kMaxNs
-  double* merge_v;      // grid * kMaxNs: entries at or above the merge threshold
-  int* merge_i;         // grid * kMaxNs
-  unsigned int* merge_ctr;  // 2: entries appended, CTAs done
-  double* qdir;         // kMaxR * kMaxR
+  double* qd_u;         // n x r: coordinates of the rows along the QDEIM residual directions
   double* mesh;         // n_s x 3 x (kMaxR + 2)
   double* minv;         // r x n_s
   GridBarrier* bar;
   int* status;
 };
 cudaError_t launch_sampling(const SampleArgs& A, int km, int grid, cudaStream_t s);
+// Length of the feature-guided candidate list: n_s + min(r, n_s) (at most n).
+int fgs_list_length(int64_t n, int r, int n_s);
+// The fgs_list_length best feature-guided candidates of the snapshot y
+// (fgs_key_kernel, fgs_select_kernel): values out_v, cell indices out_i,
+// best first; key is n words of scratch.
+cudaError_t launch_fgs(const double* y, int64_t n, int T, unsigned long long* key, double* out_v, int* out_i,
+                       cudaStream_t s);
 
 constexpr int kMeshStride = kMaxR + 2;   // per stencil row: k basis entries, q_ref, d
 

@@ -1,20 +1,30 @@
 // Sampling points of the DEIM-Galerkin model and the sampled-basis operators
-// (paper Eq. qdeim_qr, Eq. fgs_selection, Eq. deim_galerkin_rom), as one
-// cooperative kernel.
+// (paper Eq. qdeim_qr, Eq. fgs_selection, Eq. deim_galerkin_rom).
 //
-//  * QDEIM: the first k pivots of a column-pivoted QR of Phi^T, computed as
-//    greedy pivoting on the rows of Phi: take the row with the largest
-//    remaining squared norm (ties -> lowest index), append its normalised
-//    residual direction (classical Gram-Schmidt twice in R^k) to an
-//    orthonormal set, and subtract the squared component along it from every
-//    row's remaining norm.
-//  * Feature-guided points: the remaining n_s - k points are the cells with
-//    the largest squared forward difference (y_{i+1} - y_i)^2 of the
-//    correction snapshot (the feature map is the state itself), skipping
-//    cells already chosen, ties -> lowest index.
-//  * (P^T Phi)^+ = (A^T A)^{-1} A^T with A = P^T Phi (normal equations,
-//    Cholesky in FP64) and the stencil mesh (Phi, q_ref, D on the rows
-//    i-1, i, i+1 of every sampled cell) used by the hyper-reduced step.
+//  * Feature-guided candidates (fgs_key_kernel, fgs_select_kernel): the T
+//    cells with the largest squared forward difference (y_{i+1} - y_i)^2 of
+//    the correction snapshot (the feature map is the state itself), in
+//    decreasing order, ties -> lowest index. They depend only on the
+//    snapshot, so they are computed right after the coarse FOM step that
+//    produces it (beside the reduced steps of the interval), by an exact
+//    radix selection on the IEEE bit patterns of the squares.
+//  * QDEIM (sampling_kernel): the first k pivots of a column-pivoted QR of
+//    Phi^T, computed as greedy pivoting on the rows x_i of Phi: take the row
+//    with the largest remaining squared norm (ties -> lowest index). The
+//    remaining norms follow the pivoted Cholesky recursion of Phi Phi^T: with
+//    the pivot p_s of step s and its remaining norm v_s,
+//        c_i = x_i . x_{p_s} - sum_{l<s} c_i^(l) c_{p_s}^(l) / v_l,
+//        res_i <- res_i - c_i^2 / v_s,
+//    where c_i^(l) is row i's coordinate along the unnormalised residual
+//    direction of pivot l (kept in a device array). This is the same
+//    selection as Gram-Schmidt on the pivot directions, with one division
+//    per pivot and no serial orthogonalisation.
+//  * The remaining n_s - k points are the first feature-guided candidates
+//    that are not QDEIM points.
+//  * (P^T Phi)^+ = (A^T A)^{-1} A^T with A = P^T Phi (normal equations; the
+//    symmetric positive definite A^T A inverted by Gauss-Jordan elimination in
+//    FP64) and the stencil mesh (Phi, q_ref, D on the rows i-1, i, i+1 of
+//    every sampled cell) used by the hyper-reduced step.
 #include <cfloat>
 #include <cmath>
 
@@ -25,23 +35,12 @@ namespace rom {
 
 namespace {
 
-struct SampleSmem {
-  double q[kMaxR * kMaxR];   // orthonormal pivot directions (row j: direction j)
-  double v[kMaxR];
-  double w[kMaxR];
-  double red[64];
-  int redi[32];
-  double G[kMaxR * kMaxR];   // A^T A and its Cholesky factor
-  double gdinv[kMaxR];       // 1 / L_jj
-  int piv[kMaxNs];
-  long long off;
-  double cv[512];
-  int ci[512];
-  double X[256 * kMaxR];     // (P^T Phi)^+ columns being solved (n_s <= 256)
-};
+constexpr int kFgsThreads = 512;   // threads of the feature-guided selection (one CTA)
+constexpr int kFgsSort = 512;      // sort buffer of the selected candidates (T <= kFgsSort)
+constexpr int kFgsStageKeys = 24576;  // keys staged in shared memory (192 KB)
 
 // Bitonic sort (descending value, ascending index) of SIZE (value, index)
-// pairs in shared memory, SIZE a power of two <= 2 * blockDim.x.
+// pairs in shared memory, SIZE a power of two.
 template <int SIZE>
 __device__ void block_sort(double* v, int* idx) {
   for (int size = 2; size <= SIZE; size <<= 1) {
@@ -63,33 +62,196 @@ __device__ void block_sort(double* v, int* idx) {
   __syncthreads();
 }
 
+// Exclusive prefix sum of one int per thread over the block; *total gets the
+// sum. scratch: >= 33 ints.
+__device__ __forceinline__ int block_scan_excl(int v, int* scratch, int* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  __syncthreads();
+  if (lane == 31) scratch[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int w = (lane < nw) ? scratch[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) scratch[lane] = w;      // inclusive warp totals
+  }
+  __syncthreads();
+  const int before = (wid > 0) ? scratch[wid - 1] : 0;
+  *total = scratch[nw - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
 }  // namespace
 
-template <int KM, typename TPhi>
+// key_i = IEEE bits of (y_{i+1} - y_i)^2 (periodic). Squares are
+// non-negative, so the keys order like the values.
+__global__ void fgs_key_kernel(const double* __restrict__ y, int64_t n, unsigned long long* __restrict__ key) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = y[i + 1 == n ? 0 : i + 1] - y[i];
+    key[i] = (unsigned long long)__double_as_longlong(d * d);
+  }
+}
+
+// The T largest keys (ties -> lowest index), sorted, by one CTA: an MSB-first
+// radix selection with 8-bit digits finds the boundary key (or a prefix of it
+// whose whole bin is taken), then an ordered compaction collects the entries
+// above it and the lowest-index entries equal to it, and a bitonic sort
+// orders them.
+// With STAGE the keys are first copied to shared memory (n <= kFgsStageKeys),
+// so that the passes read on-chip memory.
+template <bool STAGE>
+__global__ void __launch_bounds__(kFgsThreads) fgs_select_kernel(const unsigned long long* __restrict__ gkey,
+                                                                 int64_t n, int T, double* out_v, int* out_i) {
+  extern __shared__ __align__(16) unsigned long long s_keys[];
+  const unsigned long long* key = STAGE ? s_keys : gkey;
+  if (STAGE) {
+#pragma unroll 8
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s_keys[i] = gkey[i];
+  }
+  __shared__ unsigned int hist[256];
+  __shared__ unsigned long long s_prefix, s_mask;
+  __shared__ long long s_need;
+  __shared__ int s_all_eq;
+  __shared__ int scan[33];
+  __shared__ double sv[kFgsSort];
+  __shared__ int si[kFgsSort];
+  const int t = threadIdx.x, lane = t & 31;
+  if (t == 0) {
+    s_prefix = 0ull;
+    s_mask = 0ull;
+    s_need = T;
+    s_all_eq = (n <= T) ? 1 : 0;      // fewer cells than T: every cell is a candidate
+  }
+  __syncthreads();
+  for (int shift = 56; shift >= 0 && !s_all_eq; shift -= 8) {
+    const unsigned long long prefix = s_prefix, mask = s_mask;
+    for (int b = t; b < 256; b += blockDim.x) hist[b] = 0u;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += blockDim.x) {   // every lane runs every pass
+      const int64_t i = base + t;
+      unsigned int dg = 0xffffffffu;                           // not counted
+      if (i < n) {
+        const unsigned long long kk = key[i];
+        if ((kk & mask) == prefix) dg = (unsigned int)((kk >> shift) & 255ull);
+      }
+      // one shared-memory atomic per distinct digit of the warp
+      const unsigned int peers = __match_any_sync(0xffffffffu, dg);
+      if (dg != 0xffffffffu && lane == __ffs(peers) - 1) atomicAdd(&hist[dg], (unsigned int)__popc(peers));
+    }
+    __syncthreads();
+    if (t < 32) {
+      // lane l holds the bins 255 - 8l ... 248 - 8l (descending)
+      const long long need = s_need;     // read before any lane writes it (the shuffles order them)
+      unsigned int c[8];
+      unsigned int sum = 0u;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) { c[u] = hist[255 - 8 * lane - u]; sum += c[u]; }
+      unsigned int incl = sum;
+      for (int o = 1; o < 32; o <<= 1) {
+        unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const unsigned int above = incl - sum;
+      const bool mine = (long long)above < need && need <= (long long)incl;
+      if (mine) {
+        unsigned int acc = above;
+        for (int u = 0; u < 8; ++u) {
+          if ((long long)(acc + c[u]) >= need) {
+            const unsigned long long d = (unsigned long long)(255 - 8 * lane - u);
+            const long long left = need - (long long)acc;
+            s_prefix = prefix | (d << shift);
+            s_mask = mask | (255ull << shift);
+            s_need = left;
+            s_all_eq = ((long long)c[u] == left) ? 1 : 0;   // the whole bin is taken
+            break;
+          }
+          acc += c[u];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // ordered compaction: thread t takes the contiguous rows [t R, (t+1) R)
+  const unsigned long long prefix = s_prefix, mask = s_mask;
+  const long long need = s_need;
+  const bool all_eq = s_all_eq != 0;
+  const int64_t R = (n + blockDim.x - 1) / blockDim.x;
+  const int64_t r0 = (int64_t)t * R, r1 = (r0 + R < n) ? r0 + R : n;
+  int n_above = 0, n_eq = 0;
+  for (int64_t i = r0; i < r1; ++i) {
+    const unsigned long long kk = key[i] & mask;
+    n_above += (kk > prefix) ? 1 : 0;
+    n_eq += (kk == prefix) ? 1 : 0;
+  }
+  int tot_above = 0, tot_eq = 0;
+  const int off_above = block_scan_excl(n_above, scan, &tot_above);
+  const int off_eq = block_scan_excl(n_eq, scan, &tot_eq);
+  const int take_eq = all_eq ? tot_eq : (int)need;
+  const int cnt = tot_above + take_eq;
+  for (int e = t; e < kFgsSort; e += blockDim.x) { sv[e] = -1.0; si[e] = 0x7fffffff; }
+  __syncthreads();
+  {
+    int pa = off_above, pe = off_eq;
+    for (int64_t i = r0; i < r1; ++i) {
+      const unsigned long long full = key[i];
+      const unsigned long long kk = full & mask;
+      if (kk > prefix) {
+        sv[pa] = __longlong_as_double((long long)full); si[pa] = (int)i; ++pa;
+      } else if (kk == prefix) {
+        if (pe < take_eq) { sv[tot_above + pe] = __longlong_as_double((long long)full); si[tot_above + pe] = (int)i; }
+        ++pe;
+      }
+    }
+  }
+  block_sort<kFgsSort>(sv, si);
+  for (int e = t; e < cnt && e < T; e += blockDim.x) {
+    out_v[e] = sv[e];
+    out_i[e] = si[e];
+  }
+}
+
+namespace {
+
+struct SampleSmem {
+  double xp[kMaxR];      // basis row of the current pivot
+  double up[kMaxR];      // its coordinates c_p^(l) / v_l, l < s
+  double w[kMaxR];       // 1 / v_l
+  double red[64];
+  int redi[32];
+  int scan[33];
+  int piv[kMaxNs];       // QDEIM points, then the feature-guided points
+  double G[kMaxR * kMaxR];   // A^T A, then its inverse (CTA 0)
+  // followed by A = P^T Phi (n_s x k, row-major) on CTA 0
+};
+
+}  // namespace
+
+template <typename TPhi>
 __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
   const TPhi* phi = basis<TPhi>(A);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SampleSmem& sm = *reinterpret_cast<SampleSmem*>(smem_raw);
+  double* X = reinterpret_cast<double*>(smem_raw + sizeof(SampleSmem));
   const int G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
   const int64_t N = A.n, ld = A.ld;
   const int64_t beg = (int64_t)b * N / G, end = (int64_t)(b + 1) * N / G;
   const int k = *A.rank;
   const int kq = k < A.n_s ? k : A.n_s;
-  const int lane = t & 31;
+  const int lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+  double* U = A.qd_u;   // c_i^(l): column l at U + l * N
 
-  // the merge counters (entries appended, CTAs done) are reset here, ahead of
-  // the grid barriers that separate this from their first use
-  if (b == 0 && t == 0) { A.merge_ctr[0] = 0u; A.merge_ctr[1] = 0u; }
-  // ---- initial residual norms and first local argmax ----
+  // ---- initial squared row norms and first local argmax ----
   // Each thread owns at most kRowsPerThread rows of this CTA's range and keeps
   // their remaining norms and chosen flags in registers across the pivots.
   constexpr int kRowsPerThread = 4;
-  // the first row of every thread is kept in registers across the pivots
-  // (bucket size 9; larger buckets reload it)
-  constexpr int KC = KM <= 9 ? KM : 1;
-  double x0[KC];
-#pragma unroll
-  for (int j = 0; j < KC; ++j) x0[j] = 0.0;
   double res[kRowsPerThread];
   bool taken[kRowsPerThread];
   ArgMax best{-1.0, 0x7fffffff};
@@ -100,23 +262,16 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
     taken[r] = false;
     if (i < end) {
       double s = 0.0;
-      if (KM <= 9 && r == 0) {
-#pragma unroll
-        for (int j = 0; j < KC; ++j)
-          if (j < k) x0[j] = (double)phi[j * ld + i];
-#pragma unroll
-        for (int j = 0; j < KC; ++j)
-          if (j < k) s = fma(x0[j], x0[j], s);
-      } else {
-        for (int j = 0; j < k; ++j) { double x = (double)phi[j * ld + i]; s = fma(x, x, s); }
-      }
+      for (int j = 0; j < k; ++j) { const double x = (double)phi[j * ld + i]; s = fma(x, x, s); }
       res[r] = s;
       if (argmax_better(s, (int)i, best.v, best.i)) { best.v = s; best.i = (int)i; }
     }
   }
-  best = block_argmax(best, sm.red, sm.redi);
-  if (t == 0) { A.cand_v[(size_t)b * kMaxNs] = best.v; A.cand_i[(size_t)b * kMaxNs] = best.i; }
-  if (!grid_sync(A.bar, A.status)) return;
+  if (kq > 0) {
+    best = block_argmax(best, sm.red, sm.redi);
+    if (t == 0) { A.cand_v[(size_t)b * kMaxNs] = best.v; A.cand_i[(size_t)b * kMaxNs] = best.i; }
+    if (!grid_sync(A.bar, A.status)) return;
+  }
 
   // Candidate slots are double-buffered by step parity, so one grid barrier
   // per pivot suffices: step s reads slot s&1 and writes slot (s+1)&1.
@@ -132,50 +287,24 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
     g = block_argmax(g, sm.red, sm.redi);
     const int p = g.i;
     if (t == 0) sm.piv[step] = p;
-    // residual direction of row p against the previous directions: classical
-    // Gram-Schmidt twice, by warp 0 alone (lanes over the k entries; no block
-    // barriers between the dot products and the updates)
-    if (t < 32) {
-      for (int j = lane; j < k; j += 32) sm.v[j] = (double)phi[j * ld + p];
-      __syncwarp();
-      for (int pass = 0; pass < 2; ++pass) {
-        for (int l = 0; l < step; ++l) {
-          double s = 0.0;
-          for (int j = lane; j < k; j += 32) s = fma(sm.v[j], sm.q[l * kMaxR + j], s);
-          s = warp_sum(s);
-          if (lane == 0) sm.w[l] = s;
-        }
-        __syncwarp();
-        for (int j = lane; j < k; j += 32) {
-          double x = sm.v[j];
-          for (int l = 0; l < step; ++l) x = fma(-sm.w[l], sm.q[l * kMaxR + j], x);
-          sm.v[j] = x;
-        }
-        __syncwarp();
-      }
-      double s = 0.0;
-      for (int j = lane; j < k; j += 32) s = fma(sm.v[j], sm.v[j], s);
-      s = warp_sum(s);
-      double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
-      for (int j = lane; j < k; j += 32) sm.q[step * kMaxR + j] = sm.v[j] * inv;
-    }
-    __syncthreads();
     if (step + 1 == kq) break;        // the last pivot needs no further update
-    // update residual norms, mark the pivot, next local argmax
+    // the pivot row, its scaled coordinates along the earlier directions, and
+    // 1 / v_s (independent loads and one division, issued together)
+    if (t < k) sm.xp[t] = (double)phi[t * ld + p];
+    if (t >= 64 && t - 64 < step) sm.up[t - 64] = __ldcg(&U[(size_t)(t - 64) * N + p]) * sm.w[t - 64];
+    if (t == 128) sm.w[step] = (g.v > 0.0) ? 1.0 / g.v : 0.0;
+    __syncthreads();
+    const double ws = sm.w[step];
     best = ArgMax{-1.0, 0x7fffffff};
 #pragma unroll
     for (int r = 0; r < kRowsPerThread; ++r) {
       const int64_t i = beg + t + (int64_t)r * blockDim.x;
       if (i < end) {
         double c = 0.0;
-        if (KM <= 9 && r == 0) {
-#pragma unroll
-          for (int j = 0; j < KC; ++j)
-            if (j < k) c = fma(x0[j], sm.q[step * kMaxR + j], c);
-        } else {
-          for (int j = 0; j < k; ++j) c = fma((double)phi[j * ld + i], sm.q[step * kMaxR + j], c);
-        }
-        res[r] = fma(-c, c, res[r]);
+        for (int j = 0; j < k; ++j) c = fma((double)phi[j * ld + i], sm.xp[j], c);
+        for (int l = 0; l < step; ++l) c = fma(-__ldcg(&U[(size_t)l * N + i]), sm.up[l], c);
+        U[(size_t)step * N + i] = c;
+        res[r] = fma(-c * ws, c, res[r]);
         if (i == p) taken[r] = true;
         if (!taken[r] && argmax_better(res[r], (int)i, best.v, best.i)) { best.v = res[r]; best.i = (int)i; }
       }
@@ -185,277 +314,144 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
     if (!grid_sync(A.bar, A.status)) return;
   }
 
-  // ---- feature-guided points: local top-m by (y_{i+1} - y_i)^2 ----
-  // Every CTA sorts its candidates (passes of 256 merged into a running top
-  // 256) and publishes its first min(m, 256) entries, their count and its
-  // m-th value (-1 if it has fewer than m). CTA 0 then gathers the entries at
-  // or above the largest published m-th value, lb: some list holds m
-  // entries >= lb, so the global top m are among them.
-  const int m = A.n_s - kq;
-  if (kq > 0 && !grid_sync(A.bar, A.status)) return;   // all CTAs have read the last slot
-  const int mm = m < 256 ? m : 256;
-  if (m > 0) {
-    for (int e = t; e < 512; e += blockDim.x) { sm.cv[e] = -1.0; sm.ci[e] = 0x7fffffff; }
-    __syncthreads();
-    const bool one_pass = (end - beg) <= 256;
-    for (int64_t base = beg; base < end; base += 256) {
-      int64_t i = base + t;
-      double sc = -1.0;
-      int ii = 0x7fffffff;
-      if (i < end) {
-        bool ch = false;
-        for (int s = 0; s < kq; ++s) ch = ch || (sm.piv[s] == (int)i);
-        if (!ch) {
-          double dy = A.y[(i + 1) % N] - A.y[i];
-          sc = dy * dy;
-          ii = (int)i;
-        }
+  // ---- feature-guided points: the first n_s - kq candidates that are not
+  // QDEIM points (every CTA makes the same choice) ----
+  const int ns = A.n_s;
+  const int m = ns - kq;
+  __syncthreads();
+  {
+    int off = 0;
+    for (int base = 0; base < A.fgs_t && off < m; base += blockDim.x) {
+      const int e = base + t;
+      int ci = -1;
+      if (e < A.fgs_t) {
+        ci = __ldcg(&A.fgs_i[e]);
+        for (int s = 0; s < kq; ++s) ci = (sm.piv[s] == ci) ? -1 : ci;
       }
-      if (one_pass) {
-        sm.cv[t] = sc;
-        sm.ci[t] = ii;
-        block_sort<256>(sm.cv, sm.ci);
-      } else {
-        sm.cv[256 + t] = sc;
-        sm.ci[256 + t] = ii;
-        block_sort<512>(sm.cv, sm.ci);      // top 256 end up in [0, 256)
-      }
-    }
-    int cnt = 0;                            // valid (non-negative) entries among the first mm
-    for (int e = t; e < mm; e += blockDim.x) {
-      A.cand_v[(size_t)b * kMaxNs + e] = sm.cv[e];
-      A.cand_i[(size_t)b * kMaxNs + e] = sm.ci[e];
-      cnt += (sm.cv[e] >= 0.0) ? 1 : 0;
-    }
-    cnt = (int)block_sum((double)cnt, sm.red);
-    if (t == 0) {
-      A.chosen[b] = cnt;
-      A.resid[b] = (cnt >= m) ? sm.cv[m - 1] : -1.0;
+      int tot = 0;
+      const int pos = off + block_scan_excl(ci >= 0 ? 1 : 0, sm.scan, &tot);
+      if (ci >= 0 && pos < m) sm.piv[kq + pos] = ci;
+      off += tot;
     }
   }
-  if (!grid_sync(A.bar, A.status)) return;
+  __syncthreads();
+  if (b == 0)
+    for (int s = t; s < ns; s += blockDim.x) A.samples[s] = sm.piv[s];
 
-  // ---- top-m of the G sorted candidate lists ----
-  // Every CTA finds lb (the largest published m-th value) and appends its own
-  // entries >= lb to one compact array (some list holds m such entries, so
-  // the global top m are among them; the order of appending does not matter:
-  // CTA 0 sorts them by value, then index). CTA 0 waits for the G appends
-  // (a bounded wait), sorts and keeps the first m.
-  if (m > 0) {
-    double lb = -1.0;
-    for (int bb = t; bb < G; bb += blockDim.x) lb = fmax(lb, __ldcg(&A.resid[bb]));
-    lb = block_max(lb, sm.red);
-    int c = 0;                               // this CTA's entries >= lb (a prefix: sorted)
-    for (int e = t; e < mm; e += blockDim.x) c += (sm.cv[e] >= lb && sm.cv[e] >= 0.0) ? 1 : 0;
-    c = (int)block_sum((double)c, sm.red);
-    if (t == 0) sm.off = (c > 0) ? (long long)atomicAdd(&A.merge_ctr[0], (unsigned int)c) : 0;
-    __syncthreads();
-    const long long off = sm.off;
-    for (int e = t; e < c; e += blockDim.x) {
-      A.merge_v[off + e] = sm.cv[e];
-      A.merge_i[off + e] = sm.ci[e];
+  // ---- stencil mesh: Phi, q_ref, D on rows i-1, i, i+1 of every sample;
+  // sample s by CTA s mod G (threads over the 3 (kMaxR + 2) entries) ----
+  for (int s = b; s < ns; s += G) {
+    const int64_t ic = sm.piv[s];
+    for (int e = t; e < 3 * kMeshStride; e += blockDim.x) {
+      const int o = e / kMeshStride, j = e % kMeshStride;
+      int64_t i = ic + o - 1;
+      i = (i < 0) ? i + N : ((i >= N) ? i - N : i);
+      double v;
+      if (j < kMaxR) v = (j < k) ? (double)phi[j * ld + i] : 0.0;
+      else if (j == kMaxR) v = A.q_ref[i];
+      else v = A.drow[i];
+      A.mesh[(size_t)(3 * s + o) * kMeshStride + j] = v;
     }
-    __threadfence();
-    __syncthreads();
-    if (t == 0) atomicAdd(&A.merge_ctr[1], 1u);
   }
   if (b != 0) return;
-  if (m > 0) {
-    __shared__ int s_ok;
-    if (t == 0) {
-      const volatile unsigned int* done = &A.merge_ctr[1];
-      const long long limit = c_wait_limit;
-      const long long t0 = clock64();
-      int ok = 1;
-      while (*done < (unsigned int)G) {
-        if (clock64() - t0 > limit) {
-          record_status(A.status, kStTimeout);
-          ok = 0;
-          break;
-        }
+
+  // ---- CTA 0: (P^T Phi)^+ = (A^T A)^{-1} A^T ----
+  for (int e = t; e < ns * k; e += blockDim.x) {
+    const int q = e / k, j = e % k;
+    X[e] = (double)phi[j * ld + sm.piv[q]];
+  }
+  __syncthreads();
+  // G = A^T A (upper triangle, one warp per entry, lanes over the samples)
+  for (int e = wid; e < k * k; e += nw) {
+    const int r = e / k, c = e % k;
+    if (r > c) continue;
+    double s = 0.0;
+    for (int q = lane; q < ns; q += 32) s = fma(X[q * k + r], X[q * k + c], s);
+    s = warp_sum(s);
+    if (lane == 0) { sm.G[r * kMaxR + c] = s; sm.G[c * kMaxR + r] = s; }
+  }
+  __syncthreads();
+  // in-place Gauss-Jordan inversion (no pivoting: A^T A is symmetric positive
+  // definite, so every leading pivot is positive)
+  for (int c = 0; c < k; ++c) {
+    const double inv = 1.0 / sm.G[c * kMaxR + c];
+    constexpr int kPer = kMaxR * kMaxR / kBlock;   // entries per thread at the largest k
+    double nv[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = t + u * kBlock;
+      nv[u] = 0.0;
+      if (e < k * k) {
+        const int i = e / k, j = e % k;
+        const double aij = sm.G[i * kMaxR + j], aic = sm.G[i * kMaxR + c], acj = sm.G[c * kMaxR + j];
+        if (i == c && j == c) nv[u] = inv;
+        else if (i == c) nv[u] = acj * inv;
+        else if (j == c) nv[u] = -aic * inv;
+        else nv[u] = fma(-aic * inv, acj, aij);
       }
-      __threadfence();
-      s_ok = ok;
     }
     __syncthreads();
-    if (!s_ok) return;
-    const int total = (int)__ldcg(&A.merge_ctr[0]);
-    if (total <= 512) {
-      for (int e = t; e < 512; e += blockDim.x) {
-        sm.cv[e] = (e < total) ? __ldcg(&A.merge_v[e]) : -1.0;
-        sm.ci[e] = (e < total) ? __ldcg(&A.merge_i[e]) : 0x7fffffff;
-      }
-      if (total <= 128) block_sort<128>(sm.cv, sm.ci);
-      else if (total <= 256) block_sort<256>(sm.cv, sm.ci);
-      else block_sort<512>(sm.cv, sm.ci);
-      __syncthreads();
-      for (int e = t; e < m; e += blockDim.x) sm.piv[kq + e] = sm.ci[e];
-    } else {
-      // more than 512 entries at or above lb: merge the lists one pick at a time
-      __shared__ int head[1024];
-      for (int bb = t; bb < G; bb += blockDim.x) head[bb] = 0;
-      __syncthreads();
-      for (int s = 0; s < m; ++s) {
-        ArgMax g{-2.0, 0x7fffffff};
-        int gb = -1;
-        for (int bb = t; bb < G; bb += blockDim.x) {
-          int h = head[bb];
-          if (h < __ldcg(&A.chosen[bb])) {
-            double v = A.cand_v[(size_t)bb * kMaxNs + h];
-            int i = A.cand_i[(size_t)bb * kMaxNs + h];
-            if (argmax_better(v, i, g.v, g.i)) { g.v = v; g.i = i; }
-          }
-        }
-        g = block_argmax(g, sm.red, sm.redi);
-        for (int bb = t; bb < G; bb += blockDim.x) {
-          int h = head[bb];
-          if (h < __ldcg(&A.chosen[bb]) && A.cand_i[(size_t)bb * kMaxNs + h] == g.i) gb = bb;
-        }
-        __syncthreads();
-        if (gb >= 0) head[gb] += 1;
-        if (t == 0) sm.piv[kq + s] = g.i;
-        __syncthreads();
-      }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = t + u * kBlock;
+      if (e < k * k) sm.G[(e / k) * kMaxR + e % k] = nv[u];
     }
+    __syncthreads();
   }
-  __syncthreads();
-  const int ns = A.n_s;
-  for (int s = t; s < ns; s += blockDim.x) A.samples[s] = sm.piv[s];
-
-  // ---- stencil mesh: Phi, q_ref, D on rows i-1, i, i+1 of every sample ----
-  // a warp takes kSpw samples per pass and issues all their loads (lanes over
-  // the kMaxR basis entries of the three rows; lanes 0..2 q_ref and D) before
-  // any store; the basis rows of the samples themselves (o = 1) are also
-  // staged in shared memory (X) for the Gram matrix
-  double* Ps = sm.X;                       // ns x k (row-major), rows of P^T Phi
-  {
-    constexpr int kSpw = 2;
-    const int wid = t >> 5, nw = blockDim.x >> 5;
-    for (int s0 = wid * kSpw; s0 < ns; s0 += nw * kSpw) {
-      double v[kSpw][2][3], qv[kSpw], dv[kSpw];
-#pragma unroll
-      for (int u = 0; u < kSpw; ++u) {
-        const int sidx = s0 + u;
-        const bool ok = sidx < ns;
-        const int64_t ic = ok ? (int64_t)sm.piv[sidx] : 0;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int j = lane + 32 * h;
-#pragma unroll
-          for (int o = 0; o < 3; ++o) {
-            const int64_t i = (ic + (o - 1) + N) % N;
-            v[u][h][o] = (ok && j < k) ? (double)phi[j * ld + i] : 0.0;
-          }
-        }
-        const int64_t il = (ic + ((lane < 3 ? lane : 1) - 1) + N) % N;
-        qv[u] = (ok && lane < 3) ? A.q_ref[il] : 0.0;
-        dv[u] = (ok && lane < 3) ? A.drow[il] : 0.0;
-      }
-#pragma unroll
-      for (int u = 0; u < kSpw; ++u) {
-        const int sidx = s0 + u;
-        if (sidx >= ns) continue;
-#pragma unroll
-        for (int o = 0; o < 3; ++o) {
-          double* row = A.mesh + (size_t)(3 * sidx + o) * kMeshStride;
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int j = lane + 32 * h;
-            if (j < kMaxR) row[j] = v[u][h][o];
-            if (o == 1 && j < k) Ps[sidx * k + j] = v[u][h][o];
-          }
-        }
-        if (lane < 3) {
-          double* row = A.mesh + (size_t)(3 * sidx + lane) * kMeshStride;
-          row[kMaxR] = qv[u];
-          row[kMaxR + 1] = dv[u];
-        }
-      }
-    }
-  }
-  __syncthreads();
-  // ---- G = A^T A with A = P^T Phi (k x k), FP64: one warp per entry ----
-  {
-    const int wid = t >> 5, nw = blockDim.x >> 5;
-    for (int e = wid; e < k * k; e += nw) {
-      int r = e / k, c = e % k;
-      double s = 0.0;
-      for (int q = lane; q < ns; q += 32) s = fma(Ps[q * k + r], Ps[q * k + c], s);
-      s = warp_sum(s);
-      if (lane == 0) sm.G[r * kMaxR + c] = s;
-    }
-  }
-  __syncthreads();
-  // Cholesky (lower) by warp 0, one column at a time
-  if (t < 32) {
-    for (int j = 0; j < k; ++j) {
-      double s = 0.0;
-      for (int l = lane; l < j; l += 32) s += sm.G[j * kMaxR + l] * sm.G[j * kMaxR + l];
-      s = warp_sum(s);
-      if (lane == 0) {
-        const double djj = sqrt(fmax(sm.G[j * kMaxR + j] - s, DBL_MIN));
-        sm.G[j * kMaxR + j] = djj;
-        sm.gdinv[j] = 1.0 / djj;       // one FP64 division per column
-      }
-      __syncwarp();
-      const double rj = sm.gdinv[j];
-      for (int i = j + 1 + lane; i < k; i += 32) {
-        double v = sm.G[i * kMaxR + j];
-        for (int l = 0; l < j; ++l) v -= sm.G[i * kMaxR + l] * sm.G[j * kMaxR + l];
-        sm.G[i * kMaxR + j] = v * rj;
-      }
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  // M = G^{-1} A^T: each sample column q solves L L^T x = A(q, :)^T; the
-  // solution overwrites the staged row q in shared memory
-  for (int q = t; q < ns; q += blockDim.x) {
-    double* x = Ps + q * k;
-    for (int i = 0; i < k; ++i) {
-      double s = x[i];
-      for (int l = 0; l < i; ++l) s -= sm.G[i * kMaxR + l] * x[l];
-      x[i] = s * sm.gdinv[i];
-    }
-    for (int i = k - 1; i >= 0; --i) {
-      double s = x[i];
-      for (int l = i + 1; l < k; ++l) s -= sm.G[l * kMaxR + i] * x[l];
-      x[i] = s * sm.gdinv[i];
-    }
-  }
-  __syncthreads();
+  // minv (r x n_s, row-major): rows j < k are (A^T A)^{-1} A^T, the rest zero
   for (int e = t; e < A.r * ns; e += blockDim.x) {
-    int i = e / ns, q = e % ns;
-    A.minv[e] = (i < k) ? Ps[q * k + i] : 0.0;
+    const int j = e / ns, q = e % ns;
+    double s = 0.0;
+    if (j < k)
+      for (int l = 0; l < k; ++l) s = fma(sm.G[j * kMaxR + l], X[q * k + l], s);
+    A.minv[e] = s;
   }
 }
 
-template <int KM, typename TPhi>
-static cudaError_t launch_sampling_tt(const SampleArgs& A, int grid, cudaStream_t s) {
-  size_t smem = sizeof(SampleSmem);
-  cudaError_t e = cudaFuncSetAttribute(sampling_kernel<KM, TPhi>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+int fgs_list_length(int64_t n, int r, int n_s) {
+  int64_t t = (int64_t)n_s + (r < n_s ? r : n_s);
+  return (int)(t < n ? t : n);
+}
+
+template <typename TPhi>
+static cudaError_t launch_sampling_t(const SampleArgs& A, int grid, cudaStream_t s) {
+  size_t smem = sizeof(SampleSmem) + sizeof(double) * (size_t)A.n_s * (size_t)A.r;
+  cudaError_t e = cudaFuncSetAttribute(sampling_kernel<TPhi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
   SampleArgs a = A;
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel((const void*)sampling_kernel<KM, TPhi>, dim3(grid),
-                                     dim3(kBlock), args, smem, s);
+  return cudaLaunchCooperativeKernel((const void*)sampling_kernel<TPhi>, dim3(grid), dim3(kBlock), args, smem, s);
 }
 
-template <int KM>
-static cudaError_t launch_sampling_t(const SampleArgs& A, int grid, cudaStream_t s) {
-  return A.phi32 ? launch_sampling_tt<KM, float>(A, grid, s) : launch_sampling_tt<KM, double>(A, grid, s);
-}
-
-cudaError_t launch_sampling(const SampleArgs& A, int km, int grid, cudaStream_t s) {
-  // each thread keeps the QDEIM norms of at most 4 rows in registers
+cudaError_t launch_sampling(const SampleArgs& A, int /*km*/, int grid, cudaStream_t s) {
+  // each thread keeps the QDEIM norms of at most 4 rows in registers; the
+  // feature-guided list must leave n_s - k candidates after the QDEIM points
   if ((A.n + grid - 1) / grid > 4 * kBlock) return cudaErrorInvalidValue;
-  switch (km) {
-    case 9: return launch_sampling_t<9>(A, grid, s);
-    case 17: return launch_sampling_t<17>(A, grid, s);
-    case 33: return launch_sampling_t<33>(A, grid, s);
-    default: return launch_sampling_t<65>(A, grid, s);
+  if (A.n_s > 256 || A.n_s < A.r || A.r > kMaxR || A.fgs_t > kFgsSort ||
+      A.fgs_t < fgs_list_length(A.n, A.r, A.n_s))
+    return cudaErrorInvalidValue;
+  return A.phi32 ? launch_sampling_t<float>(A, grid, s) : launch_sampling_t<double>(A, grid, s);
+}
+
+cudaError_t launch_fgs(const double* y, int64_t n, int T, unsigned long long* key, double* out_v, int* out_i,
+                       cudaStream_t s) {
+  if (T < 1 || T > kFgsSort || n < 1) return cudaErrorInvalidValue;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 256) blocks = 256;
+  fgs_key_kernel<<<blocks, 256, 0, s>>>(y, n, key);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (n <= kFgsStageKeys) {
+    const int smem = (int)(sizeof(unsigned long long) * n);
+    e = cudaFuncSetAttribute(fgs_select_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(unsigned long long) * kFgsStageKeys));
+    if (e != cudaSuccess) return e;
+    fgs_select_kernel<true><<<1, kFgsThreads, smem, s>>>(key, n, T, out_v, out_i);
+  } else {
+    fgs_select_kernel<false><<<1, kFgsThreads, 0, s>>>(key, n, T, out_v, out_i);
   }
+  return cudaGetLastError();
 }
 
 // Wait bound of this translation unit's kernels (see rom_internal.cuh).
