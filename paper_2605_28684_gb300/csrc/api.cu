@@ -248,7 +248,11 @@ SampleArgs sample_args(rom_ctx* ctx) {
   S.fgs_t = fgs_list_length(ctx->N, ctx->cfg.r, ctx->cfg.n_s);
   S.samples = ctx->d.samples;
   S.cand_v = ctx->d.cand_v;
-  S.cand_i = ctx->d.cand_i;
+  S.cand_f = ctx->d.cand_f;
+  // every launch takes kMaxR fresh epochs (one per QDEIM step), so a word
+  // left by an earlier launch never matches
+  ctx->sample_epoch += (unsigned int)kMaxR;
+  S.epoch = ctx->sample_epoch;
   S.qd_u = ctx->d.qd_u;
   S.mesh = ctx->d.mesh;
   S.minv = ctx->d.minv;
@@ -487,7 +491,7 @@ void free_state(rom_ctx* ctx) {
   void* ptrs[] = {d.q_ref, d.y_corr, d.y_tmp, d.yhat, d.qres, d.lifted, d.dvals, d.drow, d.dinv, d.phi,
                   d.phi32, d.gram, d.sigma, d.a, d.a_prev, d.rank, d.core, d.ubar, d.partials,
                   d.jpartials, d.jac, d.samples, d.qd_u, d.cand_v,
-                  d.cand_i, d.fgs_key, d.fgs_v, d.fgs_i, d.mesh, d.minv, d.bar, d.fom_bar, d.status, d.iters_rom, d.iters_fom, d.maxbuf,
+                  d.cand_f, d.fgs_key, d.fgs_v, d.fgs_i, d.mesh, d.minv, d.bar, d.fom_bar, d.status, d.iters_rom, d.iters_fom, d.maxbuf,
                   d.fom_chunk, d.npart, d.win, d.dwork, d.dsm, d.dpart, ctx->q_train};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -549,6 +553,7 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
   rom_ctx* ctx = new rom_ctx;
   memset(&ctx->d, 0, sizeof(DevState));
   ctx->fom_overlap = 0;
+  ctx->sample_epoch = 0u;
   ctx->q_train = nullptr;
   ctx->prof_on = 0;
   ctx->prof_n = 0;
@@ -605,7 +610,7 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
   ALLOC(d.core, core_ws_doubles()); ALLOC(d.ubar, kMaxCore * kMaxCore);
   ALLOC(d.partials, (size_t)3 * G * (kMaxCore + 2)); ALLOC(d.jpartials, (size_t)G * kMaxR * kMaxR);
   ALLOC(d.jac, kMaxR * kMaxR); ALLOC(d.samples, ns); ALLOC(d.cand_v, (size_t)G * kMaxNs);
-  ALLOC(d.cand_i, (size_t)G * kMaxNs); ALLOC(d.mesh, (size_t)ns * 3 * kMeshStride);
+  ALLOC(d.cand_f, (size_t)G * 2); ALLOC(d.mesh, (size_t)ns * 3 * kMeshStride);
   if (ctx->cfg.n_s > 0) {
     ALLOC(d.qd_u, (size_t)N * r); ALLOC(d.fgs_key, N);
     ALLOC(d.fgs_v, 2 * kMaxNs); ALLOC(d.fgs_i, 2 * kMaxNs);
@@ -634,6 +639,7 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
   cudaStream_t s = ctx->stream;
   RCK(cudaMemsetAsync(d.bar, 0, sizeof(GridBarrier), s));
   RCK(cudaMemsetAsync(d.fom_bar, 0, sizeof(GridBarrier), s));
+  RCK(cudaMemsetAsync(d.cand_f, 0, sizeof(unsigned long long) * G * 2, s));
   RCK(cudaMemsetAsync(d.status, 0, sizeof(int), s));
   RCK(cudaMemsetAsync(d.phi, 0, sizeof(double) * N * r_alloc, s));
   RCK(cudaMemsetAsync(d.sigma, 0, sizeof(double) * (kMaxR + 1), s));

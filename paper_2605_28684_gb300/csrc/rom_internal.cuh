@@ -401,7 +401,7 @@ struct DevState {
   int* samples;         // n_s
   double* qd_u;         // N x r: row coordinates along the QDEIM residual directions
   double* cand_v;       // grid * kMaxNs candidate values
-  int* cand_i;          // grid * kMaxNs candidate indices
+  unsigned long long* cand_f;  // grid * 2 QDEIM candidate words (epoch, index)
   unsigned long long* fgs_key;  // N: feature keys of the correction snapshot
   double* fgs_v;        // feature-guided candidates (values), best first
   int* fgs_i;           // their cell indices
@@ -447,6 +447,7 @@ struct rom_ctx {
   int64_t N;
   int64_t step;          // time level n
   int grid;              // CTAs of the generic cooperative kernels
+  unsigned int sample_epoch;  // epoch of the next sampling launch's first QDEIM step
   int poisoned;
   int win_head;          // oldest slot of the snapshot window
   rom::DevState d;

@@ -114,8 +114,9 @@ struct SampleArgs {
   const int* fgs_i;     // feature-guided candidates, best first (launch_fgs)
   int fgs_t;            // their number (>= fgs_list_length(n, r, n_s))
   int* samples;
-  double* cand_v;       // grid * kMaxNs
-  int* cand_i;          // grid * kMaxNs
+  double* cand_v;       // grid * 2: per-CTA QDEIM candidate values (two step parities)
+  unsigned long long* cand_f;  // grid * 2: (epoch << 32 | index) of those candidates
+  unsigned int epoch;   // first step epoch of this launch (the caller advances it by kMaxR per launch)
   double* qd_u;         // n x r: coordinates of the rows along the QDEIM residual directions
   double* mesh;         // n_s x 3 x (kMaxR + 2)
   double* minv;         // r x n_s

@@ -224,6 +224,7 @@ struct SampleSmem {
   double xp[kMaxR];      // basis row of the current pivot
   double up[kMaxR];      // its coordinates c_p^(l) / v_l, l < s
   double w[kMaxR];       // 1 / v_l
+  double ginv;           // reciprocal of the current Gauss-Jordan pivot
   double red[64];
   int redi[32];
   int scan[33];
@@ -250,8 +251,15 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
 
   // ---- initial squared row norms and first local argmax ----
   // Each thread owns at most kRowsPerThread rows of this CTA's range and keeps
-  // their remaining norms and chosen flags in registers across the pivots.
+  // their remaining norms and chosen flags in registers across the pivots;
+  // for its first row it also keeps the basis row and the coordinates c^(l)
+  // in registers while k <= kRegK.
   constexpr int kRowsPerThread = 4;
+  constexpr int kRegK = 8;
+  const bool regs = k <= kRegK;
+  double x0[kRegK], u0[kRegK];
+#pragma unroll
+  for (int j = 0; j < kRegK; ++j) { x0[j] = 0.0; u0[j] = 0.0; }
   double res[kRowsPerThread];
   bool taken[kRowsPerThread];
   ArgMax best{-1.0, 0x7fffffff};
@@ -262,29 +270,74 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
     taken[r] = false;
     if (i < end) {
       double s = 0.0;
-      for (int j = 0; j < k; ++j) { const double x = (double)phi[j * ld + i]; s = fma(x, x, s); }
+      if (r == 0 && regs) {
+#pragma unroll
+        for (int j = 0; j < kRegK; ++j)
+          if (j < k) x0[j] = (double)phi[j * ld + i];
+#pragma unroll
+        for (int j = 0; j < kRegK; ++j) s = fma(x0[j], x0[j], s);
+      } else {
+        for (int j = 0; j < k; ++j) { const double x = (double)phi[j * ld + i]; s = fma(x, x, s); }
+      }
       res[r] = s;
       if (argmax_better(s, (int)i, best.v, best.i)) { best.v = s; best.i = (int)i; }
     }
   }
-  if (kq > 0) {
-    best = block_argmax(best, sm.red, sm.redi);
-    if (t == 0) { A.cand_v[(size_t)b * kMaxNs] = best.v; A.cand_i[(size_t)b * kMaxNs] = best.i; }
-    if (!grid_sync(A.bar, A.status)) return;
-  }
 
-  // Candidate slots are double-buffered by step parity, so one grid barrier
-  // per pivot suffices: step s reads slot s&1 and writes slot (s+1)&1.
-  for (int step = 0; step < kq; ++step) {
-    const size_t rd = (size_t)(step & 1), wr = (size_t)((step + 1) & 1);
-    // global pivot (every CTA, same fixed-order reduction)
-    ArgMax g{-1.0, 0x7fffffff};
+  // Exchange of the per-CTA candidates without a grid barrier: CTA b writes
+  // the value of its candidate for step s to cand_v, fences, then writes the
+  // word (epoch_s << 32 | index) to cand_f; readers wait for the word of every
+  // CTA, then read the value. The slots are double-buffered by step parity:
+  // a CTA writes a step's slot only after it has seen every CTA's word of the
+  // step before, by which time every CTA has read the slot of two steps back.
+  auto publish = [&](int step_w, const ArgMax& c) {
+    if (t == 0) {
+      const size_t sl = (size_t)b * 2 + (size_t)(step_w & 1);
+      A.cand_v[sl] = c.v;
+      __threadfence();
+      const unsigned long long w = ((unsigned long long)(A.epoch + (unsigned int)step_w) << 32) |
+                                   (unsigned long long)(unsigned int)c.i;
+      *reinterpret_cast<volatile unsigned long long*>(&A.cand_f[sl]) = w;
+    }
+  };
+  // global argmax of step step_r over every CTA's candidate (fixed order);
+  // false if the wait ran out (a timeout is recorded)
+  auto gather = [&](int step_r, ArgMax& g) -> bool {
+    g = ArgMax{-1.0, 0x7fffffff};
+    bool late = false;
+    const unsigned int ep = A.epoch + (unsigned int)step_r;
     for (int bb = t; bb < G; bb += blockDim.x) {
-      double v = __ldcg(&A.cand_v[(size_t)bb * kMaxNs + rd]);
-      int i = __ldcg(&A.cand_i[(size_t)bb * kMaxNs + rd]);
+      const size_t sl = (size_t)bb * 2 + (size_t)(step_r & 1);
+      const volatile unsigned long long* f = reinterpret_cast<const volatile unsigned long long*>(&A.cand_f[sl]);
+      const long long limit = c_wait_limit;
+      const long long t0 = clock64();
+      unsigned long long w = *f;
+      while ((unsigned int)(w >> 32) != ep) {
+        if (clock64() - t0 > limit) { late = true; break; }
+        __nanosleep(32);
+        w = *f;
+      }
+      if (late) break;
+      __threadfence();
+      const double v = __ldcg(&A.cand_v[sl]);
+      const int i = (int)(unsigned int)(w & 0xffffffffull);
       if (argmax_better(v, i, g.v, g.i)) { g.v = v; g.i = i; }
     }
+    if (__syncthreads_or(late)) {
+      if (t == 0) record_status(A.status, kStTimeout);
+      return false;
+    }
     g = block_argmax(g, sm.red, sm.redi);
+    return true;
+  };
+
+  if (kq > 0) {
+    best = block_argmax(best, sm.red, sm.redi);
+    publish(0, best);
+  }
+  for (int step = 0; step < kq; ++step) {
+    ArgMax g;
+    if (!gather(step, g)) return;
     const int p = g.i;
     if (t == 0) sm.piv[step] = p;
     if (step + 1 == kq) break;        // the last pivot needs no further update
@@ -301,8 +354,20 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
       const int64_t i = beg + t + (int64_t)r * blockDim.x;
       if (i < end) {
         double c = 0.0;
-        for (int j = 0; j < k; ++j) c = fma((double)phi[j * ld + i], sm.xp[j], c);
-        for (int l = 0; l < step; ++l) c = fma(-__ldcg(&U[(size_t)l * N + i]), sm.up[l], c);
+        if (r == 0 && regs) {
+#pragma unroll
+          for (int j = 0; j < kRegK; ++j)
+            if (j < k) c = fma(x0[j], sm.xp[j], c);
+#pragma unroll
+          for (int l = 0; l < kRegK; ++l)
+            if (l < step) c = fma(-u0[l], sm.up[l], c);
+#pragma unroll
+          for (int l = 0; l < kRegK; ++l)
+            if (l == step) u0[l] = c;
+        } else {
+          for (int j = 0; j < k; ++j) c = fma((double)phi[j * ld + i], sm.xp[j], c);
+          for (int l = 0; l < step; ++l) c = fma(-__ldcg(&U[(size_t)l * N + i]), sm.up[l], c);
+        }
         U[(size_t)step * N + i] = c;
         res[r] = fma(-c * ws, c, res[r]);
         if (i == p) taken[r] = true;
@@ -310,8 +375,7 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
       }
     }
     best = block_argmax(best, sm.red, sm.redi);
-    if (t == 0) { A.cand_v[(size_t)b * kMaxNs + wr] = best.v; A.cand_i[(size_t)b * kMaxNs + wr] = best.i; }
-    if (!grid_sync(A.bar, A.status)) return;
+    publish(step + 1, best);
   }
 
   // ---- feature-guided points: the first n_s - kq candidates that are not
@@ -374,7 +438,9 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
   // in-place Gauss-Jordan inversion (no pivoting: A^T A is symmetric positive
   // definite, so every leading pivot is positive)
   for (int c = 0; c < k; ++c) {
-    const double inv = 1.0 / sm.G[c * kMaxR + c];
+    if (t == 0) sm.ginv = 1.0 / sm.G[c * kMaxR + c];   // one FP64 division per step
+    __syncthreads();
+    const double inv = sm.ginv;
     constexpr int kPer = kMaxR * kMaxR / kBlock;   // entries per thread at the largest k
     double nv[kPer];
 #pragma unroll
