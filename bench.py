@@ -661,8 +661,8 @@ def main():
     gfl = flops / avg_s / 1e9
     f_hbm = gbs / pk["hbm_gbs"]
     f_alu = gfl / FP64_PEAK_GFLOPS
-    tr = TRAFFIC.get(dom, {})
-    traffic = tr.get("bytes") if tr.get("sha1") == src_sha1(tr["src"]) else None
+    tr = TRAFFIC.get(dom)
+    traffic = tr["bytes"] if tr and tr["sha1"] == src_sha1(tr["src"]) else None
     if f_hbm >= f_alu:
         roof = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": f_hbm, "peak_source": pk["source"]}

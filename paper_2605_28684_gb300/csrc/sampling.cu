@@ -62,6 +62,16 @@ __device__ void block_sort(double* v, int* idx) {
   __syncthreads();
 }
 
+// GPU-scope acquire load and release store of a 64-bit word.
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 // Exclusive prefix sum of one int per thread over the block; *total gets the
 // sum. scratch: >= 33 ints.
 __device__ __forceinline__ int block_scan_excl(int v, int* scratch, int* total) {
@@ -101,10 +111,11 @@ __global__ void fgs_key_kernel(const double* __restrict__ y, int64_t n, unsigned
 }
 
 // The T largest keys (ties -> lowest index), sorted, by one CTA: an MSB-first
-// radix selection with 8-bit digits finds the boundary key (or a prefix of it
-// whose whole bin is taken), then an ordered compaction collects the entries
-// above it and the lowest-index entries equal to it, and a bitonic sort
-// orders them.
+// radix selection with 8-bit digits narrows the boundary until the entries
+// above it and the whole boundary bin fit the sort buffer (or the full key
+// is fixed), then an ordered compaction collects the entries above the
+// boundary and those in it (all of them, or at full key the lowest-index
+// ones), and a bitonic sort orders them; the first T are the result.
 // With STAGE the keys are first copied to shared memory (n <= kFgsStageKeys),
 // so that the passes read on-chip memory.
 template <bool STAGE>
@@ -170,7 +181,9 @@ __global__ void __launch_bounds__(kFgsThreads) fgs_select_kernel(const unsigned 
             s_prefix = prefix | (d << shift);
             s_mask = mask | (255ull << shift);
             s_need = left;
-            s_all_eq = ((long long)c[u] == left) ? 1 : 0;   // the whole bin is taken
+            // the entries above this bin and the whole bin fit the sort
+            // buffer: collect them all and let the sort decide (exact)
+            s_all_eq = ((long long)T - left + (long long)c[u] <= (long long)kFgsSort) ? 1 : 0;
             break;
           }
           acc += c[u];
@@ -179,26 +192,57 @@ __global__ void __launch_bounds__(kFgsThreads) fgs_select_kernel(const unsigned 
     }
     __syncthreads();
   }
-  // ordered compaction: thread t takes the contiguous rows [t R, (t+1) R)
   const unsigned long long prefix = s_prefix, mask = s_mask;
   const long long need = s_need;
   const bool all_eq = s_all_eq != 0;
-  const int64_t R = (n + blockDim.x - 1) / blockDim.x;
-  const int64_t r0 = (int64_t)t * R, r1 = (r0 + R < n) ? r0 + R : n;
-  int n_above = 0, n_eq = 0;
-  for (int64_t i = r0; i < r1; ++i) {
-    const unsigned long long kk = key[i] & mask;
-    n_above += (kk > prefix) ? 1 : 0;
-    n_eq += (kk == prefix) ? 1 : 0;
-  }
-  int tot_above = 0, tot_eq = 0;
-  const int off_above = block_scan_excl(n_above, scan, &tot_above);
-  const int off_eq = block_scan_excl(n_eq, scan, &tot_eq);
-  const int take_eq = all_eq ? tot_eq : (int)need;
-  const int cnt = tot_above + take_eq;
   for (int e = t; e < kFgsSort; e += blockDim.x) { sv[e] = -1.0; si[e] = 0x7fffffff; }
   __syncthreads();
-  {
+  int cnt;
+  if (all_eq) {
+    // every entry at or above the boundary prefix is collected (fewer than
+    // kFgsSort); the order of collection is irrelevant, the sort fixes it.
+    // Rows are strided over the threads (conflict-free shared-memory reads)
+    // and appended through one warp-aggregated counter.
+    __shared__ int s_cnt;
+    if (t == 0) s_cnt = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += blockDim.x) {   // every lane runs every pass
+      const int64_t i = base + t;
+      unsigned long long full = 0ull;
+      bool sel = false;
+      if (i < n) {
+        full = key[i];
+        sel = (full & mask) >= prefix;
+      }
+      const unsigned int bal = __ballot_sync(0xffffffffu, sel);
+      int pos0 = 0;
+      if (lane == 0 && bal) pos0 = atomicAdd(&s_cnt, __popc(bal));
+      pos0 = __shfl_sync(0xffffffffu, pos0, 0);
+      if (sel) {
+        const int pos = pos0 + __popc(bal & ((1u << lane) - 1u));
+        sv[pos] = __longlong_as_double((long long)full);
+        si[pos] = (int)i;
+      }
+    }
+    __syncthreads();
+    cnt = s_cnt;
+  } else {
+    // the full key is fixed and more entries share it than are needed: an
+    // ordered compaction (thread t takes the contiguous rows [t R, (t+1) R))
+    // takes the entries above it and the lowest-index ones equal to it
+    const int64_t R = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t r0 = (int64_t)t * R, r1 = (r0 + R < n) ? r0 + R : n;
+    int n_above = 0, n_eq = 0;
+    for (int64_t i = r0; i < r1; ++i) {
+      const unsigned long long kk = key[i] & mask;
+      n_above += (kk > prefix) ? 1 : 0;
+      n_eq += (kk == prefix) ? 1 : 0;
+    }
+    int tot_above = 0, tot_eq = 0;
+    const int off_above = block_scan_excl(n_above, scan, &tot_above);
+    const int off_eq = block_scan_excl(n_eq, scan, &tot_eq);
+    const int take_eq = (int)need;
+    cnt = tot_above + take_eq;
     int pa = off_above, pe = off_eq;
     for (int64_t i = r0; i < r1; ++i) {
       const unsigned long long full = key[i];
@@ -211,7 +255,11 @@ __global__ void __launch_bounds__(kFgsThreads) fgs_select_kernel(const unsigned 
       }
     }
   }
-  block_sort<kFgsSort>(sv, si);
+  // the smallest power-of-two sort that holds the collected entries (the
+  // rest of the buffer holds sentinels that sort last)
+  if (cnt <= 128) block_sort<128>(sv, si);
+  else if (cnt <= 256) block_sort<256>(sv, si);
+  else block_sort<kFgsSort>(sv, si);
   for (int e = t; e < cnt && e < T; e += blockDim.x) {
     out_v[e] = sv[e];
     out_i[e] = si[e];
@@ -224,12 +272,12 @@ struct SampleSmem {
   double xp[kMaxR];      // basis row of the current pivot
   double up[kMaxR];      // its coordinates c_p^(l) / v_l, l < s
   double w[kMaxR];       // 1 / v_l
-  double ginv;           // reciprocal of the current Gauss-Jordan pivot
   double red[64];
   int redi[32];
   int scan[33];
   int piv[kMaxNs];       // QDEIM points, then the feature-guided points
-  double G[kMaxR * kMaxR];   // A^T A, then its inverse (CTA 0)
+  double G[kMaxR * kMaxR];   // A^T A, and the Gauss-Jordan steps (CTA 0) ...
+  double G2[kMaxR * kMaxR];  // ... alternating with this buffer
   // followed by A = P^T Phi (n_s x k, row-major) on CTA 0
 };
 
@@ -294,10 +342,9 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
     if (t == 0) {
       const size_t sl = (size_t)b * 2 + (size_t)(step_w & 1);
       A.cand_v[sl] = c.v;
-      __threadfence();
       const unsigned long long w = ((unsigned long long)(A.epoch + (unsigned int)step_w) << 32) |
                                    (unsigned long long)(unsigned int)c.i;
-      *reinterpret_cast<volatile unsigned long long*>(&A.cand_f[sl]) = w;
+      st_release_u64(&A.cand_f[sl], w);   // orders the value (and the block's coordinates) before it
     }
   };
   // global argmax of step step_r over every CTA's candidate (fixed order);
@@ -308,17 +355,15 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
     const unsigned int ep = A.epoch + (unsigned int)step_r;
     for (int bb = t; bb < G; bb += blockDim.x) {
       const size_t sl = (size_t)bb * 2 + (size_t)(step_r & 1);
-      const volatile unsigned long long* f = reinterpret_cast<const volatile unsigned long long*>(&A.cand_f[sl]);
       const long long limit = c_wait_limit;
       const long long t0 = clock64();
-      unsigned long long w = *f;
+      unsigned long long w = ld_acquire_u64(&A.cand_f[sl]);
       while ((unsigned int)(w >> 32) != ep) {
         if (clock64() - t0 > limit) { late = true; break; }
         __nanosleep(32);
-        w = *f;
+        w = ld_acquire_u64(&A.cand_f[sl]);
       }
       if (late) break;
-      __threadfence();
       const double v = __ldcg(&A.cand_v[sl]);
       const int i = (int)(unsigned int)(w & 0xffffffffull);
       if (argmax_better(v, i, g.v, g.i)) { g.v = v; g.i = i; }
@@ -435,41 +480,34 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
     if (lane == 0) { sm.G[r * kMaxR + c] = s; sm.G[c * kMaxR + r] = s; }
   }
   __syncthreads();
-  // in-place Gauss-Jordan inversion (no pivoting: A^T A is symmetric positive
-  // definite, so every leading pivot is positive)
+  // Gauss-Jordan inversion (no pivoting: A^T A is symmetric positive
+  // definite, so every leading pivot is positive), one elimination step per
+  // barrier: step c reads Ga and writes Gb, then the two swap
+  double* Ga = sm.G;
+  double* Gb = sm.G2;
   for (int c = 0; c < k; ++c) {
-    if (t == 0) sm.ginv = 1.0 / sm.G[c * kMaxR + c];   // one FP64 division per step
-    __syncthreads();
-    const double inv = sm.ginv;
-    constexpr int kPer = kMaxR * kMaxR / kBlock;   // entries per thread at the largest k
-    double nv[kPer];
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-      const int e = t + u * kBlock;
-      nv[u] = 0.0;
-      if (e < k * k) {
-        const int i = e / k, j = e % k;
-        const double aij = sm.G[i * kMaxR + j], aic = sm.G[i * kMaxR + c], acj = sm.G[c * kMaxR + j];
-        if (i == c && j == c) nv[u] = inv;
-        else if (i == c) nv[u] = acj * inv;
-        else if (j == c) nv[u] = -aic * inv;
-        else nv[u] = fma(-aic * inv, acj, aij);
+    if (t < k * k) {
+      const double inv = 1.0 / Ga[c * kMaxR + c];
+      for (int e = t; e < k * k; e += blockDim.x) {
+        const int i = e / k, j = e - i * k;
+        const double aij = Ga[i * kMaxR + j], aic = Ga[i * kMaxR + c], acj = Ga[c * kMaxR + j];
+        double v;
+        if (i == c && j == c) v = inv;
+        else if (i == c) v = acj * inv;
+        else if (j == c) v = -aic * inv;
+        else v = fma(-aic * inv, acj, aij);
+        Gb[i * kMaxR + j] = v;
       }
     }
     __syncthreads();
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-      const int e = t + u * kBlock;
-      if (e < k * k) sm.G[(e / k) * kMaxR + e % k] = nv[u];
-    }
-    __syncthreads();
+    double* tmp = Ga; Ga = Gb; Gb = tmp;
   }
   // minv (r x n_s, row-major): rows j < k are (A^T A)^{-1} A^T, the rest zero
   for (int e = t; e < A.r * ns; e += blockDim.x) {
     const int j = e / ns, q = e % ns;
     double s = 0.0;
     if (j < k)
-      for (int l = 0; l < k; ++l) s = fma(sm.G[j * kMaxR + l], X[q * k + l], s);
+      for (int l = 0; l < k; ++l) s = fma(Ga[j * kMaxR + l], X[q * k + l], s);
     A.minv[e] = s;
   }
 }
