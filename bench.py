@@ -638,6 +638,12 @@ def main():
         lspg = synth.config_burgers_small()
         lspg.projection = 1
         forms["lspg_burgers_n512_r10_z10_fp64"] = timed_single(g, lspg, 2000)
+        # the instantaneous comparison rules of App. A (learning rates of the
+        # paper's Burgers tuning at z = 10)
+        for name, rule, eta in [("onestep", 3, 0.0), ("oja", 4, 0.01), ("grouse", 5, 0.01)]:
+            c = synth.config_burgers_small()
+            c.update_rule, c.learning_rate = rule, eta
+            forms[f"{name}_burgers_n512_r10_z10_fp64"] = timed_single(g, c, 2000)
         # the explicit form (SSPRK(4,3) fine and reduced steps, coarse BE
         # correction): Sod Galerkin at the configured size, and Burgers
         # DEIM-Galerkin with r QDEIM + r feature-guided points

@@ -52,7 +52,14 @@ typedef enum {
 typedef enum { ROM_BURGERS = 0, ROM_EULER = 1 } rom_problem;
 typedef enum { ROM_FP64 = 0, ROM_MIXED_FP32 = 1 } rom_precision;
 typedef enum { ROM_GALERKIN = 0, ROM_LSPG = 1 } rom_projection;
-typedef enum { ROM_UPDATE_ISVD = 0, ROM_UPDATE_WINDOWED_SVD = 1, ROM_UPDATE_DIRECT = 2 } rom_update_rule;
+typedef enum {
+    ROM_UPDATE_ISVD = 0,
+    ROM_UPDATE_WINDOWED_SVD = 1,
+    ROM_UPDATE_DIRECT = 2,
+    ROM_UPDATE_ONESTEP = 3,
+    ROM_UPDATE_OJA = 4,
+    ROM_UPDATE_GROUSE = 5
+} rom_update_rule;
 typedef enum { ROM_BACKWARD_EULER = 0, ROM_SSPRK43 = 1 } rom_time_scheme;
 
 /*
@@ -101,7 +108,21 @@ typedef enum { ROM_BACKWARD_EULER = 0, ROM_SSPRK43 = 1 } rom_time_scheme;
  *              span(Y (Phi^+ Y)^+) (Eqs. direct_optimization, direct_update),
  *              its "singular values" those of Phi^+ Y. Both transfer the state
  *              as a = Phi_new^T D (q~ - q_ref), and both are FP64 only.
- *  window      1 <= window <= min(w_init, 64) for rules 1 and 2 (unused by 0).
+ *              The instantaneous rules of App. A act on the live basis columns
+ *              and the correction snapshot already held, yhat = D (y - q_ref)
+ *              (an adaptation event updates the basis first and advances the
+ *              coarse FOM at its end, so the snapshot approximates the current
+ *              time level); the rank and sigma are kept:
+ *              ROM_UPDATE_ONESTEP (3): Phi <- orth(Phi + (yhat - Phi a) a^T / |a|^2)
+ *              with a the reduced state (Eq. onestep_update);
+ *              ROM_UPDATE_OJA (4): Phi <- orth(Phi + eta yhat (yhat^T Phi))
+ *              (Eq. oja_update); orth is CholQR applied twice, FP64;
+ *              ROM_UPDATE_GROUSE (5): the rank-one geodesic step of Eqs.
+ *              grouse_projection, grouse_update with alpha = eta |p| |r| (the
+ *              residual by Gram-Schmidt twice; orthonormal by construction).
+ *              Rules 3-5: FP64, n_s = 0, backward Euler; they transfer the state
+ *              as rules 1 and 2.
+ *  window      1 <= window <= min(w_init, 64) for rules 1 and 2 (unused otherwise).
  *  time_scheme ROM_BACKWARD_EULER (0): fine FOM steps and reduced steps by
  *              backward Euler (Newton). ROM_SSPRK43 (1): the explicit form of
  *              the paper's RDE solver (App. D): the fine FOM steps of the
@@ -113,6 +134,7 @@ typedef enum { ROM_BACKWARD_EULER = 0, ROM_SSPRK43 = 1 } rom_time_scheme;
  *              step stays backward Euler over z*dt (Eq.
  *              coarse_fom_backward_euler). Galerkin, ROM_FP64 and
  *              ROM_UPDATE_ISVD only.
+ *  learning_rate  eta >= 0 of rules 4 and 5 (unused otherwise).
  */
 typedef struct {
     int32_t problem;
@@ -134,6 +156,7 @@ typedef struct {
     int32_t update_rule;
     int32_t window;
     int32_t time_scheme;
+    double learning_rate;
 } rom_config;
 
 /*

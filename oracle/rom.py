@@ -25,6 +25,10 @@ passage of the paper:
 * ``windowed_svd_update``, ``direct_update``  the comparison rules of App. A
                      (Eqs. wsvd_window_matrix, wsvd_update; direct_optimization,
                      direct_update) on the window of correction snapshots.
+* ``onestep_update``, ``oja_update``, ``grouse_update``  the instantaneous
+                     comparison rules of App. A (Eqs. onestep_update,
+                     oja_update, grouse_projection, grouse_update) on the
+                     current correction snapshot.
 * ``AdaptiveROM``    Algorithm 1.
 
 Readings where the paper is silent: see the module-level constants and the
@@ -432,6 +436,79 @@ def direct_update(Phi, Y, r):
 
 
 # ----------------------------------------------------------------------------
+# instantaneous comparison rules (App. A): one-step, Oja, GROUSE
+# ----------------------------------------------------------------------------
+#
+# Each acts on the live (non-null) columns of the basis and keeps the rank;
+# null columns stay zero. orth(.) is read as the orthonormal factor of the
+# thin QR factorisation: the online loop only uses the subspace (the
+# Galerkin step and the state transfer are invariant under Phi -> Phi Q), so
+# any orthonormal basis of the same span serves.
+
+def _orth(X):
+    Q, _ = np.linalg.qr(X)
+    return Q
+
+
+def _live(Phi):
+    return Phi[:, :numerical_rank(Phi)]
+
+
+def _with_nulls(Phi, P):
+    out = np.zeros_like(Phi)
+    out[:, :P.shape[1]] = P
+    return out
+
+
+def onestep_update(Phi, yhat, a):
+    """Eq. onestep_update: Phi_new = orth(Phi + (yhat - Phi a) a^T / |a|^2) with
+    a the reduced state before the update; after the rank-one correction
+    (before orth) Phi a equals yhat, so yhat lies in the new span."""
+    P = _live(Phi)
+    k = P.shape[1]
+    ak = np.asarray(a[:k], dtype=np.float64)
+    nn = float(ak @ ak)
+    if k == 0 or nn == 0.0:
+        return Phi.copy()
+    X = P + np.outer(yhat - P @ ak, ak) / nn
+    return _with_nulls(Phi, _orth(X))
+
+
+def oja_update(Phi, yhat, eta):
+    """Eq. oja_update: Phi_new = orth(Phi + eta yhat (yhat^T Phi))."""
+    P = _live(Phi)
+    if P.shape[1] == 0:
+        return Phi.copy()
+    X = P + eta * np.outer(yhat, yhat @ P)
+    return _with_nulls(Phi, _orth(X))
+
+
+def grouse_update(Phi, yhat, eta):
+    """Eqs. grouse_projection and grouse_update: w the least-squares
+    coefficients of yhat in span(Phi) and r = yhat - Phi w (classical
+    Gram-Schmidt twice, which keeps r orthogonal to Phi to rounding relative to
+    |r|, so that the update stays orthonormal when yhat is nearly in the span),
+    p = Phi w,
+    alpha = eta |p| |r|, and the rank-one geodesic step
+    Phi + ((cos alpha - 1) p/|p| + sin alpha r/|r|) w^T/|w| (orthonormal by
+    construction; no update when p, r or w vanishes)."""
+    P = _live(Phi)
+    if P.shape[1] == 0:
+        return Phi.copy()
+    w, rv = project_cgs2(P, yhat)       # least squares for orthonormal P, residual by CGS2
+    pv = P @ w
+    npn, nr, nw = float(np.linalg.norm(pv)), float(np.linalg.norm(rv)), float(np.linalg.norm(w))
+    if npn == 0.0 or nr == 0.0 or nw == 0.0:
+        return Phi.copy()
+    alpha = eta * npn * nr
+    X = P + np.outer((np.cos(alpha) - 1.0) * pv / npn + np.sin(alpha) * rv / nr, w / nw)
+    return _with_nulls(Phi, X)
+
+
+INSTANT_RULES = (3, 4, 5)   # one-step, Oja, GROUSE
+
+
+# ----------------------------------------------------------------------------
 # Algorithm 1
 # ----------------------------------------------------------------------------
 
@@ -512,6 +589,9 @@ class AdaptiveROM:
     def adapt(self, q_tilde):
         """The adaptation event of Algorithm 1 for the reconstructed state q_tilde."""
         c = self.cfg
+        if self.rule in INSTANT_RULES:
+            self._adapt_instant(q_tilde)
+            return
         self.y_corr = self.coarse_step(self.y_corr)
         yhat = self.d * (self.y_corr - self.q_ref)
         if self.rule in (1, 2):
@@ -532,6 +612,26 @@ class AdaptiveROM:
         if c.n_s > 0:
             self._refresh_sampling()
         self.a = self.Phi.T @ (self.d * (q_tilde - self.q_ref))
+        self.events += 1
+
+    def _adapt_instant(self, q_tilde):
+        """Event of the instantaneous rules (App. A, and the note to Algorithm
+        1 that they take the coarse-FOM step at the end of the loop): the basis
+        update uses the correction snapshot already held, which approximates
+        the state at the current time level; the state is transferred; then
+        the coarse FOM advances that snapshot by z dt for the next event."""
+        c = self.cfg
+        yhat = self.d * (self.y_corr - self.q_ref)
+        if self.rule == 3:
+            self.Phi = onestep_update(self.Phi, yhat, self.a)
+        elif self.rule == 4:
+            self.Phi = oja_update(self.Phi, yhat, getattr(c, "learning_rate", 0.0))
+        else:
+            self.Phi = grouse_update(self.Phi, yhat, getattr(c, "learning_rate", 0.0))
+        if c.n_s > 0:
+            self._refresh_sampling()
+        self.a = self.Phi.T @ (self.d * (q_tilde - self.q_ref))
+        self.y_corr = self.coarse_step(self.y_corr)
         self.events += 1
 
     # -- driver --------------------------------------------------------------

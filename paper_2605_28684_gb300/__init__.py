@@ -46,6 +46,7 @@ def make_config(cfg) -> _lib.RomConfigC:
     c.update_rule = int(getattr(cfg, "update_rule", 0))
     c.window = int(getattr(cfg, "window", 0))
     c.time_scheme = int(getattr(cfg, "time_scheme", 0))
+    c.learning_rate = float(getattr(cfg, "learning_rate", 0.0))
     return c
 
 

@@ -40,6 +40,7 @@ class RomConfigC(ctypes.Structure):
         ("update_rule", ctypes.c_int32),
         ("window", ctypes.c_int32),
         ("time_scheme", ctypes.c_int32),
+        ("learning_rate", ctypes.c_double),
     ]
 
 

@@ -89,9 +89,13 @@ rom_status validate(const rom_config* c) {
   if (c->projection != ROM_GALERKIN && c->projection != ROM_LSPG) return ROM_EINVAL;
   if (c->projection == ROM_LSPG && (c->problem != ROM_BURGERS || c->precision != ROM_FP64))
     return ROM_EINVAL;
-  if (c->update_rule < ROM_UPDATE_ISVD || c->update_rule > ROM_UPDATE_DIRECT) return ROM_EINVAL;
-  if (c->update_rule != ROM_UPDATE_ISVD &&
+  if (c->update_rule < ROM_UPDATE_ISVD || c->update_rule > ROM_UPDATE_GROUSE) return ROM_EINVAL;
+  if ((c->update_rule == ROM_UPDATE_WINDOWED_SVD || c->update_rule == ROM_UPDATE_DIRECT) &&
       (c->precision != ROM_FP64 || c->window < 1 || c->window > c->w_init || c->window > kMaxR))
+    return ROM_EINVAL;
+  if (c->update_rule >= ROM_UPDATE_ONESTEP &&
+      (c->precision != ROM_FP64 || c->n_s != 0 || c->time_scheme != ROM_BACKWARD_EULER ||
+       !(c->learning_rate >= 0.0) || !std::isfinite(c->learning_rate)))
     return ROM_EINVAL;
   if (c->time_scheme != ROM_BACKWARD_EULER && c->time_scheme != ROM_SSPRK43) return ROM_EINVAL;
   if (c->time_scheme == ROM_SSPRK43 &&
@@ -309,7 +313,11 @@ cudaError_t run_steps(rom_ctx* ctx, int nsteps) {
 cudaError_t run_event_window(rom_ctx* ctx);
 
 // The adaptation event of Algorithm 1 on the current y_corr.
+cudaError_t run_event_instant(rom_ctx* ctx);
+bool instant_rule(const rom_ctx* ctx) { return ctx->cfg.update_rule >= ROM_UPDATE_ONESTEP; }
+
 cudaError_t run_event(rom_ctx* ctx) {
+  if (instant_rule(ctx)) return run_event_instant(ctx);
   if (ctx->cfg.update_rule != ROM_UPDATE_ISVD) return run_event_window(ctx);
   EventArgs A = event_args(ctx, ctx->d.y_corr, 1, ctx->cfg.lambda, ctx->cfg.rank_tol, ctx->cfg.r, 1);
   cudaError_t e = prof_mark(ctx, 2, true);
@@ -387,6 +395,68 @@ cudaError_t run_event_window(rom_ctx* ctx) {
     if (e == cudaSuccess) e = prof_mark(ctx, 3, false);
   }
   return e;
+}
+
+// The instantaneous rules of App. A (one-step, Oja, GROUSE) on the live
+// columns: the lifted state with the old basis, yhat = D (y_corr - q_ref)
+// (the snapshot held, approximating the current time level), the products
+// the rule needs (Phi^T yhat; for GROUSE the residual r by Gram-Schmidt twice
+// and |r|^2), the rank-one update Phi += u v^T, CholQR twice for one-step and
+// Oja, and the state transfer a = Phi_new^T D (q~ - q_ref). The caller
+// advances the coarse FOM after this. The host reads the rank for the launch
+// sizes (one synchronisation per event).
+cudaError_t run_event_instant(rom_ctx* ctx) {
+  const int64_t N = ctx->N;
+  const int r = ctx->cfg.r, G = ctx->grid, rule = ctx->cfg.update_rule;
+  cudaStream_t s = ctx->stream;
+  DevState& d = ctx->d;
+  cudaError_t e = prof_mark(ctx, 2, true);
+  if (e != cudaSuccess) return e;
+  int k = 0;
+  if ((e = cudaMemcpyAsync(&k, d.rank, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  if (k > r) k = r;
+  LiftArgs L;
+  L.n = N; L.ld = N; L.rank = d.rank; L.phi = d.phi; L.phi32 = nullptr; L.q_ref = d.q_ref;
+  L.drow = d.drow; L.dinv = d.dinv; L.a = d.a; L.out = d.lifted;
+  if ((e = launch_lift(L, km_of(ctx), s)) != cudaSuccess) return e;
+  if (k > 0) {
+    double* Gm = d.dsm;                          // k x k Gram (ld k)
+    double* Rinv = d.dsm + kMaxR * kMaxR;        // k x k (ld kMaxR)
+    double* w1 = Rinv + kMaxR * kMaxR;
+    double* w2 = w1 + kMaxR;
+    double* g = w2 + kMaxR;
+    double* v = g + kMaxR;
+    double* coef = v + kMaxR;                    // c_y, c_r, |r|^2
+    double* rr = coef + 2;
+    if ((e = launch_win_fill(d.y_corr, N, d.q_ref, d.drow, N, 1, d.yhat, s)) != cudaSuccess) return e;
+    if ((e = launch_tn(TnArgs{N, k, 1, d.phi, N, d.yhat, N, 1.0, d.dpart, w1}, G, s)) != cudaSuccess) return e;
+    if (rule == ROM_UPDATE_GROUSE) {
+      e = launch_nn(NnArgs{N, k, 1, d.phi, N, w1, 1, 1, -1.0, 1.0, d.yhat, N, d.qres, N}, s);
+      if (e == cudaSuccess) e = launch_tn(TnArgs{N, k, 1, d.phi, N, d.qres, N, 1.0, d.dpart, w2}, G, s);
+      if (e == cudaSuccess) e = launch_nn(NnArgs{N, k, 1, d.phi, N, w2, 1, 1, -1.0, 1.0, d.qres, N, d.qres, N}, s);
+      if (e == cudaSuccess) e = launch_tn(TnArgs{N, 1, 1, d.qres, N, d.qres, N, 1.0, d.dpart, rr}, G, s);
+    } else {
+      e = cudaMemsetAsync(w2, 0, sizeof(double) * (kMaxR + 8 + 3 * kMaxR), s);
+    }
+    if (e != cudaSuccess) return e;
+    e = launch_instant_coef(rule, d.rank, r, ctx->cfg.learning_rate, w1, w2, d.a, rr, coef, g, v, s);
+    if (e == cudaSuccess) e = launch_rank1_update(d.phi, N, d.rank, r, d.yhat, d.qres, coef, g, v, s);
+    for (int pass = 0; e == cudaSuccess && rule != ROM_UPDATE_GROUSE && pass < 2; ++pass) {
+      e = launch_tn(TnArgs{N, k, k, d.phi, N, d.phi, N, 1.0, d.dpart, Gm}, G, s);
+      if (e == cudaSuccess) e = launch_chol_inv(Gm, d.rank, r, Rinv, s);
+      if (e == cudaSuccess)
+        e = launch_nn(NnArgs{N, k, k, d.phi, N, Rinv, kMaxR, 1, 1.0, 0.0, d.dwork, N, d.dwork, N}, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d.phi, d.dwork, sizeof(double) * N * k, cudaMemcpyDeviceToDevice, s);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  ProjectArgs P;
+  P.n = N; P.ld = N; P.r = r; P.rank = d.rank; P.phi = d.phi; P.phi32 = nullptr; P.v = d.lifted;
+  P.q_ref = d.q_ref; P.drow = d.drow; P.a = d.a; P.partials = d.partials; P.bar = d.bar; P.status = d.status;
+  if ((e = launch_project(P, km_of(ctx), G, s)) != cudaSuccess) return e;
+  return prof_mark(ctx, 2, false);
 }
 
 // The coarse FOM step of a cycle on fom_stream, after everything queued on
@@ -626,7 +696,7 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
   if (ctx->cfg.update_rule != ROM_UPDATE_ISVD) {
     ALLOC(d.win, (size_t)N * ctx->cfg.window);
     ALLOC(d.dwork, (size_t)N * kMaxR);
-    ALLOC(d.dsm, 2 * kMaxR * kMaxR + kMaxR + 8);
+    ALLOC(d.dsm, 2 * kMaxR * kMaxR + 6 * kMaxR + 16);
     ALLOC(d.dpart, (size_t)G * kMaxR * kMaxR);
   }
 #undef ALLOC
@@ -729,7 +799,7 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
     RCK(cudaStreamSynchronize(s));
   }
   // the comparison rules' window: the last `window` training snapshots, preprocessed
-  if (ctx->cfg.update_rule != ROM_UPDATE_ISVD) {
+  if (ctx->cfg.update_rule == ROM_UPDATE_WINDOWED_SVD || ctx->cfg.update_rule == ROM_UPDATE_DIRECT) {
     const int nw = ctx->cfg.window;
     RCK(launch_win_fill(ctx->q_train + (size_t)(w - nw) * N, N, d.q_ref, d.drow, N, nw, d.win, s));
   }
@@ -781,11 +851,14 @@ rom_status rom_step(rom_ctx* ctx, int64_t n_steps) {
       RCK(coarse_fom_join(ctx));
     } else {
       RCK(run_steps(ctx, (int)seg));
-      if (event) RCK(coarse_fom(ctx));
+      if (event && !instant_rule(ctx)) RCK(coarse_fom(ctx));
     }
     ctx->step += seg;
     n_steps -= seg;
-    if (event) RCK(run_event(ctx));
+    if (event) {
+      RCK(run_event(ctx));
+      if (instant_rule(ctx)) RCK(coarse_fom(ctx));   // the instantaneous rules advance the snapshot last
+    }
   }
   return finish(ctx);
 }
@@ -798,10 +871,11 @@ rom_status rom_update_basis(rom_ctx* ctx, const double* y_host) {
     RCK(cudaMemcpyAsync(ctx->d.y_corr, y_host, sizeof(double) * ctx->N, cudaMemcpyHostToDevice,
                         ctx->stream));
     RCK(select_features(ctx, ctx->d.y_corr, ctx->stream));
-  } else {
+  } else if (!instant_rule(ctx)) {
     RCK(coarse_fom(ctx));
   }
   RCK(run_event(ctx));
+  if (!y_host && instant_rule(ctx)) RCK(coarse_fom(ctx));
   return finish(ctx);
 }
 

@@ -341,5 +341,14 @@ cudaError_t launch_truncate(double* phi, int64_t n, double* sigma, int* rank, in
 cudaError_t launch_direct_small(const double* C, int r, int w, const int* rank, double tol, double* Vc,
                                 double* s_out, int* kc, cudaStream_t s);
 cudaError_t launch_set_sigma(const double* s_in, const int* kc, double* sigma, int* rank, cudaStream_t s);
+// Instantaneous rules (one-step, Oja, GROUSE): coefficients of the rank-one
+// update, the update itself, and the inverse Cholesky factor of a Gram matrix.
+cudaError_t launch_instant_coef(int rule, const int* rank, int r, double eta, const double* w1, const double* w2,
+                                const double* a, const double* rr, double* coef, double* g, double* v,
+                                cudaStream_t s);
+cudaError_t launch_rank1_update(double* phi, int64_t n, const int* rank, int r, const double* yhat,
+                                const double* res, const double* coef, const double* g, const double* v,
+                                cudaStream_t s);
+cudaError_t launch_chol_inv(const double* G, const int* rank, int r, double* Rinv, cudaStream_t s);
 
 }  // namespace rom

@@ -10,7 +10,12 @@
 //  * Direct: C = Phi^T Y (r x w), its right singular vectors V_c of the
 //    singular values above the rank tolerance by one-sided Jacobi on C^T
 //    (one CTA, FP64), then an orthonormal basis of span(Y V_c) =
-//    span(Y (Phi^+ Y)^+) by the growing iSVD over the columns of Y V_c.
+//    span(Y (Phi^+ Y)^+) by the growing iSVD over the columns of Y V_c;
+// and the instantaneous rules on the live columns of the basis (one-step,
+// Oja, GROUSE: Eqs. onestep_update, oja_update, grouse_projection,
+// grouse_update), all of the form Phi <- Phi + u v^T with
+// u = c_y yhat + c_r r + Phi g, then (one-step, Oja) orthonormalisation by
+// CholQR: G = Phi^T Phi, Phi <- Phi R^-1 with G = R^T R (FP64).
 #include <cfloat>
 #include <cmath>
 
@@ -144,7 +149,118 @@ __global__ void set_sigma_kernel(const double* s, const int* kc, double* sigma, 
   }
 }
 
+// Coefficients of the rank-one update of an instantaneous rule (one thread):
+// in: w1 = Phi^T yhat, w2 = Phi^T q1 (GROUSE's second Gram-Schmidt pass),
+// a (reduced state), rr = |r|^2; out: coef = (c_y, c_r), g (k), v (k).
+__global__ void instant_coef_kernel(int rule, const int* rank, int r, double eta, const double* w1,
+                                    const double* w2, const double* a, const double* rr, double* coef,
+                                    double* g, double* v) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int k = *rank < r ? *rank : r;
+  double cy = 0.0, cr = 0.0;
+  for (int j = 0; j < k; ++j) { g[j] = 0.0; v[j] = 0.0; }
+  if (rule == ROM_UPDATE_ONESTEP) {             // u = yhat - Phi a, v = a / |a|^2
+    double nn = 0.0;
+    for (int j = 0; j < k; ++j) nn = fma(a[j], a[j], nn);
+    if (nn > 0.0) {
+      cy = 1.0;
+      for (int j = 0; j < k; ++j) { g[j] = -a[j]; v[j] = a[j] / nn; }
+    }
+  } else if (rule == ROM_UPDATE_OJA) {          // u = eta yhat, v = Phi^T yhat
+    cy = eta;
+    for (int j = 0; j < k; ++j) v[j] = w1[j];
+  } else {                                      // GROUSE
+    double ww = 0.0;
+    for (int j = 0; j < k; ++j) { const double wj = w1[j] + w2[j]; ww = fma(wj, wj, ww); }
+    const double np = sqrt(ww), nr = sqrt(*rr);  // |p| = |Phi w| = |w| for orthonormal Phi
+    if (np > 0.0 && nr > 0.0) {
+      const double al = eta * np * nr;
+      cr = sin(al) / nr;
+      const double cw = (cos(al) - 1.0) / np;   // u = cw Phi w + cr r, v = w / |w|
+      for (int j = 0; j < k; ++j) {
+        const double wj = w1[j] + w2[j];
+        g[j] = cw * wj;
+        v[j] = wj / np;
+      }
+    }
+  }
+  coef[0] = cy;
+  coef[1] = cr;
+}
+
+// Phi[i, j] += u_i v_j (j < k) with u_i = c_y yhat_i + c_r res_i + sum_l Phi[i, l] g_l;
+// each row is read whole before it is written, so the update is in place.
+__global__ void rank1_update_kernel(double* phi, int64_t n, const int* rank, int r, const double* yhat,
+                                    const double* res, const double* coef, const double* g, const double* v) {
+  const int k = *rank < r ? *rank : r;
+  __shared__ double sg[kMaxR], sv[kMaxR];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) { sg[j] = g[j]; sv[j] = v[j]; }
+  __syncthreads();
+  const double cy = coef[0], cr = coef[1];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double u = cy * yhat[i];
+    if (cr != 0.0) u = fma(cr, res[i], u);
+    for (int l = 0; l < k; ++l) u = fma(phi[l * n + i], sg[l], u);
+    for (int j = 0; j < k; ++j) phi[j * n + i] = fma(u, sv[j], phi[j * n + i]);
+  }
+}
+
+// R^-1 (k x k upper triangular, row-major, ld kMaxR) of the Cholesky factor
+// G = R^T R of the Gram matrix G (k x k row-major, ld k), by one warp: the
+// factor row by row (lanes over the row), then the inverse column by column
+// (lane j back-substitutes column j).
+__global__ void chol_inv_kernel(const double* G, const int* rank, int r, double* Rinv) {
+  __shared__ double R[kMaxR * kMaxR];
+  const int k = *rank < r ? *rank : r;
+  const int lane = threadIdx.x;
+  for (int e = lane; e < kMaxR * kMaxR; e += 32) R[e] = 0.0;
+  __syncwarp();
+  for (int c = 0; c < k; ++c) {
+    double s = 0.0;
+    for (int l = lane; l < c; l += 32) s = fma(R[l * kMaxR + c], R[l * kMaxR + c], s);
+    s = warp_sum(s);
+    const double d = sqrt(fmax(G[c * k + c] - s, DBL_MIN));
+    const double id = 1.0 / d;
+    for (int j = c + 1 + lane; j < k; j += 32) {
+      double x = G[c * k + j];
+      for (int l = 0; l < c; ++l) x = fma(-R[l * kMaxR + c], R[l * kMaxR + j], x);
+      R[c * kMaxR + j] = x * id;
+    }
+    if (lane == 0) R[c * kMaxR + c] = d;
+    __syncwarp();
+  }
+  for (int j = lane; j < k; j += 32) {
+    for (int i = j; i >= 0; --i) {
+      double x = (i == j) ? 1.0 : 0.0;
+      for (int l = i + 1; l <= j; ++l) x = fma(-R[i * kMaxR + l], Rinv[l * kMaxR + j], x);
+      Rinv[i * kMaxR + j] = x / R[i * kMaxR + i];
+    }
+    for (int i = j + 1; i < k; ++i) Rinv[i * kMaxR + j] = 0.0;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_instant_coef(int rule, const int* rank, int r, double eta, const double* w1, const double* w2,
+                                const double* a, const double* rr, double* coef, double* g, double* v,
+                                cudaStream_t s) {
+  instant_coef_kernel<<<1, 32, 0, s>>>(rule, rank, r, eta, w1, w2, a, rr, coef, g, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rank1_update(double* phi, int64_t n, const int* rank, int r, const double* yhat,
+                                const double* res, const double* coef, const double* g, const double* v,
+                                cudaStream_t s) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 1024) blocks = 1024;
+  rank1_update_kernel<<<blocks, 256, 0, s>>>(phi, n, rank, r, yhat, res, coef, g, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_inv(const double* G, const int* rank, int r, double* Rinv, cudaStream_t s) {
+  chol_inv_kernel<<<1, 32, 0, s>>>(G, rank, r, Rinv);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_win_fill(const double* Q, int64_t ldq, const double* q_ref, const double* drow, int64_t n,
                             int count, double* win, cudaStream_t s) {

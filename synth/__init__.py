@@ -126,7 +126,9 @@ class RomConfig:
     precision: int = 0        # 0: FP64, 1: mixed FP32
     projection: int = 0       # 0: Galerkin, 1: least-squares Petrov-Galerkin
     ic: str = "fourier"       # "fourier": the seeded family; "gaussian": the paper's pulse
-    update_rule: int = 0      # 0: iSVD (Algorithm 2); 1: windowed SVD; 2: Direct (App. A)
+    update_rule: int = 0      # 0: iSVD (Algorithm 2); 1: windowed SVD; 2: Direct; 3: one-step;
+                              # 4: Oja; 5: GROUSE (App. A)
+    learning_rate: float = 0.0  # eta of rules 4 and 5
     window: int = 0           # snapshots in the window of rules 1 and 2
     time_scheme: int = 0      # 0: backward Euler; 1: SSPRK(4,3), explicit (Galerkin only)
     seed: int = 0

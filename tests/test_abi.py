@@ -62,10 +62,21 @@ def test_invalid_configs_rejected(lib):
     c.projection, c.precision = 1, 1          # no mixed-precision LSPG form
     bad.append(c)
     # comparison update rules: unknown rule, window outside 1..min(w_init, 64), FP64 only
-    for rule, window, prec in [(3, 8, 0), (1, 0, 0), (2, 101, 0), (1, 8, 1)]:
+    for rule, window, prec in [(6, 8, 0), (1, 0, 0), (2, 101, 0), (1, 8, 1)]:
         c = synth.config_burgers_small()
         c.update_rule, c.window, c.precision = rule, window, prec
         bad.append(c)
+    # instantaneous rules: FP64, plain Galerkin sampling (n_s = 0), backward
+    # Euler, a finite non-negative learning rate
+    for rule, field, val in [(3, "precision", 1), (4, "learning_rate", -1.0), (5, "learning_rate", float("nan")),
+                             (5, "time_scheme", 1)]:
+        c = synth.config_burgers_small()
+        c.update_rule, c.learning_rate = rule, 0.01
+        setattr(c, field, val)
+        bad.append(c)
+    c = synth.config_burgers_hyper()
+    c.n_cells, c.update_rule = 2048, 4
+    bad.append(c)
     # time schemes: unknown; the explicit form is Galerkin, FP64 and iSVD only
     for field, val in [("time_scheme", 2), ("projection", 1), ("precision", 1), ("update_rule", 1)]:
         c = synth.config_burgers_small()
