@@ -65,14 +65,14 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # one ncu capture of each kernel on this workload (summarised under profiles/);
 # reported only while the kernel's source file is unchanged (sha1).
 TRAFFIC = {
-    "isvd_update": {"bytes": 1726464, "src": "paper_2605_28684_gb300/csrc/isvd.cu",
-                    "sha1": "04d9a2f76a29ce18e5b2d85d3825c6ecfdd939c1"},
-    "coarse_fom": {"bytes": 164736, "src": "paper_2605_28684_gb300/csrc/fom.cu",
-                   "sha1": "9ac9def378168c9a4419c8e6d4a2ef53e7b328b9"},
-    "reduced_steps": {"bytes": 131328, "src": "paper_2605_28684_gb300/csrc/reduced.cu",
-                      "sha1": "4a2337f50f3eabb5166972928632f5977719e5d1"},
-    "sampling": {"bytes": 1358592, "src": "paper_2605_28684_gb300/csrc/sampling.cu",
-                 "sha1": "d1c431fe36a57bd4721be962d5d4c096560e0acf"},
+    "isvd_update": {"bytes": 1721344, "src": "paper_2605_28684_gb300/csrc/isvd_impl.cuh",
+                    "sha1": "02f79657ce901fced5825170c4e8942e8be9debe"},
+    "coarse_fom": {"bytes": 162304, "src": "paper_2605_28684_gb300/csrc/fom.cu",
+                   "sha1": "4186dd4b29c5d5f770230efc2cc4ccac8888452c"},
+    "reduced_steps": {"bytes": 114432, "src": "paper_2605_28684_gb300/csrc/reduced.cu",
+                      "sha1": "3f3f179e24b109a25493bf20a1cc41a02a3eaa0d"},
+    "sampling": {"bytes": 1149440, "src": "paper_2605_28684_gb300/csrc/sampling.cu",
+                 "sha1": "e3e0b58a1af26d22a8785bcbf500a98d39951e8c"},
 }
 
 
@@ -635,6 +635,10 @@ def main():
         forms["c1_full_horizon"] = timed_full_horizon(g, workload_config(), 20000)
         sod = synth.config_sod()
         forms["sod_full_horizon"] = timed_full_horizon(g, sod, sod.n_online, chunk=100)
+        # the paper's Sod size (256 cells) over its whole horizon to t = 0.2,
+        # with the ROM error against the fine FOM
+        sod256 = synth.config_sod(256)
+        forms["sod_n256_full_horizon"] = timed_full_horizon(g, sod256, sod256.n_online)
         lspg = synth.config_burgers_small()
         lspg.projection = 1
         forms["lspg_burgers_n512_r10_z10_fp64"] = timed_single(g, lspg, 2000)
