@@ -197,14 +197,22 @@ cudaError_t fom_step(rom_ctx* ctx, const double* q_prev, double* q, double h) {
 
 // The feature-guided candidates of a new correction snapshot y (hyper-reduced
 // models only), on stream s (the stream that produced y).
-cudaError_t select_features(rom_ctx* ctx, const double* y, cudaStream_t s) {
+cudaError_t select_features(rom_ctx* ctx, const double* y, cudaStream_t s, bool stage = true) {
   if (ctx->cfg.n_s <= 0) return cudaSuccess;
   cudaError_t e = prof_mark(ctx, 4, true, s);
   if (e == cudaSuccess)
     e = launch_fgs(y, ctx->N, fgs_list_length(ctx->N, ctx->cfg.r, ctx->cfg.n_s), ctx->d.fgs_key, ctx->d.fgs_v,
-                   ctx->d.fgs_i, s);
+                   ctx->d.fgs_i, stage, s);
   if (e == cudaSuccess) e = prof_mark(ctx, 4, false, s);
   return e;
+}
+
+// The context's stream waits for a feature-guided selection still running
+// on the coarse-FOM stream (see coarse_fom_fork).
+cudaError_t wait_features(rom_ctx* ctx) {
+  if (!ctx->fgs_pending) return cudaSuccess;
+  ctx->fgs_pending = 0;
+  return cudaStreamWaitEvent(ctx->stream, ctx->ev_fgs, 0);
 }
 
 EventArgs event_args(rom_ctx* ctx, const double* y, int preprocess, double lambda, double rank_tol,
@@ -325,7 +333,8 @@ cudaError_t run_event(rom_ctx* ctx) {
   if (e == cudaSuccess) e = prof_mark(ctx, 2, false);
   if (e != cudaSuccess) return e;
   if (ctx->cfg.n_s > 0) {
-    e = prof_mark(ctx, 3, true);
+    e = wait_features(ctx);
+    if (e == cudaSuccess) e = prof_mark(ctx, 3, true);
     if (e == cudaSuccess) e = launch_sampling(sample_args(ctx), km_of(ctx), ctx->grid, ctx->stream);
     if (e == cudaSuccess) e = prof_mark(ctx, 3, false);
   }
@@ -390,7 +399,8 @@ cudaError_t run_event_window(rom_ctx* ctx) {
   if ((e = launch_project(P, km_of(ctx), G, s)) != cudaSuccess) return e;
   if ((e = prof_mark(ctx, 2, false)) != cudaSuccess) return e;
   if (ctx->cfg.n_s > 0) {
-    e = prof_mark(ctx, 3, true);
+    e = wait_features(ctx);
+    if (e == cudaSuccess) e = prof_mark(ctx, 3, true);
     if (e == cudaSuccess) e = launch_sampling(sample_args(ctx), km_of(ctx), G, s);
     if (e == cudaSuccess) e = prof_mark(ctx, 3, false);
   }
@@ -474,8 +484,16 @@ cudaError_t coarse_fom_fork(rom_ctx* ctx) {
     e = launch_fom_step(fom_params(ctx, ctx->cfg.z * ctx->cfg.dt), ctx->d.y_corr, ctx->d.y_tmp,
                         fom_scratch(ctx), fs);
   if (e == cudaSuccess) e = prof_mark(ctx, 1, false, fs);
-  if (e == cudaSuccess) e = select_features(ctx, ctx->d.y_tmp, fs);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, fs);
+  // the feature-guided selection of the new snapshot runs on, beside the
+  // iSVD update (which needs only the snapshot); the sampling launch waits
+  // for it. Its keys are read from global memory, so that its one CTA fits
+  // beside a CTA of the cooperative update on the same SM
+  if (e == cudaSuccess) e = select_features(ctx, ctx->d.y_tmp, fs, false);
+  if (e == cudaSuccess && ctx->cfg.n_s > 0) {
+    e = cudaEventRecord(ctx->ev_fgs, fs);
+    ctx->fgs_pending = 1;
+  }
   return e;
 }
 
@@ -595,6 +613,7 @@ void rom_destroy(rom_ctx* ctx) {
     cudaStreamDestroy(ctx->fom_stream);
     cudaEventDestroy(ctx->ev_fork);
     cudaEventDestroy(ctx->ev_join);
+    cudaEventDestroy(ctx->ev_fgs);
     ctx->fom_overlap = 0;
   }
   if (ctx->prof_ev_made)
@@ -623,6 +642,7 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
   rom_ctx* ctx = new rom_ctx;
   memset(&ctx->d, 0, sizeof(DevState));
   ctx->fom_overlap = 0;
+  ctx->fgs_pending = 0;
   ctx->sample_epoch = 0u;
   ctx->q_train = nullptr;
   ctx->prof_on = 0;
@@ -656,6 +676,14 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
     }
     if (cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
+      cudaEventDestroy(ctx->ev_fork);
+      cudaStreamDestroy(ctx->fom_stream);
+      delete ctx;
+      return ROM_ECUDA;
+    }
+    if (cudaEventCreateWithFlags(&ctx->ev_fgs, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      cudaEventDestroy(ctx->ev_join);
       cudaEventDestroy(ctx->ev_fork);
       cudaStreamDestroy(ctx->fom_stream);
       delete ctx;

@@ -442,8 +442,9 @@ struct rom_ctx {
   // the coarse FOM step of an adaptation cycle runs on fom_stream beside the
   // reduced steps when those are the single-CTA DEIM kernel (fom_overlap)
   cudaStream_t fom_stream;
-  cudaEvent_t ev_fork, ev_join;
+  cudaEvent_t ev_fork, ev_join, ev_fgs;   // ev_fgs: the feature-guided selection after the coarse step
   int fom_overlap;
+  int fgs_pending;       // the context's stream has not yet waited for ev_fgs
   int64_t N;
   int64_t step;          // time level n
   int grid;              // CTAs of the generic cooperative kernels

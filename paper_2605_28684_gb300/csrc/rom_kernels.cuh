@@ -128,9 +128,10 @@ cudaError_t launch_sampling(const SampleArgs& A, int km, int grid, cudaStream_t 
 int fgs_list_length(int64_t n, int r, int n_s);
 // The fgs_list_length best feature-guided candidates of the snapshot y
 // (fgs_key_kernel, fgs_select_kernel): values out_v, cell indices out_i,
-// best first; key is n words of scratch.
+// best first; key is n words of scratch. stage: copy the keys to shared
+// memory first (when they fit); otherwise they are read from global memory.
 cudaError_t launch_fgs(const double* y, int64_t n, int T, unsigned long long* key, double* out_v, int* out_i,
-                       cudaStream_t s);
+                       bool stage, cudaStream_t s);
 
 constexpr int kMeshStride = kMaxR + 2;   // per stencil row: k basis entries, q_ref, d
 

@@ -539,14 +539,14 @@ cudaError_t launch_sampling(const SampleArgs& A, int /*km*/, int grid, cudaStrea
 }
 
 cudaError_t launch_fgs(const double* y, int64_t n, int T, unsigned long long* key, double* out_v, int* out_i,
-                       cudaStream_t s) {
+                       bool stage, cudaStream_t s) {
   if (T < 1 || T > kFgsSort || n < 1) return cudaErrorInvalidValue;
   int blocks = (int)((n + 255) / 256);
   if (blocks > 256) blocks = 256;
   fgs_key_kernel<<<blocks, 256, 0, s>>>(y, n, key);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (n <= kFgsStageKeys) {
+  if (stage && n <= kFgsStageKeys) {
     const int smem = (int)(sizeof(unsigned long long) * n);
     e = cudaFuncSetAttribute(fgs_select_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(unsigned long long) * kFgsStageKeys));
