@@ -193,7 +193,11 @@ rom_status rom_step(rom_ctx* ctx, int64_t n_steps);
  * replaces the stored coarse state) or, if y_host is NULL, one coarse FOM step
  * of the stored coarse state. It is preprocessed as D (y - q_ref), the basis is
  * updated by the rank-one iSVD with forgetting, the sampling points are
- * refreshed and the reduced state is transferred to the new basis.
+ * refreshed and the reduced state is transferred to the new basis. With the
+ * comparison rules (rom_config.update_rule != ROM_UPDATE_ISVD) the basis is
+ * updated by that rule instead; the instantaneous rules (3-5) take the
+ * snapshot held (y_host, or, if y_host is NULL, the stored coarse state) and,
+ * with y_host NULL, advance the coarse FOM after the update.
  * Errors: as rom_step; a NaN or Inf in y_host returns ROM_ENONFINITE before
  * any device work and leaves the context unchanged (not poisoned).
  */
