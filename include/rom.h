@@ -74,10 +74,16 @@ typedef enum { ROM_BACKWARD_EULER = 0, ROM_SSPRK43 = 1 } rom_time_scheme;
  *              full-order model).
  *  n_cells     cells of the uniform grid on [0, 1]; n_var = 1 (Burgers) or 3.
  *  r           maximum reduced dimension (1 <= r <= 64, r <= w_init, r < N).
- *  n_s         0: plain Galerkin. > 0: DEIM-Galerkin with n_s sampled cells
- *              (r <= n_s <= 512, Burgers only): QDEIM points plus
- *              feature-guided points of largest squared forward difference of
- *              the correction snapshot.
+ *  n_s         0: plain Galerkin. > 0: DEIM-Galerkin with n_s sampled rows
+ *              (r <= n_s <= 256): QDEIM points plus feature-guided points of
+ *              largest squared forward difference of the feature of the
+ *              correction snapshot (Eq. fgs_selection). Burgers: the feature
+ *              is the state, periodic. Euler (time_scheme ROM_SSPRK43 only,
+ *              the Galerkin-FGS form of Sec. 5.3): the feature is the cell
+ *              pressure, the right end faces the zero-gradient ghost cell, and
+ *              the three rows of a cell share its score; the nine mesh rows
+ *              per sample must fit shared memory (about 72 n_s r bytes <=
+ *              220 kB), else ROM_EINVAL.
  *  w_init      fine FOM steps of the offline training window (>= 1).
  *  z           adaptation interval (>= 1); the coarse FOM step is z*dt.
  *  dt, nu, gamma, lambda   time step, viscosity, ratio of specific heats,
@@ -228,8 +234,8 @@ rom_status rom_state(rom_ctx* ctx, double* q_tilde, double* a, double* sigma,
 rom_status rom_load_state(rom_ctx* ctx, const double* phi, const double* sigma,
                           const double* a, const double* y_corr, int64_t step);
 
-/* Sampling points (n_s int32 cell indices, QDEIM points first) of a
- * hyper-reduced context. Errors: ROM_EINVAL (NULL or n_s = 0), ROM_ECUDA. */
+/* Sampling points (n_s int32 row indices of the state, QDEIM points first;
+ * for Burgers a row is a cell) of a hyper-reduced context. Errors: ROM_EINVAL (NULL or n_s = 0), ROM_ECUDA. */
 rom_status rom_samples(rom_ctx* ctx, int32_t* idx_host);
 
 /* Numerical rank of the current basis (number of non-null columns) and the

@@ -18,9 +18,11 @@ passage of the paper:
                      lspg_test_basis_be, by Gauss-Newton.
 * ``hyper_lspg_step`` Eq. hyperreduced_lspg / hyperreduced_lspg_stationarity.
 * ``qdeim``          Eq. qdeim_qr: first pivots of a column-pivoted QR of Phi^T.
-* ``fgs_extend``     Eq. fgs_selection with the feature map Theta(y) = y: the
-                     cells with the largest squared forward difference of the
-                     correction snapshot, skipping cells already chosen.
+* ``fgs_extend``     Eq. fgs_selection with the feature map Theta(y) = y
+                     (Burgers) or the cell pressures (Euler, Sec. 5.3): the
+                     rows with the largest squared forward difference of the
+                     feature of the correction snapshot, skipping rows
+                     already chosen.
 * ``isvd_update``    Algorithm 2 / Eqs. isvd_residual ... isvd_truncation.
 * ``windowed_svd_update``, ``direct_update``  the comparison rules of App. A
                      (Eqs. wsvd_window_matrix, wsvd_update; direct_optimization,
@@ -288,16 +290,28 @@ def qdeim(Phi, m):
     return [int(i) for i in piv[:min(m, numerical_rank(Phi))]]
 
 
-def fgs_scores(y):
-    """Squared forward difference (y_{i+1} - y_i)^2 (periodic), i.e. the squared
-    gradient of the feature Theta(y) = y up to the constant 1/dx^2."""
-    return (np.roll(y, -1) - y) ** 2
+def fgs_scores(y, problem=0, gamma=1.4):
+    """Score of every row of the state for Eq. fgs_selection: the squared
+    forward difference of the feature, i.e. its squared gradient up to the
+    constant 1/dx^2.
+
+    * Burgers: Theta(y) = y, periodic: (y_{i+1} - y_i)^2.
+    * Euler: Theta(y) = the cell pressures p_i (Sec. 5.3 uses pressure as the
+      feature; p recovered as in App. B, floors included). The right end has
+      the zero-gradient ghost cell of the finite-volume scheme, so the last
+      cell scores 0. The sample set is a set of rows of the 3N state, so each
+      of a cell's three rows (rho, m, E) carries the cell's score."""
+    if problem == 0:
+        return (np.roll(y, -1) - y) ** 2
+    p = fv.euler_primitives(y, gamma)[4]
+    dp = np.append(p[1:], p[-1]) - p
+    return np.tile(dp * dp, 3)
 
 
-def fgs_extend(y, chosen, count):
+def fgs_extend(y, chosen, count, problem=0, gamma=1.4):
     """Greedy feature-guided points: largest scores first (tie -> lowest index),
-    skipping cells already in ``chosen``."""
-    g = fgs_scores(y)
+    skipping rows already in ``chosen``."""
+    g = fgs_scores(y, problem, gamma)
     order = np.lexsort((np.arange(g.shape[0]), -g))
     taken = set(chosen)
     out = []
@@ -310,11 +324,11 @@ def fgs_extend(y, chosen, count):
     return out
 
 
-def sample_points(Phi, y_corr, n_s):
+def sample_points(Phi, y_corr, n_s, problem=0, gamma=1.4):
     """QDEIM points (up to r) extended to n_s by feature-guided points."""
     P = qdeim(Phi, n_s)
     if n_s > len(P):
-        P = P + fgs_extend(y_corr, P, n_s - len(P))
+        P = P + fgs_extend(y_corr, P, n_s - len(P), problem, gamma)
     return P
 
 
@@ -563,7 +577,7 @@ class AdaptiveROM:
         return fv.be_step(y, c.z * c.dt, c.problem, c.nu, c.gamma, c.newton_tol, c.newton_max)
 
     def _refresh_sampling(self):
-        self.P = sample_points(self.Phi, self.y_corr, self.cfg.n_s)
+        self.P = sample_points(self.Phi, self.y_corr, self.cfg.n_s, self.cfg.problem, self.cfg.gamma)
         self.M = sampled_pinv(self.Phi, self.P)
 
     def rom_step(self, a_prev):

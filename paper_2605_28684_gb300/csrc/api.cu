@@ -73,7 +73,8 @@ rom_status validate(const rom_config* c) {
   if (c->precision != ROM_FP64 && c->precision != ROM_MIXED_FP32) return ROM_EINVAL;
   if (c->problem == ROM_BURGERS && c->n_var != 1) return ROM_EINVAL;
   if (c->problem == ROM_EULER && c->n_var != 3) return ROM_EINVAL;
-  if (c->problem == ROM_EULER && c->n_s > 0) return ROM_EINVAL;   // DEIM: Burgers only
+  // DEIM-Galerkin Euler: the explicit form only (the paper's Galerkin-FGS ROM)
+  if (c->problem == ROM_EULER && c->n_s > 0 && c->time_scheme != ROM_SSPRK43) return ROM_EINVAL;
   if (c->problem == ROM_EULER && c->n_cells > 128 * 256) return ROM_EINVAL;
   if (c->n_cells < 8 || c->n_cells > (int64_t)kMaxChunks * kMaxChunkRows) return ROM_EINVAL;
   int64_t N = c->n_cells * c->n_var;
@@ -81,7 +82,8 @@ rom_status validate(const rom_config* c) {
   if (c->n_s < 0 || (c->n_s > 0 && (c->n_s < c->r || c->n_s > 256 || c->n_s > N))) return ROM_EINVAL;
   if (c->w_init < 1 || c->z < 1 || c->newton_max < 1) return ROM_EINVAL;
   if (c->n_s > 0) {   // the DEIM step stages the stencil mesh in shared memory
-    size_t need = (size_t)44 * c->n_s * c->r + (size_t)c->n_s * 44 + 33500;
+    size_t need = c->problem == ROM_EULER ? euler_hyper_smem(c->n_s, c->r)
+                                          : (size_t)44 * c->n_s * c->r + (size_t)c->n_s * 44 + 33500;
     if (need > 220000) return ROM_EINVAL;
   }
   if (!(c->dt > 0.0) || !(c->nu >= 0.0) || !(c->lambda >= 0.0 && c->lambda <= 1.0)) return ROM_EINVAL;
@@ -201,8 +203,8 @@ cudaError_t select_features(rom_ctx* ctx, const double* y, cudaStream_t s, bool 
   if (ctx->cfg.n_s <= 0) return cudaSuccess;
   cudaError_t e = prof_mark(ctx, 4, true, s);
   if (e == cudaSuccess)
-    e = launch_fgs(y, ctx->N, fgs_list_length(ctx->N, ctx->cfg.r, ctx->cfg.n_s), ctx->d.fgs_key, ctx->d.fgs_v,
-                   ctx->d.fgs_i, stage, s);
+    e = launch_fgs(y, ctx->N, ctx->cfg.n_var, ctx->cfg.gamma, fgs_list_length(ctx->N, ctx->cfg.r, ctx->cfg.n_s),
+                   ctx->d.fgs_key, ctx->d.fgs_v, ctx->d.fgs_i, stage, s);
   if (e == cudaSuccess) e = prof_mark(ctx, 4, false, s);
   return e;
 }
@@ -251,6 +253,7 @@ SampleArgs sample_args(rom_ctx* ctx) {
   S.ld = ctx->N;
   S.r = ctx->cfg.r;
   S.n_s = ctx->cfg.n_s;
+  S.n_var = ctx->cfg.n_var;
   S.rank = ctx->d.rank;
   S.phi = ctx->d.phi;
   S.phi32 = basis32(ctx);
@@ -310,7 +313,8 @@ cudaError_t run_steps(rom_ctx* ctx, int nsteps) {
   StepArgs A = step_args(ctx, nsteps);
   cudaError_t e = prof_mark(ctx, 0, true);
   if (e != cudaSuccess) return e;
-  if (ctx->cfg.n_s > 0) e = launch_hyper_steps(A, km_of(ctx), ctx->stream);
+  if (ctx->cfg.n_s > 0 && ctx->cfg.problem == ROM_EULER) e = launch_euler_hyper_steps(A, ctx->stream);
+  else if (ctx->cfg.n_s > 0) e = launch_hyper_steps(A, km_of(ctx), ctx->stream);
   else if (ctx->cfg.projection == ROM_LSPG) e = launch_lspg_steps(A, ctx->grid, ctx->stream);
   else if (ctx->cfg.problem == ROM_EULER) e = launch_euler_galerkin_steps(A, km_of(ctx), ctx->grid, ctx->stream);
   else e = launch_galerkin_steps(A, km_of(ctx), ctx->grid, ctx->stream);
@@ -708,7 +712,7 @@ rom_status init_ctx(const rom_config* cfg_in, const double* q0_host, void* strea
   ALLOC(d.core, core_ws_doubles()); ALLOC(d.ubar, kMaxCore * kMaxCore);
   ALLOC(d.partials, (size_t)3 * G * (kMaxCore + 2)); ALLOC(d.jpartials, (size_t)G * kMaxR * kMaxR);
   ALLOC(d.jac, kMaxR * kMaxR); ALLOC(d.samples, ns); ALLOC(d.cand_v, (size_t)G * kMaxNs);
-  ALLOC(d.cand_f, (size_t)G * 2); ALLOC(d.mesh, (size_t)ns * 3 * kMeshStride);
+  ALLOC(d.cand_f, (size_t)G * 2); ALLOC(d.mesh, (size_t)ns * 3 * ctx->cfg.n_var * kMeshStride);
   if (ctx->cfg.n_s > 0) {
     ALLOC(d.qd_u, (size_t)N * r); ALLOC(d.fgs_key, N);
     ALLOC(d.fgs_v, 2 * kMaxNs); ALLOC(d.fgs_i, 2 * kMaxNs);

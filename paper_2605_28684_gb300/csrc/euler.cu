@@ -419,6 +419,99 @@ __global__ void euler_rhs_kernel(const double* __restrict__ U, double* __restric
   }
 }
 
+// ---------------------------------------------------------------------------
+// DEIM-Galerkin reduced steps of the Euler system in the explicit form
+// (Eq. deim_galerkin_rom continuous in time, advanced by the SSPRK(4,3)
+// stages of App. D): one CTA on the sample mesh. The f of a sampled row
+// (variable v of cell i) is the difference of its two Rusanov interface
+// fluxes, which need the three variables of the cells i-1, i, i+1: nine mesh
+// rows per sample (Phi, q_ref, 1/D), staged in shared memory once per launch.
+// A stage lifts the mesh rows (one thread per row), evaluates D f at the
+// samples (one thread per sample) and adds dt/2 (P^T Phi)^+ (D f) to the
+// reduced state (one warp per coordinate, lanes over the samples).
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kBlock) euler_hyper_kernel(StepArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+  const int k = *A.rank;
+  const int ns = A.n_s, nm = 9 * ns, r = A.r;
+  const int64_t ncell = A.n / 3;
+  const double inv_dx = (double)ncell;
+  double* s_mesh = reinterpret_cast<double*>(smem_raw);  // nm x k (room for nm x r)
+  double* s_qr = s_mesh + (size_t)nm * r;                // nm
+  double* s_di = s_qr + nm;                              // nm (1/d)
+  double* s_qt = s_di + nm;                              // nm (lifted)
+  double* s_f = s_qt + nm;                               // ns (d f at the samples)
+  double* s_dc = s_f + ns;                               // ns (d at the samples)
+  double* s_a = s_dc + ns;                               // r
+  double* s_ap = s_a + r;                                // r: a^n
+  int* s_var = reinterpret_cast<int*>(s_ap + r);         // ns: variable of each sampled row
+
+  for (int e = t; e < nm * k; e += blockDim.x) {
+    const int row = e / k, j = e % k;
+    s_mesh[e] = A.mesh[(size_t)row * kMeshStride + j];
+  }
+  for (int e = t; e < nm; e += blockDim.x) {
+    s_qr[e] = A.mesh[(size_t)e * kMeshStride + kMaxR];
+    s_di[e] = 1.0 / A.mesh[(size_t)e * kMeshStride + kMaxR + 1];
+  }
+  for (int q = t; q < ns; q += blockDim.x) {
+    const int v = (int)(A.samples[q] / ncell);
+    s_var[q] = v;
+    s_dc[q] = A.mesh[(size_t)(9 * q + 3 + v) * kMeshStride + kMaxR + 1];
+  }
+  for (int j = t; j < k; j += blockDim.x) s_a[j] = A.a[j];
+  __syncthreads();
+  for (int step = 0; step < A.nsteps; ++step) {
+    for (int j = t; j < k; j += blockDim.x) s_ap[j] = s_a[j];
+    for (int it = 1; it <= 4; ++it) {
+      // lift the mesh rows at the stage value (the barrier before it also
+      // orders the a^n copy above)
+      __syncthreads();
+      for (int e = t; e < nm; e += blockDim.x) {
+        const double* row = s_mesh + (size_t)e * k;
+        double s = 0.0;
+        for (int j = 0; j < k; ++j) s = fma(row[j], s_a[j], s);
+        s_qt[e] = s_qr[e] + s * s_di[e];
+      }
+      __syncthreads();
+      for (int q = t; q < ns; q += blockDim.x) {
+        const double* u = s_qt + 9 * q;
+        const Cons L{u[0], u[1], u[2]}, C{u[3], u[4], u[5]}, R{u[6], u[7], u[8]};
+        double Fl[3], Fr[3];
+        rusanov(L, C, A.gamma, Fl);
+        rusanov(C, R, A.gamma, Fr);
+        const int v = s_var[q];
+        const double fl = v == 0 ? Fl[0] : (v == 1 ? Fl[1] : Fl[2]);
+        const double fr = v == 0 ? Fr[0] : (v == 1 ? Fr[1] : Fr[2]);
+        s_f[q] = s_dc[q] * (-(fr - fl) * inv_dx);
+      }
+      __syncthreads();
+      // stage: a_j <- a_j + dt/2 sum_q M_jq (d f)_q; after the third,
+      // a_j <- 2/3 a^n_j + 1/3 a_j (a_j is written by its own warp only)
+      int bad = 0;
+      for (int j = wid; j < k; j += nw) {
+        double s = 0.0;
+        for (int q = lane; q < ns; q += 32) s = fma(A.minv[(size_t)j * ns + q], s_f[q], s);
+        s = warp_sum(s);
+        if (lane == 0) {
+          double v = s_a[j] + 0.5 * A.dt * s;
+          if (it == 3) v = (2.0 / 3.0) * s_ap[j] + (1.0 / 3.0) * v;
+          s_a[j] = v;
+          bad |= !isfinite(v);
+        }
+      }
+      if (__syncthreads_or(bad)) {
+        if (t == 0) record_status(A.status, kStNonFinite);
+        return;
+      }
+    }
+  }
+  for (int j = t; j < r; j += blockDim.x) A.a[j] = (j < k) ? s_a[j] : 0.0;
+  if (t == 0) *A.iters = 0;
+}
+
 int euler_chunks(int64_t n) {
   int C = 1;
   while (C * 2 <= kMaxChunks && n / (C * 2) >= 32) C *= 2;
@@ -434,6 +527,23 @@ cudaError_t launch_euler_rhs(int64_t n_cells, double gamma, const double* q, dou
   int blocks = (int)((n_cells + 255) / 256);
   if (blocks > 4096) blocks = 4096;
   euler_rhs_kernel<<<blocks, 256, 0, s>>>(q, f, n_cells, gamma);
+  return cudaGetLastError();
+}
+
+size_t euler_hyper_smem(int n_s, int r) {
+  const size_t nm = 9 * (size_t)n_s;
+  return sizeof(double) * (nm * (size_t)r + 3 * nm + 2 * (size_t)n_s + 2 * (size_t)r) +
+         sizeof(int) * (size_t)n_s + 64;
+}
+
+cudaError_t launch_euler_hyper_steps(const StepArgs& A, cudaStream_t s) {
+  if (A.n_s < 1 || A.n_s > 256 || A.r < 1 || A.r > kMaxR || A.n % 3 != 0 || !A.explicit_rk)
+    return cudaErrorInvalidValue;
+  const size_t smem = euler_hyper_smem(A.n_s, A.r);
+  if (smem > 220000) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(euler_hyper_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  euler_hyper_kernel<<<1, kBlock, smem, s>>>(A);
   return cudaGetLastError();
 }
 

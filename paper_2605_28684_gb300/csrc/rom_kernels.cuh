@@ -74,7 +74,7 @@ struct StepArgs {
   // hyper-reduction
   int n_s;
   const int* samples;
-  const double* mesh;   // n_s x 3 x (kMaxR + 2): Phi rows (k), then q_ref, d
+  const double* mesh;   // n_s x 3 n_var x (kMaxR + 2): Phi rows (k), then q_ref, d
   const double* minv;   // k x n_s row-major
   double* npart;        // LSPG: lspg_partial_doubles(grid) partial sums
   GridBarrier* bar;
@@ -85,6 +85,10 @@ struct StepArgs {
 cudaError_t launch_galerkin_steps(const StepArgs& A, int km, int grid, cudaStream_t s);
 cudaError_t launch_euler_galerkin_steps(const StepArgs& A, int km, int grid, cudaStream_t s);
 cudaError_t launch_hyper_steps(const StepArgs& A, int km, cudaStream_t s);
+// DEIM-Galerkin steps of the Euler system, explicit form (euler.cu), and the
+// shared memory they stage (n_s samples of nine mesh rows, rank <= r)
+cudaError_t launch_euler_hyper_steps(const StepArgs& A, cudaStream_t s);
+size_t euler_hyper_smem(int n_s, int r);
 // LSPG steps (lspg.cu), FP64 Burgers, n_s = 0
 cudaError_t launch_lspg_steps(const StepArgs& A, int grid, cudaStream_t s);
 size_t lspg_partial_doubles(int grid);
@@ -106,6 +110,7 @@ cudaError_t launch_lift(const LiftArgs& A, int km, cudaStream_t s);
 struct SampleArgs {
   int64_t n, ld;
   int r, n_s;
+  int n_var;            // 1 (Burgers: rows are cells) or 3 (Euler: variable-blocked rows)
   const int* rank;
   const double* phi;
   const float* phi32;
@@ -118,7 +123,7 @@ struct SampleArgs {
   unsigned long long* cand_f;  // grid * 2: (epoch << 32 | index) of those candidates
   unsigned int epoch;   // first step epoch of this launch (the caller advances it by kMaxR per launch)
   double* qd_u;         // n x r: coordinates of the rows along the QDEIM residual directions
-  double* mesh;         // n_s x 3 x (kMaxR + 2)
+  double* mesh;         // n_s x 3 n_var x (kMaxR + 2)
   double* minv;         // r x n_s
   GridBarrier* bar;
   int* status;
@@ -126,12 +131,14 @@ struct SampleArgs {
 cudaError_t launch_sampling(const SampleArgs& A, int km, int grid, cudaStream_t s);
 // Length of the feature-guided candidate list: n_s + min(r, n_s) (at most n).
 int fgs_list_length(int64_t n, int r, int n_s);
-// The fgs_list_length best feature-guided candidates of the snapshot y
-// (fgs_key_kernel, fgs_select_kernel): values out_v, cell indices out_i,
-// best first; key is n words of scratch. stage: copy the keys to shared
-// memory first (when they fit); otherwise they are read from global memory.
-cudaError_t launch_fgs(const double* y, int64_t n, int T, unsigned long long* key, double* out_v, int* out_i,
-                       bool stage, cudaStream_t s);
+// The fgs_list_length best feature-guided candidates of the snapshot y of n
+// rows (fgs_key_kernel or fgs_key_euler_kernel, then fgs_select_kernel):
+// values out_v, row indices out_i, best first; key is n words of scratch.
+// n_var 1: the feature is y itself; n_var 3: the cell pressures (gamma).
+// stage: copy the keys to shared memory first (when they fit); otherwise
+// they are read from global memory.
+cudaError_t launch_fgs(const double* y, int64_t n, int n_var, double gamma, int T, unsigned long long* key,
+                       double* out_v, int* out_i, bool stage, cudaStream_t s);
 
 constexpr int kMeshStride = kMaxR + 2;   // per stencil row: k basis entries, q_ref, d
 

@@ -1,13 +1,17 @@
 // Sampling points of the DEIM-Galerkin model and the sampled-basis operators
 // (paper Eq. qdeim_qr, Eq. fgs_selection, Eq. deim_galerkin_rom).
 //
-//  * Feature-guided candidates (fgs_key_kernel, fgs_select_kernel): the T
-//    cells with the largest squared forward difference (y_{i+1} - y_i)^2 of
-//    the correction snapshot (the feature map is the state itself), in
-//    decreasing order, ties -> lowest index. They depend only on the
-//    snapshot, so they are computed right after the coarse FOM step that
-//    produces it (beside the reduced steps of the interval), by an exact
-//    radix selection on the IEEE bit patterns of the squares.
+//  * Feature-guided candidates (fgs_key_kernel or fgs_key_euler_kernel, then
+//    fgs_select_kernel): the T rows with the largest squared forward
+//    difference of the feature of the correction snapshot, in decreasing
+//    order, ties -> lowest index. Burgers: the feature is the state itself,
+//    (y_{i+1} - y_i)^2, periodic. Euler: the feature is the cell pressure
+//    (Sec. 5.3), (p_{i+1} - p_i)^2 with the zero-gradient ghost cell past the
+//    right end, and each of a cell's three rows carries its cell's score.
+//    They depend only on the snapshot, so they are computed right after the
+//    coarse FOM step that produces it (beside the reduced steps of the
+//    interval), by an exact radix selection on the IEEE bit patterns of the
+//    squares.
 //  * QDEIM (sampling_kernel): the first k pivots of a column-pivoted QR of
 //    Phi^T, computed as greedy pivoting on the rows x_i of Phi: take the row
 //    with the largest remaining squared norm (ties -> lowest index). The
@@ -23,8 +27,10 @@
 //    that are not QDEIM points.
 //  * (P^T Phi)^+ = (A^T A)^{-1} A^T with A = P^T Phi (normal equations; the
 //    symmetric positive definite A^T A inverted by Gauss-Jordan elimination in
-//    FP64) and the stencil mesh (Phi, q_ref, D on the rows i-1, i, i+1 of
-//    every sampled cell) used by the hyper-reduced step.
+//    FP64) and the stencil mesh used by the hyper-reduced step: Phi, q_ref
+//    and D on the rows i-1, i, i+1 of every sampled cell (Burgers), or on the
+//    three variable rows of the cells i-1, i, i+1 of every sampled row
+//    (Euler).
 #include <cfloat>
 #include <cmath>
 
@@ -107,6 +113,33 @@ __global__ void fgs_key_kernel(const double* __restrict__ y, int64_t n, unsigned
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double d = y[i + 1 == n ? 0 : i + 1] - y[i];
     key[i] = (unsigned long long)__double_as_longlong(d * d);
+  }
+}
+
+// Cell pressure of the Euler state (App. B, floors included), every
+// operation rounded on its own (no contraction into fused multiply-adds), so
+// that the score is that of the plain expression.
+__device__ __forceinline__ double cell_pressure(const double* __restrict__ y, int64_t nc, int64_t i,
+                                                double gamma) {
+  constexpr double kRhoFloor = 1e-10, kPFloor = 1e-10;
+  const double rho = fmax(y[i], kRhoFloor);
+  const double u = __ddiv_rn(y[nc + i], rho);
+  const double ke = __dmul_rn(__dmul_rn(__dmul_rn(0.5, rho), u), u);
+  return fmax(__dmul_rn(gamma - 1.0, __dsub_rn(y[2 * nc + i], ke)), kPFloor);
+}
+
+// Euler: key of the three rows of cell i = IEEE bits of (p_{i+1} - p_i)^2,
+// p_nc = p_{nc-1} (zero-gradient ghost cell).
+__global__ void fgs_key_euler_kernel(const double* __restrict__ y, int64_t nc, double gamma,
+                                     unsigned long long* __restrict__ key) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += (int64_t)gridDim.x * blockDim.x) {
+    const double p = cell_pressure(y, nc, i, gamma);
+    const double pn = (i + 1 < nc) ? cell_pressure(y, nc, i + 1, gamma) : p;
+    const double d = __dsub_rn(pn, p);
+    const unsigned long long k = (unsigned long long)__double_as_longlong(__dmul_rn(d, d));
+    key[i] = k;
+    key[nc + i] = k;
+    key[2 * nc + i] = k;
   }
 }
 
@@ -447,19 +480,31 @@ __global__ void __launch_bounds__(kBlock) sampling_kernel(SampleArgs A) {
   if (b == 0)
     for (int s = t; s < ns; s += blockDim.x) A.samples[s] = sm.piv[s];
 
-  // ---- stencil mesh: Phi, q_ref, D on rows i-1, i, i+1 of every sample;
-  // sample s by CTA s mod G (threads over the 3 (kMaxR + 2) entries) ----
+  // ---- stencil mesh: Phi, q_ref, D on the rows the sampled rows' f needs;
+  // sample s by CTA s mod G (threads over its 3 n_var (kMaxR + 2) entries).
+  // Burgers: rows i-1, i, i+1 (periodic). Euler, sampled row v nc + i: mesh
+  // row 3 c + w is variable w of cell i - 1 + c (ends clamped: the
+  // zero-gradient ghost cells) ----
+  const int mrows = 3 * A.n_var;
   for (int s = b; s < ns; s += G) {
     const int64_t ic = sm.piv[s];
-    for (int e = t; e < 3 * kMeshStride; e += blockDim.x) {
+    for (int e = t; e < mrows * kMeshStride; e += blockDim.x) {
       const int o = e / kMeshStride, j = e % kMeshStride;
-      int64_t i = ic + o - 1;
-      i = (i < 0) ? i + N : ((i >= N) ? i - N : i);
+      int64_t i;
+      if (A.n_var == 1) {
+        i = ic + o - 1;
+        i = (i < 0) ? i + N : ((i >= N) ? i - N : i);
+      } else {
+        const int64_t nc = N / 3;
+        int64_t c = ic % nc + o / 3 - 1;
+        c = (c < 0) ? 0 : ((c >= nc) ? nc - 1 : c);
+        i = (int64_t)(o % 3) * nc + c;
+      }
       double v;
       if (j < kMaxR) v = (j < k) ? (double)phi[j * ld + i] : 0.0;
       else if (j == kMaxR) v = A.q_ref[i];
       else v = A.drow[i];
-      A.mesh[(size_t)(3 * s + o) * kMeshStride + j] = v;
+      A.mesh[(size_t)(mrows * s + o) * kMeshStride + j] = v;
     }
   }
   if (b != 0) return;
@@ -533,17 +578,21 @@ cudaError_t launch_sampling(const SampleArgs& A, int /*km*/, int grid, cudaStrea
   // feature-guided list must leave n_s - k candidates after the QDEIM points
   if ((A.n + grid - 1) / grid > 4 * kBlock) return cudaErrorInvalidValue;
   if (A.n_s > 256 || A.n_s < A.r || A.r > kMaxR || A.fgs_t > kFgsSort ||
+      !(A.n_var == 1 || (A.n_var == 3 && A.n % 3 == 0)) ||
       A.fgs_t < fgs_list_length(A.n, A.r, A.n_s))
     return cudaErrorInvalidValue;
   return A.phi32 ? launch_sampling_t<float>(A, grid, s) : launch_sampling_t<double>(A, grid, s);
 }
 
-cudaError_t launch_fgs(const double* y, int64_t n, int T, unsigned long long* key, double* out_v, int* out_i,
-                       bool stage, cudaStream_t s) {
+cudaError_t launch_fgs(const double* y, int64_t n, int n_var, double gamma, int T, unsigned long long* key,
+                       double* out_v, int* out_i, bool stage, cudaStream_t s) {
   if (T < 1 || T > kFgsSort || n < 1) return cudaErrorInvalidValue;
-  int blocks = (int)((n + 255) / 256);
+  if (!(n_var == 1 || (n_var == 3 && n % 3 == 0))) return cudaErrorInvalidValue;
+  const int64_t cells = n / n_var;
+  int blocks = (int)((cells + 255) / 256);
   if (blocks > 256) blocks = 256;
-  fgs_key_kernel<<<blocks, 256, 0, s>>>(y, n, key);
+  if (n_var == 1) fgs_key_kernel<<<blocks, 256, 0, s>>>(y, n, key);
+  else fgs_key_euler_kernel<<<blocks, 256, 0, s>>>(y, cells, gamma, key);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (stage && n <= kFgsStageKeys) {

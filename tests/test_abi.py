@@ -61,6 +61,14 @@ def test_invalid_configs_rejected(lib):
     c = synth.config_burgers_small()
     c.projection, c.precision = 1, 1          # no mixed-precision LSPG form
     bad.append(c)
+    # DEIM-Galerkin Euler: the explicit form only, and its nine mesh rows per
+    # sample must fit shared memory (r = 40, n_s = 80 does not)
+    c = synth.config_sod(256)
+    c.r, c.n_s = 20, 40
+    bad.append(c)
+    c = synth.config_sod(256)
+    c.time_scheme, c.n_s = 1, 80
+    bad.append(c)
     # comparison update rules: unknown rule, window outside 1..min(w_init, 64), FP64 only
     for rule, window, prec in [(6, 8, 0), (1, 0, 0), (2, 101, 0), (1, 8, 1)]:
         c = synth.config_burgers_small()

@@ -255,7 +255,7 @@ def adopt_if_near_tie(ref, gpu, rtol=1e-10):
         norms = res[j]
         norms[gpu_P[:j]] = -1.0
         assert norms[p] >= (1 - rtol) * norms.max(), ("QDEIM pivot", j, p)
-    g = orom.fgs_scores(st["y_corr"])
+    g = orom.fgs_scores(st["y_corr"], ref.cfg.problem, ref.cfg.gamma)
     g[gpu_P[:kq]] = -1.0
     m = ref.cfg.n_s - kq
     thr = np.sort(g)[::-1][m - 1]
