@@ -220,3 +220,28 @@ def test_nonfinite_initial_state_refused_before_the_device(lib):
         ctx = ctypes.c_void_p()
         rc = lib.rom_init(ctypes.byref(c), q0.ctypes.data_as(D), None, ctypes.byref(ctx))
         assert rc == 5 and not ctx.value, bad       # ROM_ENONFINITE
+
+
+def test_validation_accepts_the_euler_galerkin_fgs_form(lib):
+    """Sod with feature-guided points in the explicit form passes the
+    argument checks (without a device it then fails at the first device call,
+    ROM_ECUDA); the same model in the backward-Euler form, or with a mesh too
+    large for shared memory, is refused first (ROM_EINVAL)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a device is present: rom_init would build the context")
+    except ImportError:
+        pass
+    import paper_2605_28684_gb300 as g
+    D = ctypes.POINTER(ctypes.c_double)
+    for mod, expect in [(dict(time_scheme=1, r=20, n_s=40), 3), (dict(r=20, n_s=40), 1),
+                        (dict(time_scheme=1, n_s=80), 1)]:
+        c = synth.config_sod(256)
+        for k, v in mod.items():
+            setattr(c, k, v)
+        q0 = synth.initial_state(c)
+        cfg = g.make_config(c)
+        ctx = ctypes.c_void_p()
+        rc = lib.rom_init(ctypes.byref(cfg), q0.ctypes.data_as(D), None, ctypes.byref(ctx))
+        assert rc == expect and not ctx.value, (mod, rc)
