@@ -440,6 +440,23 @@ def test_hyper_reduced_lspg_equals_deim_galerkin():
     assert np.max(np.abs(a_l - a_g)) <= 1e-11 * np.max(np.abs(a_g))
 
 
+def test_sod_lspg_qdeim_is_the_deim_galerkin_model():
+    """The same identity on the Euler system at the Sod ROM's dimensions
+    (Sec. 5.2: LSPG-QDEIM with r = n_s = w_init = 4, 256 cells): over the
+    whole horizon to t = 0.2 the adaptive LSPG-QDEIM model and the adaptive
+    DEIM-Galerkin model give the same states, every step converging."""
+    out = {}
+    for proj in (1, 0):
+        cfg = synth.config_sod(256)
+        cfg.r = cfg.n_s = cfg.w_init = 4
+        cfg.projection = proj
+        m = rom.AdaptiveROM(cfg, synth.initial_state(cfg))
+        m.run(cfg.n_online, record_every=10 ** 6)
+        out[proj] = m.lifted()
+    assert np.all(np.isfinite(out[1]))
+    assert np.max(np.abs(out[1] - out[0])) <= 1e-12 * np.max(np.abs(out[0]))
+
+
 def test_lspg_and_galerkin_agree_as_dt_vanishes():
     """LSPG tests the residual with Psi = Phi - dt D J_f D^-1 Phi, Galerkin
     with Phi; the two steps from the same state differ at least at second
