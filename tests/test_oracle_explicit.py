@@ -66,15 +66,25 @@ def test_explicit_galerkin_with_full_basis_is_the_fom_step(problem):
     assert np.linalg.norm(q_rom - q_fom) <= 1e-12 * np.linalg.norm(q_fom)
 
 
-def test_explicit_hyper_step_with_every_row_sampled_is_galerkin():
-    cfg = synth.config_burgers_small()
-    cfg.n_cells = 96
+@pytest.mark.parametrize("problem,order", [(0, "natural"), (0, "shuffled"), (1, "natural"), (1, "shuffled")])
+def test_explicit_hyper_step_with_every_row_sampled_is_galerkin(problem, order):
+    """With every row sampled (in any order) and Phi orthonormal,
+    (P^T Phi)^+ P^T = Phi^T, so the DEIM-Galerkin right-hand side is the
+    Galerkin one (Burgers, and the Euler system's 3N rows)."""
+    if problem == 0:
+        cfg = synth.config_burgers_small()
+        cfg.n_cells = 96
+    else:
+        cfg = synth.config_sod()
+        cfg.n_cells, cfg.n_var = 32, 3
     cfg.time_scheme = 1
     q = synth.initial_state(cfg)
     Phi, q_ref, d = full_basis(cfg, q)
     Phi = Phi[:, :12]
     a = Phi.T @ (d * (q - q_ref))
     P = list(range(cfg.n))
+    if order == "shuffled":
+        P = [int(i) for i in np.random.default_rng(7).permutation(cfg.n)]
     M = rom.sampled_pinv(Phi, P)
     a_g, _ = rom.explicit_galerkin_step(a, Phi, q_ref, d, cfg)
     a_h, _ = rom.explicit_galerkin_step(a, Phi, q_ref, d, cfg, P, M)
@@ -106,3 +116,28 @@ def test_explicit_adaptive_rom_tracks_the_explicit_fom():
         q_be = fv.be_step(q_be, cfg.dt, cfg.problem, cfg.nu)
     assert max(errs) < 1e-3, errs
     assert np.linalg.norm(q_be - q) / np.linalg.norm(q) < 1e-2
+
+
+def test_sod_galerkin_fgs_tracks_the_fom_better_than_galerkin():
+    """Sod, 512 cells, the Galerkin-FGS form (r = 20 QDEIM points and 20
+    points of largest squared pressure difference, n_s = 2 r as in the
+    paper's RDE ROM), 200 explicit steps: the hyper-reduced adaptive ROM
+    stays bounded and ends closer to the explicit FOM than the plain
+    Galerkin adaptive ROM of the same rank on the same training window
+    (measured 2.1e-2 against 5.1e-2)."""
+    cfg = synth.config_sod(512)
+    cfg.time_scheme, cfg.r, cfg.n_s = 1, 20, 40
+    q0 = synth.initial_state(cfg)
+    fgs = rom.AdaptiveROM(cfg, q0)
+    gal_cfg = synth.config_sod(512)
+    gal_cfg.time_scheme, gal_cfg.r = 1, 20
+    gal = rom.AdaptiveROM(gal_cfg, q0, Q_train=fgs.Q_train)
+    q = fgs.Q_train[:, -1].copy()
+    for _ in range(200):
+        fgs.step()
+        gal.step()
+        q = fv.explicit_step(q, cfg.dt, cfg.problem, cfg.nu, cfg.gamma)
+    e_fgs = rom.relative_error(fgs.lifted(), q)
+    e_gal = rom.relative_error(gal.lifted(), q)
+    assert np.isfinite(e_fgs) and e_fgs < 0.03, e_fgs
+    assert e_fgs < 0.6 * e_gal, (e_fgs, e_gal)
